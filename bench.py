@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Throughput of batched Kerr geodesic integration on one GB300 (per rank).
+
+Workload (one "step"): every ray of a 1024 x 1024 image plane, spin a = 0.99,
+inclination 17 deg, observer at r = 1000 M, image plane +-25 M, integrated
+backward to capture (r < 1.01 r_h) or escape (beyond its start radius) with
+the FP32+Kahan persistent kernel at tolerance 1e-6.  Inputs are synthetic
+(the camera specification; initial states are built on the device).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the host cores on bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("rays/s to termination at ≤1e-5 rel. err (FP32 vs FP64 path); "
+          "% of FP32 pipe peak")
+UNIT = "rays/s"
+# Algorithmic FLOPs, counted by the FLOP-counting transcription of eqs.
+# opt0/opti in oracle/flops.py (tests/test_flops.py pins both numbers):
+FLOPS_PER_RHS = 160          # one right-hand side
+FLOPS_PER_ATTEMPT = 366      # stage sums, error norm and update of one attempt
+FP32_LANES_PER_SM = 128      # FP32 FMA lanes per SM (one FMA = 2 FLOPs)
+WORKLOAD = ("camera 1024x1024, a=0.99, i=17deg, r_obs=1000M, +-25M, tol 1e-6, "
+            "FP32+Kahan persistent kernel")
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.rows = []
+        self.proc = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in self.rows for j in range(4)
+                          if r[5 + j].lower().startswith("active")})
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": reasons, "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1706_07062_gb300 import kerr as K
+    from paper_1706_07062_gb300 import workloads as W
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    spec = W.CAMERA_1024
+    cam = K.camera(*spec.as_tuple())
+    n = spec.n
+    prec = K.FP64 if args.prec == "fp64" else K.FP32_KAHAN
+    ctx = K.kerr_init(spec.a)
+    opts = K.default_opts(prec=prec, tol=W.TOL_1024)
+    if args.autotune:
+        opts.variant = K.kerr_autotune(ctx, cam, opts, sample=1 << 16)
+    out = K.alloc_out(n, dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        K.kerr_trace_camera(ctx, cam, opts, out=out, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: K steps, L2 flushed between steps (outside the events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kern_ms, flops32, flops64, rhs32, rhs64, att, att64 = [], 0, 0, 0, 0, 0, 0
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        s = K.kerr_get_stats(ctx)          # synchronises the library stream
+        kern_ms.append(s.kernel_ms)
+        rhs32 += s.rhs_fp32
+        rhs64 += s.rhs_fp64
+        att += s.attempts
+        att64 += s.attempts_fp64
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop() if sampler else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n / (ms * 1e-3)
+    stats = K.kerr_get_stats(ctx)
+
+    # ---- roofline of the persistent kernel (FP32 pipe, algorithmic FLOPs)
+    att32 = att - att64
+    fl32 = rhs32 * FLOPS_PER_RHS + att32 * FLOPS_PER_ATTEMPT
+    fl64 = rhs64 * FLOPS_PER_RHS + att64 * FLOPS_PER_ATTEMPT
+    kms = sum(kern_ms) / len(kern_ms)
+    peaks, peak_src = load_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak32 = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = fl32 / args.steps / (kms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak32, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak32, 4), "traffic": None,
+                "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
+                               f"lanes x 2 x {sm_max:.0f} MHz ({peak_src} sm_max_mhz)",
+                "kernel_ms": round(kms, 4),
+                "fp32_flops_per_step": fl32 // args.steps,
+                "fp64_flops_per_step": fl64 // args.steps,
+                "attempts_per_ray": round(att / args.steps / n, 2),
+                "fp64_attempt_share": round(att64 / max(att, 1), 4)}
+    if args.prec == "fp64":
+        roofline["note"] = "FP64 path: achieved counts FP32 FLOPs only"
+
+    result = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+              "dtype": "f32" if prec == K.FP32_KAHAN else "f64", "data": "synthetic",
+              "config": {"workload": WORKLOAD if prec == K.FP32_KAHAN else
+                         WORKLOAD.replace("FP32+Kahan", "FP64"),
+                         "rays_per_gpu": n, "parallelism": f"replicas x{world}",
+                         "l2": "flushed between steps (512 MiB write, outside the events)",
+                         "variant": stats.variant},
+              "gpu_launches": args.steps,
+              "roofline": roofline, "clocks": clocks,
+              "timed_wall_s": round(t_wall, 3)}
+
+    # ---- end to end through the C ABI with host (pinned) buffers
+    if rank == 0 and not args.skip_e2e:
+        host = K.alloc_out(n, device="cpu", pinned=True)
+        for _ in range(2):
+            K.kerr_trace_camera(ctx, cam, opts, out=host, stream=stream)
+        e2e_t = []
+        for _ in range(max(3, min(args.steps, 10))):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            K.kerr_trace_camera(ctx, cam, opts, out=host, stream=stream)
+            e2e_t.append(time.perf_counter() - t0)
+        e2e_s = sum(e2e_t) / len(e2e_t)
+        result["e2e"] = {"value": round(n / e2e_s, 1), "unit": UNIT,
+                         "h2d_bytes_per_step": 56,
+                         "d2h_bytes_per_step": n * (8 * 8 + 4 + 4 + 4 * 4)}
+
+    # ---- plain FP64 GPU path on the same workload (comparison leg)
+    if rank == 0 and prec == K.FP32_KAHAN and not args.skip_fp64:
+        o64 = K.default_opts(prec=K.FP64, tol=W.TOL_1024)
+        out64 = K.alloc_out(n, dev)
+        K.kerr_trace_camera(ctx, cam, o64, out=out64, stream=stream)
+        torch.cuda.synchronize(dev)
+        t64 = []
+        for _ in range(2):
+            flush.zero_()
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            K.kerr_trace_camera(ctx, cam, o64, out=out64, stream=stream)
+            b_.record(stream)
+            torch.cuda.synchronize(dev)
+            t64.append(a_.elapsed_time(b_))
+        result["fp64_path"] = {"value": round(n / (min(t64) * 1e-3), 1), "unit": UNIT,
+                               "ms_per_step": round(min(t64), 3)}
+        result["_fp64_out"] = out64
+
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        result["cpu_baseline"], acc = cpu_baseline(spec, W, out, result.get("_fp64_out"))
+        if acc:
+            result["accuracy"] = acc
+    result.pop("_fp64_out", None)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    ctx.close()
+
+
+def cpu_baseline(spec, W, out_gpu, out64):
+    """Time the FP64 CPU oracle on a bounded seeded sample of the same image
+    (all host cores), and use that same sample to state the GPU path's
+    end-point error against it."""
+    from oracle import oracle as O
+
+    nthreads = os.cpu_count() or 1
+    idx = W.camera_subset(spec)                       # seeded 4096-ray subset
+    y0 = O.camera_ic(spec.a, spec.incl, spec.r_obs, spec.half_width, spec.nx, spec.ny, idx)
+    oo = O.Opts(tol=W.TOL_1024)
+    t0 = time.perf_counter()
+    ref = O.trace(spec.a, y0, oo, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    n_done = len(idx)
+    # extend the sample with more seeded rays to about 10 s of CPU work
+    extra = int(min(200_000, max(0, (10.0 - dt) * n_done / dt)))
+    if extra > 0:
+        rng = np.random.default_rng(1706 + 1)
+        idx2 = np.sort(rng.choice(spec.n, size=extra, replace=False))
+        y2 = O.camera_ic(spec.a, spec.incl, spec.r_obs, spec.half_width, spec.nx, spec.ny, idx2)
+        t1 = time.perf_counter()
+        O.trace(spec.a, y2, oo, nthreads=nthreads)
+        dt += time.perf_counter() - t1
+        n_done += extra
+    base = {"value": round(n_done / dt, 1), "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"{n_done} rays of the 1024x1024 image (seeded 4096-ray subset plus "
+                      f"{extra} seeded random rays), FP64 oracle, tol 1e-6, {dt:.1f} s"}
+    # accuracy of the GPU paths on the seeded subset
+    acc = None
+    try:
+        flags = O.ill_conditioned(spec.a, y0, oo, ref=ref, rel=1e-5, nthreads=nthreads)
+
+        def errs(o):
+            x = o.x.cpu().numpy()[:, idx].T
+            k = o.k.cpu().numpy()[:, idx].T
+            st = o.status.cpu().numpy()[idx]
+            ex = np.linalg.norm(x[:, 1:4] - ref.y[:, 1:4], 1) / np.linalg.norm(ref.y[:, 1:4], 1)
+            ek = np.linalg.norm(k - ref.y[:, 4:8], 1) / np.linalg.norm(ref.y[:, 4:8], 1)
+            e = np.maximum(ex, ek)
+            g = ~flags
+            return {"max_rel_err_well_conditioned": float(e[g].max()),
+                    "median_rel_err": float(np.median(e)),
+                    "frac_le_1e-5_well_conditioned": float(np.mean(e[g] <= 1e-5)),
+                    "status_mismatch_well_conditioned": int(np.sum((st != ref.status) & g))}
+        acc = {"sample": len(idx), "reference": "FP64 CPU oracle, tol 1e-6",
+               "ill_conditioned": int(flags.sum()), "fp32_kahan": errs(out_gpu)}
+        if out64 is not None:
+            acc["fp64"] = errs(out64)
+    except Exception as exc:  # accuracy is a report, not the measurement
+        acc = {"error": repr(exc)}
+    return base, acc
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands, on host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1706_07062_gb300 import workloads as W
+
+    spec = W.CAMERA_1024
+    nthreads = os.cpu_count() or 1
+    oo = O.Opts(tol=W.TOL_1024)
+    rng = np.random.default_rng(4242)
+    per_step = 2048
+
+    def step():
+        idx = np.sort(rng.choice(spec.n, size=per_step, replace=False))
+        y0 = O.camera_ic(spec.a, spec.incl, spec.r_obs, spec.half_width, spec.nx, spec.ny, idx)
+        t0 = time.perf_counter()
+        O.trace(spec.a, y0, oo, nthreads=nthreads)
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        step()
+    ts = [step() for _ in range(args.steps)]
+    ms = 1e3 * sum(ts) / len(ts)
+    value = per_step / (ms * 1e-3)
+    res = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD.replace("FP32+Kahan persistent kernel",
+                                                   "FP64 CPU oracle"),
+                      "rays_per_step": per_step},
+           "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": nthreads,
+                            "kind": "oracle",
+                            "sample": f"{per_step} seeded random rays of the 1024x1024 image "
+                                      f"per step"},
+           "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        import __graft_entry__
+        __graft_entry__.build()
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

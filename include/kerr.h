@@ -1,0 +1,210 @@
+/*
+ * kerr.h -- C ABI of libkerr: batched integration of null and time-like
+ * geodesics of the Kerr metric in Cartesian Kerr-Schild coordinates on an
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: Chan, Medeiros, Ozel & Psaltis, "GRay2" (arXiv:1706.07062).
+ *   - metric g_ab = eta_ab + f l_a l_b, M = 1               (Sec. 2.1, eq. def:CKS, eq. CKSr)
+ *   - right-hand side in the optimised split-metric form    (Sec. 2.1, eqs. opt0 and opti)
+ *   - classic 4th-order Runge-Kutta stepping                (Sec. 3)
+ *   - termination near the horizon or beyond the start radius (Sec. 4)
+ * Step-size control (step doubling), surface clipping, the FP32+Kahan
+ * precision scheme and the persistent work queue are this library's own
+ * additions; their exact rules are stated at kerr_opts below.
+ *
+ * Conventions shared by every entry point
+ *   Units      G = c = M = 1.  State of a geodesic: x^mu = (t, x, y, z) and
+ *              k^mu = dx^mu/dlambda = (k^t, k^x, k^y, k^z).
+ *   Layout     Structure of arrays.  A "[4][n] plane" argument is 4*n doubles,
+ *              component mu of geodesic i at index mu*n + i.  status and steps
+ *              are n int32; diag is a [4][n] float plane (E, L_z, Q, u^2).
+ *   Memory     Every pointer may be host memory (pageable or pinned) or device
+ *              memory of the current device; the library tells them apart with
+ *              cudaPointerGetAttributes.  With any host pointer the call stages
+ *              through library-owned device buffers and returns only after the
+ *              stream is synchronised.  With device pointers only, the call is
+ *              asynchronous on `stream`.  Inputs are never modified.  The
+ *              caller owns all inputs and outputs; the context owns its
+ *              scratch (work-queue counter, statistics, staging buffers,
+ *              CUDA graphs) and frees it in kerr_destroy.
+ *   Streams    `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   Errors     0 on success, a negative KERR_E* code otherwise; the message
+ *              is in kerr_last_error() (thread-local).  On a negative return
+ *              the output buffers are unspecified.  Per-geodesic outcomes are
+ *              reported in status[], never as a return code.
+ *   n == 0     A no-op that returns 0.
+ */
+#ifndef KERR_H
+#define KERR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KERR_OK 0
+#define KERR_EINVAL (-1)   /* bad argument (spin, sizes, options, NULL pointer) */
+#define KERR_ENOMEM (-2)   /* device or host allocation failed                  */
+#define KERR_ECUDA (-3)    /* a CUDA runtime call failed                        */
+
+/* Per-geodesic outcome written to status[]. */
+#define KERR_ESCAPED 1     /* r > r_escape while moving outward (x^i k^i > 0)  */
+#define KERR_CAPTURED 2    /* r < 1.01 r_h, r_h = 1 + sqrt(1 - a^2)             */
+#define KERR_ENDTIME 3     /* t crossed opts.t_end                              */
+#define KERR_MAXSTEPS 4    /* opts.max_steps attempted steps without an event  */
+#define KERR_TIMEOUT 5     /* opts.budget_ns ran out; state is where it stopped */
+#define KERR_NONFINITE 6   /* the state became (or started) NaN or infinite    */
+#define KERR_INVALID_IC 7  /* no real k^t / u^t solves the norm condition       */
+
+/* Arithmetic of the integration. */
+#define KERR_FP64 0        /* every step in FP64                                */
+#define KERR_FP32_KAHAN 1  /* FP32 steps with compensated (Kahan) state update; */
+                           /* FP64 for set-up, diagnostics and steps that start */
+                           /* inside opts.fp64_zone * r_h                       */
+
+typedef struct kerr_ctx kerr_ctx;
+
+/* Integration options.  Fill with kerr_opts_default() and change fields.
+ *
+ * Step control (adaptive, tol > 0).  Each attempt of length h takes one RK4
+ * step of h and two of h/2 from the same state (11 right-hand sides, the
+ * first shared).  With delta = (y_half - y_full)/15 the error is
+ *   err = max over i in {x, y, z, k^t, k^x, k^y, k^z} of
+ *         |delta_i| / (tol * (1 + max(|y_i|, |y_half_i|)))
+ * (t is left out: it never enters the right-hand side).  err <= 1 accepts
+ * y_half; either way h is multiplied by clamp(0.9 err^(-1/5), 0.2, 5), by 5 if
+ * err == 0 and by 0.2 if err is not finite.
+ *
+ * Termination, tested after each accepted step in this order:
+ *   captured  r < 1.01 r_h;
+ *   escaped   r > r_esc and x^i k^i > 0, where r_esc = r_escape if > 0, the
+ *             geodesic's start radius if == 0, and +infinity if < 0;
+ *   end time  t - t_end changed sign from its initial value (t_end finite).
+ * The crossing step is then clipped onto the surface: the step as a function
+ * of its length (two RK4 half steps from the last accepted state) is solved
+ * for the surface by Illinois regula falsi, to |r - r_stop| <= 1e-12 r_stop in
+ * FP64 (2e-6 r_stop in FP32; the same factors for t with scale max(1,|t_end|))
+ * or clip_maxit iterations.  A geodesic that starts inside 1.01 r_h is
+ * captured with no step; one that reaches max_steps attempts is MAXSTEPS. */
+typedef struct {
+    int32_t prec;          /* KERR_FP64 or KERR_FP32_KAHAN                       */
+    int32_t renorm_every;  /* > 0: every n accepted steps re-solve k^t (FP64) so */
+                           /* that g_ab k^a k^b keeps its initial value, on the  */
+                           /* root nearest the current k^t; 0: off               */
+    double tol;            /* error tolerance, > 0                               */
+    double h0;             /* first trial step in lambda, > 0                    */
+    int64_t max_steps;     /* cap on attempted steps per geodesic, >= 0          */
+    double r_escape;       /* see above                                          */
+    double t_end;          /* +-INFINITY or NaN: no end-time event               */
+    double fp64_zone;      /* FP32 path: steps that start at r < fp64_zone * r_h */
+                           /* run in FP64; 0 = never                             */
+    int32_t clip_maxit;    /* iterations of the surface root-find, >= 1          */
+    int32_t variant;       /* kernel launch configuration: -1 = autotuned (or    */
+                           /* the default before tuning), else an index < the    */
+                           /* value of kerr_num_variants()                       */
+    uint64_t budget_ns;    /* wall-time budget of one call on the device; 0 =   */
+                           /* none.  Geodesics unfinished when it runs out get   */
+                           /* KERR_TIMEOUT and the state reached so far          */
+} kerr_opts;
+
+/* One pinhole-free parallel-ray camera (the paper's image-plane rays,
+ * Sec. 4; its geometry follows this library's reading):
+ *   observer direction n = (sin incl, 0, cos incl); image axes
+ *   e_alpha = (0, 1, 0), e_beta = (-cos incl, 0, sin incl); pixel (p, q)
+ *   has alpha = -w + (p + 1/2) 2w/nx, beta = -w + (q + 1/2) 2w/ny and flat
+ *   index q*nx + p; the ray starts at t = 0, x = r_obs n + alpha e_alpha +
+ *   beta e_beta, with spatial k = -n and k^t < 0 from g_ab k^a k^b = 0
+ *   (past-directed: the ray is traced backward from the observer).        */
+typedef struct {
+    double a;              /* spin of this image's black hole, |a| <= 1          */
+    double incl;           /* inclination in radians                             */
+    double r_obs;          /* observer distance, > 1.01 r_h                      */
+    double half_width;     /* w, > 0                                             */
+    int32_t nx, ny;        /* pixels, > 0                                        */
+} kerr_camera;
+
+/* Counters of the last trace call on a context (read after the stream is
+ * synchronised). */
+typedef struct {
+    int64_t geodesics;        /* geodesics handled                               */
+    int64_t attempts;         /* attempted steps, all precisions                 */
+    int64_t accepted;         /* accepted steps                                  */
+    int64_t rhs_fp32;         /* right-hand sides evaluated in FP32              */
+    int64_t rhs_fp64;         /* right-hand sides evaluated in FP64              */
+    int64_t attempts_fp64;    /* attempted steps taken in FP64                   */
+    int64_t status_count[8];  /* geodesics per status code                       */
+    float kernel_ms;          /* device time of the integration kernel           */
+    int32_t variant;          /* launch configuration used                       */
+} kerr_stats;
+
+/* Fills *opts with: prec FP32_KAHAN, tol 1e-6, h0 1, max_steps 1e6,
+ * r_escape 0, t_end +inf, fp64_zone 1.5, renorm_every 0, clip_maxit 40,
+ * variant -1, budget_ns 0. */
+void kerr_opts_default(kerr_opts *opts);
+
+/* Creates a context for black-hole spin a (|a| <= 1, else KERR_EINVAL) on the
+ * current CUDA device.  The spin applies to kerr_trace_rays and
+ * kerr_trace_particles; cameras carry their own. */
+int kerr_init(double a, kerr_ctx **out);
+
+/* Frees the context and everything it owns; NULL is a no-op.  Waits for the
+ * context's work to finish. */
+int kerr_destroy(kerr_ctx *ctx);
+
+/* Integrates n geodesics from the given states (any causal type; nothing is
+ * renormalised at the start).  x0, k0: [4][n] planes.  Outputs: end states
+ * x_out, k_out ([4][n]), status[n], steps[n] (attempted steps), and diag
+ * ([4][n] floats: E = -p_t, L_z = x p_y - y p_x, Carter's Q, u^2 = g_ab k^a k^b
+ * at the end state, FP64-computed) unless diag is NULL.  Sec. 2.1 (eqs.
+ * opt0/opti), Sec. 3 (RK4), Sec. 4 (termination). */
+int kerr_trace_rays(kerr_ctx *ctx, const double *x0, const double *k0, int64_t n,
+                    const kerr_opts *opts, double *x_out, double *k_out, int32_t *status,
+                    int32_t *steps, float *diag, void *stream);
+
+/* Integrates every ray of ncam cameras (Sec. 4: backward null geodesics from
+ * an image plane at large distance); the initial states are built on the
+ * device in FP64.  Rays are numbered camera by camera, row-major inside a
+ * camera; outputs as for kerr_trace_rays with n = sum of nx*ny.  With
+ * opts->r_escape == 0 each ray escapes at its own start radius. */
+int kerr_trace_camera(kerr_ctx *ctx, const kerr_camera *cams, int32_t ncam,
+                      const kerr_opts *opts, double *x_out, double *k_out, int32_t *status,
+                      int32_t *steps, float *diag, void *stream);
+
+/* Integrates n massive particles (Sec. 3.2: time-like geodesics with the same
+ * integrator).  x0: [4][n] plane of start events; v0: [3][n] plane of
+ * coordinate velocities dx^i/dt.  u^t is solved in FP64 from g_ab u^a u^b = -1
+ * with u^i = u^t v^i; a velocity that is not time-like gives KERR_INVALID_IC
+ * (end state = start event, k = 0).  t_end: n end times, one per particle,
+ * or NULL to use opts->t_end for all.  Outputs as for kerr_trace_rays (k_out
+ * holds u^mu). */
+int kerr_trace_particles(kerr_ctx *ctx, const double *x0, const double *v0, const double *t_end,
+                         int64_t n, const kerr_opts *opts, double *x_out, double *k_out,
+                         int32_t *status, int32_t *steps, float *diag, void *stream);
+
+/* Copies the counters of the last trace call into *out (synchronises the
+ * context's stream first). */
+int kerr_get_stats(kerr_ctx *ctx, kerr_stats *out);
+
+/* Number of kernel launch configurations (block size x register cap). */
+int kerr_num_variants(void);
+
+/* Describes variant v: threads per block and minimum resident blocks per SM
+ * (which sets the register cap). */
+int kerr_variant_info(int v, int32_t *block, int32_t *min_blocks);
+
+/* Times every launch configuration for the given precision on `sample`
+ * camera rays of cams[0] (spread over the image) and remembers the fastest
+ * for later calls with variant == -1 on this context.  Writes the chosen
+ * variant to *best. */
+int kerr_autotune(kerr_ctx *ctx, const kerr_camera *cam, const kerr_opts *opts,
+                  int64_t sample, int32_t *best, void *stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *kerr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KERR_H */

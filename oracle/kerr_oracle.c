@@ -614,6 +614,7 @@ int oracle_trace_one(double a, const double y0[8], const oracle_opts *o, double 
 typedef struct {
     int64_t n;
     const double *a;
+    const double *t_end;   /* per-geodesic end times or NULL */
     const double *y0;
     const oracle_opts *o;
     double *yend;
@@ -634,7 +635,10 @@ static void *batch_worker(void *arg)
         if (i >= J->n)
             break;
         oracle_counts c;
-        J->status[i] = oracle_trace_one(J->a[i], J->y0 + 8 * i, J->o, J->yend + 8 * i, &c);
+        oracle_opts o = *J->o;
+        if (J->t_end)
+            o.t_end = J->t_end[i];
+        J->status[i] = oracle_trace_one(J->a[i], J->y0 + 8 * i, &o, J->yend + 8 * i, &c);
         if (J->attempts)
             J->attempts[i] = c.attempts;
         if (J->rhs_evals)
@@ -643,11 +647,12 @@ static void *batch_worker(void *arg)
     return NULL;
 }
 
-int oracle_trace_batch(int64_t n, const double *a, const double *y0, const oracle_opts *o,
-                       double *yend, int32_t *status, int64_t *attempts, int64_t *rhs_evals,
-                       int nthreads)
+int oracle_trace_batch(int64_t n, const double *a, const double *t_end, const double *y0,
+                       const oracle_opts *o, double *yend, int32_t *status, int64_t *attempts,
+                       int64_t *rhs_evals, int nthreads)
 {
-    batch_job J = {n, a, y0, o, yend, status, attempts, rhs_evals, 0, PTHREAD_MUTEX_INITIALIZER};
+    batch_job J = {n, a, t_end, y0, o, yend, status, attempts, rhs_evals, 0,
+                   PTHREAD_MUTEX_INITIALIZER};
     if (nthreads < 1)
         nthreads = 1;
     if (nthreads > 256)

@@ -79,7 +79,7 @@ def lib():
         _lib.oracle_trace_one.argtypes = [c.c_double, D, c.POINTER(_Opts), D,
                                           c.POINTER(_Counts)]
         _lib.oracle_trace_one.restype = c.c_int
-        _lib.oracle_trace_batch.argtypes = [c.c_int64, D, D, c.POINTER(_Opts), D, I32, I64,
+        _lib.oracle_trace_batch.argtypes = [c.c_int64, D, D, D, c.POINTER(_Opts), D, I32, I64,
                                             I64, c.c_int]
         _lib.oracle_trace_batch.restype = c.c_int
     return _lib
@@ -213,11 +213,13 @@ class TraceResult:
     rhs_evals: np.ndarray  # (n,) int64 right-hand-side evaluations
 
 
-def trace(a, y0, opts: Opts, nthreads: int | None = None) -> TraceResult:
-    """Integrate each row of y0 (n, 8); `a` is a scalar or one spin per row."""
+def trace(a, y0, opts: Opts, nthreads: int | None = None, t_end=None) -> TraceResult:
+    """Integrate each row of y0 (n, 8); `a` is a scalar or one spin per row;
+    `t_end` optionally gives one end time per row (overrides opts.t_end)."""
     y0 = _f64(y0).reshape(-1, 8)
     n = y0.shape[0]
     av = _f64(np.broadcast_to(np.asarray(a, dtype=np.float64), (n,)))
+    te = None if t_end is None else _f64(np.broadcast_to(np.asarray(t_end, np.float64), (n,)))
     yend = np.zeros((n, 8))
     status = np.zeros(n, dtype=np.int32)
     att = np.zeros(n, dtype=np.int64)
@@ -227,7 +229,7 @@ def trace(a, y0, opts: Opts, nthreads: int | None = None) -> TraceResult:
     co = opts.c()
     if n:
         lib().oracle_trace_batch(
-            n, _dp(av), _dp(y0), ctypes.byref(co), _dp(yend),
+            n, _dp(av), _dp(te) if te is not None else None, _dp(y0), ctypes.byref(co), _dp(yend),
             status.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
             att.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
             ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(nthreads))
@@ -235,7 +237,7 @@ def trace(a, y0, opts: Opts, nthreads: int | None = None) -> TraceResult:
 
 
 def ill_conditioned(a, y0, opts: Opts, ref: TraceResult | None = None,
-                    rel: float = 1e-5, nthreads: int | None = None) -> np.ndarray:
+                    rel: float = 1e-5, nthreads: int | None = None, t_end=None) -> np.ndarray:
     """Flag rays whose endpoint is not determined to `rel` by the integration.
 
     A ray is ill-conditioned if its end state moves by more than `rel`
@@ -246,12 +248,12 @@ def ill_conditioned(a, y0, opts: Opts, ref: TraceResult | None = None,
     between two correct integrators."""
     y0 = _f64(y0).reshape(-1, 8)
     if ref is None:
-        ref = trace(a, y0, opts, nthreads)
+        ref = trace(a, y0, opts, nthreads, t_end=t_end)
     tight = Opts(**{**opts.__dict__, "tol": opts.tol / 100.0})
-    r_tight = trace(a, y0, tight, nthreads)
+    r_tight = trace(a, y0, tight, nthreads, t_end=t_end)
     yp = y0.copy()
     yp[:, 1:4] *= (1.0 + 1e-7)
-    r_pert = trace(a, yp, opts, nthreads)
+    r_pert = trace(a, yp, opts, nthreads, t_end=t_end)
 
     def rel_err(u, v):
         ex = np.linalg.norm(u[:, 1:4] - v[:, 1:4], axis=1) / np.linalg.norm(v[:, 1:4], axis=1)

@@ -1,0 +1,562 @@
+// kerr_api.cu -- the C ABI declared in include/kerr.h: argument checks,
+// host/device staging, the work-queue and statistics scratch, CUDA-graph
+// replay of the integration launch, and the launch-configuration autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/kerr.h"
+#include "kerr_trace.cuh"
+#include "kerr_variants.h"
+
+using namespace kerr;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define KERR_CUDA(call)                                                                        \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(KERR_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));           \
+    } while (0)
+
+bool is_device_ptr(const void *p)
+{
+    if (!p)
+        return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+} // namespace
+
+// Launch parameters that identify a cached graph.
+struct GraphKey {
+    TraceParams P;
+    int variant;
+    int f32;
+    bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof *this) == 0; }
+};
+
+struct kerr_ctx {
+    double a = 0.0;
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;               // the context's own stream
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_k0 = nullptr, ev_k1 = nullptr;
+    unsigned long long *d_scratch = nullptr;     // [0] queue head, [1..] statistics
+    CamDev *d_cams = nullptr;
+    int cam_cap = 0;
+    char *d_stage = nullptr;                     // staging arena for host buffers
+    size_t stage_cap = 0;
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey;
+    bool gvalid = false;
+    int tuned[2] = {-1, -1};                     // autotuned variant per precision
+    int last_variant = -1;
+    bool have_stats = false;
+};
+
+static const int kScratchWords = 1 + SC_COUNT;
+
+extern "C" void kerr_opts_default(kerr_opts *o)
+{
+    if (!o)
+        return;
+    std::memset(o, 0, sizeof *o);
+    o->prec = KERR_FP32_KAHAN;
+    o->renorm_every = 0;
+    o->tol = 1e-6;
+    o->h0 = 1.0;
+    o->max_steps = 1000000;
+    o->r_escape = 0.0;
+    o->t_end = INFINITY;
+    o->fp64_zone = 1.5;
+    o->clip_maxit = 40;
+    o->variant = -1;
+    o->budget_ns = 0;
+}
+
+extern "C" const char *kerr_last_error(void) { return g_err.c_str(); }
+
+extern "C" int kerr_num_variants(void) { return kNumVariants; }
+
+extern "C" int kerr_variant_info(int v, int32_t *block, int32_t *min_blocks)
+{
+    if (v < 0 || v >= kNumVariants)
+        return fail(KERR_EINVAL, "variant %d out of range [0, %d)", v, kNumVariants);
+    if (block)
+        *block = kVariants[v].block;
+    if (min_blocks)
+        *min_blocks = kVariants[v].min_blocks;
+    return KERR_OK;
+}
+
+extern "C" int kerr_init(double a, kerr_ctx **out)
+{
+    if (!out)
+        return fail(KERR_EINVAL, "kerr_init: out is NULL");
+    *out = nullptr;
+    if (!(std::fabs(a) <= 1.0))
+        return fail(KERR_EINVAL, "kerr_init: spin a = %g outside [-1, 1]", a);
+    kerr_ctx *c = new (std::nothrow) kerr_ctx();
+    if (!c)
+        return fail(KERR_ENOMEM, "kerr_init: out of host memory");
+    c->a = a;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&c->ev_k0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&c->ev_k1);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&c->d_scratch, kScratchWords * sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = cudaMemset(c->d_scratch, 0, kScratchWords * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        int code = (e == cudaErrorMemoryAllocation) ? KERR_ENOMEM : KERR_ECUDA;
+        kerr_destroy(c);
+        return fail(code, "kerr_init: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return KERR_OK;
+}
+
+extern "C" int kerr_destroy(kerr_ctx *c)
+{
+    if (!c)
+        return KERR_OK;
+    if (c->stream)
+        cudaStreamSynchronize(c->stream);
+    if (c->gexec)
+        cudaGraphExecDestroy(c->gexec);
+    cudaFree(c->d_scratch);
+    cudaFree(c->d_cams);
+    cudaFree(c->d_stage);
+    if (c->ev_in)
+        cudaEventDestroy(c->ev_in);
+    if (c->ev_out)
+        cudaEventDestroy(c->ev_out);
+    if (c->ev_k0)
+        cudaEventDestroy(c->ev_k0);
+    if (c->ev_k1)
+        cudaEventDestroy(c->ev_k1);
+    if (c->stream)
+        cudaStreamDestroy(c->stream);
+    delete c;
+    return KERR_OK;
+}
+
+static int check_opts(const kerr_opts *o)
+{
+    if (!o)
+        return fail(KERR_EINVAL, "opts is NULL");
+    if (o->prec != KERR_FP64 && o->prec != KERR_FP32_KAHAN)
+        return fail(KERR_EINVAL, "opts.prec = %d is not KERR_FP64 or KERR_FP32_KAHAN", o->prec);
+    if (!(o->tol > 0.0) || !std::isfinite(o->tol))
+        return fail(KERR_EINVAL, "opts.tol = %g must be finite and > 0", o->tol);
+    if (!(o->h0 > 0.0) || !std::isfinite(o->h0))
+        return fail(KERR_EINVAL, "opts.h0 = %g must be finite and > 0", o->h0);
+    if (o->max_steps < 0)
+        return fail(KERR_EINVAL, "opts.max_steps = %lld < 0", (long long)o->max_steps);
+    if (std::isnan(o->r_escape))
+        return fail(KERR_EINVAL, "opts.r_escape is NaN");
+    if (!(o->fp64_zone >= 0.0))
+        return fail(KERR_EINVAL, "opts.fp64_zone = %g < 0", o->fp64_zone);
+    if (o->clip_maxit < 1)
+        return fail(KERR_EINVAL, "opts.clip_maxit = %d < 1", o->clip_maxit);
+    if (o->renorm_every < 0)
+        return fail(KERR_EINVAL, "opts.renorm_every = %d < 0", o->renorm_every);
+    if (o->variant < -1 || o->variant >= kNumVariants)
+        return fail(KERR_EINVAL, "opts.variant = %d outside [-1, %d)", o->variant, kNumVariants);
+    return KERR_OK;
+}
+
+// Staging of host buffers through a library-owned device arena.
+struct Stage {
+    const void *host;
+    void **dev;     // where to put the device pointer
+    size_t bytes;
+    bool input;
+    size_t off;
+};
+
+static int ensure_stage(kerr_ctx *c, size_t bytes)
+{
+    if (bytes <= c->stage_cap)
+        return KERR_OK;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->d_stage);
+    c->d_stage = nullptr;
+    c->stage_cap = 0;
+    size_t cap = std::max(bytes, (size_t)1 << 20);
+    cudaError_t e = cudaMalloc(&c->d_stage, cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KERR_ENOMEM, "staging allocation of %zu bytes failed: %s", cap,
+                    cudaGetErrorString(e));
+    }
+    c->stage_cap = cap;
+    return KERR_OK;
+}
+
+static int launch_integration(kerr_ctx *c, const TraceParams &P, int prec, int variant)
+{
+    const int f32 = (prec == KERR_FP32_KAHAN) ? 1 : 0;
+    GraphKey key;
+    std::memset(&key, 0, sizeof key);
+    key.P = P;
+    key.variant = variant;
+    key.f32 = f32;
+    if (!(c->gvalid && c->gkey == key)) {
+        cudaGraph_t g = nullptr;
+        KERR_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = cudaMemsetAsync(c->d_scratch, 0, kScratchWords * sizeof(unsigned long long),
+                                         c->stream);
+        cudaError_t e2 = e1 == cudaSuccess
+                             ? (f32 ? launch_trace_f32(P, variant, c->sms, c->stream)
+                                    : launch_trace_f64(P, variant, c->sms, c->stream))
+                             : e1;
+        cudaError_t e3 = cudaStreamEndCapture(c->stream, &g);
+        if (e2 != cudaSuccess || e3 != cudaSuccess) {
+            if (g)
+                cudaGraphDestroy(g);
+            cudaGetLastError();
+            return fail(KERR_ECUDA, "graph capture failed: %s",
+                        cudaGetErrorString(e2 != cudaSuccess ? e2 : e3));
+        }
+        bool updated = false;
+        if (c->gexec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(c->gexec, g, &info) == cudaSuccess)
+                updated = true;
+            else {
+                cudaGetLastError();
+                cudaGraphExecDestroy(c->gexec);
+                c->gexec = nullptr;
+            }
+        }
+        if (!updated) {
+            cudaError_t e = cudaGraphInstantiate(&c->gexec, g, 0);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(g);
+                c->gvalid = false;
+                return fail(KERR_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+            }
+        }
+        cudaGraphDestroy(g);
+        c->gkey = key;
+        c->gvalid = true;
+    }
+    KERR_CUDA(cudaEventRecord(c->ev_k0, c->stream));
+    KERR_CUDA(cudaGraphLaunch(c->gexec, c->stream));
+    KERR_CUDA(cudaEventRecord(c->ev_k1, c->stream));
+    c->last_variant = variant;
+    c->have_stats = true;
+    return KERR_OK;
+}
+
+// Shared body of the three trace entry points.
+static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k0,
+                        const double *t_end_each, int64_t n,
+                        const CamDev *cams_host, int32_t ncam, const kerr_opts *o, double *x_out,
+                        double *k_out, int32_t *status, int32_t *steps, float *diag, void *stream)
+{
+    if (!c)
+        return fail(KERR_EINVAL, "context is NULL");
+    int rc = check_opts(o);
+    if (rc)
+        return rc;
+    if (n < 0)
+        return fail(KERR_EINVAL, "n = %lld < 0", (long long)n);
+    if (n == 0)
+        return KERR_OK;
+    if (!x_out || !k_out || !status || !steps)
+        return fail(KERR_EINVAL, "x_out, k_out, status and steps must not be NULL");
+    if (mode != MODE_CAMERA && (!x0 || !k0))
+        return fail(KERR_EINVAL, "input planes must not be NULL");
+    cudaStream_t us = (cudaStream_t)stream;
+
+    TraceParams P;
+    std::memset(&P, 0, sizeof P);
+    P.mode = mode;
+    P.n = n;
+    P.a = c->a;
+    P.tol = o->tol;
+    P.h0 = o->h0;
+    P.max_steps = o->max_steps;
+    P.r_escape = o->r_escape;
+    P.t_end = o->t_end;
+    P.fp64_zone = o->prec == KERR_FP32_KAHAN ? o->fp64_zone : 0.0;
+    P.renorm_every = o->renorm_every;
+    P.clip_maxit = o->clip_maxit;
+    P.budget_ns = o->budget_ns;
+    P.head = c->d_scratch;
+    P.stats = c->d_scratch + 1;
+
+    // ---- which buffers live on the host
+    const size_t nn = (size_t)n;
+    const size_t in_planes = (mode == MODE_PARTICLES) ? 3 : 4;
+    std::vector<Stage> st;
+    P.x0 = x0;
+    P.k0 = k0;
+    P.t_end_each = t_end_each;
+    P.x_out = x_out;
+    P.k_out = k_out;
+    P.status = status;
+    P.steps = steps;
+    P.diag = diag;
+    if (mode != MODE_CAMERA) {
+        if (!is_device_ptr(x0))
+            st.push_back({x0, (void **)&P.x0, 4 * nn * sizeof(double), true, 0});
+        if (!is_device_ptr(k0))
+            st.push_back({k0, (void **)&P.k0, in_planes * nn * sizeof(double), true, 0});
+        if (t_end_each && !is_device_ptr(t_end_each))
+            st.push_back({t_end_each, (void **)&P.t_end_each, nn * sizeof(double), true, 0});
+    }
+    if (!is_device_ptr(x_out))
+        st.push_back({x_out, (void **)&P.x_out, 4 * nn * sizeof(double), false, 0});
+    if (!is_device_ptr(k_out))
+        st.push_back({k_out, (void **)&P.k_out, 4 * nn * sizeof(double), false, 0});
+    if (!is_device_ptr(status))
+        st.push_back({status, (void **)&P.status, nn * sizeof(int32_t), false, 0});
+    if (!is_device_ptr(steps))
+        st.push_back({steps, (void **)&P.steps, nn * sizeof(int32_t), false, 0});
+    if (diag && !is_device_ptr(diag))
+        st.push_back({diag, (void **)&P.diag, 4 * nn * sizeof(float), false, 0});
+    size_t total = 0;
+    for (auto &s : st) {
+        s.off = total;
+        total += (s.bytes + 255) & ~(size_t)255;
+    }
+    if (total) {
+        rc = ensure_stage(c, total);
+        if (rc)
+            return rc;
+        for (auto &s : st)
+            *s.dev = c->d_stage + s.off;
+    }
+
+    // ---- order after the caller's stream
+    KERR_CUDA(cudaEventRecord(c->ev_in, us));
+    KERR_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+
+    if (mode == MODE_CAMERA) {
+        if (ncam > c->cam_cap) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->d_cams);
+            c->d_cams = nullptr;
+            c->cam_cap = 0;
+            cudaError_t e = cudaMalloc(&c->d_cams, (size_t)ncam * sizeof(CamDev));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(KERR_ENOMEM, "camera table allocation failed");
+            }
+            c->cam_cap = ncam;
+        }
+        // The camera table is small; copy it synchronously from a stack copy
+        // so the caller's array can go out of scope.
+        KERR_CUDA(cudaMemcpyAsync(c->d_cams, cams_host, (size_t)ncam * sizeof(CamDev),
+                                  cudaMemcpyHostToDevice, c->stream));
+        KERR_CUDA(cudaStreamSynchronize(c->stream));
+        P.cams = c->d_cams;
+        P.ncam = ncam;
+    }
+    for (auto &s : st)
+        if (s.input)
+            KERR_CUDA(cudaMemcpyAsync(*s.dev, s.host, s.bytes, cudaMemcpyHostToDevice, c->stream));
+
+    int prec = o->prec;
+    int variant = o->variant >= 0 ? o->variant : (c->tuned[prec] >= 0 ? c->tuned[prec] : 0);
+    rc = launch_integration(c, P, prec, variant);
+    if (rc)
+        return rc;
+
+    bool any_host = false;
+    for (auto &s : st)
+        if (!s.input) {
+            KERR_CUDA(cudaMemcpyAsync((void *)s.host, *s.dev, s.bytes, cudaMemcpyDeviceToHost,
+                                      c->stream));
+            any_host = true;
+        }
+    for (auto &s : st)
+        any_host = any_host || s.input;
+    KERR_CUDA(cudaEventRecord(c->ev_out, c->stream));
+    KERR_CUDA(cudaStreamWaitEvent(us, c->ev_out, 0));
+    if (any_host)
+        KERR_CUDA(cudaStreamSynchronize(c->stream));
+    return KERR_OK;
+}
+
+extern "C" int kerr_trace_rays(kerr_ctx *c, const double *x0, const double *k0, int64_t n,
+                               const kerr_opts *o, double *x_out, double *k_out, int32_t *status,
+                               int32_t *steps, float *diag, void *stream)
+{
+    return trace_common(c, MODE_RAYS, x0, k0, nullptr, n, nullptr, 0, o, x_out, k_out, status, steps, diag,
+                        stream);
+}
+
+extern "C" int kerr_trace_particles(kerr_ctx *c, const double *x0, const double *v0,
+                                    const double *t_end, int64_t n, const kerr_opts *o,
+                                    double *x_out, double *k_out, int32_t *status, int32_t *steps,
+                                    float *diag, void *stream)
+{
+    return trace_common(c, MODE_PARTICLES, x0, v0, t_end, n, nullptr, 0, o, x_out, k_out, status, steps,
+                        diag, stream);
+}
+
+static int build_cams(const kerr_camera *cams, int32_t ncam, std::vector<CamDev> &out, int64_t &n)
+{
+    if (!cams || ncam <= 0)
+        return fail(KERR_EINVAL, "need at least one camera (ncam = %d)", ncam);
+    out.resize(ncam);
+    n = 0;
+    for (int i = 0; i < ncam; ++i) {
+        const kerr_camera &k = cams[i];
+        if (!(std::fabs(k.a) <= 1.0))
+            return fail(KERR_EINVAL, "camera %d: spin %g outside [-1, 1]", i, k.a);
+        if (k.nx <= 0 || k.ny <= 0)
+            return fail(KERR_EINVAL, "camera %d: size %d x %d", i, k.nx, k.ny);
+        if (!(k.half_width > 0.0) || !std::isfinite(k.half_width))
+            return fail(KERR_EINVAL, "camera %d: half width %g", i, k.half_width);
+        const double rh = 1.0 + std::sqrt(std::max(0.0, 1.0 - k.a * k.a));
+        if (!(k.r_obs > 1.01 * rh) || !std::isfinite(k.r_obs) || !std::isfinite(k.incl))
+            return fail(KERR_EINVAL, "camera %d: r_obs %g / incl %g invalid", i, k.r_obs, k.incl);
+        out[i] = CamDev{k.a, k.incl, k.r_obs, k.half_width, k.nx, k.ny, n};
+        n += (int64_t)k.nx * k.ny;
+    }
+    return KERR_OK;
+}
+
+extern "C" int kerr_trace_camera(kerr_ctx *c, const kerr_camera *cams, int32_t ncam,
+                                 const kerr_opts *o, double *x_out, double *k_out, int32_t *status,
+                                 int32_t *steps, float *diag, void *stream)
+{
+    std::vector<CamDev> cd;
+    int64_t n = 0;
+    int rc = build_cams(cams, ncam, cd, n);
+    if (rc)
+        return rc;
+    return trace_common(c, MODE_CAMERA, nullptr, nullptr, nullptr, n, cd.data(), ncam, o, x_out, k_out,
+                        status, steps, diag, stream);
+}
+
+extern "C" int kerr_get_stats(kerr_ctx *c, kerr_stats *out)
+{
+    if (!c || !out)
+        return fail(KERR_EINVAL, "kerr_get_stats: NULL argument");
+    std::memset(out, 0, sizeof *out);
+    if (!c->have_stats)
+        return KERR_OK;
+    KERR_CUDA(cudaStreamSynchronize(c->stream));
+    unsigned long long h[kScratchWords];
+    KERR_CUDA(cudaMemcpy(h, c->d_scratch, sizeof h, cudaMemcpyDeviceToHost));
+    const unsigned long long *s = h + 1;
+    out->geodesics = (int64_t)s[SC_GEODESICS];
+    out->attempts = (int64_t)s[SC_ATTEMPTS];
+    out->accepted = (int64_t)s[SC_ACCEPTED];
+    out->rhs_fp32 = (int64_t)s[SC_RHS32];
+    out->rhs_fp64 = (int64_t)s[SC_RHS64];
+    out->attempts_fp64 = (int64_t)s[SC_ATT64];
+    for (int j = 0; j < 8; ++j)
+        out->status_count[j] = (int64_t)s[SC_STATUS + j];
+    float ms = 0.f;
+    KERR_CUDA(cudaEventElapsedTime(&ms, c->ev_k0, c->ev_k1));
+    out->kernel_ms = ms;
+    out->variant = c->last_variant;
+    return KERR_OK;
+}
+
+extern "C" int kerr_autotune(kerr_ctx *c, const kerr_camera *cam, const kerr_opts *o,
+                             int64_t sample, int32_t *best, void *stream)
+{
+    if (!c || !cam || !best)
+        return fail(KERR_EINVAL, "kerr_autotune: NULL argument");
+    int rc = check_opts(o);
+    if (rc)
+        return rc;
+    if (sample < 1024)
+        sample = 1024;
+    kerr_camera sub = *cam;
+    int side = (int)std::lround(std::sqrt((double)sample));
+    sub.nx = std::min(cam->nx, side);
+    sub.ny = std::min(cam->ny, side);
+    const size_t n = (size_t)sub.nx * sub.ny;
+    double *xo = nullptr, *ko = nullptr;
+    int32_t *so = nullptr, *no = nullptr;
+    cudaError_t e = cudaMalloc(&xo, 4 * n * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&ko, 4 * n * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&so, n * sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&no, n * sizeof(int32_t));
+    if (e != cudaSuccess) {
+        cudaFree(xo);
+        cudaFree(ko);
+        cudaFree(so);
+        cudaFree(no);
+        cudaGetLastError();
+        return fail(KERR_ENOMEM, "kerr_autotune: allocation failed");
+    }
+    kerr_opts oo = *o;
+    float best_ms = 1e30f;
+    int best_v = 0;
+    for (int v = 0; v < kNumVariants && rc == KERR_OK; ++v) {
+        oo.variant = v;
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 3 && rc == KERR_OK; ++rep) {
+            rc = kerr_trace_camera(c, &sub, 1, &oo, xo, ko, so, no, nullptr, stream);
+            if (rc)
+                break;
+            kerr_stats s;
+            rc = kerr_get_stats(c, &s);
+            if (rep > 0)
+                ms_min = std::min(ms_min, s.kernel_ms);
+        }
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            best_v = v;
+        }
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(xo);
+    cudaFree(ko);
+    cudaFree(so);
+    cudaFree(no);
+    if (rc)
+        return rc;
+    c->tuned[o->prec] = best_v;
+    *best = best_v;
+    return KERR_OK;
+}

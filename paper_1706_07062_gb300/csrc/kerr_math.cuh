@@ -1,0 +1,205 @@
+// kerr_math.cuh -- device arithmetic of the Cartesian Kerr-Schild geodesic
+// integrator (arXiv:1706.07062, Sec. 2.1).  Units G = c = M = 1.
+//
+// State of one geodesic: y = (t, x, y, z, k^t, k^x, k^y, k^z), k = dx/dlambda.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kerr {
+
+// ---------------------------------------------------------------------------
+// Precision-specific primitives.  FP32 uses the hardware approximations of
+// the PTX ISA (rcp/rsqrt/sqrt .approx, relative error ~2^-23); FP64 uses the
+// correctly rounded operators so that the FP64 path tracks an FP64 reference
+// to rounding.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float k_rcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float k_rsqrt(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float k_sqrt(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double k_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ double k_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ double k_rsqrt(double x) { return 1.0 / sqrt(x); }
+
+__device__ __forceinline__ float k_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double k_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Kerr-Schild radius from eq. CKSr: the positive root r^2 of
+// r^4 - (R^2 - a^2) r^2 - a^2 z^2 = 0.
+template <typename T>
+__device__ __forceinline__ T ks_r2(T a2, T x, T y, T z)
+{
+    const T d = k_fma(x, x, k_fma(y, y, z * z)) - a2;
+    return T(0.5) * (d + k_sqrt(k_fma(d, d, T(4) * a2 * (z * z))));
+}
+
+template <typename T>
+__device__ __forceinline__ T ks_r(T a2, T x, T y, T z)
+{
+    return k_sqrt(ks_r2(a2, x, y, z));
+}
+
+// ---------------------------------------------------------------------------
+// Geodesic acceleration d k^mu / d lambda in the split-metric form of
+// Sec. 2.1, eqs. opt0 and opti:
+//   x0'' =  k^al D_{0 al} - F,
+//   xi'' = -k^al (D_{i al} - D_{al i}/2) + F l^i,
+// with D_{be al} = d_al(f l_be l_ga) k^ga = l_be A_al + f L d_al l_be,
+//   L = l_ga k^ga,  A_al = (d_al f) L + f (d_al l_ga) k^ga,
+// and F = f (l^be k^al - l^al k^be / 2) D_{be al}.  Two exact properties of
+// the Kerr-Schild vector (l is null, and l^i d_i l_be = 0: it is an affinely
+// parametrised flat-space geodesic) reduce F to -f L^2 (l^i d_i f) / 2.
+// The pieces:
+//   r from eq. CKSr; d_i r = (f/2) (x, y, z (1 + a^2/r^2));
+//   f = 2 r^3 / (r^4 + a^2 z^2);  d_i f = f (3/r - 2f) d_i r - 2 f a^2 z/(r^4 + a^2 z^2) delta_iz;
+//   l_i = ((r x + a y), (r y - a x)) / (r^2 + a^2), z / r;
+//   d_al l_i = (d_al r) e_i + M_{al i},  e = ((x - 2 r l_x), (y - 2 r l_y)) / (r^2 + a^2), -l_z / r,
+//   M = [[r, -a, 0], [a, r, 0], [0, 0, 1/r... ]] / (r^2 + a^2) in the x-y block, 1/r at (z, z).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void accel(const T a, const T a2, const T x, const T y, const T z,
+                                      const T kt, const T kx, const T ky, const T kz, T &at,
+                                      T &ax, T &ay, T &az)
+{
+    const T z2 = z * z;
+    const T az2 = a2 * z2;
+    const T d = k_fma(x, x, k_fma(y, y, z2)) - a2;
+    const T r2 = T(0.5) * (d + k_sqrt(k_fma(d, d, T(4) * az2)));
+    const T ir = k_rsqrt(r2);
+    const T r = r2 * ir;
+    const T iq = k_rcp(k_fma(r2, r2, az2));     // 1 / (r^4 + a^2 z^2)
+    const T is = k_rcp(r2 + a2);                // 1 / (r^2 + a^2)
+    const T hf = r * r2 * iq;                   // f / 2
+    const T f = hf + hf;
+    const T lx = k_fma(r, x, a * y) * is;
+    const T ly = k_fma(r, y, -(a * x)) * is;
+    const T lz = z * ir;
+    const T L = k_fma(lx, kx, k_fma(ly, ky, k_fma(lz, kz, kt)));
+    // gradient of r and of f
+    const T rx = hf * x;
+    const T ry = hf * y;
+    const T rz = hf * z * k_fma(a2, ir * ir, T(1));
+    const T c1 = f * k_fma(T(3), ir, T(-2) * f);
+    const T fx = c1 * rx;
+    const T fy = c1 * ry;
+    const T fz = k_fma(c1, rz, T(-2) * f * a2 * z * iq);
+    // d_al l_i = r_al e_i + M_{al i}
+    const T ex = is * k_fma(T(-2) * r, lx, x);
+    const T ey = is * k_fma(T(-2) * r, ly, y);
+    const T ez = -lz * ir;
+    const T ek = k_fma(ex, kx, k_fma(ey, ky, ez * kz));     // e . k
+    const T kr = k_fma(rx, kx, k_fma(ry, ky, rz * kz));     // k . grad r
+    const T dLx = k_fma(rx, ek, is * k_fma(r, kx, -(a * ky)));   // (d_x l_ga) k^ga
+    const T dLy = k_fma(ry, ek, is * k_fma(r, ky, a * kx));
+    const T dLz = k_fma(rz, ek, ir * kz);
+    const T kdx = k_fma(kr, ex, is * k_fma(r, kx, a * ky));      // k^al d_al l_x
+    const T kdy = k_fma(kr, ey, is * k_fma(r, ky, -(a * kx)));
+    const T kdz = k_fma(kr, ez, ir * kz);
+    const T Ax = k_fma(fx, L, f * dLx);
+    const T Ay = k_fma(fy, L, f * dLy);
+    const T Az = k_fma(fz, L, f * dLz);
+    const T Ak = k_fma(Ax, kx, k_fma(Ay, ky, Az * kz));          // k^al D_{0 al}
+    const T lf = k_fma(lx, fx, k_fma(ly, fy, lz * fz));          // l . grad f
+    const T F = T(-0.5) * f * (L * L) * lf;
+    const T fL = f * L;
+    const T hL = T(0.5) * L;
+    at = Ak - F;
+    ax = k_fma(hL, k_fma(f, dLx, Ax), k_fma(F, lx, -k_fma(lx, Ak, fL * kdx)));
+    ay = k_fma(hL, k_fma(f, dLy, Ay), k_fma(F, ly, -k_fma(ly, Ak, fL * kdy)));
+    az = k_fma(hL, k_fma(f, dLz, Az), k_fma(F, lz, -k_fma(lz, Ak, fL * kdz)));
+}
+
+// ---------------------------------------------------------------------------
+// FP64 helpers for set-up, renormalisation and diagnostics.
+// ---------------------------------------------------------------------------
+struct KSPoint {
+    double r, f, lx, ly, lz;
+};
+
+__device__ __forceinline__ KSPoint ks_point(double a, double x, double y, double z)
+{
+    KSPoint p;
+    const double a2 = a * a;
+    const double r2 = ks_r2(a2, x, y, z);
+    p.r = sqrt(r2);
+    p.f = 2.0 * p.r * r2 / (r2 * r2 + a2 * z * z);
+    p.lx = (p.r * x + a * y) / (r2 + a2);
+    p.ly = (p.r * y - a * x) / (r2 + a2);
+    p.lz = z / p.r;
+    return p;
+}
+
+// g_ab k^a k^b = -kt^2 + |k|^2 + f (kt + l.k)^2 for g = eta + f l l (l_0 = 1).
+__device__ __forceinline__ double norm2(const KSPoint &p, const double k[4])
+{
+    const double L = k[0] + p.lx * k[1] + p.ly * k[2] + p.lz * k[3];
+    return -k[0] * k[0] + k[1] * k[1] + k[2] * k[2] + k[3] * k[3] + p.f * L * L;
+}
+
+// Solve g_ab k^a k^b = target for k^t with the spatial k fixed:
+// (f - 1) kt^2 + 2 f s kt + (|k|^2 + f s^2 - target) = 0, s = l_i k^i.
+// branch < 0: smaller root; > 0: larger root; 0: root nearest k[0].
+// Returns false when there is no real root.
+__device__ __forceinline__ bool solve_kt(const KSPoint &p, double k[4], double target, int branch)
+{
+    const double s = p.lx * k[1] + p.ly * k[2] + p.lz * k[3];
+    const double A = p.f - 1.0;
+    const double B = 2.0 * p.f * s;
+    const double C = k[1] * k[1] + k[2] * k[2] + k[3] * k[3] + p.f * s * s - target;
+    const double disc = B * B - 4.0 * A * C;
+    if (!(disc >= 0.0) || A == 0.0)
+        return false;
+    const double q = -0.5 * (B + copysign(sqrt(disc), B));
+    const double r1 = q / A;
+    const double r2 = (q != 0.0) ? C / q : r1;
+    const double lo = fmin(r1, r2), hi = fmax(r1, r2);
+    if (branch == 0)
+        k[0] = (fabs(lo - k[0]) <= fabs(hi - k[0])) ? lo : hi;
+    else
+        k[0] = branch < 0 ? lo : hi;
+    return true;
+}
+
+// Constants of motion at an FP64 state: E = -p_t, L_z = x p_y - y p_x,
+// Carter's Q = p_th^2 + cos^2(th) [a^2 (mu^2 - E^2) + L_z^2 / sin^2(th)] with
+// mu^2 = -u^2, p_th = cot(th) (x p_x + y p_y) - r sin(th) p_z, cos(th) = z/r,
+// and u^2 = g_ab k^a k^b.  p_a = eta_ab k^b + f l_a L.
+__device__ __forceinline__ void constants(double a, const double y[8], float out[4])
+{
+    const KSPoint p = ks_point(a, y[1], y[2], y[3]);
+    const double L = y[4] + p.lx * y[5] + p.ly * y[6] + p.lz * y[7];
+    const double pt = -y[4] + p.f * L;
+    const double px = y[5] + p.f * p.lx * L;
+    const double py = y[6] + p.f * p.ly * L;
+    const double pz = y[7] + p.f * p.lz * L;
+    const double u2 = pt * y[4] + px * y[5] + py * y[6] + pz * y[7];
+    const double E = -pt;
+    const double Lz = y[1] * py - y[2] * px;
+    const double c = y[3] / p.r;
+    const double s2 = 1.0 - c * c;
+    const double s = sqrt(s2);
+    const double pth = (c / s) * (y[1] * px + y[2] * py) - p.r * s * pz;
+    const double Q = pth * pth + c * c * (a * a * (-u2 - E * E) + Lz * Lz / s2);
+    out[0] = (float)E;
+    out[1] = (float)Lz;
+    out[2] = (float)Q;
+    out[3] = (float)u2;
+}
+
+} // namespace kerr

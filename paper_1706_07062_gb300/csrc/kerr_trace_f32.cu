@@ -1,0 +1,39 @@
+// FP32+Kahan instantiations of the persistent kernel (FP64 inside the zone).
+#include "kerr_trace.cuh"
+#include "kerr_variants.h"
+
+namespace kerr {
+
+template <int B, int M>
+static cudaError_t launch_one(const TraceParams &P, int sms, cudaStream_t s)
+{
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<true, B, M>, B, 0);
+        if (e != cudaSuccess)
+            return e;
+        if (per_sm < 1)
+            per_sm = 1;
+    }
+    long long grid = (long long)per_sm * sms;
+    const long long need = (P.n + B - 1) / B;
+    if (need < grid)
+        grid = need < 1 ? 1 : need;
+    trace_kernel<true, B, M><<<(unsigned)grid, B, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_f32(const TraceParams &P, int v, int sms, cudaStream_t s)
+{
+    switch (v) {
+#define KERR_CASE(i, b, m) \
+    case i:                \
+        return launch_one<b, m>(P, sms, s);
+        KERR_VARIANT_LIST(KERR_CASE)
+#undef KERR_CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+} // namespace kerr

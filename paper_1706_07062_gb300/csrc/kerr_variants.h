@@ -1,0 +1,24 @@
+// kerr_variants.h -- launch configurations of the persistent kernel.
+#pragma once
+
+namespace kerr {
+
+// (threads per block, minimum resident blocks per SM).  The second number
+// caps registers per thread at 65536 / (block * min_blocks).
+struct Variant {
+    int block, min_blocks;
+};
+
+#define KERR_VARIANT_LIST(X) X(0, 128, 4) X(1, 128, 3) X(2, 256, 2) X(3, 128, 2) X(4, 64, 8) X(5, 128, 5)
+
+constexpr int kNumVariants = 6;
+constexpr Variant kVariants[kNumVariants] = {{128, 4}, {128, 3}, {256, 2}, {128, 2}, {64, 8}, {128, 5}};
+
+struct TraceParams;
+
+// Launch the persistent kernel for variant v on a grid of `blocks_per_sm *
+// sms` blocks (0 = as many as fit).  Returns the CUDA error of the launch.
+cudaError_t launch_trace_f32(const TraceParams &P, int v, int sms, cudaStream_t s);
+cudaError_t launch_trace_f64(const TraceParams &P, int v, int sms, cudaStream_t s);
+
+} // namespace kerr

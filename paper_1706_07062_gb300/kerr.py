@@ -1,0 +1,285 @@
+"""Thin Python binding of libkerr (include/kerr.h): argument marshalling only.
+
+Every step of the integration runs in the CUDA library; this module converts
+torch tensors / numpy arrays to pointers and back.  It never computes a
+geodesic itself, and it raises if libkerr.so is missing (no CPU fallback).
+
+Names follow the C ABI: ``kerr_init``, ``kerr_trace_rays``,
+``kerr_trace_camera``, ``kerr_trace_particles``, ``kerr_get_stats``,
+``kerr_autotune``.  Array arguments are [4][n] planes (component-major); a
+torch tensor of shape (4, n) or a numpy array of that shape is accepted, on
+the GPU or on the host.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libkerr.so")
+
+FP64, FP32_KAHAN = 0, 1
+ESCAPED, CAPTURED, ENDTIME, MAXSTEPS, TIMEOUT, NONFINITE, INVALID_IC = 1, 2, 3, 4, 5, 6, 7
+STATUS_NAMES = {1: "escaped", 2: "captured", 3: "endtime", 4: "maxsteps", 5: "timeout",
+                6: "nonfinite", 7: "invalid_ic"}
+
+
+class KerrError(RuntimeError):
+    pass
+
+
+class Opts(ctypes.Structure):
+    """kerr_opts (see include/kerr.h for the meaning of every field)."""
+    _fields_ = [("prec", ctypes.c_int32), ("renorm_every", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("h0", ctypes.c_double),
+                ("max_steps", ctypes.c_int64), ("r_escape", ctypes.c_double),
+                ("t_end", ctypes.c_double), ("fp64_zone", ctypes.c_double),
+                ("clip_maxit", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("budget_ns", ctypes.c_uint64)]
+
+
+class Camera(ctypes.Structure):
+    """kerr_camera."""
+    _fields_ = [("a", ctypes.c_double), ("incl", ctypes.c_double), ("r_obs", ctypes.c_double),
+                ("half_width", ctypes.c_double), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    """kerr_stats."""
+    _fields_ = [("geodesics", ctypes.c_int64), ("attempts", ctypes.c_int64),
+                ("accepted", ctypes.c_int64), ("rhs_fp32", ctypes.c_int64),
+                ("rhs_fp64", ctypes.c_int64), ("attempts_fp64", ctypes.c_int64),
+                ("status_count", ctypes.c_int64 * 8), ("kernel_ms", ctypes.c_float),
+                ("variant", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "status_count"}
+        d["status_count"] = list(self.status_count)
+        return d
+
+
+_lib = None
+
+
+def lib():
+    """Load libkerr.so; raises KerrError when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise KerrError(f"libkerr.so not found at {LIB_PATH}; build it with "
+                            "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        c = ctypes
+        vp, i64, i32 = c.c_void_p, c.c_int64, c.c_int32
+        L.kerr_opts_default.argtypes = [c.POINTER(Opts)]
+        L.kerr_opts_default.restype = None
+        L.kerr_init.argtypes = [c.c_double, c.POINTER(vp)]
+        L.kerr_destroy.argtypes = [vp]
+        trace_args = [vp, vp, vp, i64, c.POINTER(Opts), vp, vp, vp, vp, vp, vp]
+        L.kerr_trace_rays.argtypes = trace_args
+        L.kerr_trace_particles.argtypes = [vp, vp, vp, vp, i64, c.POINTER(Opts), vp, vp, vp, vp,
+                                           vp, vp]
+        L.kerr_trace_camera.argtypes = [vp, c.POINTER(Camera), i32, c.POINTER(Opts), vp, vp, vp,
+                                        vp, vp, vp]
+        L.kerr_get_stats.argtypes = [vp, c.POINTER(Stats)]
+        L.kerr_num_variants.argtypes = []
+        L.kerr_variant_info.argtypes = [c.c_int, c.POINTER(i32), c.POINTER(i32)]
+        L.kerr_autotune.argtypes = [vp, c.POINTER(Camera), c.POINTER(Opts), i64, c.POINTER(i32), vp]
+        L.kerr_last_error.restype = c.c_char_p
+        for name in ("kerr_init", "kerr_destroy", "kerr_trace_rays", "kerr_trace_particles",
+                     "kerr_trace_camera", "kerr_get_stats", "kerr_num_variants",
+                     "kerr_variant_info", "kerr_autotune"):
+            getattr(L, name).restype = c.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise KerrError(f"{what} failed ({rc}): {lib().kerr_last_error().decode()}")
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().kerr_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def camera(a: float, incl: float, r_obs: float, half_width: float, nx: int, ny: int) -> Camera:
+    return Camera(a, incl, r_obs, half_width, nx, ny)
+
+
+# ---------------------------------------------------------------------------
+# pointer marshalling
+# ---------------------------------------------------------------------------
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):            # torch tensor
+        if not x.is_contiguous():
+            raise KerrError("tensors must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise KerrError("arrays must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream_ptr(stream, *bufs):
+    if stream is not None:
+        return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+    for b in bufs:
+        if hasattr(b, "is_cuda") and b.is_cuda:
+            import torch
+            return int(torch.cuda.current_stream(b.device).cuda_stream)
+    return None
+
+
+@dataclass
+class TraceOut:
+    x: object        # (4, n) float64: end events
+    k: object        # (4, n) float64: end momenta
+    status: object   # (n,) int32
+    steps: object    # (n,) int32 attempted steps
+    diag: object     # (4, n) float32 (E, L_z, Q, u^2) or None
+
+    @property
+    def n(self) -> int:
+        return int(self.status.shape[0])
+
+
+def alloc_out(n: int, device=None, diag: bool = True, pinned: bool = False) -> TraceOut:
+    """Output buffers: torch tensors on `device` (a CUDA device, or "cpu" with
+    optional pinned memory), or numpy arrays when device is None."""
+    if device is None:
+        return TraceOut(np.empty((4, n)), np.empty((4, n)), np.empty(n, np.int32),
+                        np.empty(n, np.int32), np.empty((4, n), np.float32) if diag else None)
+    import torch
+    kw = dict(device=device)
+    if pinned:
+        kw = dict(device="cpu", pin_memory=True)
+    return TraceOut(torch.empty((4, n), dtype=torch.float64, **kw),
+                    torch.empty((4, n), dtype=torch.float64, **kw),
+                    torch.empty(n, dtype=torch.int32, **kw),
+                    torch.empty(n, dtype=torch.int32, **kw),
+                    torch.empty((4, n), dtype=torch.float32, **kw) if diag else None)
+
+
+# ---------------------------------------------------------------------------
+# the C entry points
+# ---------------------------------------------------------------------------
+class Context:
+    """Owns a kerr_ctx (kerr_init / kerr_destroy)."""
+
+    def __init__(self, a: float):
+        h = ctypes.c_void_p()
+        _check(lib().kerr_init(float(a), ctypes.byref(h)), "kerr_init")
+        self.handle = h
+        self.a = float(a)
+
+    def close(self):
+        if self.handle:
+            lib().kerr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kerr_init(a: float) -> Context:
+    return Context(a)
+
+
+def kerr_destroy(ctx: Context):
+    ctx.close()
+
+
+def kerr_trace_rays(ctx: Context, x0, k0, opts: Opts | None = None, out: TraceOut | None = None,
+                    stream=None) -> TraceOut:
+    n = int(x0.shape[-1])
+    if tuple(x0.shape) != (4, n) or tuple(k0.shape) != (4, n):
+        raise KerrError("x0 and k0 must have shape (4, n)")
+    opts = opts or default_opts()
+    if out is None:
+        out = alloc_out(n, x0.device if hasattr(x0, "device") else None)
+    _check(lib().kerr_trace_rays(ctx.handle, _ptr(x0), _ptr(k0), n, ctypes.byref(opts),
+                                 _ptr(out.x), _ptr(out.k), _ptr(out.status), _ptr(out.steps),
+                                 _ptr(out.diag), _stream_ptr(stream, x0, out.x)),
+           "kerr_trace_rays")
+    return out
+
+
+def kerr_trace_particles(ctx: Context, x0, v0, t_end=None, opts: Opts | None = None,
+                         out: TraceOut | None = None, stream=None) -> TraceOut:
+    n = int(x0.shape[-1])
+    if tuple(x0.shape) != (4, n) or tuple(v0.shape) != (3, n):
+        raise KerrError("x0 must have shape (4, n) and v0 shape (3, n)")
+    if t_end is not None and tuple(t_end.shape) != (n,):
+        raise KerrError("t_end must have shape (n,)")
+    opts = opts or default_opts()
+    if out is None:
+        out = alloc_out(n, x0.device if hasattr(x0, "device") else None)
+    _check(lib().kerr_trace_particles(ctx.handle, _ptr(x0), _ptr(v0), _ptr(t_end), n,
+                                      ctypes.byref(opts),
+                                      _ptr(out.x), _ptr(out.k), _ptr(out.status),
+                                      _ptr(out.steps), _ptr(out.diag),
+                                      _stream_ptr(stream, x0, out.x)),
+           "kerr_trace_particles")
+    return out
+
+
+def camera_rays(cams) -> int:
+    return sum(c.nx * c.ny for c in cams)
+
+
+def kerr_trace_camera(ctx: Context, cams, opts: Opts | None = None, out: TraceOut | None = None,
+                      stream=None, device=None) -> TraceOut:
+    if isinstance(cams, Camera):
+        cams = [cams]
+    arr = (Camera * len(cams))(*cams)
+    n = camera_rays(cams)
+    opts = opts or default_opts()
+    if out is None:
+        out = alloc_out(n, device)
+    _check(lib().kerr_trace_camera(ctx.handle, arr, len(cams), ctypes.byref(opts), _ptr(out.x),
+                                   _ptr(out.k), _ptr(out.status), _ptr(out.steps),
+                                   _ptr(out.diag), _stream_ptr(stream, out.x)),
+           "kerr_trace_camera")
+    return out
+
+
+def kerr_get_stats(ctx: Context) -> Stats:
+    s = Stats()
+    _check(lib().kerr_get_stats(ctx.handle, ctypes.byref(s)), "kerr_get_stats")
+    return s
+
+
+def kerr_num_variants() -> int:
+    return lib().kerr_num_variants()
+
+
+def kerr_variant_info(v: int) -> tuple[int, int]:
+    b, m = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().kerr_variant_info(v, ctypes.byref(b), ctypes.byref(m)), "kerr_variant_info")
+    return b.value, m.value
+
+
+def kerr_autotune(ctx: Context, cam: Camera, opts: Opts | None = None, sample: int = 65536,
+                  stream=None) -> int:
+    best = ctypes.c_int32()
+    opts = opts or default_opts()
+    _check(lib().kerr_autotune(ctx.handle, ctypes.byref(cam), ctypes.byref(opts), sample,
+                               ctypes.byref(best), _stream_ptr(stream)), "kerr_autotune")
+    return best.value

@@ -1,0 +1,269 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Gates: 1e-9 relative end-point error for the FP64 path, 1e-5 for the FP32+Kahan
+path, on every geodesic the oracle does not flag as ill-conditioned (rays
+grazing the photon ring amplify any perturbation exponentially; see
+parity.oracle_flags).  Status must agree on every well-conditioned geodesic.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle import oracle as O  # noqa: E402
+from paper_1706_07062_gb300 import kerr as K  # noqa: E402
+from paper_1706_07062_gb300 import workloads as W  # noqa: E402
+from parity import compare, rel_errors, to_np  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    K.lib()
+    c = K.kerr_init(0.9)
+    yield c
+    c.close()
+
+
+def cam(spec: W.CameraSpec) -> K.Camera:
+    return K.camera(*spec.as_tuple())
+
+
+def oracle_camera_ic(spec: W.CameraSpec, idx):
+    return O.camera_ic(spec.a, spec.incl, spec.r_obs, spec.half_width, spec.nx, spec.ny, idx)
+
+
+# ---------------------------------------------------------------------------
+# 64 x 64 image, a = 0.9, i = 60 deg, tol 1e-10: every ray against the oracle
+# ---------------------------------------------------------------------------
+def test_camera64_fp64_every_ray(ctx):
+    spec = W.CAMERA_64
+    opts = K.default_opts(prec=K.FP64, tol=W.TOL_64)
+    out = K.kerr_trace_camera(ctx, cam(spec), opts, device=DEV)
+    torch.cuda.synchronize()
+    idx = np.arange(spec.n)
+    y0 = oracle_camera_ic(spec, idx)
+    s = compare("camera64/fp64", spec.a, y0, O.Opts(tol=W.TOL_64), out, idx, 1e-9, fp32=False)
+    print(s)
+    assert s["ill_conditioned"] < 0.05 * spec.n
+
+
+def test_camera64_fp32_every_ray(ctx):
+    """The FP32 path at tol 1e-6 against the oracle at the same tolerance."""
+    spec = W.CAMERA_64
+    opts = K.default_opts(prec=K.FP32_KAHAN, tol=1e-6)
+    out = K.kerr_trace_camera(ctx, cam(spec), opts, device=DEV)
+    torch.cuda.synchronize()
+    idx = np.arange(spec.n)
+    y0 = oracle_camera_ic(spec, idx)
+    s = compare("camera64/fp32", spec.a, y0, O.Opts(tol=1e-6), out, idx, 1e-5, fp32=True)
+    print(s)
+
+
+# ---------------------------------------------------------------------------
+# 1024 x 1024 image, a = 0.99, i = 17 deg, tol 1e-6: full launch, seeded
+# 4096-ray subset against the oracle (the benchmark's launch configuration)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def c1024_oracle():
+    spec = W.CAMERA_1024
+    idx = W.camera_subset(spec)
+    y0 = oracle_camera_ic(spec, idx)
+    ref = O.trace(spec.a, y0, O.Opts(tol=W.TOL_1024))
+    return idx, y0, ref
+
+
+@pytest.mark.parametrize("prec", [K.FP32_KAHAN, K.FP64])
+def test_camera1024_full_launch_subset(ctx, c1024_oracle, prec):
+    spec = W.CAMERA_1024
+    idx, y0, ref = c1024_oracle
+    opts = K.default_opts(prec=prec, tol=W.TOL_1024)
+    out = K.kerr_trace_camera(ctx, cam(spec), opts, device=DEV)
+    torch.cuda.synchronize()
+    st = to_np(out.status)
+    assert set(np.unique(st)) <= {K.ESCAPED, K.CAPTURED}
+    gate = 1e-5 if prec == K.FP32_KAHAN else 1e-9
+    s = compare(f"camera1024/{prec}", spec.a, y0, O.Opts(tol=W.TOL_1024), out, idx, gate,
+                fp32=(prec == K.FP32_KAHAN), ref=ref)
+    print(s)
+    # null constraint reported per ray (FP64 diagnostics): |u^2| small
+    u2 = to_np(out.diag)[3]
+    kt = np.abs(to_np(out.k)[0])
+    assert np.all(np.abs(u2) <= 1e-3 * np.maximum(1.0, kt) ** 2)
+
+
+# ---------------------------------------------------------------------------
+# entry points agree with each other
+# ---------------------------------------------------------------------------
+def test_trace_rays_matches_camera(ctx):
+    spec = W.CameraSpec(0.9, 1.0, 1000.0, 12.0, 16, 16)
+    opts = K.default_opts(prec=K.FP64, tol=1e-9)
+    c2 = K.kerr_init(spec.a)
+    cam_out = K.kerr_trace_camera(c2, cam(spec), opts, device=DEV)
+    y0 = oracle_camera_ic(spec, np.arange(spec.n))
+    x0 = torch.tensor(np.ascontiguousarray(y0[:, :4].T), device=DEV)
+    k0 = torch.tensor(np.ascontiguousarray(y0[:, 4:].T), device=DEV)
+    opts_r = K.default_opts(prec=K.FP64, tol=1e-9, r_escape=0.0)
+    ray_out = K.kerr_trace_rays(c2, x0, k0, opts_r)
+    torch.cuda.synchronize()
+    ex, ek, _ = rel_errors(to_np(ray_out.x), to_np(ray_out.k),
+                           np.concatenate([to_np(cam_out.x).T, to_np(cam_out.k).T], 1))
+    assert np.array_equal(to_np(ray_out.status), to_np(cam_out.status))
+    assert max(ex.max(), ek.max()) < 1e-9
+    c2.close()
+
+
+def test_host_and_device_buffers_agree(ctx):
+    spec = W.CameraSpec(0.5, 0.7, 1000.0, 10.0, 33, 31)
+    opts = K.default_opts(prec=K.FP32_KAHAN, tol=1e-6)
+    dev = K.kerr_trace_camera(ctx, cam(spec), opts, device=DEV)
+    host = K.kerr_trace_camera(ctx, cam(spec), opts)               # numpy outputs
+    pinned = K.alloc_out(spec.n, device="cpu", pinned=True)
+    K.kerr_trace_camera(ctx, cam(spec), opts, out=pinned)
+    torch.cuda.synchronize()
+    for o in (host, pinned):
+        assert np.array_equal(to_np(o.x), to_np(dev.x))
+        assert np.array_equal(to_np(o.k), to_np(dev.k))
+        assert np.array_equal(to_np(o.status), to_np(dev.status))
+        assert np.array_equal(to_np(o.steps), to_np(dev.steps))
+
+
+def test_batched_cameras_equal_single_cameras(ctx):
+    specs = [W.CameraSpec(0.3, 0.4, 1000.0, 25.0, 17, 9), W.CameraSpec(0.95, 1.2, 800.0, 15.0, 32, 32),
+             W.CameraSpec(0.0, 0.1, 1000.0, 8.0, 5, 7)]
+    opts = K.default_opts(prec=K.FP32_KAHAN, tol=1e-6)
+    batch = K.kerr_trace_camera(ctx, [cam(s) for s in specs], opts, device=DEV)
+    off = 0
+    for s in specs:
+        one = K.kerr_trace_camera(ctx, cam(s), opts, device=DEV)
+        torch.cuda.synchronize()
+        sl = slice(off, off + s.n)
+        assert torch.equal(batch.x[:, sl], one.x)
+        assert torch.equal(batch.k[:, sl], one.k)
+        assert torch.equal(batch.status[sl], one.status)
+        off += s.n
+
+
+# ---------------------------------------------------------------------------
+# particles: time-like geodesics, per-particle end times
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [K.FP64, K.FP32_KAHAN])
+def test_particles_subset(prec):
+    ps = W.particles(n=1 << 14, periods=10)
+    sub = W.particle_subset(ps, k=512)
+    a = ps.a
+    c = K.kerr_init(a)
+    opts = K.default_opts(prec=prec, tol=1e-8 if prec == K.FP64 else 1e-6, r_escape=-1.0,
+                          max_steps=10_000_000)
+    x0 = torch.tensor(ps.x0, device=DEV)
+    v0 = torch.tensor(ps.v0, device=DEV)
+    te = torch.tensor(ps.t_end, device=DEV)
+    out = K.kerr_trace_particles(c, x0, v0, te, opts)
+    torch.cuda.synchronize()
+    st = to_np(out.status)
+    assert set(np.unique(st)) <= {K.CAPTURED, K.ENDTIME, K.INVALID_IC}
+    y0, ok = O.particle_ic(a, ps.x0[:, sub].T, ps.v0[:, sub].T)
+    assert np.array_equal(st[sub] == K.INVALID_IC, ~ok)
+    keep = np.nonzero(ok)[0]
+    oo = O.Opts(tol=opts.tol, r_escape=-1.0, max_steps=10_000_000)
+    ref = O.trace(a, y0[keep], oo, t_end=ps.t_end[sub][keep])
+    gate = 1e-9 if prec == K.FP64 else 1e-5
+    # time-like end points on the t = t_end surface: compare t separately
+    s = compare(f"particles/{prec}", a, y0[keep], oo, out, sub[keep], gate,
+                fp32=(prec == K.FP32_KAHAN), ref=ref, max_bad_frac=0.0,
+                t_end=ps.t_end[sub][keep])
+    print(s)
+    c.close()
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def test_sizes_and_degenerate_states(ctx):
+    a = 0.9
+    rh = 1 + math.sqrt(1 - a * a)
+    opts = K.default_opts(prec=K.FP64, tol=1e-8)
+    for n in (1, 31, 32, 33, 1000):
+        spec = W.CameraSpec(a, 0.5, 1000.0, 10.0, n, 1)
+        out = K.kerr_trace_camera(ctx, cam(spec), opts, device=DEV)
+        torch.cuda.synchronize()
+        y0 = oracle_camera_ic(spec, np.arange(n))
+        ref = O.trace(a, y0, O.Opts(tol=1e-8))
+        assert np.array_equal(to_np(out.status), ref.status)
+    # n = 0 is a no-op
+    empty = K.alloc_out(0, DEV)
+    K.kerr_trace_rays(ctx, torch.zeros((4, 0), dtype=torch.float64, device=DEV),
+                      torch.zeros((4, 0), dtype=torch.float64, device=DEV), opts, out=empty)
+    # NaN, inside the capture radius, max_steps
+    y = np.array([[0, np.nan, 0, 0, -1, 0.1, 0, 0],
+                  [0, 1.005 * rh, 0, 0, -1, 0.1, 0, 0],
+                  oracle_camera_ic(W.CAMERA_64, [100])[0]])
+    x0 = torch.tensor(np.ascontiguousarray(y[:, :4].T), device=DEV)
+    k0 = torch.tensor(np.ascontiguousarray(y[:, 4:].T), device=DEV)
+    for prec in (K.FP64, K.FP32_KAHAN):
+        o = K.default_opts(prec=prec, tol=1e-8, max_steps=3)
+        out = K.kerr_trace_rays(ctx, x0, k0, o)
+        torch.cuda.synchronize()
+        assert to_np(out.status).tolist() == [K.NONFINITE, K.CAPTURED, K.MAXSTEPS]
+        assert to_np(out.steps).tolist() == [0, 0, 3]
+        assert np.array_equal(to_np(out.x)[:, 1], y[1, :4])
+
+
+def test_budget_gives_timeout_not_hang(ctx):
+    spec = W.CameraSpec(0.9, 0.5, 1000.0, 20.0, 256, 256)
+    opts = K.default_opts(prec=K.FP64, tol=1e-12, budget_ns=200_000)   # 0.2 ms
+    out = K.kerr_trace_camera(ctx, cam(spec), opts, device=DEV)
+    torch.cuda.synchronize()
+    st = to_np(out.status)
+    assert (st == K.TIMEOUT).sum() > 0
+    assert set(np.unique(st)) <= {K.ESCAPED, K.CAPTURED, K.TIMEOUT}
+    s = K.kerr_get_stats(ctx)
+    assert s.geodesics == spec.n and sum(s.status_count) == spec.n
+
+
+def test_renormalisation_on_gpu(ctx):
+    spec = W.CameraSpec(0.99, 0.3, 1000.0, 6.0, 16, 16)
+    for prec in (K.FP64, K.FP32_KAHAN):
+        plain = K.kerr_trace_camera(ctx, cam(spec), K.default_opts(prec=prec), device=DEV)
+        ren = K.kerr_trace_camera(ctx, cam(spec), K.default_opts(prec=prec, renorm_every=1),
+                                  device=DEV)
+        torch.cuda.synchronize()
+        esc = to_np(ren.status) == K.ESCAPED
+        assert np.abs(to_np(ren.diag)[3][esc]).max() <= np.abs(to_np(plain.diag)[3][esc]).max()
+
+
+def test_invalid_arguments_are_rejected(ctx):
+    with pytest.raises(K.KerrError):
+        K.kerr_init(1.5)
+    with pytest.raises(K.KerrError):
+        K.kerr_trace_camera(ctx, K.camera(0.5, 0.3, 1000.0, 10.0, 0, 4), device=DEV)
+    with pytest.raises(K.KerrError):
+        K.kerr_trace_camera(ctx, K.camera(1.2, 0.3, 1000.0, 10.0, 4, 4), device=DEV)
+    with pytest.raises(K.KerrError):
+        K.kerr_trace_camera(ctx, K.camera(0.5, 0.3, 1000.0, 10.0, 4, 4),
+                            K.default_opts(tol=-1.0), device=DEV)
+    with pytest.raises(K.KerrError):
+        K.kerr_trace_camera(ctx, K.camera(0.5, 0.3, 1000.0, 10.0, 4, 4),
+                            K.default_opts(variant=99), device=DEV)
+
+
+def test_every_variant_and_autotune(ctx):
+    spec = W.CameraSpec(0.9, 1.0, 1000.0, 20.0, 48, 48)
+    outs = []
+    for v in range(K.kerr_num_variants()):
+        o = K.kerr_trace_camera(ctx, cam(spec), K.default_opts(variant=v), device=DEV)
+        torch.cuda.synchronize()
+        outs.append(o)
+    for o in outs[1:]:
+        assert np.array_equal(to_np(o.status), to_np(outs[0].status))
+        ex, ek, _ = rel_errors(to_np(o.x), to_np(o.k),
+                               np.concatenate([to_np(outs[0].x).T, to_np(outs[0].k).T], 1))
+        assert max(ex.max(), ek.max()) < 1e-6
+    best = K.kerr_autotune(ctx, cam(spec), K.default_opts(), sample=2048)
+    assert 0 <= best < K.kerr_num_variants()
