@@ -291,12 +291,15 @@ def cpu_baseline(spec, W, out_gpu, out64):
             x = o.x.cpu().numpy()[:, idx].T
             k = o.k.cpu().numpy()[:, idx].T
             st = o.status.cpu().numpy()[idx]
-            ex = np.linalg.norm(x[:, 1:4] - ref.y[:, 1:4], 1) / np.linalg.norm(ref.y[:, 1:4], 1)
-            ek = np.linalg.norm(k - ref.y[:, 4:8], 1) / np.linalg.norm(ref.y[:, 4:8], 1)
+            ex = (np.linalg.norm(x[:, 1:4] - ref.y[:, 1:4], axis=1)
+                  / np.linalg.norm(ref.y[:, 1:4], axis=1))
+            ek = np.linalg.norm(k - ref.y[:, 4:8], axis=1) / np.linalg.norm(ref.y[:, 4:8], axis=1)
             e = np.maximum(ex, ek)
             g = ~flags
             return {"max_rel_err_well_conditioned": float(e[g].max()),
                     "median_rel_err": float(np.median(e)),
+                    "p99_rel_err": float(np.quantile(e, 0.99)),
+                    "frac_le_1e-5_all": float(np.mean(e <= 1e-5)),
                     "frac_le_1e-5_well_conditioned": float(np.mean(e[g] <= 1e-5)),
                     "status_mismatch_well_conditioned": int(np.sum((st != ref.status) & g))}
         acc = {"sample": len(idx), "reference": "FP64 CPU oracle, tol 1e-6",

@@ -133,6 +133,8 @@ typedef struct {
     int64_t rhs_fp32;         /* right-hand sides evaluated in FP32              */
     int64_t rhs_fp64;         /* right-hand sides evaluated in FP64              */
     int64_t attempts_fp64;    /* attempted steps taken in FP64                   */
+    int64_t deferred;         /* FP32 path: geodesics handed to the FP64-zone    */
+                              /* phase (second launch of the same call)          */
     int64_t status_count[8];  /* geodesics per status code                       */
     float kernel_ms;          /* device time of the integration kernel           */
     int32_t variant;          /* launch configuration used                       */

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/kerr.h"
+#define KERR_TYPES_ONLY
 #include "kerr_trace.cuh"
 #include "kerr_variants.h"
 
@@ -67,7 +68,12 @@ struct kerr_ctx {
     int sms = 0;
     cudaStream_t stream = nullptr;               // the context's own stream
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_k0 = nullptr, ev_k1 = nullptr;
-    unsigned long long *d_scratch = nullptr;     // [0] queue head, [1..] statistics
+    unsigned long long *d_scratch = nullptr;     // [0] queue head, [1..16] statistics,
+                                                 // [17] zone count, [18] zone-phase head
+    ZoneEntry *d_zone = nullptr;                 // deferred FP64-zone geodesics
+    int64_t zone_cap = 0;
+    float *d_work = nullptr;                     // FP32 path: state and constant planes
+    int64_t work_cap = 0;                        // geodesics d_work can hold
     CamDev *d_cams = nullptr;
     int cam_cap = 0;
     char *d_stage = nullptr;                     // staging arena for host buffers
@@ -80,7 +86,7 @@ struct kerr_ctx {
     bool have_stats = false;
 };
 
-static const int kScratchWords = 1 + SC_COUNT;
+static const int kScratchWords = 1 + SC_COUNT + 2;
 
 extern "C" void kerr_opts_default(kerr_opts *o)
 {
@@ -161,6 +167,8 @@ extern "C" int kerr_destroy(kerr_ctx *c)
     if (c->gexec)
         cudaGraphExecDestroy(c->gexec);
     cudaFree(c->d_scratch);
+    cudaFree(c->d_zone);
+    cudaFree(c->d_work);
     cudaFree(c->d_cams);
     cudaFree(c->d_stage);
     if (c->ev_in)
@@ -243,10 +251,19 @@ static int launch_integration(kerr_ctx *c, const TraceParams &P, int prec, int v
         KERR_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e1 = cudaMemsetAsync(c->d_scratch, 0, kScratchWords * sizeof(unsigned long long),
                                          c->stream);
-        cudaError_t e2 = e1 == cudaSuccess
-                             ? (f32 ? launch_trace_f32(P, variant, c->sms, c->stream)
-                                    : launch_trace_f64(P, variant, c->sms, c->stream))
-                             : e1;
+        cudaError_t e2 = e1;
+        if (f32) {
+            if (e2 == cudaSuccess)
+                e2 = launch_setup_f32(P, c->sms, c->stream);
+            if (e2 == cudaSuccess)
+                e2 = launch_trace_f32(P, variant, c->sms, c->stream);
+            if (e2 == cudaSuccess && P.zbuf)
+                e2 = launch_zone_phase(P, c->sms, c->stream);
+            if (e2 == cudaSuccess)
+                e2 = launch_finish_f32(P, c->sms, c->stream);
+        } else if (e2 == cudaSuccess) {
+            e2 = launch_trace_f64(P, variant, c->sms, c->stream);
+        }
         cudaError_t e3 = cudaStreamEndCapture(c->stream, &g);
         if (e2 != cudaSuccess || e3 != cudaSuccess) {
             if (g)
@@ -323,6 +340,46 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
     P.budget_ns = o->budget_ns;
     P.head = c->d_scratch;
     P.stats = c->d_scratch + 1;
+    P.zcount = c->d_scratch + 1 + SC_COUNT;
+    P.zhead = c->d_scratch + 2 + SC_COUNT;
+    if (o->prec == KERR_FP32_KAHAN) {
+        // state [16][n] and constant [KC_COUNT][n] float planes
+        if (n > c->work_cap) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->d_work);
+            c->d_work = nullptr;
+            c->work_cap = 0;
+            cudaError_t e = cudaMalloc(&c->d_work, (size_t)n * (16 + KC_COUNT) * sizeof(float));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(KERR_ENOMEM, "work buffer allocation (%lld geodesics) failed",
+                            (long long)n);
+            }
+            c->work_cap = n;
+        }
+        P.s_state = c->d_work;
+        P.s_const = c->d_work + (size_t)16 * n;
+    }
+    if (o->prec == KERR_FP32_KAHAN && o->fp64_zone > 0.0) {
+        // Deferred-zone buffer: a quarter of the geodesics (at least 64 Ki);
+        // geodesics beyond it take their zone steps in place.
+        const int64_t want = std::min<int64_t>(n, std::max<int64_t>(1 << 16, n / 4));
+        if (want > c->zone_cap) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->d_zone);
+            c->d_zone = nullptr;
+            c->zone_cap = 0;
+            cudaError_t e = cudaMalloc(&c->d_zone, (size_t)want * sizeof(ZoneEntry));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(KERR_ENOMEM, "zone buffer allocation (%lld entries) failed",
+                            (long long)want);
+            }
+            c->zone_cap = want;
+        }
+        P.zbuf = c->d_zone;
+        P.zcap = c->zone_cap;
+    }
 
     // ---- which buffers live on the host
     const size_t nn = (size_t)n;
@@ -488,6 +545,7 @@ extern "C" int kerr_get_stats(kerr_ctx *c, kerr_stats *out)
     out->rhs_fp32 = (int64_t)s[SC_RHS32];
     out->rhs_fp64 = (int64_t)s[SC_RHS64];
     out->attempts_fp64 = (int64_t)s[SC_ATT64];
+    out->deferred = (int64_t)s[SC_DEFERRED];
     for (int j = 0; j < 8; ++j)
         out->status_count[j] = (int64_t)s[SC_STATUS + j];
     float ms = 0.f;

@@ -35,10 +35,25 @@ __device__ __forceinline__ float k_sqrt(float x)
 }
 __device__ __forceinline__ double k_rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ double k_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ double k_rsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ double k_rsqrt(double x) { return rsqrt(x); }
 
 __device__ __forceinline__ float k_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double k_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Two reciprocals 1/p and 1/q.  FP32: two hardware approximations.  FP64:
+// one correctly rounded division of 1 by p q shared by both (p q stays far
+// from overflow for any radius below ~1e50).
+__device__ __forceinline__ void recip2(float p, float q, float &ip, float &iq)
+{
+    ip = k_rcp(p);
+    iq = k_rcp(q);
+}
+__device__ __forceinline__ void recip2(double p, double q, double &ip, double &iq)
+{
+    const double t = 1.0 / (p * q);
+    ip = q * t;
+    iq = p * t;
+}
 
 // Kerr-Schild radius from eq. CKSr: the positive root r^2 of
 // r^4 - (R^2 - a^2) r^2 - a^2 z^2 = 0.
@@ -69,8 +84,10 @@ __device__ __forceinline__ T ks_r(T a2, T x, T y, T z)
 //   r from eq. CKSr; d_i r = (f/2) (x, y, z (1 + a^2/r^2));
 //   f = 2 r^3 / (r^4 + a^2 z^2);  d_i f = f (3/r - 2f) d_i r - 2 f a^2 z/(r^4 + a^2 z^2) delta_iz;
 //   l_i = ((r x + a y), (r y - a x)) / (r^2 + a^2), z / r;
-//   d_al l_i = (d_al r) e_i + M_{al i},  e = ((x - 2 r l_x), (y - 2 r l_y)) / (r^2 + a^2), -l_z / r,
-//   M = [[r, -a, 0], [a, r, 0], [0, 0, 1/r... ]] / (r^2 + a^2) in the x-y block, 1/r at (z, z).
+//   d_al l_i = (d_al r) e_i + M_{al i}, with
+//     e = ((x - 2 r l_x) / (r^2 + a^2), (y - 2 r l_y) / (r^2 + a^2), -l_z / r),
+//     M_{xx} = M_{yy} = r / (r^2 + a^2), M_{yx} = -M_{xy} = a / (r^2 + a^2),
+//     M_{zz} = 1 / r, all other entries 0.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void accel(const T a, const T a2, const T x, const T y, const T z,
@@ -83,8 +100,8 @@ __device__ __forceinline__ void accel(const T a, const T a2, const T x, const T 
     const T r2 = T(0.5) * (d + k_sqrt(k_fma(d, d, T(4) * az2)));
     const T ir = k_rsqrt(r2);
     const T r = r2 * ir;
-    const T iq = k_rcp(k_fma(r2, r2, az2));     // 1 / (r^4 + a^2 z^2)
-    const T is = k_rcp(r2 + a2);                // 1 / (r^2 + a^2)
+    T iq, is;                                   // 1/(r^4 + a^2 z^2), 1/(r^2 + a^2)
+    recip2(k_fma(r2, r2, az2), r2 + a2, iq, is);
     const T hf = r * r2 * iq;                   // f / 2
     const T f = hf + hf;
     const T lx = k_fma(r, x, a * y) * is;

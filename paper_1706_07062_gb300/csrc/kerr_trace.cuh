@@ -47,8 +47,35 @@ enum : int {
     SC_RHS32 = 3,
     SC_RHS64 = 4,
     SC_ATT64 = 5,
+    SC_DEFERRED = 6, // geodesics handed to the zone phase
     SC_STATUS = 8,   // 8 slots: geodesics per status code
     SC_COUNT = 16
+};
+
+// State of one geodesic handed from the FP32 phase to the FP64-zone phase
+// (96 bytes): the compensated FP32 state and the stepping bookkeeping; the
+// per-geodesic constants stay in the constants planes.
+struct ZoneEntry {
+    float y[8], c[8];
+    int64_t id;
+    float h, rnow;
+    uint32_t nsteps;
+    int32_t since_renorm;
+    int32_t pad[2];
+};
+static_assert(sizeof(ZoneEntry) == 96, "zone entry layout");
+
+// Per-geodesic constants of the FP32 path, one float plane each.
+enum : int {
+    KC_A = 0,       // spin
+    KC_RCAP = 1,    // capture radius 1.01 r_h (rounded from FP64)
+    KC_RESC = 2,    // escape radius (inf: none)
+    KC_ZONE = 3,    // FP64-zone radius
+    KC_TEND = 4,    // end time, high part (float pair)
+    KC_TENDLO = 5,  // end time, low part
+    KC_U2 = 6,      // initial g k k (renormalisation target)
+    KC_FLAGS = 7,   // bit 0: end time in use; bit 1: initial sign of t - t_end
+    KC_COUNT = 8
 };
 
 struct TraceParams {
@@ -70,7 +97,15 @@ struct TraceParams {
     uint64_t budget_ns;
     unsigned long long *head;   // work-queue counter, zero at launch
     unsigned long long *stats;  // SC_COUNT counters, zero at launch
+    float *s_state;             // FP32 path: [16][n] planes y[0..7], c[0..7]
+    float *s_const;             // FP32 path: [KC_COUNT][n] planes
+    ZoneEntry *zbuf;            // deferred zone geodesics (FP32 path), or null
+    int64_t zcap;               // capacity of zbuf
+    unsigned long long *zcount; // entries appended, zero at launch
+    unsigned long long *zhead;  // zone-phase work-queue counter, zero at launch
 };
+
+#ifndef KERR_TYPES_ONLY
 
 // Per-geodesic constants fixed at set-up.
 struct RayConst {
@@ -82,6 +117,37 @@ struct RayConst {
     double u2_0;     // initial g k k (renormalisation target)
     int use_t;
     int tpos;        // initial sign of t - t_end
+    // FP32 copies, so that the FP32 loop issues no FP64 conversions;
+    // t_end is an unevaluated float pair (tendf + tendlo) to keep the end-time
+    // event exact to ~1e-14 relative
+    float af, rcapf, rescf, zonef, tendf, tendlo;
+};
+
+__device__ __forceinline__ void finish_const(RayConst &rc)
+{
+    rc.af = (float)rc.a;
+    rc.rcapf = (float)rc.rcap;
+    rc.rescf = (float)rc.resc;
+    rc.zonef = (float)rc.zone_r;
+    rc.tendf = (float)rc.tend;
+    rc.tendlo = isfinite(rc.tend) ? (float)(rc.tend - (double)rc.tendf) : 0.0f;
+}
+
+// Per-precision view of the ray constants.
+template <typename T> struct RC;
+template <> struct RC<float> {
+    static __device__ __forceinline__ float a(const RayConst &r) { return r.af; }
+    static __device__ __forceinline__ float rcap(const RayConst &r) { return r.rcapf; }
+    static __device__ __forceinline__ float resc(const RayConst &r) { return r.rescf; }
+    static __device__ __forceinline__ float tend(const RayConst &r) { return r.tendf; }
+    static __device__ __forceinline__ float tendlo(const RayConst &r) { return r.tendlo; }
+};
+template <> struct RC<double> {
+    static __device__ __forceinline__ double a(const RayConst &r) { return r.a; }
+    static __device__ __forceinline__ double rcap(const RayConst &r) { return r.rcap; }
+    static __device__ __forceinline__ double resc(const RayConst &r) { return r.resc; }
+    static __device__ __forceinline__ double tend(const RayConst &r) { return r.tend; }
+    static __device__ __forceinline__ double tendlo(const RayConst &) { return 0.0; }
 };
 
 // ---------------------------------------------------------------------------
@@ -168,15 +234,26 @@ __device__ __forceinline__ T attempt(const T a, const T a2, const T y[8], const 
     return err;
 }
 
-template <typename T>
-__device__ __forceinline__ T step_factor(T err)
+// Step-size factor after an attempt: 0.9 err^(-1/5) clamped to [0.2, 5]; 5
+// for err == 0 and 0.2 for a non-finite err.  FP32 evaluates the power with
+// the hardware log2/exp2; FP64 with the correctly rounded pow.
+__device__ __forceinline__ float step_factor(float err)
 {
     if (!isfinite(err))
-        return T(0.2);
-    if (err == T(0))
-        return T(5);
-    const T f = T(0.9) * pow(err, T(-0.2));
-    return fmin(T(5), fmax(T(0.2), f));
+        return 0.2f;
+    if (err == 0.0f)
+        return 5.0f;
+    const float f = 0.9f * exp2f(-0.2f * __log2f(err));
+    return fminf(5.0f, fmaxf(0.2f, f));
+}
+__device__ __forceinline__ double step_factor(double err)
+{
+    if (!isfinite(err))
+        return 0.2;
+    if (err == 0.0)
+        return 5.0;
+    const double f = 0.9 * pow(err, -0.2);
+    return fmin(5.0, fmax(0.2, f));
 }
 
 template <bool KAHAN, typename T>
@@ -192,13 +269,15 @@ __device__ __forceinline__ void add_incr(T &y, T &c, T d)
     }
 }
 
-// Event value on a state (y, c): r - target (kind 0) or t - target (kind 1).
+// Event value on a state (y, c): r - target (kind 0) or t - (target +
+// target_lo) (kind 1; target_lo is the low part of a float-pair end time).
 template <bool KAHAN, typename T>
-__device__ __forceinline__ T event_value(int kind, T a2, const T y[8], const T c[8], T target)
+__device__ __forceinline__ T event_value(int kind, T a2, const T y[8], const T c[8], T target,
+                                         T target_lo)
 {
     if (kind == 0)
         return ks_r(a2, y[1], y[2], y[3]) - target;
-    return KAHAN ? (y[0] - target) + c[0] : y[0] - target;
+    return KAHAN ? ((y[0] - target) + c[0]) - target_lo : y[0] - target;
 }
 
 // Clip an accepted step onto an event surface (Illinois regula falsi on the
@@ -207,7 +286,8 @@ __device__ __forceinline__ T event_value(int kind, T a2, const T y[8], const T c
 // end point.  Bracket values s_lo = s(y_old) and s_hi = s(y_new).
 template <bool KAHAN, typename T>
 __device__ void clip(const T a, const T a2, T y[8], T c[8], const T A0[4], const T h, int kind,
-                     T target, T s_lo, T s_hi, T stol, T eps, int maxit, uint32_t &nrhs)
+                     T target, T target_lo, T s_lo, T s_hi, T stol, T eps, int maxit,
+                     uint32_t &nrhs)
 {
     T lo = T(0), hi = h;
     int side = 0;
@@ -230,7 +310,7 @@ __device__ void clip(const T a, const T a2, T y[8], T c[8], const T A0[4], const
             ce[i] = c[i];
             add_incr<KAHAN>(ye[i], ce[i], d[i]);
         }
-        const T s = event_value<KAHAN>(kind, a2, ye, ce, target);
+        const T s = event_value<KAHAN>(kind, a2, ye, ce, target, target_lo);
         if (fabs(s) <= stol)
             break;
         if ((s > T(0)) == (s_hi > T(0))) {
@@ -270,16 +350,16 @@ template <> struct Prec<double> {
 // step; rn receives r of the new state when a step is accepted.  Returns a
 // status code when the geodesic terminates, ST_NONE otherwise.
 template <bool KAHAN, typename T>
-__device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &P, T y[8], T c[8],
-                                         T &h, T &rn, uint32_t &nrhs, uint32_t &nacc,
-                                         int &since_renorm)
+__device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &P, const T tol,
+                                         T y[8], T c[8], T &h, T &rn, uint32_t &nrhs,
+                                         uint32_t &nacc, int &since_renorm)
 {
-    const T a = (T)rc.a;
+    const T a = RC<T>::a(rc);
     const T a2 = a * a;
     T A0[4];
     accel(a, a2, y[1], y[2], y[3], y[4], y[5], y[6], y[7], A0[0], A0[1], A0[2], A0[3]);
     T d[8];
-    const T err = attempt(a, a2, y, A0, h, (T)P.tol, d);
+    const T err = attempt(a, a2, y, A0, h, tol, d);
     nrhs += 11;
     const T fac = step_factor(err);
     if (!(err <= T(1))) {
@@ -305,20 +385,20 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
         return ST_NONFINITE;
     }
     rn = ks_r(a2, yn[1], yn[2], yn[3]);
-    const T rcap = (T)rc.rcap;
+    const T rcap = RC<T>::rcap(rc);
     const int maxit = P.clip_maxit;
     if (rn < rcap) {
-        const T s_lo = event_value<KAHAN>(0, a2, y, c, rcap);
-        clip<KAHAN>(a, a2, y, c, A0, h, 0, rcap, s_lo, rn - rcap, Prec<T>::stol * rcap,
+        const T s_lo = event_value<KAHAN>(0, a2, y, c, rcap, T(0));
+        clip<KAHAN>(a, a2, y, c, A0, h, 0, rcap, T(0), s_lo, rn - rcap, Prec<T>::stol * rcap,
                     Prec<T>::eps, maxit, nrhs);
         return ST_CAPTURED;
     }
-    const T resc = (T)rc.resc;
+    const T resc = RC<T>::resc(rc);
     if (rn > resc && k_fma(yn[1], yn[5], k_fma(yn[2], yn[6], yn[3] * yn[7])) > T(0)) {
-        const T s_lo = event_value<KAHAN>(0, a2, y, c, resc);
+        const T s_lo = event_value<KAHAN>(0, a2, y, c, resc, T(0));
         if (s_lo <= T(0)) {
-            clip<KAHAN>(a, a2, y, c, A0, h, 0, resc, s_lo, rn - resc, Prec<T>::stol * resc,
-                        Prec<T>::eps, maxit, nrhs);
+            clip<KAHAN>(a, a2, y, c, A0, h, 0, resc, T(0), s_lo, rn - resc,
+                        Prec<T>::stol * resc, Prec<T>::eps, maxit, nrhs);
         } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -329,13 +409,13 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
         return ST_ESCAPED;
     }
     if (rc.use_t) {
-        const T tend = (T)rc.tend;
-        const T s_hi = event_value<KAHAN>(1, a2, yn, cn, tend);
+        const T tend = RC<T>::tend(rc), tlo = RC<T>::tendlo(rc);
+        const T s_hi = event_value<KAHAN>(1, a2, yn, cn, tend, tlo);
         if ((s_hi > T(0)) != (rc.tpos != 0)) {
-            const T s_lo = event_value<KAHAN>(1, a2, y, c, tend);
+            const T s_lo = event_value<KAHAN>(1, a2, y, c, tend, tlo);
             const T sc = fmax(T(1), fabs(tend));
-            clip<KAHAN>(a, a2, y, c, A0, h, 1, tend, s_lo, s_hi, Prec<T>::stol * sc, Prec<T>::eps,
-                        maxit, nrhs);
+            clip<KAHAN>(a, a2, y, c, A0, h, 1, tend, tlo, s_lo, s_hi, Prec<T>::stol * sc,
+                        Prec<T>::eps, maxit, nrhs);
             return ST_ENDTIME;
         }
     }
@@ -450,6 +530,7 @@ __device__ __forceinline__ int init_geodesic(const TraceParams &P, int64_t id, d
         if (r0 < rc.rcap)
             st = ST_CAPTURED;
     }
+    finish_const(rc);
     return st;
 }
 
@@ -487,9 +568,9 @@ __device__ __forceinline__ unsigned long long global_ns()
 // One attempted step of an FP32+Kahan geodesic taken in FP64 (inside the
 // zone r < fp64_zone r_h, where f l l is large): the compensated pair is
 // folded into one FP64 state, stepped, and split back.  Kept out of line so
-// that its FP64 registers do not raise the register count of the FP32 loop;
-// it only runs for the few steps near the horizon.  The lane state travels
-// by value so that the caller's arrays stay in registers.
+// that its FP64 registers do not raise the register count of the FP32 loop.
+// The lane state travels by value so that the caller's arrays stay in
+// registers.
 struct LaneF {
     float y[8], c[8];
     float h, rnow;
@@ -501,8 +582,8 @@ struct ZoneResult {
     int since_renorm;
 };
 
-__device__ __noinline__ ZoneResult zone_step(const RayConst rc, const TraceParams &P, LaneF s,
-                                             int since_renorm)
+static __device__ __noinline__ ZoneResult zone_step(const RayConst rc, const TraceParams &P,
+                                                    LaneF s, int since_renorm)
 {
     double yd[8], cd[8];
 #pragma unroll
@@ -514,7 +595,7 @@ __device__ __noinline__ ZoneResult zone_step(const RayConst rc, const TraceParam
     ZoneResult R;
     R.nrhs = 0;
     R.nacc = 0;
-    R.st = step_once<false, double>(rc, P, yd, cd, hd, rd, R.nrhs, R.nacc, since_renorm);
+    R.st = step_once<false, double>(rc, P, P.tol, yd, cd, hd, rd, R.nrhs, R.nacc, since_renorm);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         R.s.y[i] = (float)yd[i];
@@ -526,65 +607,116 @@ __device__ __noinline__ ZoneResult zone_step(const RayConst rc, const TraceParam
     return R;
 }
 
-// ---------------------------------------------------------------------------
-// The persistent kernel.  F32 selects the FP32+Kahan path (with FP64 steps
-// inside the zone); otherwise every step is FP64.
-// ---------------------------------------------------------------------------
-template <bool F32, int BLOCK, int MINB>
-__global__ void __launch_bounds__(BLOCK, MINB) trace_kernel(const TraceParams P)
+// Spin of geodesic id: its camera's (camera mode) or the context's.
+__device__ __forceinline__ double geodesic_spin(const TraceParams &P, int64_t id)
 {
-    using T = typename std::conditional<F32, float, double>::type;
+    if (P.mode != MODE_CAMERA)
+        return P.a;
+    int lo = 0, hi = P.ncam - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.cams[mid].offset <= id)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return P.cams[lo].a;
+}
+
+// Statistics: warp reduction, one atomic per counter per warp.
+struct Counters {
+    uint32_t geo = 0, att = 0, acc = 0, rhs32 = 0, rhs64 = 0, att64 = 0, def = 0;
+    uint32_t st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    __device__ __forceinline__ void status(int s)
+    {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            st[j] += (s == j) ? 1u : 0u;
+    }
+    __device__ __forceinline__ void flush(unsigned long long *stats) const
+    {
+        const unsigned FULL = 0xffffffffu;
+        auto wsum = [&](uint32_t v) -> unsigned long long {
+            unsigned long long x = v;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                x += __shfl_xor_sync(FULL, x, o);
+            return x;
+        };
+        const unsigned long long v[7] = {wsum(geo), wsum(att), wsum(acc), wsum(rhs32),
+                                         wsum(rhs64), wsum(att64), wsum(def)};
+        unsigned long long w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            w[j] = wsum(st[j]);
+        if ((threadIdx.x & 31) == 0) {
+            const int slot[7] = {SC_GEODESICS, SC_ATTEMPTS, SC_ACCEPTED, SC_RHS32,
+                                 SC_RHS64,     SC_ATT64,    SC_DEFERRED};
+#pragma unroll
+            for (int j = 0; j < 7; ++j)
+                if (v[j])
+                    atomicAdd(stats + slot[j], v[j]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (w[j])
+                    atomicAdd(stats + SC_STATUS + j, w[j]);
+        }
+    }
+};
+
+// Warp-aggregated claim of `cnt` consecutive items from a counter; every
+// lane of the warp gets the base.
+__device__ __forceinline__ unsigned long long warp_claim(unsigned long long *ctr, unsigned mask)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if ((int)(threadIdx.x & 31) == leader)
+        base = atomicAdd(ctr, (unsigned long long)__popc(mask));
+    return __shfl_sync(FULL, base, leader);
+}
+
+// ===========================================================================
+// FP64 path: one persistent kernel, set-up and output inline.
+// ===========================================================================
+template <int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) trace_f64_kernel(const TraceParams P)
+{
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-
-    bool has = false;
-    bool drained = false;
-    bool timed_out = false;
+    const unsigned long long n_items = (unsigned long long)P.n;
+    bool has = false, drained = false, timed_out = false;
     int64_t id = 0;
     RayConst rc;
-    T y[8], c[8];
-    T h = T(0), rnow = T(0);
+    double y[8], c[8];
+    double h = 0.0, rnow = 0.0;
     uint32_t nsteps = 0;
     int since_renorm = 0;
-    uint32_t c_geo = 0, c_att = 0, c_acc = 0, c_rhs32 = 0, c_rhs64 = 0, c_att64 = 0;
-    uint32_t c_st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    Counters C;
     const unsigned long long t_start = global_ns();
     uint32_t iter = 0;
-
     for (;;) {
-        // ---- refill idle lanes from the queue (one atomic per warp)
         const unsigned need = __ballot_sync(FULL, !has);
         if (need && !drained) {
-            const int leader = __ffs(need) - 1;
-            const unsigned cnt = __popc(need);
-            unsigned long long base = 0;
-            if (lane == leader)
-                base = atomicAdd(P.head, (unsigned long long)cnt);
-            base = __shfl_sync(FULL, base, leader);
-            if (base + cnt >= (unsigned long long)P.n)
+            const unsigned long long base = warp_claim(P.head, need);
+            if (base + __popc(need) >= n_items)
                 drained = true;
             if (!has) {
                 const unsigned long long my = base + __popc(need & lt_mask);
-                if (my < (unsigned long long)P.n) {
+                if (my < n_items) {
                     id = (int64_t)my;
-                    double yd[8];
-                    const int st0 = init_geodesic(P, id, yd, rc);
-                    ++c_geo;
+                    const int st0 = init_geodesic(P, id, y, rc);
+                    ++C.geo;
                     if (st0 != ST_NONE || timed_out) {
                         const int st = st0 != ST_NONE ? st0 : ST_TIMEOUT;
-                        write_out(P, id, yd, st, 0, rc.a);
-#pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            c_st[j] += (st == j) ? 1u : 0u;
+                        write_out(P, id, y, st, 0, rc.a);
+                        C.status(st);
                     } else {
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            y[i] = (T)yd[i];
-                            c[i] = F32 ? (T)(yd[i] - (double)y[i]) : T(0);
-                        }
-                        h = (T)P.h0;
-                        rnow = (T)ks_r(rc.a * rc.a, yd[1], yd[2], yd[3]);
+                        for (int i = 0; i < 8; ++i)
+                            c[i] = 0.0;
+                        h = P.h0;
                         nsteps = 0;
                         since_renorm = 0;
                         has = true;
@@ -593,7 +725,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_kernel(const TraceParams P)
             }
         }
         if (!__any_sync(FULL, has)) {
-            if (drained)      // warp-uniform: derived from the shuffled base
+            if (drained)
                 break;
             continue;
         }
@@ -605,49 +737,301 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_kernel(const TraceParams P)
                 st = ST_MAXSTEPS;
             } else {
                 ++nsteps;
-                ++c_att;
-                if (F32 && (double)rnow < rc.zone_r) {
+                ++C.att;
+                ++C.att64;
+                uint32_t r = 0;
+                st = step_once<false, double>(rc, P, P.tol, y, c, h, rnow, r, C.acc, since_renorm);
+                C.rhs64 += r;
+            }
+            if (st != ST_NONE) {
+                write_out(P, id, y, st, nsteps, rc.a);
+                C.status(st);
+                has = false;
+            }
+        }
+        if (P.budget_ns && ((++iter & 31u) == 0) && !timed_out) {
+            bool over = false;
+            if (lane == 0)
+                over = (global_ns() - t_start) > P.budget_ns;
+            timed_out = __shfl_sync(FULL, over, 0);
+        }
+    }
+    C.flush(P.stats);
+}
+
+// ===========================================================================
+// FP32+Kahan path: three launches.
+//   f32_setup_kernel   FP64 initial states (whole warps, coalesced) split
+//                      into FP32 pairs + per-geodesic constants in scratch;
+//                      geodesics that end at once get their status here.
+//   trace_f32_kernel   PHASE 0: persistent FP32 stepping, no FP64 arithmetic
+//                      except zone steps that do not fit the zone buffer;
+//                      PHASE 1: continues the deferred zone geodesics.
+//   f32_finish_kernel  folds the compensated pairs into FP64 outputs and
+//                      computes the FP64 diagnostics (whole warps).
+// ===========================================================================
+static __global__ void __launch_bounds__(256) f32_setup_kernel(const TraceParams P)
+{
+    const int64_t n = P.n;
+    Counters C;
+    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < n;
+         id += (int64_t)gridDim.x * blockDim.x) {
+        double yd[8];
+        RayConst rc;
+        const int st0 = init_geodesic(P, id, yd, rc);
+        ++C.geo;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float hi = (float)yd[i];
+            P.s_state[i * n + id] = hi;
+            P.s_state[(8 + i) * n + id] = isfinite(yd[i]) ? (float)(yd[i] - (double)hi) : 0.0f;
+        }
+        P.s_const[KC_A * n + id] = rc.af;
+        P.s_const[KC_RCAP * n + id] = rc.rcapf;
+        P.s_const[KC_RESC * n + id] = rc.rescf;
+        P.s_const[KC_ZONE * n + id] = rc.zonef;
+        P.s_const[KC_TEND * n + id] = rc.tendf;
+        P.s_const[KC_TENDLO * n + id] = rc.tendlo;
+        P.s_const[KC_U2 * n + id] = (float)rc.u2_0;
+        P.s_const[KC_FLAGS * n + id] = __int_as_float((rc.use_t ? 1 : 0) | (rc.tpos ? 2 : 0));
+        P.status[id] = st0;
+        P.steps[id] = 0;
+        if (st0 != ST_NONE)
+            C.status(st0);
+    }
+    // every lane of every warp reaches here (grid-stride loop above)
+    C.flush(P.stats);
+}
+
+static __global__ void __launch_bounds__(256) f32_finish_kernel(const TraceParams P)
+{
+    const int64_t n = P.n;
+    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < n;
+         id += (int64_t)gridDim.x * blockDim.x) {
+        double y[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            y[i] = (double)P.s_state[i * n + id] + (double)P.s_state[(8 + i) * n + id];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            P.x_out[j * n + id] = y[j];
+            P.k_out[j * n + id] = y[4 + j];
+        }
+        if (P.diag) {
+            const int st = P.status[id];
+            float cst[4];
+            if (st == ST_INVALID_IC || st == ST_NONFINITE) {
+                cst[0] = cst[1] = cst[2] = cst[3] = __int_as_float(0x7fc00000);
+            } else {
+                constants(geodesic_spin(P, id), y, cst);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                P.diag[j * n + id] = cst[j];
+        }
+    }
+}
+
+// FP32 lane constants from the planes (PHASE 0) -- no FP64 arithmetic.
+__device__ __forceinline__ void load_const_f32(const TraceParams &P, int64_t id, RayConst &rc)
+{
+    const int64_t n = P.n;
+    rc.af = P.s_const[KC_A * n + id];
+    rc.rcapf = P.s_const[KC_RCAP * n + id];
+    rc.rescf = P.s_const[KC_RESC * n + id];
+    rc.zonef = P.s_const[KC_ZONE * n + id];
+    rc.tendf = P.s_const[KC_TEND * n + id];
+    rc.tendlo = P.s_const[KC_TENDLO * n + id];
+    const int fl = __float_as_int(P.s_const[KC_FLAGS * n + id]);
+    rc.use_t = fl & 1;
+    rc.tpos = (fl >> 1) & 1;
+}
+
+// Full constants (FP64 fields too) for the zone phase and in-place zone steps.
+__device__ __forceinline__ void load_const_full(const TraceParams &P, int64_t id, RayConst &rc)
+{
+    const int64_t n = P.n;
+    load_const_f32(P, id, rc);
+    rc.a = geodesic_spin(P, id);
+    const double rh = 1.0 + sqrt(fmax(0.0, 1.0 - rc.a * rc.a));
+    rc.rcap = 1.01 * rh;
+    rc.zone_r = P.fp64_zone * rh;
+    rc.resc = (double)rc.rescf;
+    rc.tend = P.t_end_each ? P.t_end_each[id] : P.t_end;
+    rc.u2_0 = (double)P.s_const[KC_U2 * n + id];
+}
+
+template <int PHASE, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParams P)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t n = P.n;
+    unsigned long long n_items = (unsigned long long)n;
+    if (PHASE == 1) {
+        const unsigned long long zc = *P.zcount;
+        n_items = zc < (unsigned long long)P.zcap ? zc : (unsigned long long)P.zcap;
+    }
+    unsigned long long *const head = PHASE == 1 ? P.zhead : P.head;
+    const bool can_defer = PHASE == 0 && P.zbuf != nullptr && P.fp64_zone > 0.0;
+    const float tol = (float)P.tol;
+    const float h0 = (float)P.h0;
+
+    bool has = false, drained = false, timed_out = false;
+    int64_t id = 0;
+    RayConst rc;
+    float y[8], c[8];
+    float h = 0.f, rnow = 0.f;
+    uint32_t nsteps = 0;
+    int since_renorm = 0;
+    Counters C;
+    const unsigned long long t_start = global_ns();
+    uint32_t iter = 0;
+
+    for (;;) {
+        // ---- refill idle lanes from the queue (one atomic per warp)
+        const unsigned need = __ballot_sync(FULL, !has);
+        if (need && !drained) {
+            const unsigned long long base = warp_claim(head, need);
+            if (base + __popc(need) >= n_items)
+                drained = true;
+            if (!has) {
+                const unsigned long long my = base + __popc(need & lt_mask);
+                if (my < n_items) {
+                    bool go = true;
+                    if (PHASE == 1) {
+                        const ZoneEntry &e = P.zbuf[my];
+                        id = e.id;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            y[i] = e.y[i];
+                            c[i] = e.c[i];
+                        }
+                        h = e.h;
+                        rnow = e.rnow;
+                        nsteps = e.nsteps;
+                        since_renorm = e.since_renorm;
+                        load_const_full(P, id, rc);
+                    } else {
+                        id = (int64_t)my;
+                        go = P.status[id] == ST_NONE;     // set-up already ended it
+                        if (go) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                y[i] = P.s_state[i * n + id];
+                                c[i] = P.s_state[(8 + i) * n + id];
+                            }
+                            if (P.renorm_every > 0)
+                                load_const_full(P, id, rc);   // FP64 spin for re-solving k^t
+                            else
+                                load_const_f32(P, id, rc);
+                            h = h0;
+                            nsteps = 0;
+                            since_renorm = 0;
+                            rnow = ks_r(rc.af * rc.af, y[1], y[2], y[3]);
+                        }
+                    }
+                    if (go) {
+                        if (timed_out) {
+                            P.status[id] = ST_TIMEOUT;
+                            P.steps[id] = nsteps;
+                            C.status(ST_TIMEOUT);
+                            if (PHASE == 1) {
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) {
+                                    P.s_state[i * n + id] = y[i];
+                                    P.s_state[(8 + i) * n + id] = c[i];
+                                }
+                            }
+                        } else {
+                            has = true;
+                        }
+                    }
+                }
+            }
+        }
+        if (!__any_sync(FULL, has)) {
+            if (drained)      // warp-uniform: derived from the shuffled base
+                break;
+            continue;
+        }
+        // ---- zone entries: defer them to the zone phase (PHASE 0)
+        bool in_zone = has && rnow < rc.zonef;
+        if (can_defer) {
+            const unsigned dm = __ballot_sync(FULL, in_zone && !timed_out);
+            if (dm) {
+                const unsigned long long zb = warp_claim(P.zcount, dm);
+                if ((dm >> lane) & 1u) {
+                    const unsigned long long slot = zb + __popc(dm & lt_mask);
+                    if (slot < (unsigned long long)P.zcap) {
+                        ZoneEntry &e = P.zbuf[slot];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            e.y[i] = y[i];
+                            e.c[i] = c[i];
+                        }
+                        e.id = id;
+                        e.h = h;
+                        e.rnow = rnow;
+                        e.nsteps = nsteps;
+                        e.since_renorm = since_renorm;
+                        ++C.def;
+                        has = false;
+                        in_zone = false;
+                    }
+                }
+            }
+        }
+        if (has) {
+            int st = ST_NONE;
+            if (timed_out) {
+                st = ST_TIMEOUT;
+            } else if ((int64_t)nsteps >= P.max_steps) {
+                st = ST_MAXSTEPS;
+            } else {
+                ++nsteps;
+                ++C.att;
+                if (in_zone) {
+                    if (PHASE == 0)
+                        load_const_full(P, id, rc);   // in-place zone step: FP64 constants
                     LaneF ls;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        ls.y[i] = (float)y[i];
-                        ls.c[i] = (float)c[i];
+                        ls.y[i] = y[i];
+                        ls.c[i] = c[i];
                     }
-                    ls.h = (float)h;
-                    ls.rnow = (float)rnow;
+                    ls.h = h;
+                    ls.rnow = rnow;
                     const ZoneResult R = zone_step(rc, P, ls, since_renorm);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        y[i] = (T)R.s.y[i];
-                        c[i] = (T)R.s.c[i];
+                        y[i] = R.s.y[i];
+                        c[i] = R.s.c[i];
                     }
-                    h = (T)R.s.h;
-                    rnow = (T)R.s.rnow;
+                    h = R.s.h;
+                    rnow = R.s.rnow;
                     since_renorm = R.since_renorm;
                     st = R.st;
-                    c_rhs64 += R.nrhs;
-                    c_acc += R.nacc;
-                    ++c_att64;
+                    C.rhs64 += R.nrhs;
+                    C.acc += R.nacc;
+                    ++C.att64;
                 } else {
                     uint32_t r = 0;
-                    st = step_once<F32, T>(rc, P, y, c, h, rnow, r, c_acc, since_renorm);
-                    if (F32)
-                        c_rhs32 += r;
-                    else
-                        c_rhs64 += r;
-                    if (!F32)
-                        ++c_att64;
+                    st = step_once<true, float>(rc, P, tol, y, c, h, rnow, r, C.acc,
+                                                since_renorm);
+                    C.rhs32 += r;
                 }
             }
             if (st != ST_NONE) {
-                double yd[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    yd[i] = F32 ? (double)y[i] + (double)c[i] : (double)y[i];
-                write_out(P, id, yd, st, nsteps, rc.a);
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    c_st[j] += (st == j) ? 1u : 0u;
+                for (int i = 0; i < 8; ++i) {
+                    P.s_state[i * n + id] = y[i];
+                    P.s_state[(8 + i) * n + id] = c[i];
+                }
+                P.status[id] = st;
+                P.steps[id] = (int32_t)nsteps;
+                C.status(st);
                 has = false;
             }
         }
@@ -659,32 +1043,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_kernel(const TraceParams P)
             timed_out = __shfl_sync(FULL, over, 0);
         }
     }
-
-    // ---- statistics: warp reduction, one atomic per counter per warp
-    auto wsum = [&](uint32_t v) -> unsigned long long {
-        unsigned long long s = v;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            s += __shfl_xor_sync(FULL, s, o);
-        return s;
-    };
-    unsigned long long s_geo = wsum(c_geo), s_att = wsum(c_att), s_acc = wsum(c_acc);
-    unsigned long long s_r32 = wsum(c_rhs32), s_r64 = wsum(c_rhs64), s_a64 = wsum(c_att64);
-    unsigned long long s_st[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-        s_st[j] = wsum(c_st[j]);
-    if (lane == 0) {
-        atomicAdd(P.stats + SC_GEODESICS, s_geo);
-        atomicAdd(P.stats + SC_ATTEMPTS, s_att);
-        atomicAdd(P.stats + SC_ACCEPTED, s_acc);
-        atomicAdd(P.stats + SC_RHS32, s_r32);
-        atomicAdd(P.stats + SC_RHS64, s_r64);
-        atomicAdd(P.stats + SC_ATT64, s_a64);
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            atomicAdd(P.stats + SC_STATUS + j, s_st[j]);
-    }
+    C.flush(P.stats);
 }
+
+#endif // KERR_TYPES_ONLY
 
 } // namespace kerr

@@ -1,15 +1,38 @@
-// FP32+Kahan instantiations of the persistent kernel (FP64 inside the zone).
+// FP32+Kahan path: set-up, persistent stepping (FP32 phase and FP64-zone
+// phase) and finishing launches.
 #include "kerr_trace.cuh"
 #include "kerr_variants.h"
 
 namespace kerr {
 
-template <int B, int M>
-static cudaError_t launch_one(const TraceParams &P, int sms, cudaStream_t s)
+static int grid_for(long long n, int block, int sms)
+{
+    long long g = (n + block - 1) / block;
+    const long long cap = (long long)sms * 8;
+    if (g > cap)
+        g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+cudaError_t launch_setup_f32(const TraceParams &P, int sms, cudaStream_t s)
+{
+    f32_setup_kernel<<<grid_for(P.n, 256, sms), 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_f32(const TraceParams &P, int sms, cudaStream_t s)
+{
+    f32_finish_kernel<<<grid_for(P.n, 256, sms), 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+template <int PH, int B, int M>
+static cudaError_t launch_one(const TraceParams &P, int sms, cudaStream_t s, bool clamp_to_n)
 {
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<true, B, M>, B, 0);
+        cudaError_t e =
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_f32_kernel<PH, B, M>, B, 0);
         if (e != cudaSuccess)
             return e;
         if (per_sm < 1)
@@ -17,9 +40,9 @@ static cudaError_t launch_one(const TraceParams &P, int sms, cudaStream_t s)
     }
     long long grid = (long long)per_sm * sms;
     const long long need = (P.n + B - 1) / B;
-    if (need < grid)
+    if (clamp_to_n && need < grid)
         grid = need < 1 ? 1 : need;
-    trace_kernel<true, B, M><<<(unsigned)grid, B, 0, s>>>(P);
+    trace_f32_kernel<PH, B, M><<<(unsigned)grid, B, 0, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -28,12 +51,20 @@ cudaError_t launch_trace_f32(const TraceParams &P, int v, int sms, cudaStream_t 
     switch (v) {
 #define KERR_CASE(i, b, m) \
     case i:                \
-        return launch_one<b, m>(P, sms, s);
+        return launch_one<0, b, m>(P, sms, s, true);
         KERR_VARIANT_LIST(KERR_CASE)
 #undef KERR_CASE
     default:
         return cudaErrorInvalidValue;
     }
+}
+
+// The FP64-zone phase: continues the geodesics deferred by the FP32 phase.
+// Its item count lives on the device, so the grid is the full persistent
+// grid; threads with nothing to do exit at once.
+cudaError_t launch_zone_phase(const TraceParams &P, int sms, cudaStream_t s)
+{
+    return launch_one<1, 128, 2>(P, sms, s, false);
 }
 
 } // namespace kerr

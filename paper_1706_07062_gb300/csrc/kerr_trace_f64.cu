@@ -1,4 +1,4 @@
-// FP64 instantiations of the persistent kernel.
+// FP64 path: one persistent kernel per launch configuration.
 #include "kerr_trace.cuh"
 #include "kerr_variants.h"
 
@@ -9,7 +9,7 @@ static cudaError_t launch_one(const TraceParams &P, int sms, cudaStream_t s)
 {
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<false, B, M>, B, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_f64_kernel<B, M>, B, 0);
         if (e != cudaSuccess)
             return e;
         if (per_sm < 1)
@@ -19,7 +19,7 @@ static cudaError_t launch_one(const TraceParams &P, int sms, cudaStream_t s)
     const long long need = (P.n + B - 1) / B;
     if (need < grid)
         grid = need < 1 ? 1 : need;
-    trace_kernel<false, B, M><<<(unsigned)grid, B, 0, s>>>(P);
+    trace_f64_kernel<B, M><<<(unsigned)grid, B, 0, s>>>(P);
     return cudaGetLastError();
 }
 

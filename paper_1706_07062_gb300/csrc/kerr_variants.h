@@ -20,5 +20,8 @@ struct TraceParams;
 // sms` blocks (0 = as many as fit).  Returns the CUDA error of the launch.
 cudaError_t launch_trace_f32(const TraceParams &P, int v, int sms, cudaStream_t s);
 cudaError_t launch_trace_f64(const TraceParams &P, int v, int sms, cudaStream_t s);
+cudaError_t launch_zone_phase(const TraceParams &P, int sms, cudaStream_t s);
+cudaError_t launch_setup_f32(const TraceParams &P, int sms, cudaStream_t s);
+cudaError_t launch_finish_f32(const TraceParams &P, int sms, cudaStream_t s);
 
 } // namespace kerr

@@ -53,6 +53,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("geodesics", ctypes.c_int64), ("attempts", ctypes.c_int64),
                 ("accepted", ctypes.c_int64), ("rhs_fp32", ctypes.c_int64),
                 ("rhs_fp64", ctypes.c_int64), ("attempts_fp64", ctypes.c_int64),
+                ("deferred", ctypes.c_int64),
                 ("status_count", ctypes.c_int64 * 8), ("kernel_ms", ctypes.c_float),
                 ("variant", ctypes.c_int32)]
 

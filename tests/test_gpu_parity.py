@@ -267,3 +267,45 @@ def test_every_variant_and_autotune(ctx):
         assert max(ex.max(), ek.max()) < 1e-6
     best = K.kerr_autotune(ctx, cam(spec), K.default_opts(), sample=2048)
     assert 0 <= best < K.kerr_num_variants()
+
+
+# ---------------------------------------------------------------------------
+# deferred FP64-zone phase
+# ---------------------------------------------------------------------------
+def test_zone_phase_counts(ctx):
+    spec = W.CameraSpec(0.99, 0.3, 1000.0, 25.0, 128, 128)
+    K.kerr_trace_camera(ctx, cam(spec), K.default_opts(), device=DEV)
+    s = K.kerr_get_stats(ctx)
+    assert s.geodesics == spec.n and sum(s.status_count) == spec.n
+    assert s.deferred > 0 and s.attempts_fp64 > 0 and s.rhs_fp64 > 0
+    K.kerr_trace_camera(ctx, cam(spec), K.default_opts(fp64_zone=0.0), device=DEV)
+    s0 = K.kerr_get_stats(ctx)
+    assert s0.deferred == 0 and s0.attempts_fp64 == 0
+
+
+def test_zone_buffer_overflow_falls_back_in_place(ctx):
+    """A 512 x 512 image of the shadow itself: most rays enter the zone, more
+    than a fresh context's deferred buffer holds (a quarter of the rays), so
+    the rest take their FP64 zone steps in place.  The result must match a run
+    whose buffer holds every deferred ray (same arithmetic, other launch)."""
+    spec = W.CameraSpec(0.9, 1.0, 1000.0, 3.0, 512, 512)
+    opts = K.default_opts(tol=1e-6)
+    fresh = K.kerr_init(spec.a)
+    out1 = K.kerr_trace_camera(fresh, cam(spec), opts, device=DEV)
+    torch.cuda.synchronize()
+    s1 = K.kerr_get_stats(fresh)
+    fresh.close()
+    assert s1.deferred == spec.n // 4            # buffer full: the rest ran in place
+    big = K.kerr_init(spec.a)
+    K.kerr_trace_camera(big, cam(W.CameraSpec(0.9, 1.0, 1000.0, 3.0, 1024, 1024)), opts,
+                        device=DEV)                # grows the buffer to 2^18 entries
+    out2 = K.kerr_trace_camera(big, cam(spec), opts, device=DEV)
+    torch.cuda.synchronize()
+    s2 = K.kerr_get_stats(big)
+    big.close()
+    assert s2.deferred > s1.deferred
+    assert s1.attempts_fp64 == s2.attempts_fp64
+    assert np.array_equal(to_np(out1.status), to_np(out2.status))
+    ex, ek, _ = rel_errors(to_np(out1.x), to_np(out1.k),
+                           np.concatenate([to_np(out2.x).T, to_np(out2.k).T], 1))
+    assert max(ex.max(), ek.max()) < 1e-9
