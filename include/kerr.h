@@ -202,6 +202,37 @@ int kerr_variant_info(int v, int32_t *block, int32_t *min_blocks);
 int kerr_autotune(kerr_ctx *ctx, const kerr_camera *cam, const kerr_opts *opts,
                   int64_t sample, int32_t *best, void *stream);
 
+/* Allocation-free camera tracing.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- real-time
+ * hosts that must not call cudaMalloc/cudaFree once running (both may
+ * synchronise the device and have unbounded latency), or hosts whose device
+ * memory is owned and budgeted by another framework's pool.
+ *
+ * Same computation and outputs as kerr_trace_camera (either precision), with
+ * no context: each camera carries its spin.  All scratch lives in one
+ * file-scope device array of KERR_STATIC_SCRATCH_BYTES that every GPU that
+ * loads the library holds until the process exits; the call performs no
+ * allocation of any kind.  Limits: at most KERR_STATIC_MAX_GEODESICS rays and
+ * KERR_STATIC_MAX_CAMERAS cameras per call (KERR_EINVAL beyond); outputs must
+ * be device memory (KERR_EINVAL otherwise, since host buffers would need
+ * staging).  Geodesics entering the FP64 zone beyond the array's zone buffer
+ * (a quarter of the maximum) take their zone steps in place.
+ *
+ * The call is asynchronous on `stream`.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current
+ * and caches it; make that first call before any stream capture.  Every call
+ * shares the array and leaves its contents there (the counters are cleared at
+ * the start of each call), so calls that overlap on the GPU -- on other
+ * streams or from other host threads -- race and must be serialised by the
+ * caller.  Counters of the call are not reported (kerr_get_stats needs a
+ * context). */
+#define KERR_STATIC_MAX_GEODESICS 131072
+#define KERR_STATIC_MAX_CAMERAS 64
+#define KERR_STATIC_SCRATCH_BYTES 15731968
+int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam, const kerr_opts *opts,
+                             double *x_out, double *k_out, int32_t *status, int32_t *steps,
+                             float *diag, void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *kerr_last_error(void);
 

@@ -108,6 +108,12 @@ extern "C" void kerr_opts_default(kerr_opts *o)
 
 extern "C" const char *kerr_last_error(void) { return g_err.c_str(); }
 
+int kerr::kerr_set_error(int code, const char *msg)
+{
+    g_err = msg;
+    return code;
+}
+
 extern "C" int kerr_num_variants(void) { return kNumVariants; }
 
 extern "C" int kerr_variant_info(int v, int32_t *block, int32_t *min_blocks)

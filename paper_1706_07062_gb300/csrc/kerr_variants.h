@@ -24,4 +24,7 @@ cudaError_t launch_zone_phase(const TraceParams &P, int sms, cudaStream_t s);
 cudaError_t launch_setup_f32(const TraceParams &P, int sms, cudaStream_t s);
 cudaError_t launch_finish_f32(const TraceParams &P, int sms, cudaStream_t s);
 
+// Records `msg` as this thread's kerr_last_error() and returns `code`.
+int kerr_set_error(int code, const char *msg);
+
 } // namespace kerr

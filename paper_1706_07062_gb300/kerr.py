@@ -86,13 +86,16 @@ def lib():
                                            vp, vp]
         L.kerr_trace_camera.argtypes = [vp, c.POINTER(Camera), i32, c.POINTER(Opts), vp, vp, vp,
                                         vp, vp, vp]
+        L.kerr_trace_camera_static.argtypes = [c.POINTER(Camera), i32, c.POINTER(Opts), vp, vp,
+                                               vp, vp, vp, vp]
         L.kerr_get_stats.argtypes = [vp, c.POINTER(Stats)]
         L.kerr_num_variants.argtypes = []
         L.kerr_variant_info.argtypes = [c.c_int, c.POINTER(i32), c.POINTER(i32)]
         L.kerr_autotune.argtypes = [vp, c.POINTER(Camera), c.POINTER(Opts), i64, c.POINTER(i32), vp]
         L.kerr_last_error.restype = c.c_char_p
         for name in ("kerr_init", "kerr_destroy", "kerr_trace_rays", "kerr_trace_particles",
-                     "kerr_trace_camera", "kerr_get_stats", "kerr_num_variants",
+                     "kerr_trace_camera", "kerr_trace_camera_static", "kerr_get_stats",
+                     "kerr_num_variants",
                      "kerr_variant_info", "kerr_autotune"):
             getattr(L, name).restype = c.c_int
         _lib = L
@@ -258,6 +261,28 @@ def kerr_trace_camera(ctx: Context, cams, opts: Opts | None = None, out: TraceOu
                                    _ptr(out.k), _ptr(out.status), _ptr(out.steps),
                                    _ptr(out.diag), _stream_ptr(stream, out.x)),
            "kerr_trace_camera")
+    return out
+
+
+STATIC_MAX_GEODESICS = 131072
+STATIC_MAX_CAMERAS = 64
+
+
+def kerr_trace_camera_static(cams, opts: Opts | None = None, out: TraceOut | None = None,
+                             stream=None, device=None) -> TraceOut:
+    """Allocation-free camera tracing (kerr_trace_camera_static): no context,
+    outputs must be device tensors, at most STATIC_MAX_GEODESICS rays."""
+    if isinstance(cams, Camera):
+        cams = [cams]
+    arr = (Camera * len(cams))(*cams)
+    n = camera_rays(cams)
+    opts = opts or default_opts()
+    if out is None:
+        out = alloc_out(n, device)
+    _check(lib().kerr_trace_camera_static(arr, len(cams), ctypes.byref(opts), _ptr(out.x),
+                                          _ptr(out.k), _ptr(out.status), _ptr(out.steps),
+                                          _ptr(out.diag), _stream_ptr(stream, out.x)),
+           "kerr_trace_camera_static")
     return out
 
 
