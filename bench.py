@@ -35,8 +35,35 @@ UNIT = "rays/s"
 FLOPS_PER_RHS = 160          # one right-hand side
 FLOPS_PER_ATTEMPT = 366      # stage sums, error norm and update of one attempt
 FP32_LANES_PER_SM = 128      # FP32 FMA lanes per SM (one FMA = 2 FLOPs)
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (non-tensor) nominal rate
 WORKLOAD = ("camera 1024x1024, a=0.99, i=17deg, r_obs=1000M, +-25M, tol 1e-6, "
             "FP32+Kahan persistent kernel")
+
+
+def kernel_source_hash() -> str:
+    """Hash of the CUDA sources: ncu counters are only valid for the kernels
+    they were taken from."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1706_07062_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic() -> dict:
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    from the committed ncu summary, if it was taken from the current kernels."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return {}
+    with open(p) as fh:
+        t = json.load(fh)
+    if t.get("source_hash") != kernel_source_hash():
+        return {}
+    return t.get("bytes_per_launch", {})
 
 
 def load_peaks():
@@ -135,7 +162,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- timed region: K steps, L2 flushed between steps (outside the events)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    kern_ms, flops32, flops64, rhs32, rhs64, att, att64 = [], 0, 0, 0, 0, 0, 0
+    kern_ms, phase_ms, rhs32, rhs64, att, att64 = [], [], 0, 0, 0, 0
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -153,6 +180,7 @@ def run_ours(args, rank, world, local_rank):
         ev[i][1].record(stream)
         s = K.kerr_get_stats(ctx)          # synchronises the library stream
         kern_ms.append(s.kernel_ms)
+        phase_ms.append(list(s.phase_ms))
         rhs32 += s.rhs_fp32
         rhs64 += s.rhs_fp64
         att += s.attempts
@@ -171,27 +199,50 @@ def run_ours(args, rank, world, local_rank):
     value = world * n / (ms * 1e-3)
     stats = K.kerr_get_stats(ctx)
 
-    # ---- roofline of the persistent kernel (FP32 pipe, algorithmic FLOPs)
+    # ---- rooflines (algorithmic FLOPs from the counted right-hand sides)
     att32 = att - att64
     fl32 = rhs32 * FLOPS_PER_RHS + att32 * FLOPS_PER_ATTEMPT
     fl64 = rhs64 * FLOPS_PER_RHS + att64 * FLOPS_PER_ATTEMPT
     kms = sum(kern_ms) / len(kern_ms)
+    ph = [sum(p[i] for p in phase_ms) / len(phase_ms) for i in range(4)]
     peaks, peak_src = load_peaks()
     props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak32 = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = fl32 / args.steps / (kms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak32, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak32, 4), "traffic": None,
-                "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
-                               f"lanes x 2 x {sm_max:.0f} MHz ({peak_src} sm_max_mhz)",
-                "kernel_ms": round(kms, 4),
-                "fp32_flops_per_step": fl32 // args.steps,
-                "fp64_flops_per_step": fl64 // args.steps,
-                "attempts_per_ray": round(att / args.steps / n, 2),
-                "fp64_attempt_share": round(att64 / max(att, 1), 4)}
-    if args.prec == "fp64":
-        roofline["note"] = "FP64 path: achieved counts FP32 FLOPs only"
+    peak32 = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    peak64 = FP64_NOMINAL_TFLOPS
+    traffic = load_traffic()
+    if prec == K.FP32_KAHAN:
+        t32, t64 = ph[1], ph[2]
+        ach32 = fl32 / args.steps / (t32 * 1e-3) / 1e12 if t32 > 0 else 0.0
+        ach64 = fl64 / args.steps / (t64 * 1e-3) / 1e12 if t64 > 0 else 0.0
+        fp32_roof = {"kernel": "trace_f32_kernel (FP32 stepping phase)", "bound": "alu",
+                     "achieved": round(ach32, 3), "peak": round(peak32, 2), "unit": "TFLOP/s",
+                     "frac": round(ach32 / peak32, 4), "kernel_ms": round(t32, 4),
+                     "traffic": traffic.get("fp32_stepping"),
+                     "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                    f"{sm_max:.0f} MHz ({peak_src} sm_max_mhz)"}
+        zone_roof = {"kernel": "trace_f32_kernel (FP64 zone phase)", "bound": "alu",
+                     "achieved": round(ach64, 4), "peak": peak64, "unit": "TFLOP/s",
+                     "frac": round(ach64 / peak64, 4), "kernel_ms": round(t64, 4),
+                     "traffic": traffic.get("fp64_zone"),
+                     "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)"}
+        dominant = zone_roof if t64 > t32 else fp32_roof
+        roofline = dict(dominant)
+        roofline["phase_ms"] = {"setup": round(ph[0], 4), "fp32_stepping": round(ph[1], 4),
+                                "fp64_zone": round(ph[2], 4), "finish": round(ph[3], 4)}
+        roofline["fp32_stepping"] = fp32_roof
+        roofline["fp64_zone"] = zone_roof
+    else:
+        ach64 = fl64 / args.steps / (kms * 1e-3) / 1e12
+        roofline = {"kernel": "trace_f64_kernel", "bound": "alu", "achieved": round(ach64, 4),
+                    "peak": peak64, "unit": "TFLOP/s", "frac": round(ach64 / peak64, 4),
+                    "kernel_ms": round(kms, 4), "traffic": traffic.get("fp64_path"),
+                    "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)"}
+    roofline["attempts_per_ray"] = round(att / args.steps / n, 2)
+    roofline["fp64_attempt_share"] = round(att64 / max(att, 1), 4)
+    roofline["fp32_flops_per_step"] = fl32 // args.steps
+    roofline["fp64_flops_per_step"] = fl64 // args.steps
 
     result = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -202,7 +253,7 @@ def run_ours(args, rank, world, local_rank):
                          "rays_per_gpu": n, "parallelism": f"replicas x{world}",
                          "l2": "flushed between steps (512 MiB write, outside the events)",
                          "variant": stats.variant},
-              "gpu_launches": args.steps,
+              "gpu_launches": args.steps * (4 if prec == K.FP32_KAHAN else 1),
               "roofline": roofline, "clocks": clocks,
               "timed_wall_s": round(t_wall, 3)}
 
@@ -222,6 +273,26 @@ def run_ours(args, rank, world, local_rank):
         result["e2e"] = {"value": round(n / e2e_s, 1), "unit": UNIT,
                          "h2d_bytes_per_step": 56,
                          "d2h_bytes_per_step": n * (8 * 8 + 4 + 4 + 4 * 4)}
+
+    # ---- FP32+Kahan without the FP64 zone (comparison leg)
+    if rank == 0 and prec == K.FP32_KAHAN and not args.skip_fp64:
+        onz = K.default_opts(prec=K.FP32_KAHAN, tol=W.TOL_1024, fp64_zone=0.0)
+        outnz = K.alloc_out(n, dev)
+        K.kerr_trace_camera(ctx, cam, onz, out=outnz, stream=stream)
+        torch.cuda.synchronize(dev)
+        tnz = []
+        for _ in range(3):
+            flush.zero_()
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            K.kerr_trace_camera(ctx, cam, onz, out=outnz, stream=stream)
+            b_.record(stream)
+            torch.cuda.synchronize(dev)
+            tnz.append(a_.elapsed_time(b_))
+        result["fp32_no_zone"] = {"value": round(n / (min(tnz) * 1e-3), 1), "unit": UNIT,
+                                  "ms_per_step": round(min(tnz), 3),
+                                  "note": "same path with fp64_zone = 0 (every step FP32+Kahan)"}
+        result["_nz_out"] = outnz
 
     # ---- plain FP64 GPU path on the same workload (comparison leg)
     if rank == 0 and prec == K.FP32_KAHAN and not args.skip_fp64:
@@ -244,10 +315,12 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.skip_cpu:
-        result["cpu_baseline"], acc = cpu_baseline(spec, W, out, result.get("_fp64_out"))
+        result["cpu_baseline"], acc = cpu_baseline(spec, W, out, result.get("_fp64_out"),
+                                                   result.get("_nz_out"))
         if acc:
             result["accuracy"] = acc
     result.pop("_fp64_out", None)
+    result.pop("_nz_out", None)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist is not None:
@@ -255,7 +328,7 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
 
 
-def cpu_baseline(spec, W, out_gpu, out64):
+def cpu_baseline(spec, W, out_gpu, out64, out_nz=None):
     """Time the FP64 CPU oracle on a bounded seeded sample of the same image
     (all host cores), and use that same sample to state the GPU path's
     end-point error against it."""
@@ -306,6 +379,8 @@ def cpu_baseline(spec, W, out_gpu, out64):
                "ill_conditioned": int(flags.sum()), "fp32_kahan": errs(out_gpu)}
         if out64 is not None:
             acc["fp64"] = errs(out64)
+        if out_nz is not None:
+            acc["fp32_no_zone"] = errs(out_nz)
     except Exception as exc:  # accuracy is a report, not the measurement
         acc = {"error": repr(exc)}
     return base, acc

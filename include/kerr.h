@@ -63,6 +63,11 @@ extern "C" {
                            /* FP64 for set-up, diagnostics and steps that start */
                            /* inside opts.fp64_zone * r_h                       */
 
+/* Arithmetic of FP32-path steps inside opts.fp64_zone * r_h. */
+#define KERR_ZONE_FP64 0   /* IEEE FP64 (1/64 of the FP32 rate on GB300)         */
+#define KERR_ZONE_F32X2 1  /* float-float on the FP32 pipe: unevaluated sums of  */
+                           /* two floats, ~48-bit significand                    */
+
 typedef struct kerr_ctx kerr_ctx;
 
 /* Integration options.  Fill with kerr_opts_default() and change fields.
@@ -103,9 +108,13 @@ typedef struct {
     int32_t variant;       /* kernel launch configuration: -1 = autotuned (or    */
                            /* the default before tuning), else an index < the    */
                            /* value of kerr_num_variants()                       */
-    uint64_t budget_ns;    /* wall-time budget of one call on the device; 0 =   */
+    uint64_t budget_ns;    /* wall-time budget of each launch on the device; 0 = */
                            /* none.  Geodesics unfinished when it runs out get   */
                            /* KERR_TIMEOUT and the state reached so far          */
+    int32_t zone_prec;     /* FP32 path, arithmetic of the steps inside the     */
+                           /* zone: KERR_ZONE_FP64 or KERR_ZONE_F32X2            */
+    int32_t zone_variant;  /* launch shape of the zone phase: -1 = default, else */
+                           /* an index < kerr_num_zone_variants()                */
 } kerr_opts;
 
 /* One pinhole-free parallel-ray camera (the paper's image-plane rays,
@@ -136,13 +145,15 @@ typedef struct {
     int64_t deferred;         /* FP32 path: geodesics handed to the FP64-zone    */
                               /* phase (second launch of the same call)          */
     int64_t status_count[8];  /* geodesics per status code                       */
-    float kernel_ms;          /* device time of the integration kernel           */
+    float kernel_ms;          /* device time of the whole integration launch     */
     int32_t variant;          /* launch configuration used                       */
+    float phase_ms[4];        /* FP32 path: set-up, FP32 stepping, FP64-zone     */
+                              /* phase, finishing; FP64 path: [1] = stepping     */
 } kerr_stats;
 
 /* Fills *opts with: prec FP32_KAHAN, tol 1e-6, h0 1, max_steps 1e6,
  * r_escape 0, t_end +inf, fp64_zone 1.5, renorm_every 0, clip_maxit 40,
- * variant -1, budget_ns 0. */
+ * variant -1, budget_ns 0, zone_prec KERR_ZONE_FP64, zone_variant -1. */
 void kerr_opts_default(kerr_opts *opts);
 
 /* Creates a context for black-hole spin a (|a| <= 1, else KERR_EINVAL) on the
@@ -194,6 +205,11 @@ int kerr_num_variants(void);
 /* Describes variant v: threads per block and minimum resident blocks per SM
  * (which sets the register cap). */
 int kerr_variant_info(int v, int32_t *block, int32_t *min_blocks);
+
+/* Launch shapes of the FP32 path's zone phase (threads per block, blocks per
+ * SM); fewer threads than deferred geodesics lets lanes refill. */
+int kerr_num_zone_variants(void);
+int kerr_zone_variant_info(int v, int32_t *block, int32_t *blocks_per_sm);
 
 /* Times every launch configuration for the given precision on `sample`
  * camera rays of cams[0] (spread over the image) and remembers the fastest

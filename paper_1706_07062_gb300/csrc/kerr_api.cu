@@ -58,6 +58,7 @@ bool is_device_ptr(const void *p)
 struct GraphKey {
     TraceParams P;
     int variant;
+    int zone_variant;
     int f32;
     bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof *this) == 0; }
 };
@@ -68,6 +69,7 @@ struct kerr_ctx {
     int sms = 0;
     cudaStream_t stream = nullptr;               // the context's own stream
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_k0 = nullptr, ev_k1 = nullptr;
+    cudaEvent_t ev_ph[3] = {nullptr, nullptr, nullptr};   // phase boundaries (in the graph)
     unsigned long long *d_scratch = nullptr;     // [0] queue head, [1..16] statistics,
                                                  // [17] zone count, [18] zone-phase head
     ZoneEntry *d_zone = nullptr;                 // deferred FP64-zone geodesics
@@ -83,6 +85,7 @@ struct kerr_ctx {
     bool gvalid = false;
     int tuned[2] = {-1, -1};                     // autotuned variant per precision
     int last_variant = -1;
+    int last_f32 = 0;
     bool have_stats = false;
 };
 
@@ -104,6 +107,8 @@ extern "C" void kerr_opts_default(kerr_opts *o)
     o->clip_maxit = 40;
     o->variant = -1;
     o->budget_ns = 0;
+    o->zone_prec = KERR_ZONE_FP64;
+    o->zone_variant = -1;
 }
 
 extern "C" const char *kerr_last_error(void) { return g_err.c_str(); }
@@ -124,6 +129,19 @@ extern "C" int kerr_variant_info(int v, int32_t *block, int32_t *min_blocks)
         *block = kVariants[v].block;
     if (min_blocks)
         *min_blocks = kVariants[v].min_blocks;
+    return KERR_OK;
+}
+
+extern "C" int kerr_num_zone_variants(void) { return kNumZoneVariants; }
+
+extern "C" int kerr_zone_variant_info(int v, int32_t *block, int32_t *blocks_per_sm)
+{
+    if (v < 0 || v >= kNumZoneVariants)
+        return fail(KERR_EINVAL, "zone variant %d out of range [0, %d)", v, kNumZoneVariants);
+    if (block)
+        *block = kZoneVariants[v].block;
+    if (blocks_per_sm)
+        *blocks_per_sm = kZoneVariants[v].min_blocks;
     return KERR_OK;
 }
 
@@ -151,6 +169,8 @@ extern "C" int kerr_init(double a, kerr_ctx **out)
         e = cudaEventCreate(&c->ev_k0);
     if (e == cudaSuccess)
         e = cudaEventCreate(&c->ev_k1);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+        e = cudaEventCreate(&c->ev_ph[i]);
     if (e == cudaSuccess)
         e = cudaMalloc(&c->d_scratch, kScratchWords * sizeof(unsigned long long));
     if (e == cudaSuccess)
@@ -185,6 +205,9 @@ extern "C" int kerr_destroy(kerr_ctx *c)
         cudaEventDestroy(c->ev_k0);
     if (c->ev_k1)
         cudaEventDestroy(c->ev_k1);
+    for (int i = 0; i < 3; ++i)
+        if (c->ev_ph[i])
+            cudaEventDestroy(c->ev_ph[i]);
     if (c->stream)
         cudaStreamDestroy(c->stream);
     delete c;
@@ -211,8 +234,14 @@ static int check_opts(const kerr_opts *o)
         return fail(KERR_EINVAL, "opts.clip_maxit = %d < 1", o->clip_maxit);
     if (o->renorm_every < 0)
         return fail(KERR_EINVAL, "opts.renorm_every = %d < 0", o->renorm_every);
+    if (o->zone_prec != KERR_ZONE_FP64 && o->zone_prec != KERR_ZONE_F32X2)
+        return fail(KERR_EINVAL, "opts.zone_prec = %d is not KERR_ZONE_FP64 or KERR_ZONE_F32X2",
+                    o->zone_prec);
     if (o->variant < -1 || o->variant >= kNumVariants)
         return fail(KERR_EINVAL, "opts.variant = %d outside [-1, %d)", o->variant, kNumVariants);
+    if (o->zone_variant < -1 || o->zone_variant >= kNumZoneVariants)
+        return fail(KERR_EINVAL, "opts.zone_variant = %d outside [-1, %d)", o->zone_variant,
+                    kNumZoneVariants);
     return KERR_OK;
 }
 
@@ -244,13 +273,15 @@ static int ensure_stage(kerr_ctx *c, size_t bytes)
     return KERR_OK;
 }
 
-static int launch_integration(kerr_ctx *c, const TraceParams &P, int prec, int variant)
+static int launch_integration(kerr_ctx *c, const TraceParams &P, int prec, int variant,
+                              int zone_variant)
 {
     const int f32 = (prec == KERR_FP32_KAHAN) ? 1 : 0;
     GraphKey key;
     std::memset(&key, 0, sizeof key);
     key.P = P;
     key.variant = variant;
+    key.zone_variant = zone_variant;
     key.f32 = f32;
     if (!(c->gvalid && c->gkey == key)) {
         cudaGraph_t g = nullptr;
@@ -258,13 +289,21 @@ static int launch_integration(kerr_ctx *c, const TraceParams &P, int prec, int v
         cudaError_t e1 = cudaMemsetAsync(c->d_scratch, 0, kScratchWords * sizeof(unsigned long long),
                                          c->stream);
         cudaError_t e2 = e1;
+        // event-record nodes (external records, so that they can be timed)
+        // between the launches time each phase
         if (f32) {
             if (e2 == cudaSuccess)
                 e2 = launch_setup_f32(P, c->sms, c->stream);
             if (e2 == cudaSuccess)
+                e2 = cudaEventRecordWithFlags(c->ev_ph[0], c->stream, cudaEventRecordExternal);
+            if (e2 == cudaSuccess)
                 e2 = launch_trace_f32(P, variant, c->sms, c->stream);
+            if (e2 == cudaSuccess)
+                e2 = cudaEventRecordWithFlags(c->ev_ph[1], c->stream, cudaEventRecordExternal);
             if (e2 == cudaSuccess && P.zbuf)
-                e2 = launch_zone_phase(P, c->sms, c->stream);
+                e2 = launch_zone_phase(P, zone_variant, c->sms, c->stream);
+            if (e2 == cudaSuccess)
+                e2 = cudaEventRecordWithFlags(c->ev_ph[2], c->stream, cudaEventRecordExternal);
             if (e2 == cudaSuccess)
                 e2 = launch_finish_f32(P, c->sms, c->stream);
         } else if (e2 == cudaSuccess) {
@@ -305,6 +344,7 @@ static int launch_integration(kerr_ctx *c, const TraceParams &P, int prec, int v
     KERR_CUDA(cudaGraphLaunch(c->gexec, c->stream));
     KERR_CUDA(cudaEventRecord(c->ev_k1, c->stream));
     c->last_variant = variant;
+    c->last_f32 = f32;
     c->have_stats = true;
     return KERR_OK;
 }
@@ -343,6 +383,7 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
     P.fp64_zone = o->prec == KERR_FP32_KAHAN ? o->fp64_zone : 0.0;
     P.renorm_every = o->renorm_every;
     P.clip_maxit = o->clip_maxit;
+    P.zone_df = o->zone_prec == KERR_ZONE_F32X2 ? 1 : 0;
     P.budget_ns = o->budget_ns;
     P.head = c->d_scratch;
     P.stats = c->d_scratch + 1;
@@ -461,7 +502,8 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
 
     int prec = o->prec;
     int variant = o->variant >= 0 ? o->variant : (c->tuned[prec] >= 0 ? c->tuned[prec] : 0);
-    rc = launch_integration(c, P, prec, variant);
+    const int zvar = o->zone_variant >= 0 ? o->zone_variant : kDefaultZoneVariant;
+    rc = launch_integration(c, P, prec, variant, zvar);
     if (rc)
         return rc;
 
@@ -558,6 +600,17 @@ extern "C" int kerr_get_stats(kerr_ctx *c, kerr_stats *out)
     KERR_CUDA(cudaEventElapsedTime(&ms, c->ev_k0, c->ev_k1));
     out->kernel_ms = ms;
     out->variant = c->last_variant;
+    if (c->last_f32) {
+        float t[4] = {0.f, 0.f, 0.f, 0.f};
+        KERR_CUDA(cudaEventElapsedTime(&t[0], c->ev_k0, c->ev_ph[0]));
+        KERR_CUDA(cudaEventElapsedTime(&t[1], c->ev_ph[0], c->ev_ph[1]));
+        KERR_CUDA(cudaEventElapsedTime(&t[2], c->ev_ph[1], c->ev_ph[2]));
+        KERR_CUDA(cudaEventElapsedTime(&t[3], c->ev_ph[2], c->ev_k1));
+        for (int i = 0; i < 4; ++i)
+            out->phase_ms[i] = t[i];
+    } else {
+        out->phase_ms[1] = ms;
+    }
     return KERR_OK;
 }
 

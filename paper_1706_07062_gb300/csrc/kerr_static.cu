@@ -102,6 +102,8 @@ extern "C" int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam,
         return fail(KERR_EINVAL, "kerr_trace_camera_static: unknown precision");
     if (!(o->tol > 0.0) || !(o->h0 > 0.0) || o->max_steps < 0 || o->clip_maxit < 1 ||
         o->renorm_every < 0 || !(o->fp64_zone >= 0.0) || o->variant < -1 ||
+        (o->zone_prec != KERR_ZONE_FP64 && o->zone_prec != KERR_ZONE_F32X2) ||
+        o->zone_variant < -1 || o->zone_variant >= kNumZoneVariants ||
         o->variant >= kNumVariants)
         return fail(KERR_EINVAL, "kerr_trace_camera_static: invalid options");
     CamDev cd[kMaxCams];
@@ -170,6 +172,7 @@ extern "C" int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam,
     P.fp64_zone = o->prec == KERR_FP32_KAHAN ? o->fp64_zone : 0.0;
     P.renorm_every = o->renorm_every;
     P.clip_maxit = o->clip_maxit;
+    P.zone_df = o->zone_prec == KERR_ZONE_F32X2 ? 1 : 0;
     P.budget_ns = o->budget_ns;
     P.head = ctr;
     P.stats = ctr + 1;
@@ -187,7 +190,8 @@ extern "C" int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam,
         if (e == cudaSuccess)
             e = launch_trace_f32(P, variant, sms, s);
         if (e == cudaSuccess && P.zbuf)
-            e = launch_zone_phase(P, sms, s);
+            e = launch_zone_phase(P, o->zone_variant >= 0 ? o->zone_variant : kDefaultZoneVariant,
+                                  sms, s);
         if (e == cudaSuccess)
             e = launch_finish_f32(P, sms, s);
     } else {

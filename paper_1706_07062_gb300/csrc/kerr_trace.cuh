@@ -15,6 +15,7 @@
 #include <type_traits>
 
 #include "kerr_math.cuh"
+#include "kerr_df.cuh"
 
 namespace kerr {
 
@@ -94,6 +95,7 @@ struct TraceParams {
     int64_t max_steps;
     double r_escape, t_end, fp64_zone;
     int32_t renorm_every, clip_maxit;
+    int32_t zone_df;            // FP32 path: zone steps in float-float (1) or FP64 (0)
     uint64_t budget_ns;
     unsigned long long *head;   // work-queue counter, zero at launch
     unsigned long long *stats;  // SC_COUNT counters, zero at launch
@@ -121,6 +123,7 @@ struct RayConst {
     // t_end is an unevaluated float pair (tendf + tendlo) to keep the end-time
     // event exact to ~1e-14 relative
     float af, rcapf, rescf, zonef, tendf, tendlo;
+    float alo, rcaplo;   // low parts of a and rcap (float-float zone steps)
 };
 
 __device__ __forceinline__ void finish_const(RayConst &rc)
@@ -131,6 +134,8 @@ __device__ __forceinline__ void finish_const(RayConst &rc)
     rc.zonef = (float)rc.zone_r;
     rc.tendf = (float)rc.tend;
     rc.tendlo = isfinite(rc.tend) ? (float)(rc.tend - (double)rc.tendf) : 0.0f;
+    rc.alo = (float)(rc.a - (double)rc.af);
+    rc.rcaplo = (float)(rc.rcap - (double)rc.rcapf);
 }
 
 // Per-precision view of the ray constants.
@@ -141,6 +146,19 @@ template <> struct RC<float> {
     static __device__ __forceinline__ float resc(const RayConst &r) { return r.rescf; }
     static __device__ __forceinline__ float tend(const RayConst &r) { return r.tendf; }
     static __device__ __forceinline__ float tendlo(const RayConst &r) { return r.tendlo; }
+};
+template <> struct RC<dfloat> {
+    static __device__ __forceinline__ dfloat a(const RayConst &r) { return dfloat(r.af, r.alo); }
+    static __device__ __forceinline__ dfloat rcap(const RayConst &r)
+    {
+        return dfloat(r.rcapf, r.rcaplo);
+    }
+    static __device__ __forceinline__ dfloat resc(const RayConst &r) { return dfloat(r.rescf, 0.f); }
+    static __device__ __forceinline__ dfloat tend(const RayConst &r)
+    {
+        return quick_two_sum(r.tendf, r.tendlo);
+    }
+    static __device__ __forceinline__ dfloat tendlo(const RayConst &) { return dfloat(0.f, 0.f); }
 };
 template <> struct RC<double> {
     static __device__ __forceinline__ double a(const RayConst &r) { return r.a; }
@@ -336,15 +354,27 @@ __device__ void clip(const T a, const T a2, T y[8], T c[8], const T A0[4], const
     }
 }
 
+// Clipping tolerances per number type: |s| <= stol * scale, bracket eps * h.
 template <typename T> struct Prec;
 template <> struct Prec<float> {
-    static constexpr float stol = 2e-6f;
-    static constexpr float eps = 1e-7f;
+    static __device__ __forceinline__ float stol() { return 2e-6f; }
+    static __device__ __forceinline__ float eps() { return 1e-7f; }
 };
 template <> struct Prec<double> {
-    static constexpr double stol = 1e-12;
-    static constexpr double eps = 1e-15;
+    static __device__ __forceinline__ double stol() { return 1e-12; }
+    static __device__ __forceinline__ double eps() { return 1e-15; }
 };
+template <> struct Prec<dfloat> {
+    static __device__ __forceinline__ dfloat stol() { return dfloat(1e-12); }
+    static __device__ __forceinline__ dfloat eps() { return dfloat(1e-13); }
+};
+
+// Conversions used by the FP64 renormalisation.
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(dfloat x) { return (double)x.hi + (double)x.lo; }
+template <typename T> __device__ __forceinline__ T from_d(double d) { return (T)d; }
+template <> __device__ __forceinline__ dfloat from_d<dfloat>(double d) { return dfloat(d); }
 
 // One attempted step with events.  (y, c) is the lane state; h the trial
 // step; rn receives r of the new state when a step is accepted.  Returns a
@@ -389,8 +419,8 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
     const int maxit = P.clip_maxit;
     if (rn < rcap) {
         const T s_lo = event_value<KAHAN>(0, a2, y, c, rcap, T(0));
-        clip<KAHAN>(a, a2, y, c, A0, h, 0, rcap, T(0), s_lo, rn - rcap, Prec<T>::stol * rcap,
-                    Prec<T>::eps, maxit, nrhs);
+        clip<KAHAN>(a, a2, y, c, A0, h, 0, rcap, T(0), s_lo, rn - rcap, Prec<T>::stol() * rcap,
+                    Prec<T>::eps(), maxit, nrhs);
         return ST_CAPTURED;
     }
     const T resc = RC<T>::resc(rc);
@@ -398,7 +428,7 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
         const T s_lo = event_value<KAHAN>(0, a2, y, c, resc, T(0));
         if (s_lo <= T(0)) {
             clip<KAHAN>(a, a2, y, c, A0, h, 0, resc, T(0), s_lo, rn - resc,
-                        Prec<T>::stol * resc, Prec<T>::eps, maxit, nrhs);
+                        Prec<T>::stol() * resc, Prec<T>::eps(), maxit, nrhs);
         } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -414,8 +444,8 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
         if ((s_hi > T(0)) != (rc.tpos != 0)) {
             const T s_lo = event_value<KAHAN>(1, a2, y, c, tend, tlo);
             const T sc = fmax(T(1), fabs(tend));
-            clip<KAHAN>(a, a2, y, c, A0, h, 1, tend, tlo, s_lo, s_hi, Prec<T>::stol * sc,
-                        Prec<T>::eps, maxit, nrhs);
+            clip<KAHAN>(a, a2, y, c, A0, h, 1, tend, tlo, s_lo, s_hi, Prec<T>::stol() * sc,
+                        Prec<T>::eps(), maxit, nrhs);
             return ST_ENDTIME;
         }
     }
@@ -429,13 +459,13 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
         double k[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            k[j] = (double)y[4 + j] + (KAHAN ? (double)c[4 + j] : 0.0);
-        const KSPoint p = ks_point(rc.a, (double)y[1] + (KAHAN ? (double)c[1] : 0.0),
-                                   (double)y[2] + (KAHAN ? (double)c[2] : 0.0),
-                                   (double)y[3] + (KAHAN ? (double)c[3] : 0.0));
+            k[j] = to_d(y[4 + j]) + (KAHAN ? to_d(c[4 + j]) : 0.0);
+        const KSPoint p = ks_point(rc.a, to_d(y[1]) + (KAHAN ? to_d(c[1]) : 0.0),
+                                   to_d(y[2]) + (KAHAN ? to_d(c[2]) : 0.0),
+                                   to_d(y[3]) + (KAHAN ? to_d(c[3]) : 0.0));
         if (solve_kt(p, k, rc.u2_0, 0)) {
-            y[4] = (T)k[0];
-            c[4] = KAHAN ? (T)(k[0] - (double)y[4]) : T(0);
+            y[4] = from_d<T>(k[0]);
+            c[4] = KAHAN ? from_d<T>(k[0] - to_d(y[4])) : T(0);
         }
     }
     h *= fac;
@@ -603,6 +633,34 @@ static __device__ __noinline__ ZoneResult zone_step(const RayConst rc, const Tra
     }
     R.s.h = (float)hd;
     R.s.rnow = (float)rd;
+    R.since_renorm = since_renorm;
+    return R;
+}
+
+// The same step in float-float arithmetic: the compensated pair (y, c) is
+// already a float-float number, so no FP64 instruction is needed.
+static __device__ __noinline__ ZoneResult zone_step_df(const RayConst rc, const TraceParams &P,
+                                                       LaneF s, int since_renorm)
+{
+    dfloat yd[8], cd[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        yd[i] = quick_two_sum(s.y[i], s.c[i]);
+        cd[i] = dfloat(0.f, 0.f);
+    }
+    dfloat hd(s.h, 0.f), rd(s.rnow, 0.f);
+    ZoneResult R;
+    R.nrhs = 0;
+    R.nacc = 0;
+    R.st = step_once<false, dfloat>(rc, P, dfloat((float)P.tol), yd, cd, hd, rd, R.nrhs, R.nacc,
+                                    since_renorm);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        R.s.y[i] = yd[i].hi;
+        R.s.c[i] = yd[i].lo;
+    }
+    R.s.h = hd.hi;
+    R.s.rnow = rd.hi;
     R.since_renorm = since_renorm;
     return R;
 }
@@ -859,6 +917,8 @@ __device__ __forceinline__ void load_const_full(const TraceParams &P, int64_t id
     rc.resc = (double)rc.rescf;
     rc.tend = P.t_end_each ? P.t_end_each[id] : P.t_end;
     rc.u2_0 = (double)P.s_const[KC_U2 * n + id];
+    rc.alo = (float)(rc.a - (double)rc.af);            // low parts for float-float steps
+    rc.rcaplo = (float)(rc.rcap - (double)rc.rcapf);
 }
 
 template <int PHASE, int BLOCK, int MINB>
@@ -869,11 +929,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t n = P.n;
     unsigned long long n_items = (unsigned long long)n;
-    if (PHASE == 1) {
+    if (PHASE != 0) {
         const unsigned long long zc = *P.zcount;
         n_items = zc < (unsigned long long)P.zcap ? zc : (unsigned long long)P.zcap;
     }
-    unsigned long long *const head = PHASE == 1 ? P.zhead : P.head;
+    unsigned long long *const head = PHASE != 0 ? P.zhead : P.head;
     const bool can_defer = PHASE == 0 && P.zbuf != nullptr && P.fp64_zone > 0.0;
     const float tol = (float)P.tol;
     const float h0 = (float)P.h0;
@@ -900,7 +960,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                 const unsigned long long my = base + __popc(need & lt_mask);
                 if (my < n_items) {
                     bool go = true;
-                    if (PHASE == 1) {
+                    if (PHASE != 0) {
                         const ZoneEntry &e = P.zbuf[my];
                         id = e.id;
 #pragma unroll
@@ -937,7 +997,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                             P.status[id] = ST_TIMEOUT;
                             P.steps[id] = nsteps;
                             C.status(ST_TIMEOUT);
-                            if (PHASE == 1) {
+                            if (PHASE != 0) {
 #pragma unroll
                                 for (int i = 0; i < 8; ++i) {
                                     P.s_state[i * n + id] = y[i];
@@ -1003,7 +1063,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     }
                     ls.h = h;
                     ls.rnow = rnow;
-                    const ZoneResult R = zone_step(rc, P, ls, since_renorm);
+                    ZoneResult R;
+                    if (PHASE == 2 || (PHASE == 0 && P.zone_df))
+                        R = zone_step_df(rc, P, ls, since_renorm);
+                    else
+                        R = zone_step(rc, P, ls, since_renorm);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         y[i] = R.s.y[i];

@@ -14,13 +14,19 @@ struct Variant {
 constexpr int kNumVariants = 6;
 constexpr Variant kVariants[kNumVariants] = {{128, 4}, {128, 3}, {256, 2}, {128, 2}, {64, 8}, {128, 5}};
 
+// Launch shapes of the zone phase: (threads per block, blocks per SM).
+#define KERR_ZONE_VARIANT_LIST(X) X(0, 128, 2) X(1, 128, 1) X(2, 64, 2) X(3, 64, 1) X(4, 32, 2)
+constexpr int kNumZoneVariants = 5;
+constexpr Variant kZoneVariants[kNumZoneVariants] = {{128, 2}, {128, 1}, {64, 2}, {64, 1}, {32, 2}};
+constexpr int kDefaultZoneVariant = 1;
+
 struct TraceParams;
 
 // Launch the persistent kernel for variant v on a grid of `blocks_per_sm *
 // sms` blocks (0 = as many as fit).  Returns the CUDA error of the launch.
 cudaError_t launch_trace_f32(const TraceParams &P, int v, int sms, cudaStream_t s);
 cudaError_t launch_trace_f64(const TraceParams &P, int v, int sms, cudaStream_t s);
-cudaError_t launch_zone_phase(const TraceParams &P, int sms, cudaStream_t s);
+cudaError_t launch_zone_phase(const TraceParams &P, int zv, int sms, cudaStream_t s);
 cudaError_t launch_setup_f32(const TraceParams &P, int sms, cudaStream_t s);
 cudaError_t launch_finish_f32(const TraceParams &P, int sms, cudaStream_t s);
 

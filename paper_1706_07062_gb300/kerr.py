@@ -23,6 +23,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libkerr.so")
 
 FP64, FP32_KAHAN = 0, 1
+ZONE_FP64, ZONE_F32X2 = 0, 1
 ESCAPED, CAPTURED, ENDTIME, MAXSTEPS, TIMEOUT, NONFINITE, INVALID_IC = 1, 2, 3, 4, 5, 6, 7
 STATUS_NAMES = {1: "escaped", 2: "captured", 3: "endtime", 4: "maxsteps", 5: "timeout",
                 6: "nonfinite", 7: "invalid_ic"}
@@ -39,7 +40,8 @@ class Opts(ctypes.Structure):
                 ("max_steps", ctypes.c_int64), ("r_escape", ctypes.c_double),
                 ("t_end", ctypes.c_double), ("fp64_zone", ctypes.c_double),
                 ("clip_maxit", ctypes.c_int32), ("variant", ctypes.c_int32),
-                ("budget_ns", ctypes.c_uint64)]
+                ("budget_ns", ctypes.c_uint64), ("zone_prec", ctypes.c_int32),
+                ("zone_variant", ctypes.c_int32)]
 
 
 class Camera(ctypes.Structure):
@@ -55,11 +57,13 @@ class Stats(ctypes.Structure):
                 ("rhs_fp64", ctypes.c_int64), ("attempts_fp64", ctypes.c_int64),
                 ("deferred", ctypes.c_int64),
                 ("status_count", ctypes.c_int64 * 8), ("kernel_ms", ctypes.c_float),
-                ("variant", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("phase_ms", ctypes.c_float * 4)]
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "status_count"}
+        d = {f: getattr(self, f) for f, _ in self._fields_
+             if f not in ("status_count", "phase_ms")}
         d["status_count"] = list(self.status_count)
+        d["phase_ms"] = list(self.phase_ms)
         return d
 
 
@@ -91,12 +95,15 @@ def lib():
         L.kerr_get_stats.argtypes = [vp, c.POINTER(Stats)]
         L.kerr_num_variants.argtypes = []
         L.kerr_variant_info.argtypes = [c.c_int, c.POINTER(i32), c.POINTER(i32)]
+        L.kerr_num_zone_variants.argtypes = []
+        L.kerr_zone_variant_info.argtypes = [c.c_int, c.POINTER(i32), c.POINTER(i32)]
         L.kerr_autotune.argtypes = [vp, c.POINTER(Camera), c.POINTER(Opts), i64, c.POINTER(i32), vp]
         L.kerr_last_error.restype = c.c_char_p
         for name in ("kerr_init", "kerr_destroy", "kerr_trace_rays", "kerr_trace_particles",
                      "kerr_trace_camera", "kerr_trace_camera_static", "kerr_get_stats",
                      "kerr_num_variants",
-                     "kerr_variant_info", "kerr_autotune"):
+                     "kerr_variant_info", "kerr_autotune", "kerr_num_zone_variants",
+                     "kerr_zone_variant_info"):
             getattr(L, name).restype = c.c_int
         _lib = L
     return _lib
@@ -299,6 +306,17 @@ def kerr_num_variants() -> int:
 def kerr_variant_info(v: int) -> tuple[int, int]:
     b, m = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().kerr_variant_info(v, ctypes.byref(b), ctypes.byref(m)), "kerr_variant_info")
+    return b.value, m.value
+
+
+def kerr_num_zone_variants() -> int:
+    return lib().kerr_num_zone_variants()
+
+
+def kerr_zone_variant_info(v: int) -> tuple[int, int]:
+    b, m = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().kerr_zone_variant_info(v, ctypes.byref(b), ctypes.byref(m)),
+           "kerr_zone_variant_info")
     return b.value, m.value
 
 

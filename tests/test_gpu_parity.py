@@ -79,17 +79,18 @@ def c1024_oracle():
     return idx, y0, ref
 
 
-@pytest.mark.parametrize("prec", [K.FP32_KAHAN, K.FP64])
-def test_camera1024_full_launch_subset(ctx, c1024_oracle, prec):
+@pytest.mark.parametrize("prec,zone", [(K.FP32_KAHAN, K.ZONE_FP64), (K.FP32_KAHAN, K.ZONE_F32X2),
+                                       (K.FP64, K.ZONE_FP64)])
+def test_camera1024_full_launch_subset(ctx, c1024_oracle, prec, zone):
     spec = W.CAMERA_1024
     idx, y0, ref = c1024_oracle
-    opts = K.default_opts(prec=prec, tol=W.TOL_1024)
+    opts = K.default_opts(prec=prec, tol=W.TOL_1024, zone_prec=zone)
     out = K.kerr_trace_camera(ctx, cam(spec), opts, device=DEV)
     torch.cuda.synchronize()
     st = to_np(out.status)
     assert set(np.unique(st)) <= {K.ESCAPED, K.CAPTURED}
     gate = 1e-5 if prec == K.FP32_KAHAN else 1e-9
-    s = compare(f"camera1024/{prec}", spec.a, y0, O.Opts(tol=W.TOL_1024), out, idx, gate,
+    s = compare(f"camera1024/{prec}/{zone}", spec.a, y0, O.Opts(tol=W.TOL_1024), out, idx, gate,
                 fp32=(prec == K.FP32_KAHAN), ref=ref)
     print(s)
     # null constraint reported per ray (FP64 diagnostics): |u^2| small
@@ -272,12 +273,26 @@ def test_every_variant_and_autotune(ctx):
 # ---------------------------------------------------------------------------
 # deferred FP64-zone phase
 # ---------------------------------------------------------------------------
+def test_zone_launch_shapes_agree(ctx):
+    """Every zone-phase launch shape gives the same end states (the shape only
+    changes which lane runs a geodesic, never its arithmetic)."""
+    spec = W.CameraSpec(0.99, 0.3, 1000.0, 8.0, 96, 96)
+    outs = [K.kerr_trace_camera(ctx, cam(spec), K.default_opts(zone_variant=v), device=DEV)
+            for v in range(K.kerr_num_zone_variants())]
+    torch.cuda.synchronize()
+    for o in outs[1:]:
+        assert torch.equal(o.x, outs[0].x) and torch.equal(o.k, outs[0].k)
+        assert torch.equal(o.status, outs[0].status)
+
+
 def test_zone_phase_counts(ctx):
     spec = W.CameraSpec(0.99, 0.3, 1000.0, 25.0, 128, 128)
     K.kerr_trace_camera(ctx, cam(spec), K.default_opts(), device=DEV)
     s = K.kerr_get_stats(ctx)
     assert s.geodesics == spec.n and sum(s.status_count) == spec.n
     assert s.deferred > 0 and s.attempts_fp64 > 0 and s.rhs_fp64 > 0
+    assert all(t >= 0 for t in s.phase_ms) and s.phase_ms[1] > 0 and s.phase_ms[2] > 0
+    assert abs(sum(s.phase_ms) - s.kernel_ms) < 0.05 * s.kernel_ms + 0.05
     K.kerr_trace_camera(ctx, cam(spec), K.default_opts(fp64_zone=0.0), device=DEV)
     s0 = K.kerr_get_stats(ctx)
     assert s0.deferred == 0 and s0.attempts_fp64 == 0
