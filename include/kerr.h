@@ -170,10 +170,20 @@ int kerr_destroy(kerr_ctx *ctx);
  * x_out, k_out ([4][n]), status[n], steps[n] (attempted steps), and diag
  * ([4][n] floats: E = -p_t, L_z = x p_y - y p_x, Carter's Q, u^2 = g_ab k^a k^b
  * at the end state, FP64-computed) unless diag is NULL.  Sec. 2.1 (eqs.
- * opt0/opti), Sec. 3 (RK4), Sec. 4 (termination). */
+ * opt0/opti), Sec. 3 (RK4), Sec. 4 (termination).
+ *
+ * cross (NULL = not recorded): [5][n] floats, the first two equatorial
+ * crossings along the integration and a redshift there -- r1, phi1, r2,
+ * phi2, g1 -- with NaN where absent.  A crossing is an accepted step (or
+ * clipped end step) across z = 0, located on z = 0 by the same root-find as
+ * the clipping; r is the KS radius, phi = atan2(y, x) - atan2(a, r) the KS
+ * azimuth in (-pi, pi], and g1 = 1 / (u^t (1 - Omega xi)) the redshift of a
+ * prograde Keplerian emitter at r1 (Omega = 1/(r^{3/2} + a), xi = L_z/E of
+ * the start state), NaN inside the ISCO.  (Labels for the surrogate; the
+ * paper has none.) */
 int kerr_trace_rays(kerr_ctx *ctx, const double *x0, const double *k0, int64_t n,
                     const kerr_opts *opts, double *x_out, double *k_out, int32_t *status,
-                    int32_t *steps, float *diag, void *stream);
+                    int32_t *steps, float *diag, float *cross, void *stream);
 
 /* Integrates every ray of ncam cameras (Sec. 4: backward null geodesics from
  * an image plane at large distance); the initial states are built on the
@@ -182,7 +192,7 @@ int kerr_trace_rays(kerr_ctx *ctx, const double *x0, const double *k0, int64_t n
  * opts->r_escape == 0 each ray escapes at its own start radius. */
 int kerr_trace_camera(kerr_ctx *ctx, const kerr_camera *cams, int32_t ncam,
                       const kerr_opts *opts, double *x_out, double *k_out, int32_t *status,
-                      int32_t *steps, float *diag, void *stream);
+                      int32_t *steps, float *diag, float *cross, void *stream);
 
 /* Integrates n massive particles (Sec. 3.2: time-like geodesics with the same
  * integrator).  x0: [4][n] plane of start events; v0: [3][n] plane of
@@ -193,7 +203,8 @@ int kerr_trace_camera(kerr_ctx *ctx, const kerr_camera *cams, int32_t ncam,
  * holds u^mu). */
 int kerr_trace_particles(kerr_ctx *ctx, const double *x0, const double *v0, const double *t_end,
                          int64_t n, const kerr_opts *opts, double *x_out, double *k_out,
-                         int32_t *status, int32_t *steps, float *diag, void *stream);
+                         int32_t *status, int32_t *steps, float *diag, float *cross,
+                         void *stream);
 
 /* Copies the counters of the last trace call into *out (synchronises the
  * context's stream first). */
@@ -244,10 +255,10 @@ int kerr_autotune(kerr_ctx *ctx, const kerr_camera *cam, const kerr_opts *opts,
  * context). */
 #define KERR_STATIC_MAX_GEODESICS 131072
 #define KERR_STATIC_MAX_CAMERAS 64
-#define KERR_STATIC_SCRATCH_BYTES 15731968
+#define KERR_STATIC_SCRATCH_BYTES 16256256
 int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam, const kerr_opts *opts,
                              double *x_out, double *k_out, int32_t *status, int32_t *steps,
-                             float *diag, void *stream);
+                             float *diag, float *cross, void *stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *kerr_last_error(void);

@@ -24,6 +24,7 @@
  * Deliberately NOT the paper's optimised form (eqs. opt0/opti): the CUDA path
  * uses that form, so the two agree only if both are right.
  */
+#define _GNU_SOURCE
 #include <complex.h>
 #include <math.h>
 #include <pthread.h>
@@ -478,13 +479,14 @@ static double ev_r(double a, const double y[8], double rstop)
  * until |s| <= stol, the bracket collapses, or maxit iterations.          */
 typedef double (*event_fn)(double a, const double y[8], double c);
 
-static void clip(metric_fn m, double a, const double yold[8], const double k1[8],
-                 const double ynew[8], double h, event_fn ev, double c, double stol,
-                 int maxit, double yout[8], oracle_counts *cnt)
+static double clip(metric_fn m, double a, const double yold[8], const double k1[8],
+                   const double ynew[8], double h, event_fn ev, double c, double stol,
+                   int maxit, double yout[8], oracle_counts *cnt)
 {
     double lo = 0.0, hi = h;
     double slo = ev(a, yold, c), shi = ev(a, ynew, c);
     int side = 0;
+    double eta_out = h;
     memcpy(yout, ynew, 8 * sizeof(double));
     for (int it = 0; it < maxit; ++it) {
         double eta = hi - shi * (hi - lo) / (shi - slo);
@@ -495,6 +497,7 @@ static void clip(metric_fn m, double a, const double yold[8], const double k1[8]
         cnt->rhs_evals += 7;
         double st = ev(a, yt, c);
         memcpy(yout, yt, sizeof yt);
+        eta_out = eta;
         if (fabs(st) <= stol)
             break;
         if ((st > 0) == (shi > 0)) {
@@ -513,12 +516,73 @@ static void clip(metric_fn m, double a, const double yold[8], const double k1[8]
         if (hi - lo <= 1e-15 * h)
             break;
     }
+    return eta_out;
 }
 
 static double ev_t(double a, const double y[8], double tend)
 {
     (void)a;
     return y[0] - tend;
+}
+
+static double ev_z(double a, const double y[8], double unused)
+{
+    (void)a;
+    (void)unused;
+    return y[3];
+}
+
+/* Prograde ISCO radius (Bardeen, Press & Teukolsky 1972), M = 1. */
+static double r_isco(double a)
+{
+    double z1 = 1.0 + cbrt(1.0 - a * a) * (cbrt(1.0 + a) + cbrt(1.0 - a));
+    double z2 = sqrt(3.0 * a * a + z1 * z1);
+    return 3.0 + z2 - sqrt((3.0 - z1) * (3.0 + z1 + 2.0 * z2));
+}
+
+/* Equatorial-crossing labels (the surrogate's training targets; the paper
+ * has none, this is the project's reading).  A crossing is a step whose
+ * end has z of the other sign (or zero); it is located on that step with the
+ * same root-find as the clipping, on z = 0.  Recorded: the KS radius and the
+ * KS azimuth phi = atan2(y, x) - atan2(a, r) wrapped to (-pi, pi] of the first
+ * two crossings, and the redshift of a prograde Keplerian emitter at the
+ * first one, g = 1 / (u^t (1 - Omega xi)) with Omega = 1/(r^{3/2} + a),
+ * u^t = (r^{3/2} + a) / (r^{3/4} sqrt(r^{3/2} - 3 r^{1/2} + 2a)) and
+ * xi = L_z / E of the ray (NaN inside the ISCO).  Missing values are NaN.    */
+typedef struct {
+    int count;
+    double v[5]; /* r1, phi1, r2, phi2, g1 */
+} crossings;
+
+static void record_crossing(metric_fn m, double a, const double yold[8], const double k1[8],
+                            const double yend[8], double h_used, int maxit, double xi,
+                            crossings *cr, oracle_counts *cnt)
+{
+    const double z0 = yold[3], z1 = yend[3];
+    if (cr->count >= 2 || !((z0 > 0 && z1 <= 0) || (z0 < 0 && z1 >= 0)))
+        return;
+    double yc[8];
+    /* z tolerance scaled by the radius at the nearer end of the step */
+    const double r0 = oracle_ks_r(a, yold[1], yold[2], yold[3]);
+    const double r1 = oracle_ks_r(a, yend[1], yend[2], yend[3]);
+    clip(m, a, yold, k1, yend, h_used, ev_z, 0.0, 1e-12 * (1.0 + fmin(r0, r1)), maxit, yc, cnt);
+    const double rc = oracle_ks_r(a, yc[1], yc[2], yc[3]);
+    double ph = atan2(yc[2], yc[1]) - atan2(a, rc);
+    while (ph <= -M_PI)
+        ph += 2.0 * M_PI;
+    while (ph > M_PI)
+        ph -= 2.0 * M_PI;
+    cr->v[2 * cr->count] = rc;
+    cr->v[2 * cr->count + 1] = ph;
+    if (cr->count == 0) {
+        if (rc >= r_isco(a)) {
+            const double s = sqrt(rc), r32 = rc * s;
+            const double ut = (r32 + a) / (sqrt(s) * s * sqrt(r32 - 3.0 * s + 2.0 * a));
+            const double Om = 1.0 / (r32 + a);
+            cr->v[4] = 1.0 / (ut * (1.0 - Om * xi));
+        }
+    }
+    cr->count++;
 }
 
 /* Integrate one geodesic with adaptive step doubling until an event.
@@ -532,11 +596,17 @@ static double ev_t(double a, const double y[8], double tend)
  * step is clipped onto the surface.  A start inside 1.01 r_h is "captured"
  * with no step.  Returns the status.                                        */
 int oracle_trace_one(double a, const double y0[8], const oracle_opts *o, double yend[8],
-                     oracle_counts *cnt)
+                     oracle_counts *cnt, double cross_out[5])
 {
     metric_fn m = ks_metric_c;
     memset(cnt, 0, sizeof *cnt);
     memcpy(yend, y0, 8 * sizeof(double));
+    crossings cr;
+    cr.count = 0;
+    for (int i = 0; i < 5; ++i)
+        cr.v[i] = NAN;
+    if (cross_out)
+        memcpy(cross_out, cr.v, sizeof cr.v);
     if (!all_finite(y0))
         return ST_NONFINITE;
     const double rh = 1.0 + sqrt(1.0 - a * a);
@@ -546,10 +616,13 @@ int oracle_trace_one(double a, const double y0[8], const oracle_opts *o, double 
     const int use_t = isfinite(o->t_end);
     const double s0t = y0[0] - o->t_end;
     const double u2_0 = norm2(a, y0);
+    double c0[4];
+    oracle_constants(a, y0, c0);
+    const double xi = c0[1] / c0[0];
     if (r0 < rcap)
         return ST_CAPTURED;
 
-    double y[8], k1[8], yh[8];
+    double y[8], k1[8], yh[8], ye[8];
     memcpy(y, y0, sizeof y);
     double h = o->h0;
     int64_t since_renorm = 0;
@@ -574,31 +647,32 @@ int oracle_trace_one(double a, const double y0[8], const oracle_opts *o, double 
             status = ST_NONFINITE;
             break;
         }
+        /* termination (with the clipped end point ye and its step length) */
+        int st = 0;
+        double h_used = h;
+        memcpy(ye, yh, sizeof ye);
         double rn = oracle_ks_r(a, yh[1], yh[2], yh[3]);
         if (rn < rcap) {
-            clip(m, a, y, k1, yh, h, ev_r, rcap, 1e-12 * rcap, o->clip_maxit, yend, cnt);
-            memcpy(y, yend, sizeof y);
-            status = ST_CAPTURED;
-            break;
-        }
-        if (rn > resc && (yh[1] * yh[5] + yh[2] * yh[6] + yh[3] * yh[7]) > 0.0) {
+            h_used = clip(m, a, y, k1, yh, h, ev_r, rcap, 1e-12 * rcap, o->clip_maxit, ye, cnt);
+            st = ST_CAPTURED;
+        } else if (rn > resc && (yh[1] * yh[5] + yh[2] * yh[6] + yh[3] * yh[7]) > 0.0) {
             double rold = oracle_ks_r(a, y[1], y[2], y[3]);
             if (rold <= resc)
-                clip(m, a, y, k1, yh, h, ev_r, resc, 1e-12 * resc, o->clip_maxit, yend, cnt);
-            else
-                memcpy(yend, yh, sizeof y);
-            memcpy(y, yend, sizeof y);
-            status = ST_ESCAPED;
+                h_used = clip(m, a, y, k1, yh, h, ev_r, resc, 1e-12 * resc, o->clip_maxit, ye,
+                              cnt);
+            st = ST_ESCAPED;
+        } else if (use_t && ((yh[0] - o->t_end > 0) != (s0t > 0))) {
+            h_used = clip(m, a, y, k1, yh, h, ev_t, o->t_end,
+                          1e-12 * fmax(1.0, fabs(o->t_end)), o->clip_maxit, ye, cnt);
+            st = ST_ENDTIME;
+        }
+        if (cross_out)
+            record_crossing(m, a, y, k1, ye, h_used, o->clip_maxit, xi, &cr, cnt);
+        memcpy(y, ye, sizeof y);
+        if (st) {
+            status = st;
             break;
         }
-        if (use_t && ((yh[0] - o->t_end > 0) != (s0t > 0))) {
-            clip(m, a, y, k1, yh, h, ev_t, o->t_end, 1e-12 * fmax(1.0, fabs(o->t_end)),
-                 o->clip_maxit, yend, cnt);
-            memcpy(y, yend, sizeof y);
-            status = ST_ENDTIME;
-            break;
-        }
-        memcpy(y, yh, sizeof y);
         if (o->renorm_every > 0 && ++since_renorm >= o->renorm_every) {
             since_renorm = 0;
             solve_kt(a, y, u2_0, 0);
@@ -606,6 +680,8 @@ int oracle_trace_one(double a, const double y0[8], const oracle_opts *o, double 
         h *= fac;
     }
     memcpy(yend, y, sizeof y);
+    if (cross_out)
+        memcpy(cross_out, cr.v, sizeof cr.v);
     return status;
 }
 
@@ -621,6 +697,7 @@ typedef struct {
     int32_t *status;
     int64_t *attempts;
     int64_t *rhs_evals;
+    double *cross;         /* n x 5 or NULL */
     int64_t next;
     pthread_mutex_t mu;
 } batch_job;
@@ -638,7 +715,8 @@ static void *batch_worker(void *arg)
         oracle_opts o = *J->o;
         if (J->t_end)
             o.t_end = J->t_end[i];
-        J->status[i] = oracle_trace_one(J->a[i], J->y0 + 8 * i, &o, J->yend + 8 * i, &c);
+        J->status[i] = oracle_trace_one(J->a[i], J->y0 + 8 * i, &o, J->yend + 8 * i, &c,
+                                        J->cross ? J->cross + 5 * i : NULL);
         if (J->attempts)
             J->attempts[i] = c.attempts;
         if (J->rhs_evals)
@@ -649,9 +727,9 @@ static void *batch_worker(void *arg)
 
 int oracle_trace_batch(int64_t n, const double *a, const double *t_end, const double *y0,
                        const oracle_opts *o, double *yend, int32_t *status, int64_t *attempts,
-                       int64_t *rhs_evals, int nthreads)
+                       int64_t *rhs_evals, double *cross, int nthreads)
 {
-    batch_job J = {n, a, t_end, y0, o, yend, status, attempts, rhs_evals, 0,
+    batch_job J = {n, a, t_end, y0, o, yend, status, attempts, rhs_evals, cross, 0,
                    PTHREAD_MUTEX_INITIALIZER};
     if (nthreads < 1)
         nthreads = 1;

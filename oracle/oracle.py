@@ -77,10 +77,10 @@ def lib():
         _lib.oracle_particle_ic.restype = c.c_int
         _lib.oracle_constants.argtypes = [c.c_double, D, D]
         _lib.oracle_trace_one.argtypes = [c.c_double, D, c.POINTER(_Opts), D,
-                                          c.POINTER(_Counts)]
+                                          c.POINTER(_Counts), D]
         _lib.oracle_trace_one.restype = c.c_int
         _lib.oracle_trace_batch.argtypes = [c.c_int64, D, D, D, c.POINTER(_Opts), D, I32, I64,
-                                            I64, c.c_int]
+                                            I64, D, c.c_int]
         _lib.oracle_trace_batch.restype = c.c_int
     return _lib
 
@@ -211,11 +211,14 @@ class TraceResult:
     status: np.ndarray     # (n,) int32
     attempts: np.ndarray   # (n,) int64 attempted steps
     rhs_evals: np.ndarray  # (n,) int64 right-hand-side evaluations
+    cross: np.ndarray | None = None   # (n, 5): r1, phi1, r2, phi2, g1 (NaN if missing)
 
 
-def trace(a, y0, opts: Opts, nthreads: int | None = None, t_end=None) -> TraceResult:
+def trace(a, y0, opts: Opts, nthreads: int | None = None, t_end=None,
+          crossings: bool = False) -> TraceResult:
     """Integrate each row of y0 (n, 8); `a` is a scalar or one spin per row;
-    `t_end` optionally gives one end time per row (overrides opts.t_end)."""
+    `t_end` optionally gives one end time per row (overrides opts.t_end);
+    `crossings` also records the first two equatorial crossings and g."""
     y0 = _f64(y0).reshape(-1, 8)
     n = y0.shape[0]
     av = _f64(np.broadcast_to(np.asarray(a, dtype=np.float64), (n,)))
@@ -224,6 +227,7 @@ def trace(a, y0, opts: Opts, nthreads: int | None = None, t_end=None) -> TraceRe
     status = np.zeros(n, dtype=np.int32)
     att = np.zeros(n, dtype=np.int64)
     ev = np.zeros(n, dtype=np.int64)
+    cr = np.full((n, 5), np.nan) if crossings else None
     if nthreads is None:
         nthreads = os.cpu_count() or 1
     co = opts.c()
@@ -232,8 +236,9 @@ def trace(a, y0, opts: Opts, nthreads: int | None = None, t_end=None) -> TraceRe
             n, _dp(av), _dp(te) if te is not None else None, _dp(y0), ctypes.byref(co), _dp(yend),
             status.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
             att.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-            ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(nthreads))
-    return TraceResult(yend, status, att, ev)
+            ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            _dp(cr) if cr is not None else None, int(nthreads))
+    return TraceResult(yend, status, att, ev, cr)
 
 
 def ill_conditioned(a, y0, opts: Opts, ref: TraceResult | None = None,

@@ -353,7 +353,8 @@ static int launch_integration(kerr_ctx *c, const TraceParams &P, int prec, int v
 static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k0,
                         const double *t_end_each, int64_t n,
                         const CamDev *cams_host, int32_t ncam, const kerr_opts *o, double *x_out,
-                        double *k_out, int32_t *status, int32_t *steps, float *diag, void *stream)
+                        double *k_out, int32_t *status, int32_t *steps, float *diag, float *cross,
+                        void *stream)
 {
     if (!c)
         return fail(KERR_EINVAL, "context is NULL");
@@ -440,6 +441,7 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
     P.status = status;
     P.steps = steps;
     P.diag = diag;
+    P.cross = cross;
     if (mode != MODE_CAMERA) {
         if (!is_device_ptr(x0))
             st.push_back({x0, (void **)&P.x0, 4 * nn * sizeof(double), true, 0});
@@ -458,6 +460,8 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
         st.push_back({steps, (void **)&P.steps, nn * sizeof(int32_t), false, 0});
     if (diag && !is_device_ptr(diag))
         st.push_back({diag, (void **)&P.diag, 4 * nn * sizeof(float), false, 0});
+    if (cross && !is_device_ptr(cross))
+        st.push_back({cross, (void **)&P.cross, 5 * nn * sizeof(float), false, 0});
     size_t total = 0;
     for (auto &s : st) {
         s.off = total;
@@ -525,19 +529,19 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
 
 extern "C" int kerr_trace_rays(kerr_ctx *c, const double *x0, const double *k0, int64_t n,
                                const kerr_opts *o, double *x_out, double *k_out, int32_t *status,
-                               int32_t *steps, float *diag, void *stream)
+                               int32_t *steps, float *diag, float *cross, void *stream)
 {
-    return trace_common(c, MODE_RAYS, x0, k0, nullptr, n, nullptr, 0, o, x_out, k_out, status, steps, diag,
-                        stream);
+    return trace_common(c, MODE_RAYS, x0, k0, nullptr, n, nullptr, 0, o, x_out, k_out, status,
+                        steps, diag, cross, stream);
 }
 
 extern "C" int kerr_trace_particles(kerr_ctx *c, const double *x0, const double *v0,
                                     const double *t_end, int64_t n, const kerr_opts *o,
                                     double *x_out, double *k_out, int32_t *status, int32_t *steps,
-                                    float *diag, void *stream)
+                                    float *diag, float *cross, void *stream)
 {
-    return trace_common(c, MODE_PARTICLES, x0, v0, t_end, n, nullptr, 0, o, x_out, k_out, status, steps,
-                        diag, stream);
+    return trace_common(c, MODE_PARTICLES, x0, v0, t_end, n, nullptr, 0, o, x_out, k_out, status,
+                        steps, diag, cross, stream);
 }
 
 static int build_cams(const kerr_camera *cams, int32_t ncam, std::vector<CamDev> &out, int64_t &n)
@@ -565,15 +569,15 @@ static int build_cams(const kerr_camera *cams, int32_t ncam, std::vector<CamDev>
 
 extern "C" int kerr_trace_camera(kerr_ctx *c, const kerr_camera *cams, int32_t ncam,
                                  const kerr_opts *o, double *x_out, double *k_out, int32_t *status,
-                                 int32_t *steps, float *diag, void *stream)
+                                 int32_t *steps, float *diag, float *cross, void *stream)
 {
     std::vector<CamDev> cd;
     int64_t n = 0;
     int rc = build_cams(cams, ncam, cd, n);
     if (rc)
         return rc;
-    return trace_common(c, MODE_CAMERA, nullptr, nullptr, nullptr, n, cd.data(), ncam, o, x_out, k_out,
-                        status, steps, diag, stream);
+    return trace_common(c, MODE_CAMERA, nullptr, nullptr, nullptr, n, cd.data(), ncam, o, x_out,
+                        k_out, status, steps, diag, cross, stream);
 }
 
 extern "C" int kerr_get_stats(kerr_ctx *c, kerr_stats *out)
@@ -653,7 +657,7 @@ extern "C" int kerr_autotune(kerr_ctx *c, const kerr_camera *cam, const kerr_opt
         oo.variant = v;
         float ms_min = 1e30f;
         for (int rep = 0; rep < 3 && rc == KERR_OK; ++rep) {
-            rc = kerr_trace_camera(c, &sub, 1, &oo, xo, ko, so, no, nullptr, stream);
+            rc = kerr_trace_camera(c, &sub, 1, &oo, xo, ko, so, no, nullptr, nullptr, stream);
             if (rc)
                 break;
             kerr_stats s;

@@ -92,7 +92,7 @@ int scratch_ptr(int dev, char **out)
 extern "C" int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam,
                                         const kerr_opts *o, double *x_out, double *k_out,
                                         int32_t *status, int32_t *steps, float *diag,
-                                        void *stream)
+                                        float *cross, void *stream)
 {
     if (!cams || ncam < 1 || ncam > kMaxCams)
         return fail(KERR_EINVAL, "kerr_trace_camera_static: need 1..KERR_STATIC_MAX_CAMERAS cameras");
@@ -121,7 +121,8 @@ extern "C" int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam,
         return fail(KERR_EINVAL, "kerr_trace_camera_static: more rays than "
                                  "KERR_STATIC_MAX_GEODESICS; use kerr_trace_camera");
     if (!is_device_ptr(x_out) || !is_device_ptr(k_out) || !is_device_ptr(status) ||
-        !is_device_ptr(steps) || (diag && !is_device_ptr(diag)))
+        !is_device_ptr(steps) || (diag && !is_device_ptr(diag)) ||
+        (cross && !is_device_ptr(cross)))
         return fail(KERR_EINVAL, "kerr_trace_camera_static: outputs must be device memory "
                                  "(host buffers would need staging allocations)");
     int dev = 0;
@@ -164,6 +165,7 @@ extern "C" int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam,
     P.status = status;
     P.steps = steps;
     P.diag = diag;
+    P.cross = cross;
     P.tol = o->tol;
     P.h0 = o->h0;
     P.max_steps = o->max_steps;

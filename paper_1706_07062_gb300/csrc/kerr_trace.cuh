@@ -76,7 +76,8 @@ enum : int {
     KC_TENDLO = 5,  // end time, low part
     KC_U2 = 6,      // initial g k k (renormalisation target)
     KC_FLAGS = 7,   // bit 0: end time in use; bit 1: initial sign of t - t_end
-    KC_COUNT = 8
+    KC_XI = 8,      // L_z / E of the start state (redshift label)
+    KC_COUNT = 9
 };
 
 struct TraceParams {
@@ -91,6 +92,7 @@ struct TraceParams {
     double *x_out, *k_out;      // [4][n]
     int32_t *status, *steps;    // [n]
     float *diag;                // [4][n] or null
+    float *cross;               // [5][n] equatorial-crossing labels or null
     double tol, h0;
     int64_t max_steps;
     double r_escape, t_end, fp64_zone;
@@ -117,6 +119,7 @@ struct RayConst {
     double zone_r;   // FP64 zone radius (FP32 path)
     double tend;     // end time (only if use_t)
     double u2_0;     // initial g k k (renormalisation target)
+    double xi;       // L_z / E of the start state
     int use_t;
     int tpos;        // initial sign of t - t_end
     // FP32 copies, so that the FP32 loop issues no FP64 conversions;
@@ -287,34 +290,32 @@ __device__ __forceinline__ void add_incr(T &y, T &c, T d)
     }
 }
 
-// Event value on a state (y, c): r - target (kind 0) or t - (target +
-// target_lo) (kind 1; target_lo is the low part of a float-pair end time).
+// Event value on a state (y, c): r - target (kind 0), t - (target +
+// target_lo) (kind 1; target_lo is the low part of a float-pair end time),
+// or z (kind 2, equatorial crossings).
 template <bool KAHAN, typename T>
 __device__ __forceinline__ T event_value(int kind, T a2, const T y[8], const T c[8], T target,
                                          T target_lo)
 {
     if (kind == 0)
         return ks_r(a2, y[1], y[2], y[3]) - target;
+    if (kind == 2)
+        return KAHAN ? y[3] + c[3] : y[3];
     return KAHAN ? ((y[0] - target) + c[0]) - target_lo : y[0] - target;
 }
 
 // Clip an accepted step onto an event surface (Illinois regula falsi on the
 // step length eta in (0, h), Phi(eta) = two RK4 half steps from the last
-// accepted state).  (y, c) is the last accepted state; on return it holds the
-// end point.  Bracket values s_lo = s(y_old) and s_hi = s(y_new).
+// accepted state (y, c)).  Writes the state on the surface to (ye, ce) and
+// returns its step length.  Bracket values s_lo = s(y_old), s_hi = s(y_new).
 template <bool KAHAN, typename T>
-__device__ void clip(const T a, const T a2, T y[8], T c[8], const T A0[4], const T h, int kind,
-                     T target, T target_lo, T s_lo, T s_hi, T stol, T eps, int maxit,
-                     uint32_t &nrhs)
+__device__ T clip(const T a, const T a2, const T y[8], const T c[8], const T A0[4], const T h,
+                  int kind, T target, T target_lo, T s_lo, T s_hi, T stol, T eps, int maxit,
+                  T ye[8], T ce[8], uint32_t &nrhs)
 {
     T lo = T(0), hi = h;
+    T eta_out = h;
     int side = 0;
-    T ye[8], ce[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        ye[i] = y[i];
-        ce[i] = c[i];
-    }
     T d[8];
     for (int it = 0; it < maxit; ++it) {
         T eta = hi - s_hi * (hi - lo) / (s_hi - s_lo);
@@ -328,6 +329,7 @@ __device__ void clip(const T a, const T a2, T y[8], T c[8], const T A0[4], const
             ce[i] = c[i];
             add_incr<KAHAN>(ye[i], ce[i], d[i]);
         }
+        eta_out = eta;
         const T s = event_value<KAHAN>(kind, a2, ye, ce, target, target_lo);
         if (fabs(s) <= stol)
             break;
@@ -347,24 +349,31 @@ __device__ void clip(const T a, const T a2, T y[8], T c[8], const T A0[4], const
         if (hi - lo <= eps * h)
             break;
     }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        y[i] = ye[i];
-        c[i] = ce[i];
-    }
+    return eta_out;
 }
+
+__device__ __forceinline__ float k_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double k_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float k_atan2(dfloat y, dfloat x) { return atan2f(y.hi, x.hi); }
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(double x) { return (float)x; }
+__device__ __forceinline__ float to_f(dfloat x) { return x.hi; }
 
 // Clipping tolerances per number type: |s| <= stol * scale, bracket eps * h.
 template <typename T> struct Prec;
+// ztol: equatorial-crossing root-find (z = 0 has no natural scale of its own).
 template <> struct Prec<float> {
+    static __device__ __forceinline__ float ztol() { return 6e-8f; }
     static __device__ __forceinline__ float stol() { return 2e-6f; }
     static __device__ __forceinline__ float eps() { return 1e-7f; }
 };
 template <> struct Prec<double> {
+    static __device__ __forceinline__ double ztol() { return 1e-12; }
     static __device__ __forceinline__ double stol() { return 1e-12; }
     static __device__ __forceinline__ double eps() { return 1e-15; }
 };
 template <> struct Prec<dfloat> {
+    static __device__ __forceinline__ dfloat ztol() { return dfloat(1e-12); }
     static __device__ __forceinline__ dfloat stol() { return dfloat(1e-12); }
     static __device__ __forceinline__ dfloat eps() { return dfloat(1e-13); }
 };
@@ -380,9 +389,9 @@ template <> __device__ __forceinline__ dfloat from_d<dfloat>(double d) { return 
 // step; rn receives r of the new state when a step is accepted.  Returns a
 // status code when the geodesic terminates, ST_NONE otherwise.
 template <bool KAHAN, typename T>
-__device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &P, const T tol,
-                                         T y[8], T c[8], T &h, T &rn, uint32_t &nrhs,
-                                         uint32_t &nacc, int &since_renorm)
+__device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &P, int64_t id,
+                                         const T tol, T y[8], T c[8], T &h, T &rn,
+                                         uint32_t &nrhs, uint32_t &nacc, int &since_renorm)
 {
     const T a = RC<T>::a(rc);
     const T a2 = a * a;
@@ -415,38 +424,58 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
         return ST_NONFINITE;
     }
     rn = ks_r(a2, yn[1], yn[2], yn[3]);
+    // termination: (yn, cn) becomes the end point of the step, clipped onto
+    // the surface when an event fires; h_used is its step length
     const T rcap = RC<T>::rcap(rc);
+    const T resc = RC<T>::resc(rc);
     const int maxit = P.clip_maxit;
+    int st = ST_NONE;
+    T h_used = h;
     if (rn < rcap) {
         const T s_lo = event_value<KAHAN>(0, a2, y, c, rcap, T(0));
-        clip<KAHAN>(a, a2, y, c, A0, h, 0, rcap, T(0), s_lo, rn - rcap, Prec<T>::stol() * rcap,
-                    Prec<T>::eps(), maxit, nrhs);
-        return ST_CAPTURED;
-    }
-    const T resc = RC<T>::resc(rc);
-    if (rn > resc && k_fma(yn[1], yn[5], k_fma(yn[2], yn[6], yn[3] * yn[7])) > T(0)) {
+        h_used = clip<KAHAN>(a, a2, y, c, A0, h, 0, rcap, T(0), s_lo, rn - rcap,
+                             Prec<T>::stol() * rcap, Prec<T>::eps(), maxit, yn, cn, nrhs);
+        st = ST_CAPTURED;
+    } else if (rn > resc && k_fma(yn[1], yn[5], k_fma(yn[2], yn[6], yn[3] * yn[7])) > T(0)) {
         const T s_lo = event_value<KAHAN>(0, a2, y, c, resc, T(0));
-        if (s_lo <= T(0)) {
-            clip<KAHAN>(a, a2, y, c, A0, h, 0, resc, T(0), s_lo, rn - resc,
-                        Prec<T>::stol() * resc, Prec<T>::eps(), maxit, nrhs);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                y[i] = yn[i];
-                c[i] = cn[i];
-            }
-        }
-        return ST_ESCAPED;
-    }
-    if (rc.use_t) {
+        if (s_lo <= T(0))
+            h_used = clip<KAHAN>(a, a2, y, c, A0, h, 0, resc, T(0), s_lo, rn - resc,
+                                 Prec<T>::stol() * resc, Prec<T>::eps(), maxit, yn, cn, nrhs);
+        st = ST_ESCAPED;
+    } else if (rc.use_t) {
         const T tend = RC<T>::tend(rc), tlo = RC<T>::tendlo(rc);
         const T s_hi = event_value<KAHAN>(1, a2, yn, cn, tend, tlo);
         if ((s_hi > T(0)) != (rc.tpos != 0)) {
             const T s_lo = event_value<KAHAN>(1, a2, y, c, tend, tlo);
             const T sc = fmax(T(1), fabs(tend));
-            clip<KAHAN>(a, a2, y, c, A0, h, 1, tend, tlo, s_lo, s_hi, Prec<T>::stol() * sc,
-                        Prec<T>::eps(), maxit, nrhs);
-            return ST_ENDTIME;
+            h_used = clip<KAHAN>(a, a2, y, c, A0, h, 1, tend, tlo, s_lo, s_hi,
+                                 Prec<T>::stol() * sc, Prec<T>::eps(), maxit, yn, cn, nrhs);
+            st = ST_ENDTIME;
+        }
+    }
+    // equatorial crossings within [y, end point]
+    if (P.cross) {
+        const T z0 = y[3], z1 = yn[3];
+        if ((z0 > T(0) && !(z1 > T(0))) || (z0 < T(0) && !(z1 < T(0)))) {
+            const int64_t n = P.n;
+            const int slot = isnan(P.cross[id]) ? 0 : (isnan(P.cross[2 * n + id]) ? 1 : 2);
+            if (slot < 2) {
+                T yc[8], cc[8];
+                // scale of z at the crossing: the nearer end of the step
+                const T r0 = ks_r(a2, y[1], y[2], y[3]);
+                const T r1 = ks_r(a2, yn[1], yn[2], yn[3]);
+                clip<KAHAN>(a, a2, y, c, A0, h_used, 2, T(0), T(0), z0, z1,
+                            Prec<T>::ztol() * (T(1) + fmin(r0, r1)), Prec<T>::eps(), maxit, yc,
+                            cc, nrhs);
+                const T rcx = ks_r(a2, yc[1], yc[2], yc[3]);
+                float ph = k_atan2(yc[2], yc[1]) - k_atan2(a, rcx);
+                if (ph <= -3.14159265f)
+                    ph += 6.28318531f;
+                else if (ph > 3.14159265f)
+                    ph -= 6.28318531f;
+                P.cross[(2 * slot) * n + id] = to_f(rcx);
+                P.cross[(2 * slot + 1) * n + id] = ph;
+            }
         }
     }
 #pragma unroll
@@ -454,6 +483,8 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
         y[i] = yn[i];
         c[i] = cn[i];
     }
+    if (st != ST_NONE)
+        return st;
     if (P.renorm_every > 0 && ++since_renorm >= P.renorm_every) {
         since_renorm = 0;
         double k[4];
@@ -554,9 +585,15 @@ __device__ __forceinline__ int init_geodesic(const TraceParams &P, int64_t id, d
         st = ST_NONFINITE;
     const double r0 = finite ? ks_r(a * a, y[1], y[2], y[3]) : 0.0;
     rc.resc = P.r_escape > 0.0 ? P.r_escape : (P.r_escape == 0.0 ? r0 : INFINITY);
+    rc.xi = 0.0;
     if (st == ST_NONE) {
         const KSPoint kp = ks_point(a, y[1], y[2], y[3]);
         rc.u2_0 = norm2(kp, y + 4);
+        // E = -p_t and L_z = x p_y - y p_x with p = eta k + f l (l.k)
+        const double L = y[4] + kp.lx * y[5] + kp.ly * y[6] + kp.lz * y[7];
+        const double E = y[4] - kp.f * L;
+        const double Lz = y[1] * (y[6] + kp.f * kp.ly * L) - y[2] * (y[5] + kp.f * kp.lx * L);
+        rc.xi = Lz / E;
         if (r0 < rc.rcap)
             st = ST_CAPTURED;
     }
@@ -564,9 +601,42 @@ __device__ __forceinline__ int init_geodesic(const TraceParams &P, int64_t id, d
     return st;
 }
 
-__device__ __forceinline__ void write_out(const TraceParams &P, int64_t id, const double y[8],
-                                          int st, uint32_t nsteps, double a)
+// Prograde ISCO radius (Bardeen, Press & Teukolsky 1972).
+__device__ __forceinline__ double r_isco(double a)
 {
+    const double z1 = 1.0 + cbrt(1.0 - a * a) * (cbrt(1.0 + a) + cbrt(1.0 - a));
+    const double z2 = sqrt(3.0 * a * a + z1 * z1);
+    return 3.0 + z2 - sqrt((3.0 - z1) * (3.0 + z1 + 2.0 * z2));
+}
+
+// Redshift of a prograde Keplerian emitter at radius r seen along a ray with
+// xi = L_z / E: g = 1 / (u^t (1 - Omega xi)), Omega = 1/(r^{3/2} + a),
+// u^t = (r^{3/2} + a) / (r^{3/4} sqrt(r^{3/2} - 3 r^{1/2} + 2a)); NaN inside
+// the ISCO or for a missing crossing.
+__device__ __forceinline__ float redshift_label(double a, double r, double xi)
+{
+    if (!(r >= r_isco(a)))
+        return __int_as_float(0x7fc00000);
+    const double s = sqrt(r), r32 = r * s;
+    const double ut = (r32 + a) / (sqrt(s) * s * sqrt(r32 - 3.0 * s + 2.0 * a));
+    const double Om = 1.0 / (r32 + a);
+    return (float)(1.0 / (ut * (1.0 - Om * xi)));
+}
+
+__device__ __forceinline__ void clear_cross(const TraceParams &P, int64_t id)
+{
+    if (P.cross) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j)
+            P.cross[j * P.n + id] = __int_as_float(0x7fc00000);
+    }
+}
+
+__device__ __forceinline__ void write_out(const TraceParams &P, int64_t id, const double y[8],
+                                          int st, uint32_t nsteps, double a, double xi)
+{
+    if (P.cross)
+        P.cross[4 * P.n + id] = redshift_label(a, (double)P.cross[id], xi);
     const int64_t n = P.n;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -613,7 +683,7 @@ struct ZoneResult {
 };
 
 static __device__ __noinline__ ZoneResult zone_step(const RayConst rc, const TraceParams &P,
-                                                    LaneF s, int since_renorm)
+                                                    int64_t id, LaneF s, int since_renorm)
 {
     double yd[8], cd[8];
 #pragma unroll
@@ -625,7 +695,8 @@ static __device__ __noinline__ ZoneResult zone_step(const RayConst rc, const Tra
     ZoneResult R;
     R.nrhs = 0;
     R.nacc = 0;
-    R.st = step_once<false, double>(rc, P, P.tol, yd, cd, hd, rd, R.nrhs, R.nacc, since_renorm);
+    R.st = step_once<false, double>(rc, P, id, P.tol, yd, cd, hd, rd, R.nrhs, R.nacc,
+                                    since_renorm);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         R.s.y[i] = (float)yd[i];
@@ -640,7 +711,7 @@ static __device__ __noinline__ ZoneResult zone_step(const RayConst rc, const Tra
 // The same step in float-float arithmetic: the compensated pair (y, c) is
 // already a float-float number, so no FP64 instruction is needed.
 static __device__ __noinline__ ZoneResult zone_step_df(const RayConst rc, const TraceParams &P,
-                                                       LaneF s, int since_renorm)
+                                                       int64_t id, LaneF s, int since_renorm)
 {
     dfloat yd[8], cd[8];
 #pragma unroll
@@ -652,7 +723,8 @@ static __device__ __noinline__ ZoneResult zone_step_df(const RayConst rc, const 
     ZoneResult R;
     R.nrhs = 0;
     R.nacc = 0;
-    R.st = step_once<false, dfloat>(rc, P, dfloat((float)P.tol), yd, cd, hd, rd, R.nrhs, R.nacc,
+    R.st = step_once<false, dfloat>(rc, P, id, dfloat((float)P.tol), yd, cd, hd, rd, R.nrhs,
+                                    R.nacc,
                                     since_renorm);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -765,10 +837,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f64_kernel(const TraceParam
                 if (my < n_items) {
                     id = (int64_t)my;
                     const int st0 = init_geodesic(P, id, y, rc);
+                    clear_cross(P, id);
                     ++C.geo;
                     if (st0 != ST_NONE || timed_out) {
                         const int st = st0 != ST_NONE ? st0 : ST_TIMEOUT;
-                        write_out(P, id, y, st, 0, rc.a);
+                        write_out(P, id, y, st, 0, rc.a, rc.xi);
                         C.status(st);
                     } else {
 #pragma unroll
@@ -798,11 +871,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f64_kernel(const TraceParam
                 ++C.att;
                 ++C.att64;
                 uint32_t r = 0;
-                st = step_once<false, double>(rc, P, P.tol, y, c, h, rnow, r, C.acc, since_renorm);
+                st = step_once<false, double>(rc, P, id, P.tol, y, c, h, rnow, r, C.acc,
+                                              since_renorm);
                 C.rhs64 += r;
             }
             if (st != ST_NONE) {
-                write_out(P, id, y, st, nsteps, rc.a);
+                write_out(P, id, y, st, nsteps, rc.a, rc.xi);
                 C.status(st);
                 has = false;
             }
@@ -852,6 +926,8 @@ static __global__ void __launch_bounds__(256) f32_setup_kernel(const TraceParams
         P.s_const[KC_TENDLO * n + id] = rc.tendlo;
         P.s_const[KC_U2 * n + id] = (float)rc.u2_0;
         P.s_const[KC_FLAGS * n + id] = __int_as_float((rc.use_t ? 1 : 0) | (rc.tpos ? 2 : 0));
+        P.s_const[KC_XI * n + id] = (float)rc.xi;
+        clear_cross(P, id);
         P.status[id] = st0;
         P.steps[id] = 0;
         if (st0 != ST_NONE)
@@ -875,6 +951,9 @@ static __global__ void __launch_bounds__(256) f32_finish_kernel(const TraceParam
             P.x_out[j * n + id] = y[j];
             P.k_out[j * n + id] = y[4 + j];
         }
+        if (P.cross)
+            P.cross[4 * n + id] = redshift_label(geodesic_spin(P, id), (double)P.cross[id],
+                                                 (double)P.s_const[KC_XI * n + id]);
         if (P.diag) {
             const int st = P.status[id];
             float cst[4];
@@ -1065,9 +1144,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     ls.rnow = rnow;
                     ZoneResult R;
                     if (PHASE == 2 || (PHASE == 0 && P.zone_df))
-                        R = zone_step_df(rc, P, ls, since_renorm);
+                        R = zone_step_df(rc, P, id, ls, since_renorm);
                     else
-                        R = zone_step(rc, P, ls, since_renorm);
+                        R = zone_step(rc, P, id, ls, since_renorm);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         y[i] = R.s.y[i];
@@ -1082,7 +1161,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     ++C.att64;
                 } else {
                     uint32_t r = 0;
-                    st = step_once<true, float>(rc, P, tol, y, c, h, rnow, r, C.acc,
+                    st = step_once<true, float>(rc, P, id, tol, y, c, h, rnow, r, C.acc,
                                                 since_renorm);
                     C.rhs32 += r;
                 }

@@ -46,41 +46,19 @@ static cudaError_t launch_one(const TraceParams &P, int sms, cudaStream_t s, boo
     return cudaGetLastError();
 }
 
+// Variants 0-2 are compiled here, 3-5 in kerr_trace_f32b.cu (in parallel).
+cudaError_t launch_trace_f32_hi(const TraceParams &P, int v, int sms, cudaStream_t s);
+
 cudaError_t launch_trace_f32(const TraceParams &P, int v, int sms, cudaStream_t s)
 {
     switch (v) {
 #define KERR_CASE(i, b, m) \
     case i:                \
         return launch_one<0, b, m>(P, sms, s, true);
-        KERR_VARIANT_LIST(KERR_CASE)
+        KERR_VARIANT_LIST_LO(KERR_CASE)
 #undef KERR_CASE
     default:
-        return cudaErrorInvalidValue;
-    }
-}
-
-// The FP64-zone phase: continues the geodesics deferred by the FP32 phase
-// (float-float zone steps use one launch shape: their register demand leaves
-// no room to choose).
-// Its item count lives on the device, so the grid is fixed by the launch
-// shape (blocks per SM x SMs); threads with nothing to do exit at once.
-template <int PH, int B, int BPS>
-static cudaError_t launch_zone(const TraceParams &P, int sms, cudaStream_t s)
-{
-    trace_f32_kernel<PH, B, BPS><<<(unsigned)(BPS * sms), B, 0, s>>>(P);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_zone_phase(const TraceParams &P, int zv, int sms, cudaStream_t s)
-{
-    switch (zv) {
-#define KERR_ZCASE(i, b, m)                                                            \
-    case i:                                                                            \
-        return P.zone_df ? launch_zone<2, 128, 2>(P, sms, s) : launch_zone<1, b, m>(P, sms, s);
-        KERR_ZONE_VARIANT_LIST(KERR_ZCASE)
-#undef KERR_ZCASE
-    default:
-        return cudaErrorInvalidValue;
+        return launch_trace_f32_hi(P, v, sms, s);
     }
 }
 

@@ -1,0 +1,34 @@
+// FP32 path, zone phase: continues the geodesics that the FP32 stepping
+// phase deferred to the FP64 zone (its own translation unit so that it
+// compiles in parallel with the stepping kernels).
+#include "kerr_trace.cuh"
+#include "kerr_variants.h"
+
+namespace kerr {
+
+// The FP64-zone phase: continues the geodesics deferred by the FP32 phase
+// (float-float zone steps use one launch shape: their register demand leaves
+// no room to choose).
+// Its item count lives on the device, so the grid is fixed by the launch
+// shape (blocks per SM x SMs); threads with nothing to do exit at once.
+template <int PH, int B, int BPS>
+static cudaError_t launch_zone(const TraceParams &P, int sms, cudaStream_t s)
+{
+    trace_f32_kernel<PH, B, BPS><<<(unsigned)(BPS * sms), B, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zone_phase(const TraceParams &P, int zv, int sms, cudaStream_t s)
+{
+    switch (zv) {
+#define KERR_ZCASE(i, b, m)                                                            \
+    case i:                                                                            \
+        return P.zone_df ? launch_zone<2, 128, 2>(P, sms, s) : launch_zone<1, b, m>(P, sms, s);
+        KERR_ZONE_VARIANT_LIST(KERR_ZCASE)
+#undef KERR_ZCASE
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+} // namespace kerr

@@ -9,7 +9,9 @@ struct Variant {
     int block, min_blocks;
 };
 
-#define KERR_VARIANT_LIST(X) X(0, 128, 4) X(1, 128, 3) X(2, 256, 2) X(3, 128, 2) X(4, 64, 8) X(5, 128, 5)
+#define KERR_VARIANT_LIST_LO(X) X(0, 128, 4) X(1, 128, 3) X(2, 256, 2)
+#define KERR_VARIANT_LIST_HI(X) X(3, 128, 2) X(4, 64, 8) X(5, 128, 5)
+#define KERR_VARIANT_LIST(X) KERR_VARIANT_LIST_LO(X) KERR_VARIANT_LIST_HI(X)
 
 constexpr int kNumVariants = 6;
 constexpr Variant kVariants[kNumVariants] = {{128, 4}, {128, 3}, {256, 2}, {128, 2}, {64, 8}, {128, 5}};

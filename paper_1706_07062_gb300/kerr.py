@@ -84,14 +84,14 @@ def lib():
         L.kerr_opts_default.restype = None
         L.kerr_init.argtypes = [c.c_double, c.POINTER(vp)]
         L.kerr_destroy.argtypes = [vp]
-        trace_args = [vp, vp, vp, i64, c.POINTER(Opts), vp, vp, vp, vp, vp, vp]
-        L.kerr_trace_rays.argtypes = trace_args
+        L.kerr_trace_rays.argtypes = [vp, vp, vp, i64, c.POINTER(Opts), vp, vp, vp, vp, vp, vp,
+                                      vp]
         L.kerr_trace_particles.argtypes = [vp, vp, vp, vp, i64, c.POINTER(Opts), vp, vp, vp, vp,
-                                           vp, vp]
+                                           vp, vp, vp]
         L.kerr_trace_camera.argtypes = [vp, c.POINTER(Camera), i32, c.POINTER(Opts), vp, vp, vp,
-                                        vp, vp, vp]
+                                        vp, vp, vp, vp]
         L.kerr_trace_camera_static.argtypes = [c.POINTER(Camera), i32, c.POINTER(Opts), vp, vp,
-                                               vp, vp, vp, vp]
+                                               vp, vp, vp, vp, vp]
         L.kerr_get_stats.argtypes = [vp, c.POINTER(Stats)]
         L.kerr_num_variants.argtypes = []
         L.kerr_variant_info.argtypes = [c.c_int, c.POINTER(i32), c.POINTER(i32)]
@@ -162,18 +162,21 @@ class TraceOut:
     status: object   # (n,) int32
     steps: object    # (n,) int32 attempted steps
     diag: object     # (4, n) float32 (E, L_z, Q, u^2) or None
+    cross: object = None   # (5, n) float32 (r1, phi1, r2, phi2, g1) or None
 
     @property
     def n(self) -> int:
         return int(self.status.shape[0])
 
 
-def alloc_out(n: int, device=None, diag: bool = True, pinned: bool = False) -> TraceOut:
+def alloc_out(n: int, device=None, diag: bool = True, pinned: bool = False,
+              cross: bool = False) -> TraceOut:
     """Output buffers: torch tensors on `device` (a CUDA device, or "cpu" with
     optional pinned memory), or numpy arrays when device is None."""
     if device is None:
         return TraceOut(np.empty((4, n)), np.empty((4, n)), np.empty(n, np.int32),
-                        np.empty(n, np.int32), np.empty((4, n), np.float32) if diag else None)
+                        np.empty(n, np.int32), np.empty((4, n), np.float32) if diag else None,
+                        np.empty((5, n), np.float32) if cross else None)
     import torch
     kw = dict(device=device)
     if pinned:
@@ -182,7 +185,8 @@ def alloc_out(n: int, device=None, diag: bool = True, pinned: bool = False) -> T
                     torch.empty((4, n), dtype=torch.float64, **kw),
                     torch.empty(n, dtype=torch.int32, **kw),
                     torch.empty(n, dtype=torch.int32, **kw),
-                    torch.empty((4, n), dtype=torch.float32, **kw) if diag else None)
+                    torch.empty((4, n), dtype=torch.float32, **kw) if diag else None,
+                    torch.empty((5, n), dtype=torch.float32, **kw) if cross else None)
 
 
 # ---------------------------------------------------------------------------
@@ -227,7 +231,7 @@ def kerr_trace_rays(ctx: Context, x0, k0, opts: Opts | None = None, out: TraceOu
         out = alloc_out(n, x0.device if hasattr(x0, "device") else None)
     _check(lib().kerr_trace_rays(ctx.handle, _ptr(x0), _ptr(k0), n, ctypes.byref(opts),
                                  _ptr(out.x), _ptr(out.k), _ptr(out.status), _ptr(out.steps),
-                                 _ptr(out.diag), _stream_ptr(stream, x0, out.x)),
+                                 _ptr(out.diag), _ptr(out.cross), _stream_ptr(stream, x0, out.x)),
            "kerr_trace_rays")
     return out
 
@@ -245,7 +249,7 @@ def kerr_trace_particles(ctx: Context, x0, v0, t_end=None, opts: Opts | None = N
     _check(lib().kerr_trace_particles(ctx.handle, _ptr(x0), _ptr(v0), _ptr(t_end), n,
                                       ctypes.byref(opts),
                                       _ptr(out.x), _ptr(out.k), _ptr(out.status),
-                                      _ptr(out.steps), _ptr(out.diag),
+                                      _ptr(out.steps), _ptr(out.diag), _ptr(out.cross),
                                       _stream_ptr(stream, x0, out.x)),
            "kerr_trace_particles")
     return out
@@ -266,7 +270,7 @@ def kerr_trace_camera(ctx: Context, cams, opts: Opts | None = None, out: TraceOu
         out = alloc_out(n, device)
     _check(lib().kerr_trace_camera(ctx.handle, arr, len(cams), ctypes.byref(opts), _ptr(out.x),
                                    _ptr(out.k), _ptr(out.status), _ptr(out.steps),
-                                   _ptr(out.diag), _stream_ptr(stream, out.x)),
+                                   _ptr(out.diag), _ptr(out.cross), _stream_ptr(stream, out.x)),
            "kerr_trace_camera")
     return out
 
@@ -288,7 +292,8 @@ def kerr_trace_camera_static(cams, opts: Opts | None = None, out: TraceOut | Non
         out = alloc_out(n, device)
     _check(lib().kerr_trace_camera_static(arr, len(cams), ctypes.byref(opts), _ptr(out.x),
                                           _ptr(out.k), _ptr(out.status), _ptr(out.steps),
-                                          _ptr(out.diag), _stream_ptr(stream, out.x)),
+                                          _ptr(out.diag), _ptr(out.cross),
+                                          _stream_ptr(stream, out.x)),
            "kerr_trace_camera_static")
     return out
 

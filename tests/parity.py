@@ -67,3 +67,33 @@ def compare(name, a, y0, opts, out, idx, gate, fp32, ref=None, max_bad_frac=0.0,
                    median_err=float(np.median(e)), over_gate=int(over.sum()))
     assert frac <= max_bad_frac, f"{name}: {summary}"
     return summary
+
+
+def label_flags(a, y0, opts: O.Opts, ref: O.TraceResult, gate: float, fp32: bool = True):
+    """Crossing labels not determined to `gate` by the integration: a label
+    (r, phi or g of either crossing) is ill-conditioned if the oracle's own
+    value moves by more than the gate (relative for r and g, absolute for
+    phi), or appears/disappears, when the start position is perturbed by
+    1e-6 relative or the tolerance is tightened 100x (FP32 comparison: an
+    FP32 trajectory accumulates ~1e-6 relative rounding over its steps), or
+    when the start position is perturbed by 1e-12 (FP64 comparison, which
+    follows the oracle's step sequence).  Grazing crossings, where the ray
+    meets z = 0 at a shallow angle, turn a tiny error in z into a large one in
+    r.  Returns a (n, 5) boolean array."""
+    yp = y0.copy()
+    yp[:, 1:4] *= 1.0 + (1e-6 if fp32 else 1e-12)
+    runs = [O.trace(a, yp, opts, crossings=True)]
+    if fp32:
+        runs.append(O.trace(a, y0, O.Opts(**{**opts.__dict__, "tol": opts.tol / 100.0}),
+                            crossings=True))
+    bad = np.zeros(ref.cross.shape, dtype=bool)
+    rc = ref.cross
+    for r in runs:
+        c = r.cross
+        bad |= np.isnan(c) != np.isnan(rc)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            d = np.abs(c - rc)
+            d[:, [0, 2, 4]] /= np.abs(rc[:, [0, 2, 4]])
+            d[:, [1, 3]] = np.abs((c[:, [1, 3]] - rc[:, [1, 3]] + np.pi) % (2 * np.pi) - np.pi)
+        bad |= np.nan_to_num(d, nan=0.0) > gate
+    return bad

@@ -589,3 +589,79 @@ def test_time_surface_for_particles():
     res = O.trace(a, y0[None], O.Opts(tol=1e-10, r_escape=-1.0, t_end=500.0))
     assert res.status[0] == O.ENDTIME
     assert abs(res.y[0, 0] - 500.0) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# equatorial-crossing labels (the surrogate's targets)
+# ---------------------------------------------------------------------------
+def test_crossing_labels_schwarzschild_face_on():
+    """a = 0, face-on camera: every orbital plane contains the z axis, so the
+    first equatorial crossing is where the in-plane angle, measured from the
+    z axis, reaches pi/2.  With u = 1/r and b = L/E from the start state,
+    phi(u) = phi0 + int_{u0}^{u} du / sqrt(1/b^2 - u^2 + 2u^3) (inward branch)
+    gives r1 by quadrature; a prograde Keplerian emitter there has
+    g = sqrt(1 - 3/r1) (L_z = 0 for this camera)."""
+    from scipy import integrate, optimize
+    a, r_obs = 0.0, 1000.0
+    pts = [(6.0, 0.0), (0.0, 9.0), (-12.0, 4.0), (15.0, -15.0)]
+    y0 = np.stack([camera_ic_at(a, 0.0, r_obs, al, be) for al, be in pts])
+    res = O.trace(a, y0, O.Opts(tol=1e-11), crossings=True)
+    for j, (al, be) in enumerate(pts):
+        E, Lz, Q, u2 = O.constants(a, y0[j])
+        # total angular momentum from Carter's constant at a = 0: L^2 = Q + L_z^2
+        b = np.sqrt(Q + Lz ** 2) / abs(E)
+        u0 = 1.0 / O.ks_r(a, *y0[j, 1:4])
+        phi0 = np.arctan2(np.hypot(y0[j, 1], y0[j, 2]), y0[j, 3])
+
+        def ang(u):
+            return phi0 + integrate.quad(lambda w: 1.0 / np.sqrt(1 / b ** 2 - w * w + 2 * w ** 3),
+                                         u0, u, epsabs=1e-13, epsrel=1e-12, limit=200)[0]
+        # periastron: largest root below u where 1/b^2 - u^2 + 2u^3 = 0
+        up = optimize.brentq(lambda w: 1 / b ** 2 - w * w + 2 * w ** 3, u0, 1.0 / 3.0)
+        assert ang(up * (1 - 1e-12)) > np.pi / 2          # crosses before periastron
+        u1 = optimize.brentq(lambda w: ang(w) - np.pi / 2, u0, up * (1 - 1e-12), xtol=1e-15)
+        r1 = 1.0 / u1
+        assert res.status[j] == O.ESCAPED
+        assert abs(res.cross[j, 0] / r1 - 1) < 1e-8, (j, res.cross[j, 0], r1)
+        if r1 >= 6.0:                                   # ISCO of a = 0
+            assert abs(res.cross[j, 4] - np.sqrt(1 - 3 / r1)) < 1e-8
+        else:
+            assert np.isnan(res.cross[j, 4])
+        # azimuth: the first crossing lies on the start's side of the axis
+        wrap = lambda p: (p + np.pi) % (2 * np.pi) - np.pi
+        az = np.arctan2(y0[j, 2], y0[j, 1])
+        assert abs(wrap(res.cross[j, 1] - az)) < 1e-9
+        # second crossing: in-plane angle 3 pi / 2, on the outward branch
+        # after periastron (angle there: ang(up)), or absent if the total
+        # swept angle to infinity stays below 3 pi / 2
+        phi_p = ang(up * (1 - 1e-12))
+
+        def ang_out(u):
+            return phi_p + integrate.quad(lambda w: 1.0 / np.sqrt(1 / b ** 2 - w * w + 2 * w ** 3),
+                                          u, up * (1 - 1e-12), epsabs=1e-13, epsrel=1e-12,
+                                          limit=200)[0]
+        total = ang_out(1e-300)
+        if total > 1.5 * np.pi:
+            u2c = optimize.brentq(lambda w: ang_out(w) - 1.5 * np.pi, 1e-12, up * (1 - 1e-12),
+                                  xtol=1e-15)
+            assert abs(res.cross[j, 2] * u2c - 1) < 1e-7, (j, res.cross[j, 2], 1 / u2c)
+            assert abs(wrap(res.cross[j, 3] - az - np.pi)) < 1e-9
+        elif total < 1.5 * np.pi - 1e-3:
+            assert np.isnan(res.cross[j, 2])
+
+
+def test_crossing_labels_are_on_the_plane_and_ordered():
+    a = 0.9
+    y0 = O.camera_ic(a, np.radians(75), 1000.0, 15.0, 24, 24, np.arange(576))
+    res = O.trace(a, y0, O.Opts(tol=1e-9), crossings=True)
+    c = res.cross
+    has1 = ~np.isnan(c[:, 0])
+    has2 = ~np.isnan(c[:, 2])
+    assert has1.sum() > 400 and has2.sum() > 10
+    assert not np.any(has2 & ~has1)                     # second only after first
+    assert np.all((c[has1, 1] > -np.pi) & (c[has1, 1] <= np.pi))
+    rh = C.r_horizon(a)
+    assert np.all(c[has1, 0] > rh)
+    g_ok = ~np.isnan(c[:, 4])
+    assert np.all(c[g_ok, 0] >= C.r_isco(a) - 1e-9) and g_ok.sum() > 100
+    assert np.all(np.isnan(c[has1 & ~g_ok, 4]))
