@@ -260,6 +260,89 @@ int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam, const kerr_o
                              double *x_out, double *k_out, int32_t *status, int32_t *steps,
                              float *diag, float *cross, void *stream);
 
+/* Integrates rays from n image-plane points, each with its own camera:
+ * points[4 * i + 0..3] = (alpha, beta, spin a, inclination) as in
+ * kerr_camera (pixel (alpha, beta) of a camera at r_obs with that spin and
+ * inclination).  Outputs as for kerr_trace_rays.  Used to generate the
+ * surrogate's training rays, whose spins and inclinations vary per ray. */
+int kerr_trace_points(kerr_ctx *ctx, const double *points, int64_t n, double r_obs,
+                      const kerr_opts *opts, double *x_out, double *k_out, int32_t *status,
+                      int32_t *steps, float *diag, float *cross, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Learned surrogate (the paper has none): an MLP                            */
+/*   (alpha/s, beta/s, a, cos i) -> 4 x 256 (SiLU) -> 8 outputs             */
+/* (s = KERR_SURR_INPUT_SCALE) predicting the capture logit, the first two    */
+/* equatorial crossings as (log-radius, cos phi, sin phi) and the redshift:   */
+/*   out = (logit, (ln r1 - 2)/2, cos phi1, sin phi1, (ln r2 - 2)/2,          */
+/*          cos phi2, sin phi2, g1 - 1).                                     */
+/* Weights are BF16 in the products, FP32 master copies are trained; every    */
+/* matrix product runs on the tensor cores with FP32 accumulation.           */
+/* Parameters are one FP32 vector: for layer l = 0..4, W_l [out][in] then     */
+/* b_l [out] with padded widths in = 16, 256, 256, 256, 256 and out = 256,    */
+/* 256, 256, 256, 64 (only 4 inputs and 8 outputs are live; the padding must  */
+/* be zero).  All pointers of the surrogate calls are device memory except    */
+/* where "host" is stated.                                                    */
+/* ------------------------------------------------------------------------ */
+#define KERR_SURR_INPUT_SCALE 25.0f
+#define KERR_SURR_OUTPUTS 8
+typedef struct kerr_surrogate kerr_surrogate;
+
+/* Number of floats in the parameter vector. */
+int64_t kerr_surrogate_num_params(void);
+
+/* Creates a surrogate on the current device from host parameters `init`
+ * (kerr_surrogate_num_params() floats; initial values are the caller's --
+ * e.g. seeded random numbers). */
+int kerr_surrogate_create(const float *init, kerr_surrogate **out);
+int kerr_surrogate_destroy(kerr_surrogate *s);
+
+/* Copies the FP32 parameters (or the last computed gradient) to host. */
+int kerr_surrogate_get_params(kerr_surrogate *s, float *host_out);
+int kerr_surrogate_get_grad(kerr_surrogate *s, float *host_out);
+
+/* Network inputs and training targets from points (device, [n][4] doubles as
+ * for kerr_trace_points): in [n][4] = (alpha/s, beta/s, a, cos i); the rays
+ * are integrated (opts) with crossing labels, and targets [n][8] / masks
+ * [n][8] are filled in the output encoding above (mask 0 where a crossing or
+ * g1 is absent; the logit target is 1 for captured rays). */
+int kerr_surrogate_targets(kerr_ctx *ctx, const double *points, int64_t n, double r_obs,
+                           const kerr_opts *opts, float *in, float *targets, float *mask,
+                           void *stream);
+
+/* Forward pass: out [n][8] from in [n][4]. */
+int kerr_surrogate_forward(kerr_surrogate *s, const float *in, int64_t n, float *out,
+                           void *stream);
+
+/* Loss and gradient of one batch (kept in the surrogate; read it with
+ * kerr_surrogate_get_grad).  Loss = mean over rows of
+ *   softplus(o0) - y0 o0  +  sum_{j=1..7} m_j (o_j - y_j)^2.
+ * *loss (host) receives the value; the call synchronises `stream`. */
+int kerr_surrogate_grad(kerr_surrogate *s, const float *in, const float *targets,
+                        const float *mask, int64_t n, float *loss, void *stream);
+
+/* Trains with Adam (beta1 0.9, beta2 0.999, eps 1e-8) on n rows for `epochs`
+ * passes in order, `batch` rows per step, learning rate lr decayed by cosine
+ * to lr/20 over all steps.  loss_per_epoch (host, `epochs` floats, or NULL)
+ * receives the mean batch loss of each epoch.  Synchronises `stream`. */
+int kerr_surrogate_train(kerr_surrogate *s, const float *in, const float *targets,
+                         const float *mask, int64_t n, int32_t epochs, int32_t batch, float lr,
+                         float *loss_per_epoch, void *stream);
+
+/* Renders a camera with the surrogate: the network predicts every pixel; a
+ * pixel falls back to the integrator (opts, with crossing labels) when its
+ * capture probability lies in [p_lo, p_hi] or its image-plane distance to the
+ * Bardeen critical curve of (cam->a, cam->incl) is below crit_dist.
+ * out [6][n] planes (n = nx ny): capture probability, r1, phi1, r2, phi2, g1
+ * (integrator pixels: probability 0 or 1 and the integrator's labels;
+ * network pixels: decoded predictions, NaN where the network's own capture
+ * probability is >= 0.5 for the crossing planes).  fallback[n] (uint8, or
+ * NULL) marks integrator pixels; *n_fallback (host, or NULL) their count.
+ * Synchronises `stream`. */
+int kerr_surrogate_render(kerr_ctx *ctx, kerr_surrogate *s, const kerr_camera *cam,
+                          const kerr_opts *opts, float p_lo, float p_hi, float crit_dist,
+                          float *out, uint8_t *fallback, int64_t *n_fallback, void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *kerr_last_error(void);
 

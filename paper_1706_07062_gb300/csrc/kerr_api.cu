@@ -350,11 +350,19 @@ static int launch_integration(kerr_ctx *c, const TraceParams &P, int prec, int v
 }
 
 // Shared body of the three trace entry points.
+// Extra launch inputs of the internal callers (surrogate fallback).
+struct TraceExtra {
+    const double *points = nullptr;
+    double r_obs = 0.0;
+    const int64_t *index = nullptr;                 // device
+    const unsigned long long *n_dev = nullptr;      // device
+};
+
 static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k0,
                         const double *t_end_each, int64_t n,
                         const CamDev *cams_host, int32_t ncam, const kerr_opts *o, double *x_out,
                         double *k_out, int32_t *status, int32_t *steps, float *diag, float *cross,
-                        void *stream)
+                        void *stream, const TraceExtra &X = TraceExtra())
 {
     if (!c)
         return fail(KERR_EINVAL, "context is NULL");
@@ -367,8 +375,10 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
         return KERR_OK;
     if (!x_out || !k_out || !status || !steps)
         return fail(KERR_EINVAL, "x_out, k_out, status and steps must not be NULL");
-    if (mode != MODE_CAMERA && (!x0 || !k0))
+    if ((mode == MODE_RAYS || mode == MODE_PARTICLES) && (!x0 || !k0))
         return fail(KERR_EINVAL, "input planes must not be NULL");
+    if (mode == MODE_POINTS && !X.points)
+        return fail(KERR_EINVAL, "points must not be NULL");
     cudaStream_t us = (cudaStream_t)stream;
 
     TraceParams P;
@@ -442,7 +452,13 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
     P.steps = steps;
     P.diag = diag;
     P.cross = cross;
-    if (mode != MODE_CAMERA) {
+    P.points = X.points;
+    P.r_obs = X.r_obs;
+    P.index = X.index;
+    P.n_dev = X.n_dev;
+    if (mode == MODE_POINTS && !is_device_ptr(X.points))
+        st.push_back({X.points, (void **)&P.points, 4 * nn * sizeof(double), true, 0});
+    if (mode == MODE_RAYS || mode == MODE_PARTICLES) {
         if (!is_device_ptr(x0))
             st.push_back({x0, (void **)&P.x0, 4 * nn * sizeof(double), true, 0});
         if (!is_device_ptr(k0))
@@ -578,6 +594,40 @@ extern "C" int kerr_trace_camera(kerr_ctx *c, const kerr_camera *cams, int32_t n
         return rc;
     return trace_common(c, MODE_CAMERA, nullptr, nullptr, nullptr, n, cd.data(), ncam, o, x_out,
                         k_out, status, steps, diag, cross, stream);
+}
+
+extern "C" int kerr_trace_points(kerr_ctx *c, const double *points, int64_t n, double r_obs,
+                                 const kerr_opts *o, double *x_out, double *k_out,
+                                 int32_t *status, int32_t *steps, float *diag, float *cross,
+                                 void *stream)
+{
+    if (!(r_obs > 0.0) || !std::isfinite(r_obs))
+        return fail(KERR_EINVAL, "r_obs = %g must be finite and > 0", r_obs);
+    TraceExtra X;
+    X.points = points;
+    X.r_obs = r_obs;
+    return trace_common(c, MODE_POINTS, nullptr, nullptr, nullptr, n, nullptr, 0, o, x_out, k_out,
+                        status, steps, diag, cross, stream, X);
+}
+
+// Camera tracing of a device-side list of pixels (the surrogate's fallback):
+// geodesic id traces pixel index[id] of cam; n_dev (device) holds how many
+// of the capacity n are live.  Outputs are compact (indexed by id).
+int kerr_trace_camera_list(kerr_ctx *c, const kerr_camera *cam, const int64_t *index,
+                           const unsigned long long *n_dev, int64_t capacity, const kerr_opts *o,
+                           double *x_out, double *k_out, int32_t *status, int32_t *steps,
+                           float *diag, float *cross, void *stream)
+{
+    std::vector<CamDev> cd;
+    int64_t n = 0;
+    int rc = build_cams(cam, 1, cd, n);
+    if (rc)
+        return rc;
+    TraceExtra X;
+    X.index = index;
+    X.n_dev = n_dev;
+    return trace_common(c, MODE_CAMERA, nullptr, nullptr, nullptr, capacity, cd.data(), 1, o,
+                        x_out, k_out, status, steps, diag, cross, stream, X);
 }
 
 extern "C" int kerr_get_stats(kerr_ctx *c, kerr_stats *out)

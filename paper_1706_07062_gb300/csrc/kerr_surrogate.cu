@@ -1,0 +1,940 @@
+// kerr_surrogate.cu -- the learned surrogate of the geodesic integrator:
+// network object, training (forward, loss, backward, Adam), inference, and
+// rendering with an integrator fallback near the shadow edge.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/kerr.h"
+#define KERR_TYPES_ONLY
+#include "kerr_trace.cuh"
+#include "kerr_mlp.cuh"
+#include "kerr_variants.h"
+
+using namespace kerr;
+using namespace kerr::mlp;
+using bf16 = __nv_bfloat16;
+
+// Camera tracing of a device-side pixel list (kerr_api.cu).
+int kerr_trace_camera_list(kerr_ctx *c, const kerr_camera *cam, const int64_t *index,
+                           const unsigned long long *n_dev, int64_t capacity, const kerr_opts *o,
+                           double *x_out, double *k_out, int32_t *status, int32_t *steps,
+                           float *diag, float *cross, void *stream);
+
+namespace {
+
+int fail(int code, const char *msg) { return kerr_set_error(code, msg); }
+
+#define SURR_CUDA(call)                                                                        \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            cudaGetLastError();                                                                \
+            return fail(KERR_ECUDA, #call " failed");                                          \
+        }                                                                                      \
+    } while (0)
+
+// Parameter layout: for l = 0..4, W_l [out][in] then b_l [out].
+struct Layout {
+    size_t w[kLayers], b[kLayers], total;
+    Layout()
+    {
+        size_t o = 0;
+        for (int l = 0; l < kLayers; ++l) {
+            w[l] = o;
+            o += (size_t)out_dim(l) * in_dim(l);
+            b[l] = o;
+            o += out_dim(l);
+        }
+        total = o;
+    }
+};
+const Layout kL;
+
+// ---------------------------------------------------------------------------
+// elementwise kernels
+// ---------------------------------------------------------------------------
+__global__ void to_bf16_kernel(const float *__restrict__ src, bf16 *__restrict__ dst, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __float2bfloat16(src[i]);
+}
+
+// Network input rows [n][16] (bf16, 4 live) from in [n][4].
+__global__ void input_kernel(const float *__restrict__ in, bf16 *__restrict__ A0, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * kInPad;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / kInPad;
+        const int c = (int)(i % kInPad);
+        A0[i] = __float2bfloat16(c < kIn ? in[r * kIn + c] : 0.0f);
+    }
+}
+
+// Loss and output gradient.  out [n][64] fp32 (8 live), targets/mask [n][8].
+// Loss row = softplus(o0) - y0 o0 + sum_{j>=1} m_j (o_j - y_j)^2; the
+// gradient of the batch mean goes to dOut [n][64] (bf16, padding zero).
+__global__ void loss_kernel(const float *__restrict__ out, const float *__restrict__ tgt,
+                            const float *__restrict__ msk, int64_t n, float inv_n,
+                            bf16 *__restrict__ dOut, float *__restrict__ loss_sum)
+{
+    float local = 0.0f;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const float *o = out + r * kOutPad;
+        const float *y = tgt + r * kOut;
+        const float *m = msk + r * kOut;
+        bf16 *d = dOut + r * kOutPad;
+        const float z = o[0];
+        const float sp = z > 0.f ? z + log1pf(__expf(-z)) : log1pf(__expf(z));
+        local += sp - y[0] * z;
+        const float sig = 1.0f / (1.0f + __expf(-z));
+        d[0] = __float2bfloat16((sig - y[0]) * inv_n);
+#pragma unroll
+        for (int j = 1; j < kOut; ++j) {
+            const float e = m[j] * (o[j] - y[j]);
+            local += e * (o[j] - y[j]);
+            d[j] = __float2bfloat16(2.0f * e * inv_n);
+        }
+        for (int j = kOut; j < kOutPad; ++j)
+            d[j] = __float2bfloat16(0.0f);
+    }
+    // block reduction
+    __shared__ float red[32];
+    for (int o2 = 16; o2 > 0; o2 >>= 1)
+        local += __shfl_xor_sync(0xffffffffu, local, o2);
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+        for (int o2 = 16; o2 > 0; o2 >>= 1)
+            v += __shfl_xor_sync(0xffffffffu, v, o2);
+        if (threadIdx.x == 0)
+            atomicAdd(loss_sum, v * inv_n);
+    }
+}
+
+// dZ = dA * silu'(Z) (bf16 out) for [n][w]; column sums of dZ added to db.
+__global__ void silu_back_kernel(const float *__restrict__ dA, const float *__restrict__ Z,
+                                 bf16 *__restrict__ dZ, int64_t n, int w, float *__restrict__ db)
+{
+    // one thread per column, rows strided over blockIdx.y
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= w)
+        return;
+    float s = 0.0f;
+    for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
+        const float g = dA[r * w + c] * silu_grad(Z[r * w + c]);
+        dZ[r * w + c] = __float2bfloat16(g);
+        s += g;
+    }
+    atomicAdd(&db[c], s);
+}
+
+// Column sums of a bf16 [n][w] matrix into db (output-layer bias gradient).
+__global__ void colsum_kernel(const bf16 *__restrict__ X, int64_t n, int w, float *__restrict__ db)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= w)
+        return;
+    float s = 0.0f;
+    for (int64_t r = blockIdx.y; r < n; r += gridDim.y)
+        s += __bfloat162float(X[r * w + c]);
+    atomicAdd(&db[c], s);
+}
+
+// Adam on the whole parameter vector; refreshes the bf16 copy of each weight.
+__global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g,
+                            float *__restrict__ m, float *__restrict__ v, bf16 *__restrict__ wbf,
+                            int64_t n, float lr, float b1, float b2, float c1, float c2, float eps)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+        w[i] = wi;
+        wbf[i] = __float2bfloat16(wi);
+    }
+}
+
+int grid_1d(int64_t n, int block = 256)
+{
+    int64_t g = (n + block - 1) / block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+}
+
+template <bool TA, bool TB, int EPI>
+cudaError_t gemm(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K, EpiArgs e,
+                 cudaStream_t s, int splits = 1)
+{
+    const int kchunk = ((K + splits - 1) / splits + GBK - 1) / GBK * GBK;
+    splits = (K + kchunk - 1) / kchunk;
+    dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, splits);
+    gemm_bf16<TA, TB, EPI><<<grid, 128, 0, s>>>(A, lda, B, ldb, M, N, K, kchunk, e);
+    return cudaGetLastError();
+}
+
+// Split count for a weight gradient contracted over `rows` batch rows.
+int wsplits(int64_t rows) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, rows / 512)); }
+
+} // namespace
+
+// ===========================================================================
+// the surrogate object
+// ===========================================================================
+struct kerr_surrogate {
+    int device = 0;
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;   // fp32 [total]
+    bf16 *wbf = nullptr;                                           // bf16 copy [total]
+    int64_t step = 0;
+    // activations for a batch of `cap` rows
+    int64_t cap = 0;
+    bf16 *A[kLayers] = {};        // layer inputs (A[0]: [cap][16]; others [cap][256])
+    float *Z[kLayers - 1] = {};   // hidden pre-activations [cap][256]
+    float *out = nullptr;         // [cap][64]
+    bf16 *dOut = nullptr;         // [cap][64]
+    float *dA = nullptr;          // [cap][256]
+    bf16 *dZ = nullptr;           // [cap][256]
+    float *loss = nullptr;        // [1]
+};
+
+static void free_batch(kerr_surrogate *s)
+{
+    for (int l = 0; l < kLayers; ++l)
+        cudaFree(s->A[l]), s->A[l] = nullptr;
+    for (int l = 0; l < kLayers - 1; ++l)
+        cudaFree(s->Z[l]), s->Z[l] = nullptr;
+    cudaFree(s->out);
+    cudaFree(s->dOut);
+    cudaFree(s->dA);
+    cudaFree(s->dZ);
+    s->out = s->dA = nullptr;
+    s->dOut = s->dZ = nullptr;
+    s->cap = 0;
+}
+
+static int ensure_batch(kerr_surrogate *s, int64_t rows, bool training)
+{
+    if (rows <= s->cap && (!training || s->Z[0]))
+        return KERR_OK;
+    free_batch(s);
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < kLayers && e == cudaSuccess; ++l)
+        e = cudaMalloc(&s->A[l], (size_t)rows * in_dim(l) * sizeof(bf16));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&s->out, (size_t)rows * kOutPad * sizeof(float));
+    if (training) {
+        for (int l = 0; l < kLayers - 1 && e == cudaSuccess; ++l)
+            e = cudaMalloc(&s->Z[l], (size_t)rows * kHidden * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&s->dOut, (size_t)rows * kOutPad * sizeof(bf16));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&s->dA, (size_t)rows * kHidden * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&s->dZ, (size_t)rows * kHidden * sizeof(bf16));
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_batch(s);
+        return fail(KERR_ENOMEM, "surrogate: activation buffers");
+    }
+    s->cap = rows;
+    return KERR_OK;
+}
+
+extern "C" int64_t kerr_surrogate_num_params(void) { return (int64_t)kL.total; }
+
+extern "C" int kerr_surrogate_destroy(kerr_surrogate *s)
+{
+    if (!s)
+        return KERR_OK;
+    cudaDeviceSynchronize();
+    free_batch(s);
+    cudaFree(s->w);
+    cudaFree(s->g);
+    cudaFree(s->m);
+    cudaFree(s->v);
+    cudaFree(s->wbf);
+    cudaFree(s->loss);
+    delete s;
+    return KERR_OK;
+}
+
+extern "C" int kerr_surrogate_create(const float *init, kerr_surrogate **out)
+{
+    if (!init || !out)
+        return fail(KERR_EINVAL, "kerr_surrogate_create: NULL argument");
+    *out = nullptr;
+    kerr_surrogate *s = new (std::nothrow) kerr_surrogate();
+    if (!s)
+        return fail(KERR_ENOMEM, "kerr_surrogate_create: host allocation");
+    const size_t n = kL.total;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&s->w, n * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&s->g, n * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&s->m, n * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&s->v, n * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&s->wbf, n * sizeof(bf16));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&s->loss, sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(s->w, init, n * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemset(s->g, 0, n * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMemset(s->m, 0, n * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMemset(s->v, 0, n * sizeof(float));
+    if (e == cudaSuccess) {
+        to_bf16_kernel<<<grid_1d(n), 256>>>(s->w, s->wbf, n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        kerr_surrogate_destroy(s);
+        return fail(KERR_ENOMEM, "kerr_surrogate_create: device allocation");
+    }
+    *out = s;
+    return KERR_OK;
+}
+
+extern "C" int kerr_surrogate_get_params(kerr_surrogate *s, float *host_out)
+{
+    if (!s || !host_out)
+        return fail(KERR_EINVAL, "kerr_surrogate_get_params: NULL argument");
+    SURR_CUDA(cudaDeviceSynchronize());
+    SURR_CUDA(cudaMemcpy(host_out, s->w, kL.total * sizeof(float), cudaMemcpyDeviceToHost));
+    return KERR_OK;
+}
+
+extern "C" int kerr_surrogate_get_grad(kerr_surrogate *s, float *host_out)
+{
+    if (!s || !host_out)
+        return fail(KERR_EINVAL, "kerr_surrogate_get_grad: NULL argument");
+    SURR_CUDA(cudaDeviceSynchronize());
+    SURR_CUDA(cudaMemcpy(host_out, s->g, kL.total * sizeof(float), cudaMemcpyDeviceToHost));
+    return KERR_OK;
+}
+
+// Forward pass of `rows` rows already in s->A[0]; keeps pre-activations when
+// training.  The final outputs land in s->out [rows][64].
+static cudaError_t forward_rows(kerr_surrogate *s, int64_t rows, bool training, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
+        const int K = in_dim(l), N = out_dim(l);
+        EpiArgs ea;
+        std::memset(&ea, 0, sizeof ea);
+        ea.bias = s->w + kL.b[l];
+        const bf16 *W = s->wbf + kL.w[l];
+        if (l < kLayers - 1) {
+            ea.Aout = s->A[l + 1];
+            ea.lda_out = N;
+            if (training) {
+                ea.C = s->Z[l];
+                ea.ldc = N;
+                e = gemm<false, false, EPI_BIAS_SILU>(s->A[l], K, W, K, (int)rows, N, K, ea, st);
+            } else {
+                e = gemm<false, false, EPI_BIAS_SILU_BF16>(s->A[l], K, W, K, (int)rows, N, K, ea,
+                                                          st);
+            }
+        } else {
+            ea.C = s->out;
+            ea.ldc = N;
+            e = gemm<false, false, EPI_BIAS_F32>(s->A[l], K, W, K, (int)rows, N, K, ea, st);
+        }
+    }
+    return e;
+}
+
+// Backward pass after forward_rows(training) and loss_kernel: gradients of
+// the batch accumulate into s->g (zeroed first).
+static cudaError_t backward_rows(kerr_surrogate *s, int64_t rows, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(s->g, 0, kL.total * sizeof(float), st);
+    const int R = (int)rows;
+    const int ygrid = (int)std::min<int64_t>(rows, 512);
+    // output layer
+    {
+        const int l = kLayers - 1, K = in_dim(l), N = out_dim(l);
+        EpiArgs ea;
+        std::memset(&ea, 0, sizeof ea);
+        ea.C = s->g + kL.w[l];
+        ea.ldc = K;
+        if (e == cudaSuccess)   // dW_l [N][K] += dOut^T A_l
+            e = gemm<true, true, EPI_F32_ATOMIC>(s->dOut, N, s->A[l], K, N, K, R, ea, st,
+                                                 wsplits(rows));
+        if (e == cudaSuccess) {
+            colsum_kernel<<<dim3((N + 127) / 128, ygrid), 128, 0, st>>>(s->dOut, rows, N,
+                                                                        s->g + kL.b[l]);
+            e = cudaGetLastError();
+        }
+        EpiArgs eb;
+        std::memset(&eb, 0, sizeof eb);
+        eb.C = s->dA;
+        eb.ldc = K;
+        if (e == cudaSuccess)   // dA_l [R][K] = dOut W_l
+            e = gemm<false, true, EPI_F32>(s->dOut, N, s->wbf + kL.w[l], K, R, K, N, eb, st);
+    }
+    for (int l = kLayers - 2; l >= 0 && e == cudaSuccess; --l) {
+        const int K = in_dim(l), N = out_dim(l);
+        silu_back_kernel<<<dim3((N + 127) / 128, ygrid), 128, 0, st>>>(s->dA, s->Z[l], s->dZ, rows,
+                                                                       N, s->g + kL.b[l]);
+        e = cudaGetLastError();
+        EpiArgs ea;
+        std::memset(&ea, 0, sizeof ea);
+        ea.C = s->g + kL.w[l];
+        ea.ldc = K;
+        if (e == cudaSuccess)
+            e = gemm<true, true, EPI_F32_ATOMIC>(s->dZ, N, s->A[l], K, N, K, R, ea, st,
+                                                 wsplits(rows));
+        if (l > 0 && e == cudaSuccess) {
+            EpiArgs eb;
+            std::memset(&eb, 0, sizeof eb);
+            eb.C = s->dA;
+            eb.ldc = K;
+            e = gemm<false, true, EPI_F32>(s->dZ, N, s->wbf + kL.w[l], K, R, K, N, eb, st);
+        }
+    }
+    return e;
+}
+
+static int check_rows(int64_t n)
+{
+    if (n < 0 || n > (int64_t)1 << 30)
+        return fail(KERR_EINVAL, "surrogate: row count out of range");
+    return KERR_OK;
+}
+
+extern "C" int kerr_surrogate_forward(kerr_surrogate *s, const float *in, int64_t n, float *out,
+                                      void *stream)
+{
+    if (!s || (n > 0 && (!in || !out)))
+        return fail(KERR_EINVAL, "kerr_surrogate_forward: NULL argument");
+    int rc = check_rows(n);
+    if (rc || n == 0)
+        return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t chunk = 1 << 20;
+    rc = ensure_batch(s, std::min(n, chunk), false);
+    if (rc)
+        return rc;
+    for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+        const int64_t rows = std::min(chunk, n - r0);
+        input_kernel<<<grid_1d(rows * kInPad), 256, 0, st>>>(in + r0 * kIn, s->A[0], rows);
+        SURR_CUDA(cudaGetLastError());
+        SURR_CUDA(forward_rows(s, rows, false, st));
+        SURR_CUDA(cudaMemcpy2DAsync(out + r0 * kOut, kOut * sizeof(float), s->out,
+                                    kOutPad * sizeof(float), kOut * sizeof(float), rows,
+                                    cudaMemcpyDeviceToDevice, st));
+    }
+    return KERR_OK;
+}
+
+extern "C" int kerr_surrogate_grad(kerr_surrogate *s, const float *in, const float *targets,
+                                   const float *mask, int64_t n, float *loss, void *stream)
+{
+    if (!s || !in || !targets || !mask || n < 1)
+        return fail(KERR_EINVAL, "kerr_surrogate_grad: bad argument");
+    int rc = check_rows(n);
+    if (rc)
+        return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = ensure_batch(s, n, true);
+    if (rc)
+        return rc;
+    input_kernel<<<grid_1d(n * kInPad), 256, 0, st>>>(in, s->A[0], n);
+    SURR_CUDA(cudaGetLastError());
+    SURR_CUDA(forward_rows(s, n, true, st));
+    SURR_CUDA(cudaMemsetAsync(s->loss, 0, sizeof(float), st));
+    loss_kernel<<<grid_1d(n), 256, 0, st>>>(s->out, targets, mask, n, 1.0f / (float)n, s->dOut,
+                                            s->loss);
+    SURR_CUDA(cudaGetLastError());
+    SURR_CUDA(backward_rows(s, n, st));
+    float h = 0.f;
+    SURR_CUDA(cudaMemcpyAsync(&h, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+    SURR_CUDA(cudaStreamSynchronize(st));
+    if (loss)
+        *loss = h;
+    return KERR_OK;
+}
+
+extern "C" int kerr_surrogate_train(kerr_surrogate *s, const float *in, const float *targets,
+                                    const float *mask, int64_t n, int32_t epochs, int32_t batch,
+                                    float lr, float *loss_per_epoch, void *stream)
+{
+    if (!s || !in || !targets || !mask || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.f))
+        return fail(KERR_EINVAL, "kerr_surrogate_train: bad argument");
+    int rc = check_rows(n);
+    if (rc)
+        return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t B = std::min<int64_t>(batch, n);
+    rc = ensure_batch(s, B, true);
+    if (rc)
+        return rc;
+    const int64_t steps_per_epoch = n / B;
+    const int64_t total = std::max<int64_t>(1, steps_per_epoch * epochs);
+    float *d_epoch = nullptr;
+    SURR_CUDA(cudaMalloc(&d_epoch, sizeof(float) * epochs));
+    SURR_CUDA(cudaMemsetAsync(d_epoch, 0, sizeof(float) * epochs, st));
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    int64_t k = 0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        for (int64_t bi = 0; bi < steps_per_epoch; ++bi, ++k) {
+            const int64_t r0 = bi * B;
+            input_kernel<<<grid_1d(B * kInPad), 256, 0, st>>>(in + r0 * kIn, s->A[0], B);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess)
+                e = forward_rows(s, B, true, st);
+            if (e == cudaSuccess) {
+                loss_kernel<<<grid_1d(B), 256, 0, st>>>(s->out, targets + r0 * kOut,
+                                                        mask + r0 * kOut, B, 1.0f / (float)B,
+                                                        s->dOut, d_epoch + ep);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess)
+                e = backward_rows(s, B, st);
+            if (e == cudaSuccess) {
+                ++s->step;
+                const double frac = (double)k / (double)total;
+                const float lr_k = (float)(lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(M_PI * frac))));
+                const float c1 = (float)(1.0 / (1.0 - std::pow(b1, (double)s->step)));
+                const float c2 = (float)(1.0 / (1.0 - std::pow(b2, (double)s->step)));
+                adam_kernel<<<grid_1d(kL.total), 256, 0, st>>>(s->w, s->g, s->m, s->v, s->wbf,
+                                                               kL.total, lr_k, b1, b2, c1, c2, eps);
+                e = cudaGetLastError();
+            }
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                cudaFree(d_epoch);
+                return fail(KERR_ECUDA, "kerr_surrogate_train: launch failed");
+            }
+        }
+    }
+    std::vector<float> h(epochs);
+    cudaError_t e = cudaMemcpyAsync(h.data(), d_epoch, sizeof(float) * epochs,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    cudaFree(d_epoch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KERR_ECUDA, "kerr_surrogate_train: synchronisation failed");
+    }
+    if (loss_per_epoch)
+        for (int ep = 0; ep < epochs; ++ep)
+            loss_per_epoch[ep] = h[ep] / (float)std::max<int64_t>(1, steps_per_epoch);
+    return KERR_OK;
+}
+
+// ===========================================================================
+// training targets from integrated rays
+// ===========================================================================
+namespace {
+
+__global__ void targets_kernel(const double *__restrict__ pts, const int32_t *__restrict__ status,
+                               const float *__restrict__ cross, int64_t n, float *__restrict__ in,
+                               float *__restrict__ tgt, float *__restrict__ msk)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double *p = pts + 4 * i;
+        in[4 * i + 0] = (float)p[0] / KERR_SURR_INPUT_SCALE;
+        in[4 * i + 1] = (float)p[1] / KERR_SURR_INPUT_SCALE;
+        in[4 * i + 2] = (float)p[2];
+        in[4 * i + 3] = (float)cos(p[3]);
+        float *y = tgt + kOut * i;
+        float *m = msk + kOut * i;
+        y[0] = status[i] == ST_CAPTURED ? 1.0f : 0.0f;
+        m[0] = 1.0f;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float r = cross[(2 * c) * n + i], ph = cross[(2 * c + 1) * n + i];
+            const bool ok = !isnan(r) && !isnan(ph);
+            y[1 + 3 * c] = ok ? 0.5f * (logf(r) - 2.0f) : 0.0f;
+            y[2 + 3 * c] = ok ? cosf(ph) : 0.0f;
+            y[3 + 3 * c] = ok ? sinf(ph) : 0.0f;
+            m[1 + 3 * c] = m[2 + 3 * c] = m[3 + 3 * c] = ok ? 1.0f : 0.0f;
+        }
+        const float g = cross[4 * n + i];
+        y[7] = isnan(g) ? 0.0f : g - 1.0f;
+        m[7] = isnan(g) ? 0.0f : 1.0f;
+    }
+}
+
+} // namespace
+
+extern "C" int kerr_surrogate_targets(kerr_ctx *ctx, const double *points, int64_t n, double r_obs,
+                                      const kerr_opts *opts, float *in, float *targets,
+                                      float *mask, void *stream)
+{
+    if (!ctx || !points || !in || !targets || !mask || n < 1)
+        return fail(KERR_EINVAL, "kerr_surrogate_targets: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    double *x = nullptr, *k = nullptr;
+    int32_t *stat = nullptr, *nst = nullptr;
+    float *cr = nullptr;
+    cudaError_t e = cudaMalloc(&x, (size_t)n * 4 * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&k, (size_t)n * 4 * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&stat, (size_t)n * sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&nst, (size_t)n * sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&cr, (size_t)n * 5 * sizeof(float));
+    int rc = KERR_OK;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(KERR_ENOMEM, "kerr_surrogate_targets: allocation");
+    }
+    if (rc == KERR_OK)
+        rc = kerr_trace_points(ctx, points, n, r_obs, opts, x, k, stat, nst, nullptr, cr, stream);
+    if (rc == KERR_OK) {
+        targets_kernel<<<grid_1d(n), 256, 0, st>>>(points, stat, cr, n, in, targets, mask);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(KERR_ECUDA, "kerr_surrogate_targets: kernel failed");
+        }
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(x);
+    cudaFree(k);
+    cudaFree(stat);
+    cudaFree(nst);
+    cudaFree(cr);
+    return rc;
+}
+
+// ===========================================================================
+// rendering with integrator fallback
+// ===========================================================================
+namespace {
+
+// Bardeen's critical curve of a distant observer (M = 1): spherical photon
+// orbits r in [r_ph+, r_ph-] with xi(r) = -(r^3 - 3r^2 + a^2 r + a^2)/(a(r-1)),
+// eta(r) = -r^3 (r^3 - 6r^2 + 9r - 4a^2)/(a^2 (r-1)^2), seen at
+// alpha = -xi / sin i, beta = +-sqrt(eta + a^2 cos^2 i - xi^2 cot^2 i).  The
+// camera's alpha axis is (0, 1, 0) with n = (sin i, 0, cos i), so its alpha
+// is Bardeen's alpha.  For a -> 0 the curve is the circle of radius 3 sqrt 3.
+__device__ __forceinline__ double crit_beta2(double a, double si, double ci, double r,
+                                             double &alpha)
+{
+    const double xi = -(r * r * r - 3.0 * r * r + a * a * r + a * a) / (a * (r - 1.0));
+    const double eta =
+        -r * r * r * (r * r * r - 6.0 * r * r + 9.0 * r - 4.0 * a * a) / (a * a * (r - 1.0) * (r - 1.0));
+    alpha = -xi / si;
+    return eta + a * a * ci * ci - xi * xi * (ci * ci) / (si * si);
+}
+
+// The visible part of the curve is the r interval where beta^2 >= 0: one
+// block samples beta^2 over [r_p, r_r], keeps the first and last
+// non-negative samples and bisects each edge to double precision.
+__global__ void crit_interval_kernel(double a, double incl, double *__restrict__ rr_out)
+{
+    constexpr int S = 4096;
+    __shared__ int lo_i, hi_i;
+    const double si = sin(incl), ci = cos(incl);
+    const double rp = 2.0 * (1.0 + cos(2.0 / 3.0 * acos(-fabs(a))));
+    const double rr = 2.0 * (1.0 + cos(2.0 / 3.0 * acos(fabs(a))));
+    if (threadIdx.x == 0) {
+        lo_i = S;
+        hi_i = -1;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < S; j += blockDim.x) {
+        double al;
+        const double r = rp + (rr - rp) * (j + 0.5) / S;
+        if (crit_beta2(a, si, ci, r, al) >= 0.0) {
+            atomicMin(&lo_i, j);
+            atomicMax(&hi_i, j);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r1 = NAN, r2 = NAN;
+        if (hi_i >= lo_i) {
+            // lower edge: beta^2 < 0 at rA, >= 0 at rB
+            double rA = rp + (rr - rp) * (lo_i - 0.5) / S, rB = rp + (rr - rp) * (lo_i + 0.5) / S;
+            rA = fmax(rA, rp);
+            double al;
+            if (crit_beta2(a, si, ci, rA, al) >= 0.0)
+                rB = rA;
+            for (int it = 0; it < 60; ++it) {
+                const double rm = 0.5 * (rA + rB);
+                if (crit_beta2(a, si, ci, rm, al) >= 0.0)
+                    rB = rm;
+                else
+                    rA = rm;
+            }
+            r1 = rB;
+            double rC = rp + (rr - rp) * (hi_i + 0.5) / S, rD = rp + (rr - rp) * (hi_i + 1.5) / S;
+            rD = fmin(rD, rr);
+            if (crit_beta2(a, si, ci, rD, al) >= 0.0)
+                rC = rD;
+            for (int it = 0; it < 60; ++it) {
+                const double rm = 0.5 * (rC + rD);
+                if (crit_beta2(a, si, ci, rm, al) >= 0.0)
+                    rC = rm;
+                else
+                    rD = rm;
+            }
+            r2 = rC;
+        }
+        rr_out[0] = r1;
+        rr_out[1] = r2;
+    }
+}
+
+// Samples of the curve, `ns` per branch (2 ns points; NaN if none visible),
+// cosine-spaced in r over the visible interval (dense at the ends, where
+// beta goes to zero like the square root of the distance in r).
+__global__ void crit_curve_kernel(double a, double incl, int ns, const double *__restrict__ rr,
+                                  float2 *__restrict__ pts)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ns)
+        return;
+    const double si = sin(incl), ci = cos(incl);
+    const float nanf_ = __int_as_float(0x7fc00000);
+    float2 p0 = make_float2(nanf_, nanf_);
+    float2 p1 = p0;
+    if (fabs(a) < 1e-4) {
+        const double b = 3.0 * sqrt(3.0);
+        const double th = 2.0 * M_PI * (j + 0.5) / ns;
+        const double th2 = th + M_PI / ns;
+        p0 = make_float2((float)(b * cos(th)), (float)(b * sin(th)));
+        p1 = make_float2((float)(b * cos(th2)), (float)(b * sin(th2)));
+    } else if (!isnan(rr[0])) {
+        const double u = 0.5 * (1.0 - cos(M_PI * j / (ns - 1)));
+        const double r = rr[0] + (rr[1] - rr[0]) * u;
+        double al;
+        const double b2 = fmax(0.0, crit_beta2(a, si, ci, r, al));
+        const double be = sqrt(b2);
+        p0 = make_float2((float)al, (float)be);
+        p1 = make_float2((float)al, (float)-be);
+    }
+    pts[j] = p0;
+    pts[ns + j] = p1;
+}
+
+// Gate and decode: one pass over the pixels.  Network outputs o [n][8];
+// fallback when p in [p_lo, p_hi] or distance to the curve < crit_dist;
+// fallback pixels are appended (warp-aggregated) to idx.
+__global__ void __launch_bounds__(256) gate_kernel(const float *__restrict__ o, kerr_camera cam,
+                                                   const float2 *__restrict__ curve, int ncurve,
+                                                   float p_lo, float p_hi, float crit_dist,
+                                                   int64_t n, float *__restrict__ out,
+                                                   uint8_t *__restrict__ fb,
+                                                   int64_t *__restrict__ idx,
+                                                   unsigned long long *__restrict__ count)
+{
+    extern __shared__ float2 sc[];
+    for (int j = threadIdx.x; j < ncurve; j += blockDim.x)
+        sc[j] = curve[j];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        bool use_fb = false;
+        if (i < n) {
+            const float *oi = o + kOut * i;
+            const float p = 1.0f / (1.0f + __expf(-oi[0]));
+            const int64_t px = i % cam.nx, qy = i / cam.nx;
+            const float al = (float)(-cam.half_width + (px + 0.5) * 2.0 * cam.half_width / cam.nx);
+            const float be = (float)(-cam.half_width + (qy + 0.5) * 2.0 * cam.half_width / cam.ny);
+            float d2 = 3.0e38f;
+            for (int j = 0; j < ncurve; ++j) {
+                const float dx = sc[j].x - al, dy = sc[j].y - be;
+                const float dd = dx * dx + dy * dy;
+                d2 = dd < d2 ? dd : d2;      // NaN samples never win
+            }
+            use_fb = (p >= p_lo && p <= p_hi) || d2 < crit_dist * crit_dist;
+            const float nan = __int_as_float(0x7fc00000);
+            out[i] = p;
+            const bool cap = p >= 0.5f;
+            for (int c = 0; c < 2; ++c) {
+                const float lr = oi[1 + 3 * c], cph = oi[2 + 3 * c], sph = oi[3 + 3 * c];
+                out[(1 + 2 * c) * n + i] = cap ? nan : __expf(2.0f * lr + 2.0f);
+                out[(2 + 2 * c) * n + i] = cap ? nan : atan2f(sph, cph);
+            }
+            out[5 * n + i] = cap ? nan : oi[7] + 1.0f;
+            if (fb)
+                fb[i] = use_fb ? 1 : 0;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, use_fb);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long b = 0;
+            if (lane == leader)
+                b = atomicAdd(count, (unsigned long long)__popc(m));
+            b = __shfl_sync(0xffffffffu, b, leader);
+            if (use_fb)
+                idx[b + __popc(m & ((1u << lane) - 1u))] = i;
+        }
+    }
+}
+
+// Network inputs (alpha/s, beta/s, a, cos i) of every pixel of a camera.
+__global__ void surr_query_kernel(float *in, kerr_camera cam, int64_t n)
+{
+    const float ci = (float)cos(cam.incl);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t px = i % cam.nx, qy = i / cam.nx;
+        const double al = -cam.half_width + (px + 0.5) * 2.0 * cam.half_width / cam.nx;
+        const double be = -cam.half_width + (qy + 0.5) * 2.0 * cam.half_width / cam.ny;
+        in[4 * i + 0] = (float)al / KERR_SURR_INPUT_SCALE;
+        in[4 * i + 1] = (float)be / KERR_SURR_INPUT_SCALE;
+        in[4 * i + 2] = (float)cam.a;
+        in[4 * i + 3] = ci;
+    }
+}
+
+// Scatter the integrator's results of the fallback pixels into the planes.
+__global__ void merge_kernel(const int64_t *__restrict__ idx,
+                             const unsigned long long *__restrict__ count,
+                             const int32_t *__restrict__ status, const float *__restrict__ cross,
+                             int64_t cap_rows, int64_t n, float *__restrict__ out)
+{
+    const int64_t live = (int64_t)*count;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < live;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx[j];
+        out[i] = status[j] == ST_CAPTURED ? 1.0f : 0.0f;
+        for (int c = 0; c < 5; ++c)
+            out[(1 + c) * n + i] = cross[c * cap_rows + j];
+    }
+}
+
+} // namespace
+
+extern "C" int kerr_surrogate_render(kerr_ctx *ctx, kerr_surrogate *s, const kerr_camera *cam,
+                                     const kerr_opts *opts, float p_lo, float p_hi,
+                                     float crit_dist, float *out, uint8_t *fallback,
+                                     int64_t *n_fallback, void *stream)
+{
+    if (!ctx || !s || !cam || !opts || !out)
+        return fail(KERR_EINVAL, "kerr_surrogate_render: NULL argument");
+    if (cam->nx <= 0 || cam->ny <= 0 || !(std::fabs(cam->a) <= 1.0))
+        return fail(KERR_EINVAL, "kerr_surrogate_render: invalid camera");
+    const int64_t n = (int64_t)cam->nx * cam->ny;
+    cudaStream_t st = (cudaStream_t)stream;
+    // device scratch for this call
+    float *in = nullptr, *o = nullptr, *crs = nullptr;
+    float2 *curve = nullptr;
+    double *rint = nullptr;
+    int64_t *idx = nullptr;
+    unsigned long long *cnt = nullptr;
+    double *x = nullptr, *k = nullptr;
+    int32_t *stat = nullptr, *nst = nullptr;
+    const int ns = 2048;
+    cudaError_t e = cudaMalloc(&in, (size_t)n * kIn * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&o, (size_t)n * kOut * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&curve, (size_t)2 * ns * sizeof(float2));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&rint, 2 * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&idx, (size_t)n * sizeof(int64_t));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&cnt, sizeof(unsigned long long));
+    int rc = KERR_OK;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(KERR_ENOMEM, "kerr_surrogate_render: allocation");
+    }
+    unsigned long long hcount = 0;
+    if (rc == KERR_OK) {
+        // network inputs from the pixel grid
+        e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) {
+            surr_query_kernel<<<grid_1d(n), 256, 0, st>>>(in, *cam, n);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(KERR_ECUDA, "kerr_surrogate_render: query kernel");
+        }
+    }
+    if (rc == KERR_OK)
+        rc = kerr_surrogate_forward(s, in, n, o, stream);
+    if (rc == KERR_OK) {
+        if (std::fabs(cam->a) >= 1e-4)
+            crit_interval_kernel<<<1, 256, 0, st>>>(cam->a, cam->incl, rint);
+        crit_curve_kernel<<<(ns + 127) / 128, 128, 0, st>>>(cam->a, cam->incl, ns, rint, curve);
+        gate_kernel<<<grid_1d(n), 256, 2 * ns * sizeof(float2), st>>>(
+            o, *cam, curve, 2 * ns, p_lo, p_hi, crit_dist, n, out, fallback, idx, cnt);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&hcount, cnt, sizeof hcount, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(KERR_ECUDA, "kerr_surrogate_render: gate");
+        }
+    }
+    if (rc == KERR_OK && hcount > 0) {
+        const int64_t m = (int64_t)hcount;
+        e = cudaMalloc(&x, (size_t)m * 4 * sizeof(double));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&k, (size_t)m * 4 * sizeof(double));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&stat, (size_t)m * sizeof(int32_t));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&nst, (size_t)m * sizeof(int32_t));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&crs, (size_t)m * 5 * sizeof(float));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(KERR_ENOMEM, "kerr_surrogate_render: fallback buffers");
+        }
+        if (rc == KERR_OK)
+            rc = kerr_trace_camera_list(ctx, cam, idx, cnt, m, opts, x, k, stat, nst, nullptr, crs,
+                                        stream);
+        if (rc == KERR_OK) {
+            merge_kernel<<<grid_1d(m), 256, 0, st>>>(idx, cnt, stat, crs, m, n, out);
+            if (cudaGetLastError() != cudaSuccess) {
+                cudaGetLastError();
+                rc = fail(KERR_ECUDA, "kerr_surrogate_render: merge");
+            }
+        }
+    }
+    cudaStreamSynchronize(st);
+    if (n_fallback)
+        *n_fallback = (int64_t)hcount;
+    cudaFree(in);
+    cudaFree(o);
+    cudaFree(curve);
+    cudaFree(rint);
+    cudaFree(idx);
+    cudaFree(cnt);
+    cudaFree(x);
+    cudaFree(k);
+    cudaFree(stat);
+    cudaFree(nst);
+    cudaFree(crs);
+    return rc;
+}
+

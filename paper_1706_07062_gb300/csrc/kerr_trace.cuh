@@ -30,7 +30,7 @@ enum : int {
     ST_INVALID_IC = 7
 };
 
-enum : int { MODE_RAYS = 0, MODE_CAMERA = 1, MODE_PARTICLES = 2 };
+enum : int { MODE_RAYS = 0, MODE_CAMERA = 1, MODE_PARTICLES = 2, MODE_POINTS = 3 };
 
 // Camera as the kernel sees it: the public kerr_camera plus the index of its
 // first ray.
@@ -89,6 +89,10 @@ struct TraceParams {
     const double *t_end_each;   // [n] per-geodesic end times, or null
     const CamDev *cams;
     int32_t ncam;
+    const int64_t *index;       // camera mode: pixel index of geodesic id (or null: id itself)
+    const unsigned long long *n_dev;  // number of geodesics on the device (or null: n)
+    const double *points;       // MODE_POINTS: [n][4] (alpha, beta, a, incl)
+    double r_obs;               // MODE_POINTS: observer distance
     double *x_out, *k_out;      // [4][n]
     int32_t *status, *steps;    // [n]
     float *diag;                // [4][n] or null
@@ -515,27 +519,39 @@ __device__ __forceinline__ int init_geodesic(const TraceParams &P, int64_t id, d
     const int64_t n = P.n;
     double a = P.a;
     int st = ST_NONE;
-    if (P.mode == MODE_CAMERA) {
-        int lo = 0, hi = P.ncam - 1;
-        while (lo < hi) {   // last camera with offset <= id
-            const int mid = (lo + hi + 1) >> 1;
-            if (P.cams[mid].offset <= id)
-                lo = mid;
-            else
-                hi = mid - 1;
+    if (P.mode == MODE_CAMERA || P.mode == MODE_POINTS) {
+        double al, be, incl, r_obs;
+        if (P.mode == MODE_CAMERA) {
+            const int64_t pix = P.index ? P.index[id] : id;
+            int lo = 0, hi = P.ncam - 1;
+            while (lo < hi) {   // last camera with offset <= pix
+                const int mid = (lo + hi + 1) >> 1;
+                if (P.cams[mid].offset <= pix)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            const CamDev cam = P.cams[lo];
+            a = cam.a;
+            const int64_t local = pix - cam.offset;
+            const int64_t p = local % cam.nx, q = local / cam.nx;
+            al = -cam.w + (p + 0.5) * 2.0 * cam.w / cam.nx;
+            be = -cam.w + (q + 0.5) * 2.0 * cam.w / cam.ny;
+            incl = cam.incl;
+            r_obs = cam.r_obs;
+        } else {
+            al = P.points[4 * id];
+            be = P.points[4 * id + 1];
+            a = P.points[4 * id + 2];
+            incl = P.points[4 * id + 3];
+            r_obs = P.r_obs;
         }
-        const CamDev cam = P.cams[lo];
-        a = cam.a;
-        const int64_t local = id - cam.offset;
-        const int64_t p = local % cam.nx, q = local / cam.nx;
-        const double al = -cam.w + (p + 0.5) * 2.0 * cam.w / cam.nx;
-        const double be = -cam.w + (q + 0.5) * 2.0 * cam.w / cam.ny;
         double si, ci;
-        sincos(cam.incl, &si, &ci);
+        sincos(incl, &si, &ci);
         y[0] = 0.0;
-        y[1] = cam.r_obs * si - be * ci;
+        y[1] = r_obs * si - be * ci;
         y[2] = al;
-        y[3] = cam.r_obs * ci + be * si;
+        y[3] = r_obs * ci + be * si;
         y[5] = -si;
         y[6] = 0.0;
         y[7] = -ci;
@@ -740,12 +756,15 @@ static __device__ __noinline__ ZoneResult zone_step_df(const RayConst rc, const 
 // Spin of geodesic id: its camera's (camera mode) or the context's.
 __device__ __forceinline__ double geodesic_spin(const TraceParams &P, int64_t id)
 {
+    if (P.mode == MODE_POINTS)
+        return P.points[4 * id + 2];
     if (P.mode != MODE_CAMERA)
         return P.a;
+    const int64_t pix = P.index ? P.index[id] : id;
     int lo = 0, hi = P.ncam - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (P.cams[mid].offset <= id)
+        if (P.cams[mid].offset <= pix)
             lo = mid;
         else
             hi = mid - 1;
@@ -815,7 +834,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f64_kernel(const TraceParam
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const unsigned long long n_items = (unsigned long long)P.n;
+    unsigned long long n_items = (unsigned long long)P.n;
+    if (P.n_dev && *P.n_dev < n_items)
+        n_items = *P.n_dev;
     bool has = false, drained = false, timed_out = false;
     int64_t id = 0;
     RayConst rc;
@@ -902,11 +923,20 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f64_kernel(const TraceParam
 //   f32_finish_kernel  folds the compensated pairs into FP64 outputs and
 //                      computes the FP64 diagnostics (whole warps).
 // ===========================================================================
+// Number of geodesics of a launch: n, or the device-side count when given.
+__device__ __forceinline__ int64_t live_count(const TraceParams &P)
+{
+    if (P.n_dev && (int64_t)*P.n_dev < P.n)
+        return (int64_t)*P.n_dev;
+    return P.n;
+}
+
 static __global__ void __launch_bounds__(256) f32_setup_kernel(const TraceParams P)
 {
     const int64_t n = P.n;
+    const int64_t live = live_count(P);
     Counters C;
-    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < n;
+    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < live;
          id += (int64_t)gridDim.x * blockDim.x) {
         double yd[8];
         RayConst rc;
@@ -940,7 +970,8 @@ static __global__ void __launch_bounds__(256) f32_setup_kernel(const TraceParams
 static __global__ void __launch_bounds__(256) f32_finish_kernel(const TraceParams P)
 {
     const int64_t n = P.n;
-    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < n;
+    const int64_t live = live_count(P);
+    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < live;
          id += (int64_t)gridDim.x * blockDim.x) {
         double y[8];
 #pragma unroll
@@ -1008,6 +1039,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t n = P.n;
     unsigned long long n_items = (unsigned long long)n;
+    if (P.n_dev && *P.n_dev < n_items)
+        n_items = *P.n_dev;
     if (PHASE != 0) {
         const unsigned long long zc = *P.zcount;
         n_items = zc < (unsigned long long)P.zcap ? zc : (unsigned long long)P.zcap;

@@ -93,6 +93,21 @@ def lib():
         L.kerr_trace_camera_static.argtypes = [c.POINTER(Camera), i32, c.POINTER(Opts), vp, vp,
                                                vp, vp, vp, vp, vp]
         L.kerr_get_stats.argtypes = [vp, c.POINTER(Stats)]
+        L.kerr_trace_points.argtypes = [vp, vp, i64, c.c_double, c.POINTER(Opts), vp, vp, vp, vp,
+                                        vp, vp, vp]
+        L.kerr_surrogate_num_params.argtypes = []
+        L.kerr_surrogate_num_params.restype = i64
+        L.kerr_surrogate_create.argtypes = [vp, c.POINTER(vp)]
+        L.kerr_surrogate_destroy.argtypes = [vp]
+        L.kerr_surrogate_get_params.argtypes = [vp, vp]
+        L.kerr_surrogate_get_grad.argtypes = [vp, vp]
+        L.kerr_surrogate_targets.argtypes = [vp, vp, i64, c.c_double, c.POINTER(Opts), vp, vp, vp,
+                                             vp]
+        L.kerr_surrogate_forward.argtypes = [vp, vp, i64, vp, vp]
+        L.kerr_surrogate_grad.argtypes = [vp, vp, vp, vp, i64, c.POINTER(c.c_float), vp]
+        L.kerr_surrogate_train.argtypes = [vp, vp, vp, vp, i64, i32, i32, c.c_float, vp, vp]
+        L.kerr_surrogate_render.argtypes = [vp, vp, c.POINTER(Camera), c.POINTER(Opts), c.c_float,
+                                            c.c_float, c.c_float, vp, vp, c.POINTER(i64), vp]
         L.kerr_num_variants.argtypes = []
         L.kerr_variant_info.argtypes = [c.c_int, c.POINTER(i32), c.POINTER(i32)]
         L.kerr_num_zone_variants.argtypes = []
@@ -103,7 +118,11 @@ def lib():
                      "kerr_trace_camera", "kerr_trace_camera_static", "kerr_get_stats",
                      "kerr_num_variants",
                      "kerr_variant_info", "kerr_autotune", "kerr_num_zone_variants",
-                     "kerr_zone_variant_info"):
+                     "kerr_zone_variant_info", "kerr_trace_points", "kerr_surrogate_create",
+                     "kerr_surrogate_destroy", "kerr_surrogate_get_params",
+                     "kerr_surrogate_get_grad", "kerr_surrogate_targets",
+                     "kerr_surrogate_forward", "kerr_surrogate_grad", "kerr_surrogate_train",
+                     "kerr_surrogate_render"):
             getattr(L, name).restype = c.c_int
         _lib = L
     return _lib
@@ -332,3 +351,127 @@ def kerr_autotune(ctx: Context, cam: Camera, opts: Opts | None = None, sample: i
     _check(lib().kerr_autotune(ctx.handle, ctypes.byref(cam), ctypes.byref(opts), sample,
                                ctypes.byref(best), _stream_ptr(stream)), "kerr_autotune")
     return best.value
+
+
+# ---------------------------------------------------------------------------
+# image points and the learned surrogate
+# ---------------------------------------------------------------------------
+SURR_INPUT_SCALE = 25.0
+SURR_OUTPUTS = 8
+
+
+def kerr_trace_points(ctx: Context, points, r_obs: float, opts: Opts | None = None,
+                      out: TraceOut | None = None, stream=None) -> TraceOut:
+    """points: (n, 4) float64 rows (alpha, beta, a, inclination)."""
+    n = int(points.shape[0])
+    if tuple(points.shape) != (n, 4):
+        raise KerrError("points must have shape (n, 4)")
+    opts = opts or default_opts()
+    if out is None:
+        out = alloc_out(n, points.device if hasattr(points, "device") else None, cross=True)
+    _check(lib().kerr_trace_points(ctx.handle, _ptr(points), n, float(r_obs), ctypes.byref(opts),
+                                   _ptr(out.x), _ptr(out.k), _ptr(out.status), _ptr(out.steps),
+                                   _ptr(out.diag), _ptr(out.cross),
+                                   _stream_ptr(stream, points, out.x)), "kerr_trace_points")
+    return out
+
+
+def kerr_surrogate_num_params() -> int:
+    return int(lib().kerr_surrogate_num_params())
+
+
+class Surrogate:
+    """Owns a kerr_surrogate (kerr_surrogate_create / kerr_surrogate_destroy)."""
+
+    def __init__(self, init_params: np.ndarray):
+        p = np.ascontiguousarray(init_params, dtype=np.float32)
+        if p.size != kerr_surrogate_num_params():
+            raise KerrError("init_params has the wrong size")
+        h = ctypes.c_void_p()
+        _check(lib().kerr_surrogate_create(p.ctypes.data, ctypes.byref(h)),
+               "kerr_surrogate_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().kerr_surrogate_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.empty(kerr_surrogate_num_params(), np.float32)
+        _check(lib().kerr_surrogate_get_params(self.handle, out.ctypes.data),
+               "kerr_surrogate_get_params")
+        return out
+
+    def grad(self) -> np.ndarray:
+        out = np.empty(kerr_surrogate_num_params(), np.float32)
+        _check(lib().kerr_surrogate_get_grad(self.handle, out.ctypes.data),
+               "kerr_surrogate_get_grad")
+        return out
+
+
+def kerr_surrogate_targets(ctx: Context, points, r_obs: float, opts: Opts | None = None,
+                           stream=None):
+    """(in, targets, mask) device tensors from (n, 4) device points."""
+    import torch
+    n = int(points.shape[0])
+    dev = points.device
+    inp = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    tgt = torch.empty((n, 8), dtype=torch.float32, device=dev)
+    msk = torch.empty((n, 8), dtype=torch.float32, device=dev)
+    opts = opts or default_opts()
+    _check(lib().kerr_surrogate_targets(ctx.handle, _ptr(points), n, float(r_obs),
+                                        ctypes.byref(opts), _ptr(inp), _ptr(tgt), _ptr(msk),
+                                        _stream_ptr(stream, points)), "kerr_surrogate_targets")
+    return inp, tgt, msk
+
+
+def kerr_surrogate_forward(s: Surrogate, inp, out=None, stream=None):
+    import torch
+    n = int(inp.shape[0])
+    if out is None:
+        out = torch.empty((n, 8), dtype=torch.float32, device=inp.device)
+    _check(lib().kerr_surrogate_forward(s.handle, _ptr(inp), n, _ptr(out),
+                                        _stream_ptr(stream, inp)), "kerr_surrogate_forward")
+    return out
+
+
+def kerr_surrogate_grad(s: Surrogate, inp, tgt, msk, stream=None) -> float:
+    loss = ctypes.c_float()
+    _check(lib().kerr_surrogate_grad(s.handle, _ptr(inp), _ptr(tgt), _ptr(msk),
+                                     int(inp.shape[0]), ctypes.byref(loss),
+                                     _stream_ptr(stream, inp)), "kerr_surrogate_grad")
+    return loss.value
+
+
+def kerr_surrogate_train(s: Surrogate, inp, tgt, msk, epochs: int, batch: int, lr: float,
+                         stream=None) -> np.ndarray:
+    losses = np.zeros(epochs, np.float32)
+    _check(lib().kerr_surrogate_train(s.handle, _ptr(inp), _ptr(tgt), _ptr(msk),
+                                      int(inp.shape[0]), int(epochs), int(batch), float(lr),
+                                      losses.ctypes.data, _stream_ptr(stream, inp)),
+           "kerr_surrogate_train")
+    return losses
+
+
+def kerr_surrogate_render(ctx: Context, s: Surrogate, cam: Camera, opts: Opts | None = None,
+                          p_lo: float = 0.05, p_hi: float = 0.95, crit_dist: float = 0.5,
+                          device="cuda", stream=None):
+    """Returns (out (6, n) float32, fallback (n,) uint8, n_fallback)."""
+    import torch
+    n = cam.nx * cam.ny
+    out = torch.empty((6, n), dtype=torch.float32, device=device)
+    fb = torch.empty(n, dtype=torch.uint8, device=device)
+    nfb = ctypes.c_int64()
+    opts = opts or default_opts()
+    _check(lib().kerr_surrogate_render(ctx.handle, s.handle, ctypes.byref(cam),
+                                       ctypes.byref(opts), p_lo, p_hi, crit_dist, _ptr(out),
+                                       _ptr(fb), ctypes.byref(nfb), _stream_ptr(stream, out)),
+           "kerr_surrogate_render")
+    return out, fb, nfb.value

@@ -150,3 +150,24 @@ def kerr_radial_potential(r, xi: float, eta: float, a: float):
     """R(r) = (r^2 + a^2 - a xi)^2 - Delta (eta + (xi - a)^2), E = 1 units."""
     Delta = r * r - 2 * r + a * a
     return (r * r + a * a - a * xi) ** 2 - Delta * (eta + (xi - a) ** 2)
+
+
+def bardeen_curve(a: float, incl: float, n: int = 20000) -> np.ndarray:
+    """Critical curve of a distant observer (Bardeen 1973) as (m, 2) points
+    (alpha, beta): spherical photon orbits r in [r_p, r_r] with
+    xi = -(r^3 - 3r^2 + a^2 r + a^2)/(a(r - 1)) (the Teo Phi above),
+    eta = -r^3 (r^3 - 6r^2 + 9r - 4a^2)/(a^2 (r - 1)^2) (Teo's Q),
+    alpha = -xi / sin i, beta = +-sqrt(eta + a^2 cos^2 i - xi^2 cot^2 i).
+    a = 0: the circle of radius 3 sqrt 3."""
+    if abs(a) < 1e-9:
+        th = np.linspace(0, 2 * np.pi, n, endpoint=False)
+        return 3 * np.sqrt(3) * np.stack([np.cos(th), np.sin(th)], axis=1)
+    rp, rr = r_circular_photon(a)
+    r = np.linspace(rp, rr, n)
+    xi, eta = spherical_photon_constants(r, a)
+    si, ci = np.sin(incl), np.cos(incl)
+    b2 = eta + a * a * ci * ci - xi * xi * ci * ci / (si * si)
+    ok = b2 >= 0
+    al = -xi[ok] / si
+    be = np.sqrt(b2[ok])
+    return np.concatenate([np.stack([al, be], 1), np.stack([al, -be], 1)])
