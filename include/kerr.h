@@ -115,6 +115,11 @@ typedef struct {
                            /* zone: KERR_ZONE_FP64 or KERR_ZONE_F32X2            */
     int32_t zone_variant;  /* launch shape of the zone phase: -1 = default, else */
                            /* an index < kerr_num_zone_variants()                */
+    int32_t zone_quantum;  /* FP32 path, zone phase: after this many attempts a  */
+                           /* geodesic gives its lane to one that waits for a    */
+                           /* lane and goes to the back of the queue (processor  */
+                           /* sharing; results do not depend on it); 0 = each    */
+                           /* geodesic keeps its lane to the end; >= 0           */
 } kerr_opts;
 
 /* One pinhole-free parallel-ray camera (the paper's image-plane rays,
@@ -149,11 +154,17 @@ typedef struct {
     int32_t variant;          /* launch configuration used                       */
     float phase_ms[4];        /* FP32 path: set-up, FP32 stepping, FP64-zone     */
                               /* phase, finishing; FP64 path: [1] = stepping     */
+    int64_t requeued;         /* FP32 path: zone-phase geodesics that gave their */
+                              /* lane to a waiting one (see zone_quantum)        */
+    int64_t queue_errors;     /* zone-phase queue hand-overs that timed out (the */
+                              /* geodesic is then lost); 0 unless the library is */
+                              /* faulty                                          */
 } kerr_stats;
 
 /* Fills *opts with: prec FP32_KAHAN, tol 1e-6, h0 1, max_steps 1e6,
  * r_escape 0, t_end +inf, fp64_zone 1.5, renorm_every 0, clip_maxit 40,
- * variant -1, budget_ns 0, zone_prec KERR_ZONE_FP64, zone_variant -1. */
+ * variant -1, budget_ns 0, zone_prec KERR_ZONE_FP64, zone_variant -1,
+ * zone_quantum 32. */
 void kerr_opts_default(kerr_opts *opts);
 
 /* Creates a context for black-hole spin a (|a| <= 1, else KERR_EINVAL) on the

@@ -89,7 +89,7 @@ struct kerr_ctx {
     bool have_stats = false;
 };
 
-static const int kScratchWords = 1 + SC_COUNT + 2;
+static const int kScratchWords = 1 + SC_COUNT + 3;
 
 extern "C" void kerr_opts_default(kerr_opts *o)
 {
@@ -109,6 +109,7 @@ extern "C" void kerr_opts_default(kerr_opts *o)
     o->budget_ns = 0;
     o->zone_prec = KERR_ZONE_FP64;
     o->zone_variant = -1;
+    o->zone_quantum = 32;
 }
 
 extern "C" const char *kerr_last_error(void) { return g_err.c_str(); }
@@ -239,6 +240,8 @@ static int check_opts(const kerr_opts *o)
                     o->zone_prec);
     if (o->variant < -1 || o->variant >= kNumVariants)
         return fail(KERR_EINVAL, "opts.variant = %d outside [-1, %d)", o->variant, kNumVariants);
+    if (o->zone_quantum < 0)
+        return fail(KERR_EINVAL, "opts.zone_quantum = %d < 0", o->zone_quantum);
     if (o->zone_variant < -1 || o->zone_variant >= kNumZoneVariants)
         return fail(KERR_EINVAL, "opts.zone_variant = %d outside [-1, %d)", o->zone_variant,
                     kNumZoneVariants);
@@ -395,11 +398,13 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
     P.renorm_every = o->renorm_every;
     P.clip_maxit = o->clip_maxit;
     P.zone_df = o->zone_prec == KERR_ZONE_F32X2 ? 1 : 0;
+    P.zone_quantum = o->zone_quantum;
     P.budget_ns = o->budget_ns;
     P.head = c->d_scratch;
     P.stats = c->d_scratch + 1;
     P.zcount = c->d_scratch + 1 + SC_COUNT;
     P.zhead = c->d_scratch + 2 + SC_COUNT;
+    P.zpush = c->d_scratch + 3 + SC_COUNT;
     if (o->prec == KERR_FP32_KAHAN) {
         // state [16][n] and constant [KC_COUNT][n] float planes
         if (n > c->work_cap) {
@@ -428,6 +433,8 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
             c->d_zone = nullptr;
             c->zone_cap = 0;
             cudaError_t e = cudaMalloc(&c->d_zone, (size_t)want * sizeof(ZoneEntry));
+            if (e == cudaSuccess)    // queue slots start empty (seq = 0)
+                e = cudaMemset(c->d_zone, 0, (size_t)want * sizeof(ZoneEntry));
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 return fail(KERR_ENOMEM, "zone buffer allocation (%lld entries) failed",
@@ -648,6 +655,8 @@ extern "C" int kerr_get_stats(kerr_ctx *c, kerr_stats *out)
     out->rhs_fp64 = (int64_t)s[SC_RHS64];
     out->attempts_fp64 = (int64_t)s[SC_ATT64];
     out->deferred = (int64_t)s[SC_DEFERRED];
+    out->requeued = (int64_t)s[SC_REQUEUED];
+    out->queue_errors = (int64_t)s[SC_STATUS + ST_NONE];
     for (int j = 0; j < 8; ++j)
         out->status_count[j] = (int64_t)s[SC_STATUS + j];
     float ms = 0.f;

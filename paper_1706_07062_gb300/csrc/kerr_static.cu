@@ -39,7 +39,7 @@ constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 // Layout of the scratch array (byte offsets, each part 256-byte aligned).
-constexpr size_t kCountersWords = 1 + SC_COUNT + 2;     // queue head, stats, zone count/head
+constexpr size_t kCountersWords = 1 + SC_COUNT + 3;     // queue head, stats, zone count/head/push
 constexpr size_t kOffCounters = 0;
 constexpr size_t kOffCams = align_up(kOffCounters + kCountersWords * sizeof(unsigned long long));
 constexpr size_t kOffWork = align_up(kOffCams + kMaxCams * sizeof(CamDev));
@@ -104,7 +104,7 @@ extern "C" int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam,
         o->renorm_every < 0 || !(o->fp64_zone >= 0.0) || o->variant < -1 ||
         (o->zone_prec != KERR_ZONE_FP64 && o->zone_prec != KERR_ZONE_F32X2) ||
         o->zone_variant < -1 || o->zone_variant >= kNumZoneVariants ||
-        o->variant >= kNumVariants)
+        o->zone_quantum < 0 || o->variant >= kNumVariants)
         return fail(KERR_EINVAL, "kerr_trace_camera_static: invalid options");
     CamDev cd[kMaxCams];
     int64_t n = 0;
@@ -175,11 +175,13 @@ extern "C" int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam,
     P.renorm_every = o->renorm_every;
     P.clip_maxit = o->clip_maxit;
     P.zone_df = o->zone_prec == KERR_ZONE_F32X2 ? 1 : 0;
+    P.zone_quantum = o->zone_quantum;
     P.budget_ns = o->budget_ns;
     P.head = ctr;
     P.stats = ctr + 1;
     P.zcount = ctr + 1 + SC_COUNT;
     P.zhead = ctr + 2 + SC_COUNT;
+    P.zpush = ctr + 3 + SC_COUNT;
     const int variant = o->variant >= 0 ? o->variant : 0;
     if (o->prec == KERR_FP32_KAHAN) {
         P.s_state = work;

@@ -49,7 +49,9 @@ enum : int {
     SC_RHS64 = 4,
     SC_ATT64 = 5,
     SC_DEFERRED = 6, // geodesics handed to the zone phase
-    SC_STATUS = 8,   // 8 slots: geodesics per status code
+    SC_REQUEUED = 7, // zone phase: geodesics put back behind waiting ones
+    SC_STATUS = 8,   // 8 slots: geodesics per status code; slot 0 (no status)
+                     // counts zone-queue hand-overs that timed out (never expected)
     SC_COUNT = 16
 };
 
@@ -62,7 +64,8 @@ struct ZoneEntry {
     float h, rnow;
     uint32_t nsteps;
     int32_t since_renorm;
-    int32_t pad[2];
+    uint32_t seq;      // zone queue: (index + 1) mod 2^32 once written, 0 once read
+    int32_t pad;
 };
 static_assert(sizeof(ZoneEntry) == 96, "zone entry layout");
 
@@ -102,6 +105,8 @@ struct TraceParams {
     double r_escape, t_end, fp64_zone;
     int32_t renorm_every, clip_maxit;
     int32_t zone_df;            // FP32 path: zone steps in float-float (1) or FP64 (0)
+    int32_t zone_quantum;       // zone phase: attempts before a geodesic yields its
+                                // lane to a waiting one (0: run to the end)
     uint64_t budget_ns;
     unsigned long long *head;   // work-queue counter, zero at launch
     unsigned long long *stats;  // SC_COUNT counters, zero at launch
@@ -111,6 +116,7 @@ struct TraceParams {
     int64_t zcap;               // capacity of zbuf
     unsigned long long *zcount; // entries appended, zero at launch
     unsigned long long *zhead;  // zone-phase work-queue counter, zero at launch
+    unsigned long long *zpush;  // zone phase: re-queued geodesics, zero at launch
 };
 
 #ifndef KERR_TYPES_ONLY
@@ -281,6 +287,14 @@ __device__ __forceinline__ double step_factor(double err)
     return fmin(5.0, fmax(0.2, f));
 }
 
+// The step-size factor of an FP64 zone step of the FP32+Kahan path, taken in
+// FP32: it only scales the next trial step, and the FP32 path's accuracy
+// target (1e-5) leaves ample room for a factor rounded to FP32.
+__device__ __forceinline__ double step_factor_f(double err)
+{
+    return (double)step_factor((float)err);
+}
+
 template <bool KAHAN, typename T>
 __device__ __forceinline__ void add_incr(T &y, T &c, T d)
 {
@@ -392,7 +406,7 @@ template <> __device__ __forceinline__ dfloat from_d<dfloat>(double d) { return 
 // One attempted step with events.  (y, c) is the lane state; h the trial
 // step; rn receives r of the new state when a step is accepted.  Returns a
 // status code when the geodesic terminates, ST_NONE otherwise.
-template <bool KAHAN, typename T>
+template <bool KAHAN, typename T, bool FAST_FACTOR = false>
 __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &P, int64_t id,
                                          const T tol, T y[8], T c[8], T &h, T &rn,
                                          uint32_t &nrhs, uint32_t &nacc, int &since_renorm)
@@ -404,7 +418,11 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
     T d[8];
     const T err = attempt(a, a2, y, A0, h, tol, d);
     nrhs += 11;
-    const T fac = step_factor(err);
+    T fac;
+    if constexpr (FAST_FACTOR)
+        fac = step_factor_f(err);
+    else
+        fac = step_factor(err);
     if (!(err <= T(1))) {
         h *= fac;
         return ST_NONE;
@@ -711,8 +729,8 @@ static __device__ __noinline__ ZoneResult zone_step(const RayConst rc, const Tra
     ZoneResult R;
     R.nrhs = 0;
     R.nacc = 0;
-    R.st = step_once<false, double>(rc, P, id, P.tol, yd, cd, hd, rd, R.nrhs, R.nacc,
-                                    since_renorm);
+    R.st = step_once<false, double, true>(rc, P, id, P.tol, yd, cd, hd, rd, R.nrhs, R.nacc,
+                                          since_renorm);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         R.s.y[i] = (float)yd[i];
@@ -774,7 +792,7 @@ __device__ __forceinline__ double geodesic_spin(const TraceParams &P, int64_t id
 
 // Statistics: warp reduction, one atomic per counter per warp.
 struct Counters {
-    uint32_t geo = 0, att = 0, acc = 0, rhs32 = 0, rhs64 = 0, att64 = 0, def = 0;
+    uint32_t geo = 0, att = 0, acc = 0, rhs32 = 0, rhs64 = 0, att64 = 0, def = 0, req = 0;
     uint32_t st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     __device__ __forceinline__ void status(int s)
     {
@@ -792,17 +810,17 @@ struct Counters {
                 x += __shfl_xor_sync(FULL, x, o);
             return x;
         };
-        const unsigned long long v[7] = {wsum(geo), wsum(att), wsum(acc), wsum(rhs32),
-                                         wsum(rhs64), wsum(att64), wsum(def)};
+        const unsigned long long v[8] = {wsum(geo),   wsum(att),   wsum(acc), wsum(rhs32),
+                                         wsum(rhs64), wsum(att64), wsum(def), wsum(req)};
         unsigned long long w[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
             w[j] = wsum(st[j]);
         if ((threadIdx.x & 31) == 0) {
-            const int slot[7] = {SC_GEODESICS, SC_ATTEMPTS, SC_ACCEPTED, SC_RHS32,
-                                 SC_RHS64,     SC_ATT64,    SC_DEFERRED};
+            const int slot[8] = {SC_GEODESICS, SC_ATTEMPTS, SC_ACCEPTED, SC_RHS32,
+                                 SC_RHS64,     SC_ATT64,    SC_DEFERRED, SC_REQUEUED};
 #pragma unroll
-            for (int j = 0; j < 7; ++j)
+            for (int j = 0; j < 8; ++j)
                 if (v[j])
                     atomicAdd(stats + slot[j], v[j]);
 #pragma unroll
@@ -823,6 +841,84 @@ __device__ __forceinline__ unsigned long long warp_claim(unsigned long long *ctr
     if ((int)(threadIdx.x & 31) == leader)
         base = atomicAdd(ctr, (unsigned long long)__popc(mask));
     return __shfl_sync(FULL, base, leader);
+}
+
+// ---------------------------------------------------------------------------
+// Zone-phase queue.  The deferred geodesics sit in a ring of zcap entries:
+// index i lives in slot i mod zcap.  The FP32 phase writes indices
+// 0 .. n0 - 1 (n0 = min(zcount, zcap)); the zone phase re-queues at
+// n0 + zpush (zpush counts re-queued geodesics) and claims at zhead.  A
+// writer fills the entry and then publishes seq = i + 1 (release); a reader waits for that value (acquire), reads, and
+// sets seq = 0, which a writer of the slot's next index waits for.  The ring
+// never holds more geodesics than the phase started with (each is either
+// in a lane or in the ring), so zcap >= that count keeps indices i and
+// i + zcap from meeting.  Both waits are bounded.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Waits (bounded: about 2^22 polls, ~0.5 s) until *p == want.
+__device__ __forceinline__ bool wait_seq(const uint32_t *p, uint32_t want)
+{
+    for (uint32_t it = 0; it < (1u << 22); ++it) {
+        if (ld_acquire(p) == want)
+            return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+// Warp-aggregated claim of up to popc(mask) indices below the queue tail
+// t0 + *pushed.  Returns the first index; *take (warp-uniform) is how many
+// were claimed and *empty whether the leader saw head >= tail.
+__device__ __forceinline__ unsigned long long warp_claim_queue(unsigned long long *head,
+                                                               unsigned long long t0,
+                                                               const unsigned long long *pushed,
+                                                               unsigned mask, unsigned *take,
+                                                               bool *empty)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    unsigned got = 0;
+    int emp = 0;
+    if ((int)(threadIdx.x & 31) == leader) {
+        unsigned long long h = ld_relaxed(head);
+        for (int tries = 0; tries < 64; ++tries) {
+            const unsigned long long t = t0 + (pushed ? ld_relaxed(pushed) : 0ull);
+            if (h >= t) {
+                emp = 1;
+                break;
+            }
+            const unsigned long long k =
+                min((unsigned long long)__popc(mask), t - h);
+            const unsigned long long old = atomicCAS(head, h, h + k);
+            if (old == h) {
+                base = h;
+                got = (unsigned)k;
+                break;
+            }
+            h = old;
+        }
+    }
+    base = __shfl_sync(FULL, base, leader);
+    *take = __shfl_sync(FULL, got, leader);
+    *empty = __shfl_sync(FULL, emp, leader) != 0;
+    return base;
 }
 
 // ===========================================================================
@@ -1041,11 +1137,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
     unsigned long long n_items = (unsigned long long)n;
     if (P.n_dev && *P.n_dev < n_items)
         n_items = *P.n_dev;
+    // zone phase: n0 entries from the FP32 phase; re-queueing needs them all
+    // in the ring (no overflow)
+    unsigned long long n0 = 0;
+    bool requeue = false;
     if (PHASE != 0) {
         const unsigned long long zc = *P.zcount;
-        n_items = zc < (unsigned long long)P.zcap ? zc : (unsigned long long)P.zcap;
+        const unsigned long long cap = (unsigned long long)P.zcap;
+        n0 = zc < cap ? zc : cap;
+        requeue = P.zone_quantum > 0 && zc <= cap && P.zpush != nullptr;
     }
-    unsigned long long *const head = PHASE != 0 ? P.zhead : P.head;
+    const unsigned long long zcap = (unsigned long long)P.zcap;
     const bool can_defer = PHASE == 0 && P.zbuf != nullptr && P.fp64_zone > 0.0;
     const float tol = (float)P.tol;
     const float h0 = (float)P.h0;
@@ -1055,7 +1157,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
     RayConst rc;
     float y[8], c[8];
     float h = 0.f, rnow = 0.f;
-    uint32_t nsteps = 0;
+    uint32_t nsteps = 0, quantum = 0;
     int since_renorm = 0;
     Counters C;
     const unsigned long long t_start = global_ns();
@@ -1064,67 +1166,95 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
     for (;;) {
         // ---- refill idle lanes from the queue (one atomic per warp)
         const unsigned need = __ballot_sync(FULL, !has);
+        bool empty = false;
         if (need && !drained) {
-            const unsigned long long base = warp_claim(head, need);
-            if (base + __popc(need) >= n_items)
-                drained = true;
-            if (!has) {
-                const unsigned long long my = base + __popc(need & lt_mask);
-                if (my < n_items) {
-                    bool go = true;
-                    if (PHASE != 0) {
-                        const ZoneEntry &e = P.zbuf[my];
-                        id = e.id;
+            unsigned long long my = 0;
+            bool got = false;
+            if (PHASE != 0) {
+                unsigned take = 0;
+                const unsigned long long base = warp_claim_queue(
+                    P.zhead, n0, requeue ? P.zpush : nullptr, need, &take, &empty);
+                const unsigned rank = __popc(need & lt_mask);
+                my = base + rank;
+                got = !has && rank < take;
+            } else {
+                const unsigned long long base = warp_claim(P.head, need);
+                if (base + __popc(need) >= n_items)
+                    drained = true;
+                my = base + __popc(need & lt_mask);
+                got = !has && my < n_items;
+            }
+            if (got) {
+                bool go = true;
+                if (PHASE != 0) {
+                    ZoneEntry &e = P.zbuf[my % zcap];
+                    go = wait_seq(&e.seq, (uint32_t)(my + 1ull));
+                    if (go) {
+                        // read past L1: the slot may have been read here before
+                        const float4 *v = reinterpret_cast<const float4 *>(e.y);
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const float4 a4 = __ldcg(v + q), c4 = __ldcg(v + 2 + q);
+                            y[4 * q] = a4.x;
+                            y[4 * q + 1] = a4.y;
+                            y[4 * q + 2] = a4.z;
+                            y[4 * q + 3] = a4.w;
+                            c[4 * q] = c4.x;
+                            c[4 * q + 1] = c4.y;
+                            c[4 * q + 2] = c4.z;
+                            c[4 * q + 3] = c4.w;
+                        }
+                        id = (int64_t)__ldcg(reinterpret_cast<const long long *>(&e.id));
+                        h = __ldcg(&e.h);
+                        rnow = __ldcg(&e.rnow);
+                        nsteps = __ldcg(&e.nsteps);
+                        since_renorm = __ldcg(&e.since_renorm);
+                        st_release(&e.seq, 0u);
+                        load_const_full(P, id, rc);
+                        quantum = 0;
+                    } else {
+                        C.status(ST_NONE);   // hand-over timed out (counted, never expected)
+                    }
+                } else {
+                    id = (int64_t)my;
+                    go = P.status[id] == ST_NONE;     // set-up already ended it
+                    if (go) {
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            y[i] = e.y[i];
-                            c[i] = e.c[i];
+                            y[i] = P.s_state[i * n + id];
+                            c[i] = P.s_state[(8 + i) * n + id];
                         }
-                        h = e.h;
-                        rnow = e.rnow;
-                        nsteps = e.nsteps;
-                        since_renorm = e.since_renorm;
-                        load_const_full(P, id, rc);
-                    } else {
-                        id = (int64_t)my;
-                        go = P.status[id] == ST_NONE;     // set-up already ended it
-                        if (go) {
+                        if (P.renorm_every > 0)
+                            load_const_full(P, id, rc);   // FP64 spin for re-solving k^t
+                        else
+                            load_const_f32(P, id, rc);
+                        h = h0;
+                        nsteps = 0;
+                        since_renorm = 0;
+                        rnow = ks_r(rc.af * rc.af, y[1], y[2], y[3]);
+                    }
+                }
+                if (go) {
+                    if (timed_out) {
+                        P.status[id] = ST_TIMEOUT;
+                        P.steps[id] = nsteps;
+                        C.status(ST_TIMEOUT);
+                        if (PHASE != 0) {
 #pragma unroll
                             for (int i = 0; i < 8; ++i) {
-                                y[i] = P.s_state[i * n + id];
-                                c[i] = P.s_state[(8 + i) * n + id];
+                                P.s_state[i * n + id] = y[i];
+                                P.s_state[(8 + i) * n + id] = c[i];
                             }
-                            if (P.renorm_every > 0)
-                                load_const_full(P, id, rc);   // FP64 spin for re-solving k^t
-                            else
-                                load_const_f32(P, id, rc);
-                            h = h0;
-                            nsteps = 0;
-                            since_renorm = 0;
-                            rnow = ks_r(rc.af * rc.af, y[1], y[2], y[3]);
                         }
-                    }
-                    if (go) {
-                        if (timed_out) {
-                            P.status[id] = ST_TIMEOUT;
-                            P.steps[id] = nsteps;
-                            C.status(ST_TIMEOUT);
-                            if (PHASE != 0) {
-#pragma unroll
-                                for (int i = 0; i < 8; ++i) {
-                                    P.s_state[i * n + id] = y[i];
-                                    P.s_state[(8 + i) * n + id] = c[i];
-                                }
-                            }
-                        } else {
-                            has = true;
-                        }
+                    } else {
+                        has = true;
                     }
                 }
             }
         }
         if (!__any_sync(FULL, has)) {
-            if (drained)      // warp-uniform: derived from the shuffled base
+            // warp-uniform: drained / empty come from the shuffled claim
+            if (PHASE != 0 ? empty : drained)
                 break;
             continue;
         }
@@ -1136,7 +1266,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                 const unsigned long long zb = warp_claim(P.zcount, dm);
                 if ((dm >> lane) & 1u) {
                     const unsigned long long slot = zb + __popc(dm & lt_mask);
-                    if (slot < (unsigned long long)P.zcap) {
+                    if (slot < zcap) {
                         ZoneEntry &e = P.zbuf[slot];
 #pragma unroll
                         for (int i = 0; i < 8; ++i) {
@@ -1148,6 +1278,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                         e.rnow = rnow;
                         e.nsteps = nsteps;
                         e.since_renorm = since_renorm;
+                        e.seq = (uint32_t)(slot + 1ull);   // visible to the next launch
                         ++C.def;
                         has = false;
                         in_zone = false;
@@ -1163,6 +1294,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                 st = ST_MAXSTEPS;
             } else {
                 ++nsteps;
+                ++quantum;
                 ++C.att;
                 if (in_zone) {
                     if (PHASE == 0)
@@ -1209,6 +1341,47 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                 P.steps[id] = (int32_t)nsteps;
                 C.status(st);
                 has = false;
+            }
+        }
+        // ---- zone phase: after zone_quantum attempts a geodesic yields its
+        // lane to one that waits in the queue (processor sharing), so that
+        // the phase is not left with a second, partly filled wave of lanes
+        if (PHASE != 0 && requeue) {
+            const bool want = has && !timed_out && quantum >= (uint32_t)P.zone_quantum;
+            const unsigned pm = __ballot_sync(FULL, want);
+            if (pm) {
+                const int leader = __ffs(pm) - 1;
+                int waiting = 0;
+                if (lane == leader)
+                    waiting = n0 + ld_relaxed(P.zpush) > ld_relaxed(P.zhead) ? 1 : 0;
+                waiting = __shfl_sync(FULL, waiting, leader);
+                if (waiting) {
+                    const unsigned long long b = warp_claim(P.zpush, pm);
+                    if (want) {
+                        const unsigned long long idx = n0 + b + __popc(pm & lt_mask);
+                        ZoneEntry &e = P.zbuf[idx % zcap];
+                        if (wait_seq(&e.seq, 0u)) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                e.y[i] = y[i];
+                                e.c[i] = c[i];
+                            }
+                            e.id = id;
+                            e.h = h;
+                            e.rnow = rnow;
+                            e.nsteps = nsteps;
+                            e.since_renorm = since_renorm;
+                            st_release(&e.seq, (uint32_t)(idx + 1ull));
+                            ++C.req;
+                            has = false;
+                        } else {
+                            C.status(ST_NONE);   // slot never freed (counted, never expected)
+                            quantum = 0;
+                        }
+                    }
+                } else if (want) {
+                    quantum = 0;     // nobody waits: another quantum here
+                }
             }
         }
         // ---- wall-time budget (warp-uniform decision)

@@ -41,7 +41,7 @@ class Opts(ctypes.Structure):
                 ("t_end", ctypes.c_double), ("fp64_zone", ctypes.c_double),
                 ("clip_maxit", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("budget_ns", ctypes.c_uint64), ("zone_prec", ctypes.c_int32),
-                ("zone_variant", ctypes.c_int32)]
+                ("zone_variant", ctypes.c_int32), ("zone_quantum", ctypes.c_int32)]
 
 
 class Camera(ctypes.Structure):
@@ -57,7 +57,8 @@ class Stats(ctypes.Structure):
                 ("rhs_fp64", ctypes.c_int64), ("attempts_fp64", ctypes.c_int64),
                 ("deferred", ctypes.c_int64),
                 ("status_count", ctypes.c_int64 * 8), ("kernel_ms", ctypes.c_float),
-                ("variant", ctypes.c_int32), ("phase_ms", ctypes.c_float * 4)]
+                ("variant", ctypes.c_int32), ("phase_ms", ctypes.c_float * 4),
+                ("requeued", ctypes.c_int64), ("queue_errors", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_

@@ -148,3 +148,46 @@ def particle_subset(ps: ParticleSet, k: int = 4096, seed: int = PARTICLE_SEED) -
         idx = np.nonzero((la >= bins[b]) & (la < bins[b + 1]))[0]
         out.append(rng.choice(idx, size=min(per, idx.size), replace=False))
     return np.sort(np.concatenate(out))
+
+
+# ---------------------------------------------------------------------------
+# the learned surrogate: training rays and evaluation images
+# ---------------------------------------------------------------------------
+SURR_TRAIN_SEED = 1710
+SURR_EVAL_SEED = 1709
+
+
+def surrogate_points(n: int = 10_000_000, seed: int = SURR_TRAIN_SEED,
+                     half_width: float = 25.0) -> np.ndarray:
+    """Training rays (n, 4): alpha, beta ~ U[-25, 25], spin a ~ U[0, 0.998],
+    inclination ~ U[5, 85] deg (radians)."""
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.uniform(-half_width, half_width, n),
+                     rng.uniform(-half_width, half_width, n),
+                     rng.uniform(0.0, 0.998, n),
+                     rng.uniform(5.0, 85.0, n) * DEG], axis=1)
+
+
+def surrogate_eval_cameras(n_images: int = 8, side: int = 2048, seed: int = SURR_EVAL_SEED,
+                           r_obs: float = 1000.0, half_width: float = 25.0) -> list[CameraSpec]:
+    """Evaluation images: spin and inclination drawn per image as for training."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.0, 0.998, n_images)
+    inc = rng.uniform(5.0, 85.0, n_images) * DEG
+    return [CameraSpec(float(a[i]), float(inc[i]), r_obs, half_width, side, side)
+            for i in range(n_images)]
+
+
+def surrogate_init(seed: int = SURR_TRAIN_SEED) -> np.ndarray:
+    """Seeded initial parameters of the surrogate in the C ABI's padded layout
+    (uniform +-1/sqrt(fan_in) on the live weights, zero padding and biases)."""
+    rng = np.random.default_rng(seed + 1000)
+    ins, outs = [16, 256, 256, 256, 256], [256, 256, 256, 256, 64]
+    live_in, live_out = [4, 256, 256, 256, 256], [256, 256, 256, 256, 8]
+    parts = []
+    for l in range(5):
+        W = np.zeros((outs[l], ins[l]), dtype=np.float32)
+        lim = 1.0 / np.sqrt(live_in[l])
+        W[:live_out[l], :live_in[l]] = rng.uniform(-lim, lim, size=(live_out[l], live_in[l]))
+        parts += [W.ravel(), np.zeros(outs[l], dtype=np.float32)]
+    return np.concatenate(parts)

@@ -293,9 +293,41 @@ def test_zone_phase_counts(ctx):
     assert s.deferred > 0 and s.attempts_fp64 > 0 and s.rhs_fp64 > 0
     assert all(t >= 0 for t in s.phase_ms) and s.phase_ms[1] > 0 and s.phase_ms[2] > 0
     assert abs(sum(s.phase_ms) - s.kernel_ms) < 0.05 * s.kernel_ms + 0.05
+    assert s.queue_errors == 0
     K.kerr_trace_camera(ctx, cam(spec), K.default_opts(fp64_zone=0.0), device=DEV)
     s0 = K.kerr_get_stats(ctx)
-    assert s0.deferred == 0 and s0.attempts_fp64 == 0
+    assert s0.deferred == 0 and s0.attempts_fp64 == 0 and s0.requeued == 0
+
+
+@pytest.mark.parametrize("zone_prec", [K.ZONE_FP64, K.ZONE_F32X2])
+def test_zone_requeue_is_exact(ctx, zone_prec):
+    """Re-queueing zone geodesics (processor sharing) only moves a geodesic
+    between lanes with its whole state, so every output is bit-identical for
+    any quantum; a quantum of 1 hands geodesics over after every attempt.
+    About half of the 320 x 320 rays enter the zone: more than the zone
+    phase has lanes, so geodesics wait and get re-queued."""
+    spec = W.CameraSpec(0.99, 0.3, 1000.0, 6.0, 320, 320)
+    res = {}
+    for q in (0, 1, 16):
+        out = K.alloc_out(spec.n, DEV, cross=True)
+        K.kerr_trace_camera(ctx, cam(spec), K.default_opts(zone_quantum=q, zone_prec=zone_prec),
+                            out=out)
+        torch.cuda.synchronize()
+        res[q] = (out, K.kerr_get_stats(ctx))
+    base, s0 = res[0]
+    assert s0.requeued == 0 and s0.deferred > 0
+    for q in (1, 16):
+        out, s = res[q]
+        assert s.queue_errors == 0
+        assert s.requeued > 0
+        assert s.geodesics == spec.n and sum(s.status_count[1:]) == spec.n
+        for name in ("x", "k", "status", "steps", "diag", "cross"):
+            a, b = getattr(out, name), getattr(base, name)
+            if a.is_floating_point():
+                assert torch.equal(a.isnan(), b.isnan()), name
+                a, b = torch.nan_to_num(a), torch.nan_to_num(b)
+            assert torch.equal(a, b), name
+        assert s.attempts_fp64 == s0.attempts_fp64 and s.rhs_fp64 == s0.rhs_fp64
 
 
 def test_zone_buffer_overflow_falls_back_in_place(ctx):
@@ -311,6 +343,7 @@ def test_zone_buffer_overflow_falls_back_in_place(ctx):
     s1 = K.kerr_get_stats(fresh)
     fresh.close()
     assert s1.deferred == spec.n // 4            # buffer full: the rest ran in place
+    assert s1.requeued == 0 and s1.queue_errors == 0   # no re-queueing after an overflow
     big = K.kerr_init(spec.a)
     K.kerr_trace_camera(big, cam(W.CameraSpec(0.9, 1.0, 1000.0, 3.0, 1024, 1024)), opts,
                         device=DEV)                # grows the buffer to 2^18 entries

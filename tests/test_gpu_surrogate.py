@@ -196,3 +196,58 @@ def test_critical_curve_bounds_the_captured_region():
     lo, hi = curve[:, 0].min(), curve[:, 0].max()   # the extremes in alpha lie on beta = 0
     assert abs(cap.min() - lo) < 0.1 and abs(cap.max() - hi) < 0.1, (cap.min(), cap.max(), lo, hi)
     ctx.close()
+
+
+def test_trained_surrogate_gains_over_the_integrator():
+    """What the learned part buys: trained on 2M integrator rays (seeded as
+    in the evaluation workload), the surrogate with fallback renders a
+    2048 x 2048 image faster than the integrator alone, with no capture
+    disagreement on the pixels it answers (checked against the FP64
+    integrator and, on a sample, the FP64 oracle) and small label errors."""
+    from paper_1706_07062_gb300 import workloads as W
+    ctx = K.kerr_init(0.5)
+    opts = K.default_opts()
+    pts = torch.tensor(W.surrogate_points(2_000_000), device=DEV)
+    inp, tgt, msk = K.kerr_surrogate_targets(ctx, pts, 1000.0, opts)
+    s = K.Surrogate(W.surrogate_init())
+    losses = K.kerr_surrogate_train(s, inp, tgt, msk, epochs=6, batch=8192, lr=2e-3)
+    assert losses[-1] < 0.5 * losses[0]
+    cs = W.CameraSpec(0.7, np.radians(50.0), 1000.0, 25.0, 2048, 2048)
+    cam = K.camera(*cs.as_tuple())
+    ref = K.alloc_out(cs.n, DEV, diag=False, cross=True)
+    K.kerr_surrogate_render(ctx, s, cam, opts)                 # warm-up
+    K.kerr_trace_camera(ctx, cam, opts, out=ref)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out, fb, nfb = K.kerr_surrogate_render(ctx, s, cam, opts)
+    torch.cuda.synchronize()
+    t_sur = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    K.kerr_trace_camera(ctx, cam, opts, out=ref)
+    torch.cuda.synchronize()
+    t_int = time.perf_counter() - t0
+    assert t_int / t_sur > 1.3, (t_int, t_sur)
+    assert 0 < nfb < 0.1 * cs.n
+    ref64 = K.alloc_out(cs.n, DEV, diag=False, cross=True)
+    K.kerr_trace_camera(ctx, cam, K.default_opts(prec=K.FP64), out=ref64)
+    o, f = to_np(out), to_np(fb).astype(bool)
+    st = to_np(ref64.status)
+    cr = to_np(ref64.cross)
+    net = ~f
+    assert np.mean((o[0][net] >= 0.5) != (st[net] == 2)) < 1e-4
+    ok = net & ~np.isnan(o[1]) & ~np.isnan(cr[0])
+    assert ok.sum() > 0.5 * cs.n
+    r1 = np.abs(o[1][ok] - cr[0][ok]) / cr[0][ok]
+    ph = np.abs(np.remainder(o[2][ok] - cr[1][ok] + np.pi, 2 * np.pi) - np.pi)
+    assert np.median(r1) < 0.03 and np.percentile(r1, 99) < 0.2
+    assert np.median(ph) < 0.03
+    # fallback pixels carry the integrator's answer
+    np.testing.assert_array_equal(o[0][f], (to_np(ref.status)[f] == 2).astype(np.float32))
+    # a sample of network pixels against the FP64 oracle
+    rng = np.random.default_rng(3)
+    idx = np.sort(rng.choice(np.nonzero(net)[0], 256, replace=False))
+    y0 = O.camera_ic(*cs.as_tuple(), idx)
+    res = O.trace(cs.a, y0, O.Opts(tol=1e-8))
+    assert np.mean((o[0][idx] >= 0.5) != (res.status == 2)) <= 1 / 256
+    s.close()
+    ctx.close()
