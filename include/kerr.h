@@ -354,6 +354,15 @@ int kerr_surrogate_render(kerr_ctx *ctx, kerr_surrogate *s, const kerr_camera *c
                           const kerr_opts *opts, float p_lo, float p_hi, float crit_dist,
                           float *out, uint8_t *fallback, int64_t *n_fallback, void *stream);
 
+/* Check of the integrator's FP64 reciprocal, reciprocal square root and
+ * square root (Newton-refined hardware approximations, see the FP64 steps;
+ * this library's own primitives, with no counterpart in the paper): for
+ * device x[n] writes device out[3][n] = 1/x, 1/sqrt(x), sqrt(x) as the
+ * integrator computes them (for finite x > 0; sqrt(0) = 0, and NaN or a
+ * negative x gives NaN).  Asynchronous on `stream`.  KERR_EINVAL for
+ * n < 0 or NULL buffers with n > 0; n == 0 is a no-op. */
+int kerr_check_fp64_math(const double *x, int64_t n, double *out, void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *kerr_last_error(void);
 

@@ -11,9 +11,16 @@ namespace kerr {
 
 // ---------------------------------------------------------------------------
 // Precision-specific primitives.  FP32 uses the hardware approximations of
-// the PTX ISA (rcp/rsqrt/sqrt .approx, relative error ~2^-23); FP64 uses the
-// correctly rounded operators so that the FP64 path tracks an FP64 reference
-// to rounding.
+// the PTX ISA (rcp/rsqrt/sqrt .approx, relative error ~2^-23).  FP64 refines
+// the PTX ISA's approximate FP64 reciprocal and reciprocal square root by one
+// higher-order Newton-Raphson step (Markstein-style refinement: with
+// e = 1 - x y0 for 1/x, or e = 1 - x y0^2 for 1/sqrt(x), the series
+// y0 (1 + e + e^2) and y0 (1 + e/2 + 3e^2/8) leave an error of order e^3),
+// and takes sqrt(v) as v rsqrt(v) plus one residual correction
+// s + (v - s^2) rsqrt(v) / 2.  On GB300 FP64 runs at 1/64 of the FP32 rate,
+// and these take about a third of the FP64 instructions of the correctly
+// rounded operators; their error stays within a few units in the last place
+// (tested against 1/x, 1/sqrt(x) and sqrt(x) on the device).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float k_rcp(float x)
 {
@@ -33,16 +40,35 @@ __device__ __forceinline__ float k_sqrt(float x)
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-__device__ __forceinline__ double k_rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ double k_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ double k_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ double k_rcp(double x)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double e = __fma_rn(-x, y, 1.0);
+    return __fma_rn(y, __fma_rn(e, e, e), y);
+}
+__device__ __forceinline__ double k_rsqrt(double x)
+{
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double e = __fma_rn(-(x * y), y, 1.0);
+    return __fma_rn(y * e, __fma_rn(0.375, e, 0.5), y);
+}
+__device__ __forceinline__ double k_sqrt(double v)
+{
+    const double y = k_rsqrt(v);
+    const double s = v * y;
+    const double r = __fma_rn(-s, s, v);
+    const double q = __fma_rn(r, 0.5 * y, s);
+    return v == 0.0 ? v : q;          // sqrt(+-0) = +-0 (v y would be NaN)
+}
 
 __device__ __forceinline__ float k_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double k_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Two reciprocals 1/p and 1/q.  FP32: two hardware approximations.  FP64:
-// one correctly rounded division of 1 by p q shared by both (p q stays far
-// from overflow for any radius below ~1e50).
+// one reciprocal of p q shared by both (p q stays far from overflow for any
+// radius below ~1e50).
 __device__ __forceinline__ void recip2(float p, float q, float &ip, float &iq)
 {
     ip = k_rcp(p);
@@ -50,7 +76,7 @@ __device__ __forceinline__ void recip2(float p, float q, float &ip, float &iq)
 }
 __device__ __forceinline__ void recip2(double p, double q, double &ip, double &iq)
 {
-    const double t = 1.0 / (p * q);
+    const double t = k_rcp(p * q);
     ip = q * t;
     iq = p * t;
 }
@@ -140,6 +166,45 @@ __device__ __forceinline__ void accel(const T a, const T a2, const T x, const T 
     ax = k_fma(hL, k_fma(f, dLx, Ax), k_fma(F, lx, -k_fma(lx, Ak, fL * kdx)));
     ay = k_fma(hL, k_fma(f, dLy, Ay), k_fma(F, ly, -k_fma(ly, Ak, fL * kdy)));
     az = k_fma(hL, k_fma(f, dLz, Az), k_fma(F, lz, -k_fma(lz, Ak, fL * kdz)));
+}
+
+// ---------------------------------------------------------------------------
+// Out-of-line FP64 right-hand sides.  FP64 steps are latency-bound on GB300
+// (1/64 of the FP32 rate, one or two warps per scheduler): a kernel that
+// inlines the eleven right-hand sides of an attempt outgrows the
+// instruction cache, so its zone steps can call one copy instead; the pair
+// form evaluates two independent right-hand sides in one call, interleaved,
+// for instruction-level parallelism.  Same arithmetic as accel<double>.
+// ---------------------------------------------------------------------------
+struct Acc64 {
+    double t, x, y, z;
+};
+struct Acc64x2 {
+    Acc64 p, q;
+};
+
+static __device__ __noinline__ Acc64 accel_call(const double a, const double a2, const double x,
+                                                const double y, const double z, const double kt,
+                                                const double kx, const double ky, const double kz)
+{
+    Acc64 r;
+    accel<double>(a, a2, x, y, z, kt, kx, ky, kz, r.t, r.x, r.y, r.z);
+    return r;
+}
+
+static __device__ __noinline__ Acc64x2 accel_pair(const double a, const double a2,
+                                                  const double x1, const double y1,
+                                                  const double z1, const double kt1,
+                                                  const double kx1, const double ky1,
+                                                  const double kz1, const double x2,
+                                                  const double y2, const double z2,
+                                                  const double kt2, const double kx2,
+                                                  const double ky2, const double kz2)
+{
+    Acc64x2 r;
+    accel<double>(a, a2, x1, y1, z1, kt1, kx1, ky1, kz1, r.p.t, r.p.x, r.p.y, r.p.z);
+    accel<double>(a, a2, x2, y2, z2, kt2, kx2, ky2, kz2, r.q.t, r.q.x, r.q.y, r.q.z);
+    return r;
 }
 
 // ---------------------------------------------------------------------------

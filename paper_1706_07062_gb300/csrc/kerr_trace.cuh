@@ -185,9 +185,53 @@ template <> struct RC<double> {
 // Runge-Kutta pieces
 // ---------------------------------------------------------------------------
 
+// How an attempt evaluates its right-hand sides.  Only FP64 has a choice
+// (the other number types are always inline): inline (the compiler schedules
+// all of them together), one out-of-line copy (far less code for the
+// instruction cache), or out-of-line pairs of independent right-hand sides.
+// The arithmetic of every right-hand side is the same in all three.
+enum : int { RHS_INLINE = 0, RHS_CALL = 1, RHS_PAIR = 2 };
+
+template <int RM, typename T>
+__device__ __forceinline__ void rhs(const T a, const T a2, const T x, const T y, const T z,
+                                    const T kt, const T kx, const T ky, const T kz, T A[4])
+{
+    if constexpr (RM != RHS_INLINE && std::is_same<T, double>::value) {
+        const Acc64 r = accel_call(a, a2, x, y, z, kt, kx, ky, kz);
+        A[0] = r.t;
+        A[1] = r.x;
+        A[2] = r.y;
+        A[3] = r.z;
+    } else {
+        accel(a, a2, x, y, z, kt, kx, ky, kz, A[0], A[1], A[2], A[3]);
+    }
+}
+
+// Two independent right-hand sides at p and q = (x, y, z, k^t, k^x, k^y, k^z).
+template <int RM, typename T>
+__device__ __forceinline__ void rhs2(const T a, const T a2, const T p[7], const T q[7], T Ap[4],
+                                     T Aq[4])
+{
+    if constexpr (RM == RHS_PAIR && std::is_same<T, double>::value) {
+        const Acc64x2 r = accel_pair(a, a2, p[0], p[1], p[2], p[3], p[4], p[5], p[6], q[0], q[1],
+                                     q[2], q[3], q[4], q[5], q[6]);
+        Ap[0] = r.p.t;
+        Ap[1] = r.p.x;
+        Ap[2] = r.p.y;
+        Ap[3] = r.p.z;
+        Aq[0] = r.q.t;
+        Aq[1] = r.q.x;
+        Aq[2] = r.q.y;
+        Aq[3] = r.q.z;
+    } else {
+        rhs<RM>(a, a2, p[0], p[1], p[2], p[3], p[4], p[5], p[6], Ap);
+        rhs<RM>(a, a2, q[0], q[1], q[2], q[3], q[4], q[5], q[6], Aq);
+    }
+}
+
 // Increments d = y(lambda + h) - y(lambda) of one classic RK4 step (Sec. 3)
 // from y, with A0 = accel(y) already known: 3 right-hand sides.
-template <typename T>
+template <int RM = RHS_INLINE, typename T>
 __device__ __forceinline__ void rk4_incr(const T a, const T a2, const T y[8], const T A0[4],
                                          const T h, T d[8])
 {
@@ -200,8 +244,8 @@ __device__ __forceinline__ void rk4_incr(const T a, const T a2, const T y[8], co
         SA[j] = A0[j];
         m[j] = k_fma(hh, A0[j], y[4 + j]);
     }
-    accel(a, a2, k_fma(hh, y[5], y[1]), k_fma(hh, y[6], y[2]), k_fma(hh, y[7], y[3]), m[0], m[1],
-          m[2], m[3], A[0], A[1], A[2], A[3]);
+    rhs<RM>(a, a2, k_fma(hh, y[5], y[1]), k_fma(hh, y[6], y[2]), k_fma(hh, y[7], y[3]), m[0],
+            m[1], m[2], m[3], A);
     T m3[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -209,16 +253,16 @@ __device__ __forceinline__ void rk4_incr(const T a, const T a2, const T y[8], co
         SA[j] = k_fma(T(2), A[j], SA[j]);
         m3[j] = k_fma(hh, A[j], y[4 + j]);
     }
-    accel(a, a2, k_fma(hh, m[1], y[1]), k_fma(hh, m[2], y[2]), k_fma(hh, m[3], y[3]), m3[0], m3[1],
-          m3[2], m3[3], A[0], A[1], A[2], A[3]);
+    rhs<RM>(a, a2, k_fma(hh, m[1], y[1]), k_fma(hh, m[2], y[2]), k_fma(hh, m[3], y[3]), m3[0],
+            m3[1], m3[2], m3[3], A);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         Sk[j] = k_fma(T(2), m3[j], Sk[j]);
         SA[j] = k_fma(T(2), A[j], SA[j]);
         m[j] = k_fma(h, A[j], y[4 + j]);
     }
-    accel(a, a2, k_fma(h, m3[1], y[1]), k_fma(h, m3[2], y[2]), k_fma(h, m3[3], y[3]), m[0], m[1],
-          m[2], m[3], A[0], A[1], A[2], A[3]);
+    rhs<RM>(a, a2, k_fma(h, m3[1], y[1]), k_fma(h, m3[2], y[2]), k_fma(h, m3[3], y[3]), m[0],
+            m[1], m[2], m[3], A);
     const T h6 = h * T(1.0 / 6.0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -227,42 +271,141 @@ __device__ __forceinline__ void rk4_incr(const T a, const T a2, const T y[8], co
     }
 }
 
+// Two RK4 steps from the same y and A0, of lengths h1 and h2, in lockstep:
+// their right-hand sides go in pairs.  Each chain's arithmetic is that of
+// rk4_incr.
+template <int RM, typename T>
+__device__ __forceinline__ void rk4_incr2(const T a, const T a2, const T y[8], const T A0[4],
+                                          const T h1, const T h2, T d1[8], T d2[8])
+{
+    const T hh1 = T(0.5) * h1, hh2 = T(0.5) * h2;
+    T Sk1[4], SA1[4], m1[4], A1[4], Sk2[4], SA2[4], m2[4], A2[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        Sk1[j] = Sk2[j] = y[4 + j];
+        SA1[j] = SA2[j] = A0[j];
+        m1[j] = k_fma(hh1, A0[j], y[4 + j]);
+        m2[j] = k_fma(hh2, A0[j], y[4 + j]);
+    }
+    {
+        const T p[7] = {k_fma(hh1, y[5], y[1]), k_fma(hh1, y[6], y[2]), k_fma(hh1, y[7], y[3]),
+                        m1[0], m1[1], m1[2], m1[3]};
+        const T q[7] = {k_fma(hh2, y[5], y[1]), k_fma(hh2, y[6], y[2]), k_fma(hh2, y[7], y[3]),
+                        m2[0], m2[1], m2[2], m2[3]};
+        rhs2<RM>(a, a2, p, q, A1, A2);
+    }
+    T n1[4], n2[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        Sk1[j] = k_fma(T(2), m1[j], Sk1[j]);
+        SA1[j] = k_fma(T(2), A1[j], SA1[j]);
+        n1[j] = k_fma(hh1, A1[j], y[4 + j]);
+        Sk2[j] = k_fma(T(2), m2[j], Sk2[j]);
+        SA2[j] = k_fma(T(2), A2[j], SA2[j]);
+        n2[j] = k_fma(hh2, A2[j], y[4 + j]);
+    }
+    {
+        const T p[7] = {k_fma(hh1, m1[1], y[1]), k_fma(hh1, m1[2], y[2]), k_fma(hh1, m1[3], y[3]),
+                        n1[0], n1[1], n1[2], n1[3]};
+        const T q[7] = {k_fma(hh2, m2[1], y[1]), k_fma(hh2, m2[2], y[2]), k_fma(hh2, m2[3], y[3]),
+                        n2[0], n2[1], n2[2], n2[3]};
+        rhs2<RM>(a, a2, p, q, A1, A2);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        Sk1[j] = k_fma(T(2), n1[j], Sk1[j]);
+        SA1[j] = k_fma(T(2), A1[j], SA1[j]);
+        m1[j] = k_fma(h1, A1[j], y[4 + j]);
+        Sk2[j] = k_fma(T(2), n2[j], Sk2[j]);
+        SA2[j] = k_fma(T(2), A2[j], SA2[j]);
+        m2[j] = k_fma(h2, A2[j], y[4 + j]);
+    }
+    {
+        const T p[7] = {k_fma(h1, n1[1], y[1]), k_fma(h1, n1[2], y[2]), k_fma(h1, n1[3], y[3]),
+                        m1[0], m1[1], m1[2], m1[3]};
+        const T q[7] = {k_fma(h2, n2[1], y[1]), k_fma(h2, n2[2], y[2]), k_fma(h2, n2[3], y[3]),
+                        m2[0], m2[1], m2[2], m2[3]};
+        rhs2<RM>(a, a2, p, q, A1, A2);
+    }
+    const T h61 = h1 * T(1.0 / 6.0), h62 = h2 * T(1.0 / 6.0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        d1[j] = h61 * (Sk1[j] + m1[j]);
+        d1[4 + j] = h61 * (SA1[j] + A1[j]);
+        d2[j] = h62 * (Sk2[j] + m2[j]);
+        d2[4 + j] = h62 * (SA2[j] + A2[j]);
+    }
+}
+
 // Two RK4 steps of h/2 from y (A0 = accel(y)): total increment d, 7 RHS.
-template <typename T>
+template <int RM = RHS_INLINE, typename T>
 __device__ __forceinline__ void two_halves(const T a, const T a2, const T y[8], const T A0[4],
                                            const T h, T d[8])
 {
     T d1[8];
-    rk4_incr(a, a2, y, A0, T(0.5) * h, d1);
+    rk4_incr<RM>(a, a2, y, A0, T(0.5) * h, d1);
     T ym[8], Am[4];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
         ym[i] = y[i] + d1[i];
-    accel(a, a2, ym[1], ym[2], ym[3], ym[4], ym[5], ym[6], ym[7], Am[0], Am[1], Am[2], Am[3]);
-    rk4_incr(a, a2, ym, Am, T(0.5) * h, d);
+    rhs<RM>(a, a2, ym[1], ym[2], ym[3], ym[4], ym[5], ym[6], ym[7], Am);
+    rk4_incr<RM>(a, a2, ym, Am, T(0.5) * h, d);
 #pragma unroll
     for (int i = 0; i < 8; ++i)
         d[i] = d1[i] + d[i];
 }
 
 // One step-doubling attempt: returns the error measure and the increment of
-// the two-half-step solution (10 RHS beyond A0).
-template <typename T>
+// the two-half-step solution (10 RHS beyond A0).  With paired right-hand
+// sides the full step and the first half step run in lockstep.
+template <int RM = RHS_INLINE, typename T>
 __device__ __forceinline__ T attempt(const T a, const T a2, const T y[8], const T A0[4], const T h,
                                      const T tol, T d[8])
 {
     T df[8];
-    rk4_incr(a, a2, y, A0, h, df);
-    two_halves(a, a2, y, A0, h, d);
-    T err = T(0);
+    if constexpr (RM == RHS_PAIR) {
+        T d1[8];
+        rk4_incr2<RM>(a, a2, y, A0, h, T(0.5) * h, df, d1);
+        T ym[8], Am[4];
 #pragma unroll
-    for (int i = 1; i < 8; ++i) {
-        const T delta = (d[i] - df[i]) * T(1.0 / 15.0);
-        const T sc = tol * (T(1) + fmax(fabs(y[i]), fabs(y[i] + d[i])));
-        const T e = fabs(delta) / sc;
-        err = (e <= err) ? err : e;    // NaN propagates
+        for (int i = 0; i < 8; ++i)
+            ym[i] = y[i] + d1[i];
+        rhs<RM>(a, a2, ym[1], ym[2], ym[3], ym[4], ym[5], ym[6], ym[7], Am);
+        rk4_incr<RM>(a, a2, ym, Am, T(0.5) * h, d);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            d[i] = d1[i] + d[i];
+    } else {
+        rk4_incr<RM>(a, a2, y, A0, h, df);
+        two_halves<RM>(a, a2, y, A0, h, d);
     }
-    return err;
+    if constexpr (std::is_same<T, float>::value) {
+        T err = T(0);
+#pragma unroll
+        for (int i = 1; i < 8; ++i) {
+            const T delta = (d[i] - df[i]) * T(1.0 / 15.0);
+            const T sc = tol * (T(1) + fmax(fabs(y[i]), fabs(y[i] + d[i])));
+            const T e = fabs(delta) / sc;
+            err = (e <= err) ? err : e;    // NaN propagates
+        }
+        return err;
+    } else {
+        // FP64 / float-float: the max over i of |delta_i| / sc_i is kept as
+        // one fraction num / den, each comparison cross-multiplied (sc_i,
+        // den > 0) and one reciprocal at the end instead of a division per
+        // component; a NaN takes over and propagates
+        T num = T(0), den = T(1);
+#pragma unroll
+        for (int i = 1; i < 8; ++i) {
+            const T delta = (d[i] - df[i]) * T(1.0 / 15.0);
+            const T sc = tol * (T(1) + fmax(fabs(y[i]), fabs(y[i] + d[i])));
+            const T e = fabs(delta);
+            const bool take = !(e * den <= num * sc);
+            num = take ? e : num;
+            den = take ? sc : den;
+        }
+        return num * k_rcp(den);
+    }
 }
 
 // Step-size factor after an attempt: 0.9 err^(-1/5) clamped to [0.2, 5]; 5
@@ -326,7 +469,7 @@ __device__ __forceinline__ T event_value(int kind, T a2, const T y[8], const T c
 // step length eta in (0, h), Phi(eta) = two RK4 half steps from the last
 // accepted state (y, c)).  Writes the state on the surface to (ye, ce) and
 // returns its step length.  Bracket values s_lo = s(y_old), s_hi = s(y_new).
-template <bool KAHAN, typename T>
+template <bool KAHAN, typename T, int RM = RHS_INLINE>
 __device__ T clip(const T a, const T a2, const T y[8], const T c[8], const T A0[4], const T h,
                   int kind, T target, T target_lo, T s_lo, T s_hi, T stol, T eps, int maxit,
                   T ye[8], T ce[8], uint32_t &nrhs)
@@ -339,7 +482,7 @@ __device__ T clip(const T a, const T a2, const T y[8], const T c[8], const T A0[
         T eta = hi - s_hi * (hi - lo) / (s_hi - s_lo);
         if (!(eta > lo && eta < hi))
             eta = T(0.5) * (lo + hi);
-        two_halves(a, a2, y, A0, eta, d);
+        two_halves<RM>(a, a2, y, A0, eta, d);
         nrhs += 7;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -406,7 +549,7 @@ template <> __device__ __forceinline__ dfloat from_d<dfloat>(double d) { return 
 // One attempted step with events.  (y, c) is the lane state; h the trial
 // step; rn receives r of the new state when a step is accepted.  Returns a
 // status code when the geodesic terminates, ST_NONE otherwise.
-template <bool KAHAN, typename T, bool FAST_FACTOR = false>
+template <bool KAHAN, typename T, bool FAST_FACTOR = false, int RM = RHS_INLINE>
 __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &P, int64_t id,
                                          const T tol, T y[8], T c[8], T &h, T &rn,
                                          uint32_t &nrhs, uint32_t &nacc, int &since_renorm)
@@ -414,9 +557,9 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
     const T a = RC<T>::a(rc);
     const T a2 = a * a;
     T A0[4];
-    accel(a, a2, y[1], y[2], y[3], y[4], y[5], y[6], y[7], A0[0], A0[1], A0[2], A0[3]);
+    rhs<RM>(a, a2, y[1], y[2], y[3], y[4], y[5], y[6], y[7], A0);
     T d[8];
-    const T err = attempt(a, a2, y, A0, h, tol, d);
+    const T err = attempt<RM>(a, a2, y, A0, h, tol, d);
     nrhs += 11;
     T fac;
     if constexpr (FAST_FACTOR)
@@ -455,13 +598,13 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
     T h_used = h;
     if (rn < rcap) {
         const T s_lo = event_value<KAHAN>(0, a2, y, c, rcap, T(0));
-        h_used = clip<KAHAN>(a, a2, y, c, A0, h, 0, rcap, T(0), s_lo, rn - rcap,
+        h_used = clip<KAHAN, T, RM>(a, a2, y, c, A0, h, 0, rcap, T(0), s_lo, rn - rcap,
                              Prec<T>::stol() * rcap, Prec<T>::eps(), maxit, yn, cn, nrhs);
         st = ST_CAPTURED;
     } else if (rn > resc && k_fma(yn[1], yn[5], k_fma(yn[2], yn[6], yn[3] * yn[7])) > T(0)) {
         const T s_lo = event_value<KAHAN>(0, a2, y, c, resc, T(0));
         if (s_lo <= T(0))
-            h_used = clip<KAHAN>(a, a2, y, c, A0, h, 0, resc, T(0), s_lo, rn - resc,
+            h_used = clip<KAHAN, T, RM>(a, a2, y, c, A0, h, 0, resc, T(0), s_lo, rn - resc,
                                  Prec<T>::stol() * resc, Prec<T>::eps(), maxit, yn, cn, nrhs);
         st = ST_ESCAPED;
     } else if (rc.use_t) {
@@ -470,7 +613,7 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
         if ((s_hi > T(0)) != (rc.tpos != 0)) {
             const T s_lo = event_value<KAHAN>(1, a2, y, c, tend, tlo);
             const T sc = fmax(T(1), fabs(tend));
-            h_used = clip<KAHAN>(a, a2, y, c, A0, h, 1, tend, tlo, s_lo, s_hi,
+            h_used = clip<KAHAN, T, RM>(a, a2, y, c, A0, h, 1, tend, tlo, s_lo, s_hi,
                                  Prec<T>::stol() * sc, Prec<T>::eps(), maxit, yn, cn, nrhs);
             st = ST_ENDTIME;
         }
@@ -486,7 +629,7 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
                 // scale of z at the crossing: the nearer end of the step
                 const T r0 = ks_r(a2, y[1], y[2], y[3]);
                 const T r1 = ks_r(a2, yn[1], yn[2], yn[3]);
-                clip<KAHAN>(a, a2, y, c, A0, h_used, 2, T(0), T(0), z0, z1,
+                clip<KAHAN, T, RM>(a, a2, y, c, A0, h_used, 2, T(0), T(0), z0, z1,
                             Prec<T>::ztol() * (T(1) + fmin(r0, r1)), Prec<T>::eps(), maxit, yc,
                             cc, nrhs);
                 const T rcx = ks_r(a2, yc[1], yc[2], yc[3]);
@@ -716,6 +859,7 @@ struct ZoneResult {
     int since_renorm;
 };
 
+template <int RM>
 static __device__ __noinline__ ZoneResult zone_step(const RayConst rc, const TraceParams &P,
                                                     int64_t id, LaneF s, int since_renorm)
 {
@@ -729,8 +873,8 @@ static __device__ __noinline__ ZoneResult zone_step(const RayConst rc, const Tra
     ZoneResult R;
     R.nrhs = 0;
     R.nacc = 0;
-    R.st = step_once<false, double, true>(rc, P, id, P.tol, yd, cd, hd, rd, R.nrhs, R.nacc,
-                                          since_renorm);
+    R.st = step_once<false, double, true, RM>(rc, P, id, P.tol, yd, cd, hd, rd, R.nrhs,
+                                              R.nacc, since_renorm);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         R.s.y[i] = (float)yd[i];
@@ -988,8 +1132,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f64_kernel(const TraceParam
                 ++C.att;
                 ++C.att64;
                 uint32_t r = 0;
-                st = step_once<false, double>(rc, P, id, P.tol, y, c, h, rnow, r, C.acc,
-                                              since_renorm);
+                // right-hand sides out of line: one copy keeps the kernel in
+                // the instruction cache (same arithmetic as inline)
+                st = step_once<false, double, false, RHS_CALL>(rc, P, id, P.tol, y, c, h, rnow,
+                                                               r, C.acc, since_renorm);
                 C.rhs64 += r;
             }
             if (st != ST_NONE) {
@@ -1127,7 +1273,7 @@ __device__ __forceinline__ void load_const_full(const TraceParams &P, int64_t id
     rc.rcaplo = (float)(rc.rcap - (double)rc.rcapf);
 }
 
-template <int PHASE, int BLOCK, int MINB>
+template <int PHASE, int BLOCK, int MINB, int RM = RHS_INLINE>
 __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParams P)
 {
     const unsigned FULL = 0xffffffffu;
@@ -1311,7 +1457,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     if (PHASE == 2 || (PHASE == 0 && P.zone_df))
                         R = zone_step_df(rc, P, id, ls, since_renorm);
                     else
-                        R = zone_step(rc, P, id, ls, since_renorm);
+                        R = zone_step<RM>(rc, P, id, ls, since_renorm);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         y[i] = R.s.y[i];

@@ -11,19 +11,20 @@ namespace kerr {
 // no room to choose).
 // Its item count lives on the device, so the grid is fixed by the launch
 // shape (blocks per SM x SMs); threads with nothing to do exit at once.
-template <int PH, int B, int BPS>
+template <int PH, int B, int BPS, int RM>
 static cudaError_t launch_zone(const TraceParams &P, int sms, cudaStream_t s)
 {
-    trace_f32_kernel<PH, B, BPS><<<(unsigned)(BPS * sms), B, 0, s>>>(P);
+    trace_f32_kernel<PH, B, BPS, RM><<<(unsigned)(BPS * sms), B, 0, s>>>(P);
     return cudaGetLastError();
 }
 
 cudaError_t launch_zone_phase(const TraceParams &P, int zv, int sms, cudaStream_t s)
 {
     switch (zv) {
-#define KERR_ZCASE(i, b, m)                                                            \
+#define KERR_ZCASE(i, b, m, rm)                                                        \
     case i:                                                                            \
-        return P.zone_df ? launch_zone<2, 128, 2>(P, sms, s) : launch_zone<1, b, m>(P, sms, s);
+        return P.zone_df ? launch_zone<2, 128, 2, RHS_INLINE>(P, sms, s)                 \
+                         : launch_zone<1, b, m, rm>(P, sms, s);
         KERR_ZONE_VARIANT_LIST(KERR_ZCASE)
 #undef KERR_ZCASE
     default:

@@ -16,11 +16,16 @@ struct Variant {
 constexpr int kNumVariants = 6;
 constexpr Variant kVariants[kNumVariants] = {{128, 4}, {128, 3}, {256, 2}, {128, 2}, {64, 8}, {128, 5}};
 
-// Launch shapes of the zone phase: (threads per block, blocks per SM).
-#define KERR_ZONE_VARIANT_LIST(X) X(0, 128, 2) X(1, 128, 1) X(2, 64, 2) X(3, 64, 1) X(4, 32, 2)
-constexpr int kNumZoneVariants = 5;
-constexpr Variant kZoneVariants[kNumZoneVariants] = {{128, 2}, {128, 1}, {64, 2}, {64, 1}, {32, 2}};
-constexpr int kDefaultZoneVariant = 1;
+// Zone-phase variants: (threads per block, blocks per SM, how FP64 steps
+// evaluate their right-hand sides: 0 inline, 1 one out-of-line copy, 2
+// out-of-line pairs -- see RHS_INLINE / RHS_CALL / RHS_PAIR).
+#define KERR_ZONE_VARIANT_LIST(X)                                                          \
+    X(0, 128, 2, 0) X(1, 128, 1, 0) X(2, 64, 2, 0) X(3, 128, 1, 1) X(4, 128, 1, 2)          \
+    X(5, 128, 2, 2) X(6, 64, 2, 2)
+constexpr int kNumZoneVariants = 7;
+constexpr Variant kZoneVariants[kNumZoneVariants] = {{128, 2}, {128, 1}, {64, 2}, {128, 1},
+                                                     {128, 1}, {128, 2}, {64, 2}};
+constexpr int kDefaultZoneVariant = 3;
 
 struct TraceParams;
 

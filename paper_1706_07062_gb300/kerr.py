@@ -114,6 +114,7 @@ def lib():
         L.kerr_num_zone_variants.argtypes = []
         L.kerr_zone_variant_info.argtypes = [c.c_int, c.POINTER(i32), c.POINTER(i32)]
         L.kerr_autotune.argtypes = [vp, c.POINTER(Camera), c.POINTER(Opts), i64, c.POINTER(i32), vp]
+        L.kerr_check_fp64_math.argtypes = [vp, i64, vp, vp]
         L.kerr_last_error.restype = c.c_char_p
         for name in ("kerr_init", "kerr_destroy", "kerr_trace_rays", "kerr_trace_particles",
                      "kerr_trace_camera", "kerr_trace_camera_static", "kerr_get_stats",
@@ -123,7 +124,7 @@ def lib():
                      "kerr_surrogate_destroy", "kerr_surrogate_get_params",
                      "kerr_surrogate_get_grad", "kerr_surrogate_targets",
                      "kerr_surrogate_forward", "kerr_surrogate_grad", "kerr_surrogate_train",
-                     "kerr_surrogate_render"):
+                     "kerr_surrogate_render", "kerr_check_fp64_math"):
             getattr(L, name).restype = c.c_int
         _lib = L
     return _lib
@@ -476,3 +477,13 @@ def kerr_surrogate_render(ctx: Context, s: Surrogate, cam: Camera, opts: Opts | 
                                        _ptr(fb), ctypes.byref(nfb), _stream_ptr(stream, out)),
            "kerr_surrogate_render")
     return out, fb, nfb.value
+
+
+def kerr_check_fp64_math(x, stream=None):
+    """(3, n) device tensor: the integrator's FP64 1/x, 1/sqrt(x), sqrt(x)."""
+    import torch
+    n = int(x.numel())
+    out = torch.empty((3, n), dtype=torch.float64, device=x.device)
+    _check(lib().kerr_check_fp64_math(_ptr(x), n, _ptr(out), _stream_ptr(stream, x)),
+           "kerr_check_fp64_math")
+    return out

@@ -273,16 +273,35 @@ def test_every_variant_and_autotune(ctx):
 # ---------------------------------------------------------------------------
 # deferred FP64-zone phase
 # ---------------------------------------------------------------------------
+# zone variants: (threads per block, blocks per SM, right-hand-side mode)
+ZONE_RHS_MODE = [0, 0, 0, 1, 2, 2, 2]
+
+
 def test_zone_launch_shapes_agree(ctx):
-    """Every zone-phase launch shape gives the same end states (the shape only
-    changes which lane runs a geodesic, never its arithmetic)."""
+    """Zone-phase variants with the same right-hand-side code give identical
+    end states (the launch shape only changes which lane runs a geodesic).
+    Inline and out-of-line right-hand sides are the same source arithmetic,
+    but the compiler may fuse a multiply-add differently across the call
+    boundary: end states then agree to rounding, with the same statuses and
+    step counts."""
+    assert K.kerr_num_zone_variants() == len(ZONE_RHS_MODE)
     spec = W.CameraSpec(0.99, 0.3, 1000.0, 8.0, 96, 96)
     outs = [K.kerr_trace_camera(ctx, cam(spec), K.default_opts(zone_variant=v), device=DEV)
             for v in range(K.kerr_num_zone_variants())]
     torch.cuda.synchronize()
-    for o in outs[1:]:
-        assert torch.equal(o.x, outs[0].x) and torch.equal(o.k, outs[0].k)
-        assert torch.equal(o.status, outs[0].status)
+    first = {}
+    for v, o in enumerate(outs):
+        m = ZONE_RHS_MODE[v]
+        if m in first:
+            b = outs[first[m]]
+            assert torch.equal(o.x, b.x) and torch.equal(o.k, b.k)
+        else:
+            first[m] = v
+        b = outs[0]
+        assert torch.equal(o.status, b.status) and torch.equal(o.steps, b.steps)
+        ex, ek, _ = rel_errors(to_np(o.x), to_np(o.k),
+                               np.concatenate([to_np(b.x).T, to_np(b.k).T], 1))
+        assert max(ex.max(), ek.max()) < 1e-9
 
 
 def test_zone_phase_counts(ctx):
