@@ -528,7 +528,8 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
             KERR_CUDA(cudaMemcpyAsync(*s.dev, s.host, s.bytes, cudaMemcpyHostToDevice, c->stream));
 
     int prec = o->prec;
-    int variant = o->variant >= 0 ? o->variant : (c->tuned[prec] >= 0 ? c->tuned[prec] : 0);
+    int variant = o->variant >= 0 ? o->variant
+                                   : (c->tuned[prec] >= 0 ? c->tuned[prec] : kDefaultVariant[prec]);
     const int zvar = o->zone_variant >= 0 ? o->zone_variant : kDefaultZoneVariant;
     rc = launch_integration(c, P, prec, variant, zvar);
     if (rc)

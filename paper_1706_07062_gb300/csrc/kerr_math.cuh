@@ -169,26 +169,28 @@ __device__ __forceinline__ void accel(const T a, const T a2, const T x, const T 
 }
 
 // ---------------------------------------------------------------------------
-// Out-of-line FP64 right-hand sides.  FP64 steps are latency-bound on GB300
-// (1/64 of the FP32 rate, one or two warps per scheduler): a kernel that
-// inlines the eleven right-hand sides of an attempt outgrows the
-// instruction cache, so its zone steps can call one copy instead; the pair
-// form evaluates two independent right-hand sides in one call, interleaved,
-// for instruction-level parallelism.  Same arithmetic as accel<double>.
+// Out-of-line right-hand sides.  A kernel that inlines the eleven right-hand
+// sides of an attempt outgrows the instruction cache; its steps can call one
+// copy instead.  FP64 steps are also latency-bound on GB300 (1/64 of the
+// FP32 rate, one or two warps per scheduler): the pair form evaluates two
+// independent right-hand sides in one call, interleaved, for
+// instruction-level parallelism.  Same arithmetic as accel<T>.
 // ---------------------------------------------------------------------------
-struct Acc64 {
-    double t, x, y, z;
+template <typename T> struct Acc {
+    T t, x, y, z;
 };
+using Acc64 = Acc<double>;
 struct Acc64x2 {
     Acc64 p, q;
 };
 
-static __device__ __noinline__ Acc64 accel_call(const double a, const double a2, const double x,
-                                                const double y, const double z, const double kt,
-                                                const double kx, const double ky, const double kz)
+template <typename T>
+static __device__ __noinline__ Acc<T> accel_call(const T a, const T a2, const T x, const T y,
+                                                 const T z, const T kt, const T kx, const T ky,
+                                                 const T kz)
 {
-    Acc64 r;
-    accel<double>(a, a2, x, y, z, kt, kx, ky, kz, r.t, r.x, r.y, r.z);
+    Acc<T> r;
+    accel<T>(a, a2, x, y, z, kt, kx, ky, kz, r.t, r.x, r.y, r.z);
     return r;
 }
 

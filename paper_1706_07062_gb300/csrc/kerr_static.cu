@@ -182,7 +182,7 @@ extern "C" int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam,
     P.zcount = ctr + 1 + SC_COUNT;
     P.zhead = ctr + 2 + SC_COUNT;
     P.zpush = ctr + 3 + SC_COUNT;
-    const int variant = o->variant >= 0 ? o->variant : 0;
+    const int variant = o->variant >= 0 ? o->variant : kDefaultVariant[o->prec == KERR_FP32_KAHAN];
     if (o->prec == KERR_FP32_KAHAN) {
         P.s_state = work;
         P.s_const = work + (size_t)16 * n;

@@ -185,19 +185,20 @@ template <> struct RC<double> {
 // Runge-Kutta pieces
 // ---------------------------------------------------------------------------
 
-// How an attempt evaluates its right-hand sides.  Only FP64 has a choice
-// (the other number types are always inline): inline (the compiler schedules
-// all of them together), one out-of-line copy (far less code for the
-// instruction cache), or out-of-line pairs of independent right-hand sides.
-// The arithmetic of every right-hand side is the same in all three.
+// How an attempt evaluates its right-hand sides: inline (the compiler
+// schedules all of them together), one out-of-line copy (far less code for
+// the instruction cache; FP32 and FP64), or out-of-line pairs of independent
+// right-hand sides (FP64; float-float is always inline).  The source
+// arithmetic of every right-hand side is the same in all three.
 enum : int { RHS_INLINE = 0, RHS_CALL = 1, RHS_PAIR = 2 };
 
 template <int RM, typename T>
 __device__ __forceinline__ void rhs(const T a, const T a2, const T x, const T y, const T z,
                                     const T kt, const T kx, const T ky, const T kz, T A[4])
 {
-    if constexpr (RM != RHS_INLINE && std::is_same<T, double>::value) {
-        const Acc64 r = accel_call(a, a2, x, y, z, kt, kx, ky, kz);
+    if constexpr (RM != RHS_INLINE &&
+                  (std::is_same<T, double>::value || std::is_same<T, float>::value)) {
+        const Acc<T> r = accel_call<T>(a, a2, x, y, z, kt, kx, ky, kz);
         A[0] = r.t;
         A[1] = r.x;
         A[2] = r.y;
@@ -1472,8 +1473,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     ++C.att64;
                 } else {
                     uint32_t r = 0;
-                    st = step_once<true, float>(rc, P, id, tol, y, c, h, rnow, r, C.acc,
-                                                since_renorm);
+                    // FP32 steps: the variant's right-hand-side mode in the
+                    // stepping phase; out of line in the zone phase (as in the
+                    // default stepping variant, so that a geodesic's FP32
+                    // steps are the same arithmetic in either launch)
+                    st = step_once<true, float, false, PHASE == 0 ? RM : RHS_CALL>(
+                        rc, P, id, tol, y, c, h, rnow, r, C.acc, since_renorm);
                     C.rhs32 += r;
                 }
             }

@@ -26,13 +26,14 @@ cudaError_t launch_finish_f32(const TraceParams &P, int sms, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int PH, int B, int M>
+template <int PH, int B, int M, int RM>
 static cudaError_t launch_one(const TraceParams &P, int sms, cudaStream_t s, bool clamp_to_n)
 {
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaError_t e =
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_f32_kernel<PH, B, M>, B, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_f32_kernel<PH, B, M, RM>, B,
+                                                          0);
         if (e != cudaSuccess)
             return e;
         if (per_sm < 1)
@@ -42,19 +43,19 @@ static cudaError_t launch_one(const TraceParams &P, int sms, cudaStream_t s, boo
     const long long need = (P.n + B - 1) / B;
     if (clamp_to_n && need < grid)
         grid = need < 1 ? 1 : need;
-    trace_f32_kernel<PH, B, M><<<(unsigned)grid, B, 0, s>>>(P);
+    trace_f32_kernel<PH, B, M, RM><<<(unsigned)grid, B, 0, s>>>(P);
     return cudaGetLastError();
 }
 
-// Variants 0-2 are compiled here, 3-5 in kerr_trace_f32b.cu (in parallel).
+// Variants 0-4 are compiled here, 5-9 in kerr_trace_f32b.cu (in parallel).
 cudaError_t launch_trace_f32_hi(const TraceParams &P, int v, int sms, cudaStream_t s);
 
 cudaError_t launch_trace_f32(const TraceParams &P, int v, int sms, cudaStream_t s)
 {
     switch (v) {
-#define KERR_CASE(i, b, m) \
-    case i:                \
-        return launch_one<0, b, m>(P, sms, s, true);
+#define KERR_CASE(i, b, m, rm) \
+    case i:                    \
+        return launch_one<0, b, m, rm>(P, sms, s, true);
         KERR_VARIANT_LIST_LO(KERR_CASE)
 #undef KERR_CASE
     default:

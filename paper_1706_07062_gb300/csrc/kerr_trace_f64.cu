@@ -30,8 +30,8 @@ static cudaError_t launch_one(const TraceParams &P, int sms, cudaStream_t s)
 cudaError_t launch_trace_f64(const TraceParams &P, int v, int sms, cudaStream_t s)
 {
     switch (v) {
-#define KERR_CASE(i, b, m) \
-    case i:                \
+#define KERR_CASE(i, b, m, rm) \
+    case i:                    \
         return launch_one<b, m>(P, sms, s);
         KERR_VARIANT_LIST(KERR_CASE)
 #undef KERR_CASE

@@ -9,12 +9,21 @@ struct Variant {
     int block, min_blocks;
 };
 
-#define KERR_VARIANT_LIST_LO(X) X(0, 128, 4) X(1, 128, 3) X(2, 256, 2)
-#define KERR_VARIANT_LIST_HI(X) X(3, 128, 2) X(4, 64, 8) X(5, 128, 5)
+// Stepping-kernel variants: (index, threads per block, minimum blocks per SM,
+// FP32-phase right-hand sides: 0 inline, 1 one out-of-line copy).  The FP64
+// path uses the launch shape only (its right-hand sides are out of line).
+#define KERR_VARIANT_LIST_LO(X) X(0, 128, 4, 0) X(1, 128, 3, 0) X(2, 256, 2, 0) X(3, 128, 4, 1) \
+    X(4, 128, 3, 1)
+#define KERR_VARIANT_LIST_HI(X) X(5, 128, 2, 0) X(6, 64, 8, 0) X(7, 128, 5, 0) X(8, 256, 2, 1) \
+    X(9, 128, 5, 1)
 #define KERR_VARIANT_LIST(X) KERR_VARIANT_LIST_LO(X) KERR_VARIANT_LIST_HI(X)
 
-constexpr int kNumVariants = 6;
-constexpr Variant kVariants[kNumVariants] = {{128, 4}, {128, 3}, {256, 2}, {128, 2}, {64, 8}, {128, 5}};
+constexpr int kNumVariants = 10;
+// Defaults before autotuning, per precision (KERR_FP64, KERR_FP32_KAHAN):
+// the fastest on the 1024 x 1024, a = 0.99 camera.
+constexpr int kDefaultVariant[2] = {1, 3};
+constexpr Variant kVariants[kNumVariants] = {{128, 4}, {128, 3}, {256, 2}, {128, 4}, {128, 3},
+                                             {128, 2}, {64, 8},  {128, 5}, {256, 2}, {128, 5}};
 
 // Zone-phase variants: (threads per block, blocks per SM, how FP64 steps
 // evaluate their right-hand sides: 0 inline, 1 one out-of-line copy, 2
