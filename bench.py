@@ -40,16 +40,22 @@ WORKLOAD = ("camera 1024x1024, a=0.99, i=17deg, r_obs=1000M, +-25M, tol 1e-6, "
             "FP32+Kahan persistent kernel")
 
 
+# Sources of the integrator kernels (the surrogate's files are left out:
+# they do not change these kernels).
+TRACE_SOURCES = ("kerr_math.cuh", "kerr_df.cuh", "kerr_trace.cuh", "kerr_variants.h",
+                 "kerr_trace_f32.cu", "kerr_trace_f32b.cu", "kerr_trace_zone.cu",
+                 "kerr_trace_f64.cu")
+
+
 def kernel_source_hash() -> str:
-    """Hash of the CUDA sources: ncu counters are only valid for the kernels
-    they were taken from."""
+    """Hash of the integrator's CUDA sources: ncu counters are only valid for
+    the kernels they were taken from."""
     import hashlib
     d = os.path.join(ROOT, "paper_1706_07062_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(f.encode() + fh.read())
+    for f in TRACE_SOURCES:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
