@@ -321,9 +321,22 @@ int kerr_surrogate_targets(kerr_ctx *ctx, const double *points, int64_t n, doubl
                            const kerr_opts *opts, float *in, float *targets, float *mask,
                            void *stream);
 
-/* Forward pass: out [n][8] from in [n][4]. */
+/* Forward pass: out [n][8] from in [n][4] (device buffers), on the fused
+ * tensor-core kernel: all five layers per 128-row tile, tcgen05 MMAs with
+ * the accumulator in tensor memory, weights staged by bulk TMA copies.
+ * Synchronises `stream`; KERR_ECUDA if the kernel's pipeline timed out. */
 int kerr_surrogate_forward(kerr_surrogate *s, const float *in, int64_t n, float *out,
                            void *stream);
+
+/* The same forward on a chosen implementation: KERR_SURR_FWD_TENSOR_CORE
+ * (as kerr_surrogate_forward) or KERR_SURR_FWD_GEMM (the layer-by-layer
+ * mma.sync GEMM kernels of the training path; asynchronous).  Both compute
+ * bf16 operands with fp32 accumulation; results differ by accumulation
+ * order only. */
+#define KERR_SURR_FWD_TENSOR_CORE 0
+#define KERR_SURR_FWD_GEMM 1
+int kerr_surrogate_forward_impl(kerr_surrogate *s, const float *in, int64_t n, float *out,
+                                int32_t impl, void *stream);
 
 /* Loss and gradient of one batch (kept in the surrogate; read it with
  * kerr_surrogate_get_grad).  Loss = mean over rows of

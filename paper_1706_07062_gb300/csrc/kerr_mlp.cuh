@@ -39,7 +39,9 @@ struct EpiArgs {
     int lda_out;
 };
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+// SiLU with the hardware exp2 and reciprocal approximations (relative error
+// ~1e-7, far below the bfloat16 rounding applied to the result).
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 __device__ __forceinline__ float silu_grad(float z)
 {
     const float s = 1.0f / (1.0f + __expf(-z));
@@ -190,6 +192,19 @@ __global__ void __launch_bounds__(128) gemm_bf16(const __nv_bfloat16 *__restrict
                 }
             }
 }
+
+// Fused tensor-core inference forward (kerr_mlp_tc.cu).  Weights are first
+// packed from the bf16 copy ([out][in] per layer at offsets woff) into the
+// MMA operand layout (packed_weight_elems() bf16); forward_tc then maps
+// in [n][4] to out [n][8] on a persistent grid of at most `sms` CTAs.  *err
+// becomes nonzero if a pipeline wait gave up (never expected).
+size_t packed_weight_elems();
+int forward_tc_shared_bytes();
+cudaError_t pack_weights(const __nv_bfloat16 *wbf, const size_t woff[kLayers],
+                         __nv_bfloat16 *wpk, cudaStream_t s);
+cudaError_t forward_tc(const float *in, int64_t n, float *out, const __nv_bfloat16 *wpk,
+                       const float *const bias[kLayers], unsigned *err, int sms,
+                       cudaStream_t s);
 
 } // namespace mlp
 } // namespace kerr

@@ -206,6 +206,9 @@ struct kerr_surrogate {
     float *dA = nullptr;          // [cap][256]
     bf16 *dZ = nullptr;           // [cap][256]
     float *loss = nullptr;        // [1]
+    bf16 *wpk = nullptr;          // weights in the tensor-core operand layout
+    unsigned *tc_err = nullptr;   // fused forward: a pipeline wait gave up
+    int sms = 0;
 };
 
 static void free_batch(kerr_surrogate *s)
@@ -266,6 +269,8 @@ extern "C" int kerr_surrogate_destroy(kerr_surrogate *s)
     cudaFree(s->v);
     cudaFree(s->wbf);
     cudaFree(s->loss);
+    cudaFree(s->wpk);
+    cudaFree(s->tc_err);
     delete s;
     return KERR_OK;
 }
@@ -292,6 +297,14 @@ extern "C" int kerr_surrogate_create(const float *init, kerr_surrogate **out)
         e = cudaMalloc(&s->wbf, n * sizeof(bf16));
     if (e == cudaSuccess)
         e = cudaMalloc(&s->loss, sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&s->wpk, packed_weight_elems() * sizeof(bf16));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&s->tc_err, sizeof(unsigned));
+    if (e == cudaSuccess)
+        e = cudaMemset(s->tc_err, 0, sizeof(unsigned));
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
     if (e == cudaSuccess)
         e = cudaMemcpy(s->w, init, n * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -423,17 +436,37 @@ static int check_rows(int64_t n)
     return KERR_OK;
 }
 
-extern "C" int kerr_surrogate_forward(kerr_surrogate *s, const float *in, int64_t n, float *out,
-                                      void *stream)
+// Inference forward: the fused tensor-core kernel (kerr_mlp_tc.cu) on the
+// current bf16 weights, packed into its operand layout first.
+static int forward_fused(kerr_surrogate *s, const float *in, int64_t n, float *out,
+                         cudaStream_t st)
 {
-    if (!s || (n > 0 && (!in || !out)))
-        return fail(KERR_EINVAL, "kerr_surrogate_forward: NULL argument");
-    int rc = check_rows(n);
-    if (rc || n == 0)
-        return rc;
-    cudaStream_t st = (cudaStream_t)stream;
+    SURR_CUDA(pack_weights(s->wbf, kL.w, s->wpk, st));
+    const float *bias[kLayers];
+    for (int l = 0; l < kLayers; ++l)
+        bias[l] = s->w + kL.b[l];
+    SURR_CUDA(forward_tc(in, n, out, s->wpk, bias, s->tc_err, s->sms, st));
+    return KERR_OK;
+}
+
+// After a synchronisation: KERR_ECUDA if a fused-forward pipeline wait gave up.
+static int check_tc(kerr_surrogate *s)
+{
+    unsigned h = 0;
+    SURR_CUDA(cudaMemcpy(&h, s->tc_err, sizeof h, cudaMemcpyDeviceToHost));
+    if (h) {
+        cudaMemset(s->tc_err, 0, sizeof h);
+        return fail(KERR_ECUDA, "surrogate forward: tensor-core pipeline wait timed out");
+    }
+    return KERR_OK;
+}
+
+// The same forward on the layer-by-layer GEMM kernels (training path).
+static int forward_gemm(kerr_surrogate *s, const float *in, int64_t n, float *out,
+                        cudaStream_t st)
+{
     const int64_t chunk = 1 << 20;
-    rc = ensure_batch(s, std::min(n, chunk), false);
+    int rc = ensure_batch(s, std::min(n, chunk), false);
     if (rc)
         return rc;
     for (int64_t r0 = 0; r0 < n; r0 += chunk) {
@@ -446,6 +479,32 @@ extern "C" int kerr_surrogate_forward(kerr_surrogate *s, const float *in, int64_
                                     cudaMemcpyDeviceToDevice, st));
     }
     return KERR_OK;
+}
+
+extern "C" int kerr_surrogate_forward(kerr_surrogate *s, const float *in, int64_t n, float *out,
+                                      void *stream)
+{
+    return kerr_surrogate_forward_impl(s, in, n, out, KERR_SURR_FWD_TENSOR_CORE, stream);
+}
+
+extern "C" int kerr_surrogate_forward_impl(kerr_surrogate *s, const float *in, int64_t n,
+                                           float *out, int32_t impl, void *stream)
+{
+    if (!s || (n > 0 && (!in || !out)))
+        return fail(KERR_EINVAL, "kerr_surrogate_forward: NULL argument");
+    if (impl != KERR_SURR_FWD_TENSOR_CORE && impl != KERR_SURR_FWD_GEMM)
+        return fail(KERR_EINVAL, "kerr_surrogate_forward: unknown implementation");
+    int rc = check_rows(n);
+    if (rc || n == 0)
+        return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (impl == KERR_SURR_FWD_GEMM)
+        return forward_gemm(s, in, n, out, st);
+    rc = forward_fused(s, in, n, out, st);
+    if (rc)
+        return rc;
+    SURR_CUDA(cudaStreamSynchronize(st));
+    return check_tc(s);
 }
 
 extern "C" int kerr_surrogate_grad(kerr_surrogate *s, const float *in, const float *targets,
@@ -878,7 +937,7 @@ extern "C" int kerr_surrogate_render(kerr_ctx *ctx, kerr_surrogate *s, const ker
         }
     }
     if (rc == KERR_OK)
-        rc = kerr_surrogate_forward(s, in, n, o, stream);
+        rc = forward_fused(s, in, n, o, st);
     if (rc == KERR_OK) {
         if (std::fabs(cam->a) >= 1e-4)
             crit_interval_kernel<<<1, 256, 0, st>>>(cam->a, cam->incl, rint);
@@ -894,6 +953,8 @@ extern "C" int kerr_surrogate_render(kerr_ctx *ctx, kerr_surrogate *s, const ker
             cudaGetLastError();
             rc = fail(KERR_ECUDA, "kerr_surrogate_render: gate");
         }
+        if (rc == KERR_OK)
+            rc = check_tc(s);
     }
     if (rc == KERR_OK && hcount > 0) {
         const int64_t m = (int64_t)hcount;

@@ -105,6 +105,7 @@ def lib():
         L.kerr_surrogate_targets.argtypes = [vp, vp, i64, c.c_double, c.POINTER(Opts), vp, vp, vp,
                                              vp]
         L.kerr_surrogate_forward.argtypes = [vp, vp, i64, vp, vp]
+        L.kerr_surrogate_forward_impl.argtypes = [vp, vp, i64, vp, i32, vp]
         L.kerr_surrogate_grad.argtypes = [vp, vp, vp, vp, i64, c.POINTER(c.c_float), vp]
         L.kerr_surrogate_train.argtypes = [vp, vp, vp, vp, i64, i32, i32, c.c_float, vp, vp]
         L.kerr_surrogate_render.argtypes = [vp, vp, c.POINTER(Camera), c.POINTER(Opts), c.c_float,
@@ -124,7 +125,8 @@ def lib():
                      "kerr_surrogate_destroy", "kerr_surrogate_get_params",
                      "kerr_surrogate_get_grad", "kerr_surrogate_targets",
                      "kerr_surrogate_forward", "kerr_surrogate_grad", "kerr_surrogate_train",
-                     "kerr_surrogate_render", "kerr_check_fp64_math"):
+                     "kerr_surrogate_render", "kerr_check_fp64_math",
+                     "kerr_surrogate_forward_impl"):
             getattr(L, name).restype = c.c_int
         _lib = L
     return _lib
@@ -434,13 +436,22 @@ def kerr_surrogate_targets(ctx: Context, points, r_obs: float, opts: Opts | None
     return inp, tgt, msk
 
 
-def kerr_surrogate_forward(s: Surrogate, inp, out=None, stream=None):
+SURR_FWD_TENSOR_CORE, SURR_FWD_GEMM = 0, 1
+
+
+def kerr_surrogate_forward(s: Surrogate, inp, out=None, stream=None, impl=None):
+    """(n, 8) network outputs; impl None = the fused tensor-core kernel."""
     import torch
     n = int(inp.shape[0])
     if out is None:
         out = torch.empty((n, 8), dtype=torch.float32, device=inp.device)
-    _check(lib().kerr_surrogate_forward(s.handle, _ptr(inp), n, _ptr(out),
-                                        _stream_ptr(stream, inp)), "kerr_surrogate_forward")
+    if impl is None:
+        _check(lib().kerr_surrogate_forward(s.handle, _ptr(inp), n, _ptr(out),
+                                            _stream_ptr(stream, inp)), "kerr_surrogate_forward")
+    else:
+        _check(lib().kerr_surrogate_forward_impl(s.handle, _ptr(inp), n, _ptr(out), int(impl),
+                                                 _stream_ptr(stream, inp)),
+               "kerr_surrogate_forward_impl")
     return out
 
 
