@@ -367,6 +367,21 @@ int kerr_surrogate_render(kerr_ctx *ctx, kerr_surrogate *s, const kerr_camera *c
                           const kerr_opts *opts, float p_lo, float p_hi, float crit_dist,
                           float *out, uint8_t *fallback, int64_t *n_fallback, void *stream);
 
+/* Paper-mode integration (Sec. 3, the timing setting of Sec. 4.2 and
+ * Tables 2-3): every geodesic of `state` takes exactly nsteps classic RK4
+ * steps of length h in place, with the right-hand side of eqs. opt0/opti,
+ * no error control and no termination test (a geodesic that reaches the
+ * singularity turns non-finite and keeps costing the same).  state: device
+ * memory, n states (t, x, y, z, k^t, k^x, k^y, k^z) of float (fp64 = 0, plain
+ * FP32 arithmetic) or double (fp64 = 1), in layout KERR_LAYOUT_SOA ([8][n])
+ * or KERR_LAYOUT_AOS ([n][8], 16-byte aligned).  Spin a, |a| <= 1.
+ * Asynchronous on `stream`.  KERR_EINVAL for bad arguments or host memory;
+ * n == 0 or nsteps == 0 is a no-op. */
+#define KERR_LAYOUT_SOA 0
+#define KERR_LAYOUT_AOS 1
+int kerr_rk4_fixed(double a, int32_t fp64, int32_t layout, void *state, int64_t n,
+                   int32_t nsteps, double h, void *stream);
+
 /* Check of the integrator's FP64 reciprocal, reciprocal square root and
  * square root (Newton-refined hardware approximations, see the FP64 steps;
  * this library's own primitives, with no counterpart in the paper): for

@@ -116,6 +116,7 @@ def lib():
         L.kerr_zone_variant_info.argtypes = [c.c_int, c.POINTER(i32), c.POINTER(i32)]
         L.kerr_autotune.argtypes = [vp, c.POINTER(Camera), c.POINTER(Opts), i64, c.POINTER(i32), vp]
         L.kerr_check_fp64_math.argtypes = [vp, i64, vp, vp]
+        L.kerr_rk4_fixed.argtypes = [c.c_double, i32, i32, vp, i64, i32, c.c_double, vp]
         L.kerr_last_error.restype = c.c_char_p
         for name in ("kerr_init", "kerr_destroy", "kerr_trace_rays", "kerr_trace_particles",
                      "kerr_trace_camera", "kerr_trace_camera_static", "kerr_get_stats",
@@ -126,7 +127,7 @@ def lib():
                      "kerr_surrogate_get_grad", "kerr_surrogate_targets",
                      "kerr_surrogate_forward", "kerr_surrogate_grad", "kerr_surrogate_train",
                      "kerr_surrogate_render", "kerr_check_fp64_math",
-                     "kerr_surrogate_forward_impl"):
+                     "kerr_surrogate_forward_impl", "kerr_rk4_fixed"):
             getattr(L, name).restype = c.c_int
         _lib = L
     return _lib
@@ -498,3 +499,20 @@ def kerr_check_fp64_math(x, stream=None):
     _check(lib().kerr_check_fp64_math(_ptr(x), n, _ptr(out), _stream_ptr(stream, x)),
            "kerr_check_fp64_math")
     return out
+
+
+LAYOUT_SOA, LAYOUT_AOS = 0, 1
+
+
+def kerr_rk4_fixed(a: float, state, nsteps: int, h: float, layout: int = LAYOUT_SOA,
+                   stream=None):
+    """Paper-mode fixed-step RK4 in place on a device tensor: float32 or
+    float64, shape (8, n) for LAYOUT_SOA or (n, 8) for LAYOUT_AOS."""
+    import torch
+    if state.dtype not in (torch.float32, torch.float64):
+        raise KerrError("state must be float32 or float64")
+    n = int(state.shape[1] if layout == LAYOUT_SOA else state.shape[0])
+    _check(lib().kerr_rk4_fixed(float(a), int(state.dtype == torch.float64), int(layout),
+                                _ptr(state), n, int(nsteps), float(h),
+                                _stream_ptr(stream, state)), "kerr_rk4_fixed")
+    return state
