@@ -189,6 +189,39 @@ int wsplits(int64_t rows) { return (int)std::max<int64_t>(1, std::min<int64_t>(6
 
 } // namespace
 
+// Grow-only device scratch of kerr_surrogate_render (kept by the surrogate,
+// so that a render allocates nothing once the sizes are reached).
+struct RenderScratch {
+    int64_t cap_n = 0, cap_m = 0;
+    float *in = nullptr, *o = nullptr;
+    int64_t *idx = nullptr;
+    float2 *curve = nullptr;
+    double *rint = nullptr;
+    float4 *bounds = nullptr;
+    unsigned long long *cnt = nullptr;
+    double *x = nullptr, *k = nullptr;
+    int32_t *stat = nullptr, *nst = nullptr;
+    float *crs = nullptr;
+};
+constexpr int kCurveSamples = 2048;   // per branch
+
+static void free_render(RenderScratch &r)
+{
+    cudaFree(r.in);
+    cudaFree(r.o);
+    cudaFree(r.idx);
+    cudaFree(r.curve);
+    cudaFree(r.rint);
+    cudaFree(r.bounds);
+    cudaFree(r.cnt);
+    cudaFree(r.x);
+    cudaFree(r.k);
+    cudaFree(r.stat);
+    cudaFree(r.nst);
+    cudaFree(r.crs);
+    r = RenderScratch();
+}
+
 // ===========================================================================
 // the surrogate object
 // ===========================================================================
@@ -206,6 +239,7 @@ struct kerr_surrogate {
     float *dA = nullptr;          // [cap][256]
     bf16 *dZ = nullptr;           // [cap][256]
     float *loss = nullptr;        // [1]
+    RenderScratch *render = nullptr;   // kerr_surrogate_render's scratch
     bf16 *wpk = nullptr;          // weights in the tensor-core operand layout
     unsigned *tc_err = nullptr;   // fused forward: a pipeline wait gave up
     int sms = 0;
@@ -271,6 +305,10 @@ extern "C" int kerr_surrogate_destroy(kerr_surrogate *s)
     cudaFree(s->loss);
     cudaFree(s->wpk);
     cudaFree(s->tc_err);
+    if (s->render) {
+        free_render(*s->render);
+        delete s->render;
+    }
     delete s;
     return KERR_OK;
 }
@@ -283,6 +321,11 @@ extern "C" int kerr_surrogate_create(const float *init, kerr_surrogate **out)
     kerr_surrogate *s = new (std::nothrow) kerr_surrogate();
     if (!s)
         return fail(KERR_ENOMEM, "kerr_surrogate_create: host allocation");
+    s->render = new (std::nothrow) RenderScratch();
+    if (!s->render) {
+        delete s;
+        return fail(KERR_ENOMEM, "kerr_surrogate_create: host allocation");
+    }
     const size_t n = kL.total;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess)
@@ -795,11 +838,68 @@ __global__ void crit_curve_kernel(double a, double incl, int ns, const double *_
     pts[ns + j] = p1;
 }
 
+// Annulus holding the curve samples: centre (bounding-box midpoint of the
+// finite samples) and the smallest / largest sample distance from it.  A
+// pixel at distance d from the centre is at least min over samples of
+// |d - |q - c|| from every sample (triangle inequality), so with d outside
+// [rmin - crit, rmax + crit] no sample is within crit.  One block.
+__global__ void curve_bounds_kernel(const float2 *__restrict__ curve, int ncurve,
+                                    float4 *__restrict__ bounds)
+{
+    __shared__ float red[4][256];
+    float x0 = 3.0e38f, x1 = -3.0e38f, y0 = 3.0e38f, y1 = -3.0e38f;
+    for (int j = threadIdx.x; j < ncurve; j += blockDim.x) {
+        const float2 q = curve[j];
+        if (isfinite(q.x) && isfinite(q.y)) {
+            x0 = fminf(x0, q.x);
+            x1 = fmaxf(x1, q.x);
+            y0 = fminf(y0, q.y);
+            y1 = fmaxf(y1, q.y);
+        }
+    }
+    red[0][threadIdx.x] = x0;
+    red[1][threadIdx.x] = -x1;
+    red[2][threadIdx.x] = y0;
+    red[3][threadIdx.x] = -y1;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 4; ++k)
+                red[k][threadIdx.x] = fminf(red[k][threadIdx.x], red[k][threadIdx.x + w]);
+        __syncthreads();
+    }
+    const float cx = 0.5f * (red[0][0] - red[1][0]), cy = 0.5f * (red[2][0] - red[3][0]);
+    __syncthreads();
+    float r0 = 3.0e38f, r1 = -3.0e38f;
+    for (int j = threadIdx.x; j < ncurve; j += blockDim.x) {
+        const float2 q = curve[j];
+        if (isfinite(q.x) && isfinite(q.y)) {
+            const float d = hypotf(q.x - cx, q.y - cy);
+            r0 = fminf(r0, d);
+            r1 = fmaxf(r1, d);
+        }
+    }
+    red[0][threadIdx.x] = r0;
+    red[1][threadIdx.x] = -r1;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 2; ++k)
+                red[k][threadIdx.x] = fminf(red[k][threadIdx.x], red[k][threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        *bounds = make_float4(cx, cy, red[0][0], -red[1][0]);   // no sample: rmin > rmax
+}
+
 // Gate and decode: one pass over the pixels.  Network outputs o [n][8];
-// fallback when p in [p_lo, p_hi] or distance to the curve < crit_dist;
-// fallback pixels are appended (warp-aggregated) to idx.
+// fallback when p in [p_lo, p_hi] or distance to the curve < crit_dist
+// (the sample scan only for pixels inside the annulus of curve_bounds_kernel
+// widened by crit_dist); fallback pixels are appended (warp-aggregated) to
+// idx.
 __global__ void __launch_bounds__(256) gate_kernel(const float *__restrict__ o, kerr_camera cam,
                                                    const float2 *__restrict__ curve, int ncurve,
+                                                   const float4 *__restrict__ bounds,
                                                    float p_lo, float p_hi, float crit_dist,
                                                    int64_t n, float *__restrict__ out,
                                                    uint8_t *__restrict__ fb,
@@ -809,6 +909,7 @@ __global__ void __launch_bounds__(256) gate_kernel(const float *__restrict__ o, 
     extern __shared__ float2 sc[];
     for (int j = threadIdx.x; j < ncurve; j += blockDim.x)
         sc[j] = curve[j];
+    const float4 bd = *bounds;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n;
@@ -822,10 +923,13 @@ __global__ void __launch_bounds__(256) gate_kernel(const float *__restrict__ o, 
             const float al = (float)(-cam.half_width + (px + 0.5) * 2.0 * cam.half_width / cam.nx);
             const float be = (float)(-cam.half_width + (qy + 0.5) * 2.0 * cam.half_width / cam.ny);
             float d2 = 3.0e38f;
-            for (int j = 0; j < ncurve; ++j) {
-                const float dx = sc[j].x - al, dy = sc[j].y - be;
-                const float dd = dx * dx + dy * dy;
-                d2 = dd < d2 ? dd : d2;      // NaN samples never win
+            const float dc = hypotf(al - bd.x, be - bd.y);
+            if (dc >= bd.z - crit_dist && dc <= bd.w + crit_dist) {
+                for (int j = 0; j < ncurve; ++j) {
+                    const float dx = sc[j].x - al, dy = sc[j].y - be;
+                    const float dd = dx * dx + dy * dy;
+                    d2 = dd < d2 ? dd : d2;      // NaN samples never win
+                }
             }
             use_fb = (p >= p_lo && p <= p_hi) || d2 < crit_dist * crit_dist;
             const float nan = __int_as_float(0x7fc00000);
@@ -887,6 +991,75 @@ __global__ void merge_kernel(const int64_t *__restrict__ idx,
 
 } // namespace
 
+static int ensure_render(RenderScratch &r, int64_t n, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    if (!r.curve) {
+        e = cudaMalloc(&r.curve, (size_t)2 * kCurveSamples * sizeof(float2));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&r.rint, 2 * sizeof(double));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&r.bounds, sizeof(float4));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&r.cnt, sizeof(unsigned long long));
+    }
+    if (e == cudaSuccess && n > r.cap_n) {
+        cudaStreamSynchronize(st);
+        cudaFree(r.in);
+        cudaFree(r.o);
+        cudaFree(r.idx);
+        r.in = r.o = nullptr;
+        r.idx = nullptr;
+        r.cap_n = 0;
+        e = cudaMalloc(&r.in, (size_t)n * kIn * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&r.o, (size_t)n * kOut * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&r.idx, (size_t)n * sizeof(int64_t));
+        if (e == cudaSuccess)
+            r.cap_n = n;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_render(r);
+        return fail(KERR_ENOMEM, "kerr_surrogate_render: scratch allocation");
+    }
+    return KERR_OK;
+}
+
+static int ensure_fallback(RenderScratch &r, int64_t m, cudaStream_t st)
+{
+    if (m <= r.cap_m)
+        return KERR_OK;
+    cudaStreamSynchronize(st);
+    cudaFree(r.x);
+    cudaFree(r.k);
+    cudaFree(r.stat);
+    cudaFree(r.nst);
+    cudaFree(r.crs);
+    r.x = r.k = nullptr;
+    r.stat = r.nst = nullptr;
+    r.crs = nullptr;
+    r.cap_m = 0;
+    const int64_t want = std::max<int64_t>(m, 1 << 16);
+    cudaError_t e = cudaMalloc(&r.x, (size_t)want * 4 * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&r.k, (size_t)want * 4 * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&r.stat, (size_t)want * sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&r.nst, (size_t)want * sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&r.crs, (size_t)want * 5 * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_render(r);
+        return fail(KERR_ENOMEM, "kerr_surrogate_render: fallback buffers");
+    }
+    r.cap_m = want;
+    return KERR_OK;
+}
+
 extern "C" int kerr_surrogate_render(kerr_ctx *ctx, kerr_surrogate *s, const kerr_camera *cam,
                                      const kerr_opts *opts, float p_lo, float p_hi,
                                      float crit_dist, float *out, uint8_t *fallback,
@@ -898,104 +1071,69 @@ extern "C" int kerr_surrogate_render(kerr_ctx *ctx, kerr_surrogate *s, const ker
         return fail(KERR_EINVAL, "kerr_surrogate_render: invalid camera");
     const int64_t n = (int64_t)cam->nx * cam->ny;
     cudaStream_t st = (cudaStream_t)stream;
-    // device scratch for this call
-    float *in = nullptr, *o = nullptr, *crs = nullptr;
-    float2 *curve = nullptr;
-    double *rint = nullptr;
-    int64_t *idx = nullptr;
-    unsigned long long *cnt = nullptr;
-    double *x = nullptr, *k = nullptr;
-    int32_t *stat = nullptr, *nst = nullptr;
-    const int ns = 2048;
-    cudaError_t e = cudaMalloc(&in, (size_t)n * kIn * sizeof(float));
-    if (e == cudaSuccess)
-        e = cudaMalloc(&o, (size_t)n * kOut * sizeof(float));
-    if (e == cudaSuccess)
-        e = cudaMalloc(&curve, (size_t)2 * ns * sizeof(float2));
-    if (e == cudaSuccess)
-        e = cudaMalloc(&rint, 2 * sizeof(double));
-    if (e == cudaSuccess)
-        e = cudaMalloc(&idx, (size_t)n * sizeof(int64_t));
-    if (e == cudaSuccess)
-        e = cudaMalloc(&cnt, sizeof(unsigned long long));
-    int rc = KERR_OK;
+    RenderScratch &r = *s->render;
+    int rc = ensure_render(r, n, st);
+    if (rc)
+        return rc;
+    const int ns = kCurveSamples;
+    unsigned long long hcount = 0;
+    // network inputs from the pixel grid, then the fused forward
+    cudaError_t e = cudaMemsetAsync(r.cnt, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) {
+        surr_query_kernel<<<grid_1d(n), 256, 0, st>>>(r.in, *cam, n);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
-        rc = fail(KERR_ENOMEM, "kerr_surrogate_render: allocation");
+        return fail(KERR_ECUDA, "kerr_surrogate_render: query kernel");
     }
-    unsigned long long hcount = 0;
-    if (rc == KERR_OK) {
-        // network inputs from the pixel grid
-        e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st);
-        if (e == cudaSuccess) {
-            surr_query_kernel<<<grid_1d(n), 256, 0, st>>>(in, *cam, n);
-            e = cudaGetLastError();
-        }
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            rc = fail(KERR_ECUDA, "kerr_surrogate_render: query kernel");
-        }
+    rc = forward_fused(s, r.in, n, r.o, st);
+    if (rc)
+        return rc;
+    // critical curve, gate + decode, compaction of the fallback pixels
+    if (std::fabs(cam->a) >= 1e-4)
+        crit_interval_kernel<<<1, 256, 0, st>>>(cam->a, cam->incl, r.rint);
+    crit_curve_kernel<<<(ns + 127) / 128, 128, 0, st>>>(cam->a, cam->incl, ns, r.rint, r.curve);
+    curve_bounds_kernel<<<1, 256, 0, st>>>(r.curve, 2 * ns, r.bounds);
+    gate_kernel<<<grid_1d(n), 256, 2 * ns * sizeof(float2), st>>>(
+        r.o, *cam, r.curve, 2 * ns, r.bounds, p_lo, p_hi, crit_dist, n, out, fallback, r.idx,
+        r.cnt);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&hcount, r.cnt, sizeof hcount, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KERR_ECUDA, "kerr_surrogate_render: gate");
     }
-    if (rc == KERR_OK)
-        rc = forward_fused(s, in, n, o, st);
-    if (rc == KERR_OK) {
-        if (std::fabs(cam->a) >= 1e-4)
-            crit_interval_kernel<<<1, 256, 0, st>>>(cam->a, cam->incl, rint);
-        crit_curve_kernel<<<(ns + 127) / 128, 128, 0, st>>>(cam->a, cam->incl, ns, rint, curve);
-        gate_kernel<<<grid_1d(n), 256, 2 * ns * sizeof(float2), st>>>(
-            o, *cam, curve, 2 * ns, p_lo, p_hi, crit_dist, n, out, fallback, idx, cnt);
-        e = cudaGetLastError();
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(&hcount, cnt, sizeof hcount, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess)
-            e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            rc = fail(KERR_ECUDA, "kerr_surrogate_render: gate");
-        }
-        if (rc == KERR_OK)
-            rc = check_tc(s);
-    }
-    if (rc == KERR_OK && hcount > 0) {
+    rc = check_tc(s);
+    if (rc)
+        return rc;
+    // the integrator on the fallback pixels, merged into the planes
+    if (hcount > 0) {
         const int64_t m = (int64_t)hcount;
-        e = cudaMalloc(&x, (size_t)m * 4 * sizeof(double));
-        if (e == cudaSuccess)
-            e = cudaMalloc(&k, (size_t)m * 4 * sizeof(double));
-        if (e == cudaSuccess)
-            e = cudaMalloc(&stat, (size_t)m * sizeof(int32_t));
-        if (e == cudaSuccess)
-            e = cudaMalloc(&nst, (size_t)m * sizeof(int32_t));
-        if (e == cudaSuccess)
-            e = cudaMalloc(&crs, (size_t)m * 5 * sizeof(float));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            rc = fail(KERR_ENOMEM, "kerr_surrogate_render: fallback buffers");
-        }
+        rc = ensure_fallback(r, m, st);
+        // capacity = the buffers' size (the live count is read on the device),
+        // so that renders of any fallback count replay one captured graph
         if (rc == KERR_OK)
-            rc = kerr_trace_camera_list(ctx, cam, idx, cnt, m, opts, x, k, stat, nst, nullptr, crs,
-                                        stream);
+            rc = kerr_trace_camera_list(ctx, cam, r.idx, r.cnt, r.cap_m, opts, r.x, r.k, r.stat,
+                                        r.nst, nullptr, r.crs, stream);
         if (rc == KERR_OK) {
-            merge_kernel<<<grid_1d(m), 256, 0, st>>>(idx, cnt, stat, crs, m, n, out);
+            merge_kernel<<<grid_1d(m), 256, 0, st>>>(r.idx, r.cnt, r.stat, r.crs, r.cap_m, n,
+                                                     out);
             if (cudaGetLastError() != cudaSuccess) {
                 cudaGetLastError();
                 rc = fail(KERR_ECUDA, "kerr_surrogate_render: merge");
             }
         }
     }
-    cudaStreamSynchronize(st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == KERR_OK) {
+        cudaGetLastError();
+        rc = fail(KERR_ECUDA, "kerr_surrogate_render: synchronisation");
+    }
     if (n_fallback)
         *n_fallback = (int64_t)hcount;
-    cudaFree(in);
-    cudaFree(o);
-    cudaFree(curve);
-    cudaFree(rint);
-    cudaFree(idx);
-    cudaFree(cnt);
-    cudaFree(x);
-    cudaFree(k);
-    cudaFree(stat);
-    cudaFree(nst);
-    cudaFree(crs);
     return rc;
 }
 
