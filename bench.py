@@ -391,8 +391,10 @@ def run_surrogate(args, K, W, dev, stream):
         K.kerr_surrogate_render(ctx, net, cam, opts, stream=stream)      # warm (graphs)
         ref32 = K.alloc_out(n, dev, diag=False, cross=True)
         K.kerr_trace_camera(ctx, cam, opts, out=ref32, stream=stream)
+        torch.cuda.nvtx.range_push("surrogate_render")      # for profiler filters
         (out, fb, nfb), dt = timed(lambda: K.kerr_surrogate_render(ctx, net, cam, opts,
                                                                    stream=stream))
+        torch.cuda.nvtx.range_pop()
         _, dti = timed(lambda: K.kerr_trace_camera(ctx, cam, opts, out=ref32, stream=stream))
         ref = K.alloc_out(n, dev, diag=False, cross=True)
         K.kerr_trace_camera(ctx, cam, o64, out=ref, stream=stream)

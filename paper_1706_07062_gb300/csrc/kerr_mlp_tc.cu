@@ -189,6 +189,16 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t v[8])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// One 16-byte shared store (a whole quarter-warp then covers 128 contiguous
+// bytes of a core matrix: no bank conflicts).
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                             uint32_t d)
+{
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+                 "r"(d)
+                 : "memory");
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -198,9 +208,9 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 // Hidden-layer epilogue of one thread: row `row` of the accumulator, columns
 // [32 c0, 32 c1) -> bias + SiLU -> bf16 A operand of the next layer.
 __device__ __forceinline__ void epilogue_hidden(uint32_t tmem_row, const float *bias,
-                                                uint8_t *act, int t, int c0, int c1)
+                                                uint32_t act, int t, int c0, int c1)
 {
-    uint8_t *row = act + (t >> 3) * (kHidden * 16) + (t & 7) * 16;
+    const uint32_t row = act + (t >> 3) * (kHidden * 16) + (t & 7) * 16;
 #pragma unroll 1
     for (int c = c0; c < c1; ++c) {
         uint32_t v[32];
@@ -215,7 +225,7 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t tmem_row, const float *
                 const float z1 = __uint_as_float(v[8 * q + 2 * j + 1]) + bias[col + 1];
                 w[j] = pack_bf16(silu(z0), silu(z1));
             }
-            *reinterpret_cast<uint4 *>(row + (4 * c + q) * 128) = make_uint4(w[0], w[1], w[2], w[3]);
+            st_shared_v4(row + (4 * c + q) * 128, w[0], w[1], w[2], w[3]);
         }
     }
 }
@@ -299,10 +309,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int j = 0; j < 4; ++j)
                     x[j] = in[r * kIn + j];
             }
-            uint8_t *row = smem + SM_X + (t >> 3) * (kInPad * 16) + (t & 7) * 16;
-            *reinterpret_cast<uint4 *>(row) =
-                make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), 0u, 0u);
-            *reinterpret_cast<uint4 *>(row + 128) = make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t xrow = s_x + (t >> 3) * (kInPad * 16) + (t & 7) * 16;
+            st_shared_v4(xrow, pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), 0u, 0u);
+            st_shared_v4(xrow + 128, 0u, 0u, 0u, 0u);
         }
         fence_proxy_async();
         fence_before();
@@ -317,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = ok && mbar_wait(bar_mma, ph_mma);
         ph_mma ^= 1;
         fence_after();
-        epilogue_hidden(tmem_row, sb, smem + SM_ACT, row, 4 * half, 4 * half + 4);
+        epilogue_hidden(tmem_row, sb, s_act, row, 4 * half, 4 * half + 4);
         fence_proxy_async();
         fence_before();
         __syncthreads();
@@ -346,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             fence_after();
             if (!last) {
-                epilogue_hidden(tmem_row, sb + l * kHidden, smem + SM_ACT, row, 4 * half,
+                epilogue_hidden(tmem_row, sb + l * kHidden, s_act, row, 4 * half,
                                 4 * half + 4);
                 fence_proxy_async();
             } else if (half == 0) {
