@@ -742,3 +742,125 @@ int oracle_trace_batch(int64_t n, const double *a, const double *t_end, const do
         pthread_join(th[t], NULL);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Coordinate-time integration (Sec. 2.2, eq. geo_t)                        */
+/* ------------------------------------------------------------------------ */
+
+/* With the coordinate time t as the independent variable the state is
+ * w = (x, y, z, v^x, v^y, v^z), v = dx/dt.  Along a geodesic k = k^t u with
+ * u = (1, v); the affine acceleration A(k) = dk/dlambda is quadratic in k and
+ * d/dlambda = k^t d/dt, so
+ *   dx^i/dt = v^i,   dv^i/dt = (A^i(k) - v^i A^t(k)) / (k^t)^2
+ *                            = A^i(u) - v^i A^t(u).
+ * The oracle evaluates A(u) with the Christoffel form (rhs_geo).  (Eq. geo_t
+ * writes the same right-hand side in the split-metric variables.)          */
+static void rhs_coordtime(metric_fn m, double a, double t, const double w[6], double dw[6])
+{
+    const double y[8] = {t, w[0], w[1], w[2], 1.0, w[3], w[4], w[5]};
+    double dy[8];
+    rhs_geo(m, a, y, dy);
+    for (int i = 0; i < 3; ++i) {
+        dw[i] = w[3 + i];
+        dw[3 + i] = dy[5 + i] - w[3 + i] * dy[4];
+    }
+}
+
+/* Classic RK4 step of the coordinate-time system (Sec. 3). */
+static void rk4_step_t(metric_fn m, double a, double t, const double w[6], double h,
+                       double out[6])
+{
+    double k1[6], k2[6], k3[6], k4[6], s[6];
+    rhs_coordtime(m, a, t, w, k1);
+    for (int i = 0; i < 6; ++i)
+        s[i] = w[i] + 0.5 * h * k1[i];
+    rhs_coordtime(m, a, t + 0.5 * h, s, k2);
+    for (int i = 0; i < 6; ++i)
+        s[i] = w[i] + 0.5 * h * k2[i];
+    rhs_coordtime(m, a, t + 0.5 * h, s, k3);
+    for (int i = 0; i < 6; ++i)
+        s[i] = w[i] + h * k3[i];
+    rhs_coordtime(m, a, t + h, s, k4);
+    for (int i = 0; i < 6; ++i)
+        out[i] = w[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+/* Adaptive integration in coordinate time from (t0, w0) to t_end, with the
+ * affine integrator's controller (step doubling, err over the six
+ * components, the same factor rule).  A trial step never passes t_end: the
+ * last accepted step lands on it exactly.  Termination after each accepted
+ * step: captured r < 1.01 r_h; escaped r > r_esc while moving outward in the
+ * direction of integration (sign(t_end - t0) x.v > 0); end time reached.
+ * No surface clipping (the end time needs none).  Returns the status.      */
+int oracle_trace_coordtime(double a, double t0, const double w0[6], double t_end,
+                           const oracle_opts *o, double wend[6], double *t_out,
+                           int64_t *attempts_out)
+{
+    metric_fn m = ks_metric_c;
+    double w[6], t = t0;
+    memcpy(w, w0, sizeof w);
+    int64_t att = 0;
+    int st = 0;
+    const double rh = 1.0 + sqrt(fmax(0.0, 1.0 - a * a));
+    const double rcap = 1.01 * rh;
+    const double r0 = oracle_ks_r(a, w[0], w[1], w[2]);
+    const double resc = o->r_escape > 0.0 ? o->r_escape : (o->r_escape == 0.0 ? r0 : INFINITY);
+    const double dir = t_end >= t0 ? 1.0 : -1.0;
+    double h = dir * o->h0;
+    int finite = 1;
+    for (int i = 0; i < 6; ++i)
+        finite = finite && isfinite(w[i]);
+    if (!finite || !isfinite(t0) || !isfinite(t_end))
+        st = ST_NONFINITE;
+    else if (r0 < rcap)
+        st = ST_CAPTURED;
+    else if (t_end == t0)
+        st = ST_ENDTIME;
+    while (st == 0) {
+        if (att >= o->max_steps) {
+            st = ST_MAXSTEPS;
+            break;
+        }
+        const int last = dir * (t + h - t_end) >= 0.0;   /* this trial reaches t_end */
+        const double hs = last ? t_end - t : h;
+        ++att;
+        double wf[6], wm[6], wh[6];
+        rk4_step_t(m, a, t, w, hs, wf);
+        rk4_step_t(m, a, t, w, 0.5 * hs, wm);
+        rk4_step_t(m, a, t + 0.5 * hs, wm, 0.5 * hs, wh);
+        double err = 0.0;
+        for (int i = 0; i < 6; ++i) {
+            const double d = (wh[i] - wf[i]) / 15.0;
+            const double sc = o->tol * (1.0 + fmax(fabs(w[i]), fabs(wh[i])));
+            const double e = fabs(d) / sc;
+            if (!(e <= err))
+                err = e;
+        }
+        const double fac = step_factor(err);
+        if (!(err <= 1.0)) {
+            h = hs * fac;
+            continue;
+        }
+        memcpy(w, wh, sizeof w);
+        t = last ? t_end : t + hs;
+        finite = 1;
+        for (int i = 0; i < 6; ++i)
+            finite = finite && isfinite(w[i]);
+        if (!finite) {
+            st = ST_NONFINITE;
+            break;
+        }
+        const double r = oracle_ks_r(a, w[0], w[1], w[2]);
+        if (r < rcap)
+            st = ST_CAPTURED;
+        else if (r > resc && dir * (w[0] * w[3] + w[1] * w[4] + w[2] * w[5]) > 0.0)
+            st = ST_ESCAPED;
+        else if (last)
+            st = ST_ENDTIME;
+        h = (last ? h : hs) * fac;
+    }
+    memcpy(wend, w, sizeof w);
+    *t_out = t;
+    *attempts_out = att;
+    return st;
+}

@@ -82,6 +82,9 @@ def lib():
         _lib.oracle_trace_batch.argtypes = [c.c_int64, D, D, D, c.POINTER(_Opts), D, I32, I64,
                                             I64, D, c.c_int]
         _lib.oracle_trace_batch.restype = c.c_int
+        _lib.oracle_trace_coordtime.argtypes = [c.c_double, c.c_double, D, c.c_double,
+                                                c.POINTER(_Opts), D, D, I64]
+        _lib.oracle_trace_coordtime.restype = c.c_int
     return _lib
 
 
@@ -268,3 +271,35 @@ def ill_conditioned(a, y0, opts: Opts, ref: TraceResult | None = None,
     bad = (rel_err(r_tight.y, ref.y) > rel) | (r_tight.status != ref.status)
     bad |= (rel_err(r_pert.y, ref.y) > rel) | (r_pert.status != ref.status)
     return bad
+
+
+@dataclass
+class CoordTimeResult:
+    w: np.ndarray        # (n, 6): x, y, z, v^x, v^y, v^z at the end
+    t: np.ndarray        # (n,) coordinate time at the end
+    status: np.ndarray   # (n,) int32
+    attempts: np.ndarray
+
+
+def trace_coordtime(a: float, t0, w0, t_end, opts: Opts) -> CoordTimeResult:
+    """Coordinate-time integration (Sec. 2.2, eq. geo_t) of each row of
+    w0 (n, 6) = (x, y, z, dx/dt, dy/dt, dz/dt) from t0 to t_end (scalars or
+    one per row); see oracle_trace_coordtime in kerr_oracle.c."""
+    w0 = _f64(w0).reshape(-1, 6)
+    n = w0.shape[0]
+    t0 = np.broadcast_to(np.asarray(t0, dtype=np.float64), (n,))
+    te = np.broadcast_to(np.asarray(t_end, dtype=np.float64), (n,))
+    w = np.zeros((n, 6))
+    t = np.zeros(n)
+    st = np.zeros(n, dtype=np.int32)
+    att = np.zeros(n, dtype=np.int64)
+    o = opts.c()
+    for i in range(n):
+        wi = np.zeros(6)
+        ti = ctypes.c_double()
+        ai = ctypes.c_int64()
+        st[i] = lib().oracle_trace_coordtime(a, float(t0[i]), _dp(np.ascontiguousarray(w0[i])),
+                                             float(te[i]), ctypes.byref(o), _dp(wi),
+                                             ctypes.byref(ti), ctypes.byref(ai))
+        w[i], t[i], att[i] = wi, ti.value, ai.value
+    return CoordTimeResult(w, t, st, att)

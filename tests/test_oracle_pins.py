@@ -665,3 +665,65 @@ def test_crossing_labels_are_on_the_plane_and_ordered():
     g_ok = ~np.isnan(c[:, 4])
     assert np.all(c[g_ok, 0] >= C.r_isco(a) - 1e-9) and g_ok.sum() > 100
     assert np.all(np.isnan(c[has1 & ~g_ok, 4]))
+
+
+# ---------------------------------------------------------------------------
+# coordinate-time form (Sec. 2.2, eq. geo_t)
+# ---------------------------------------------------------------------------
+def test_coordtime_matches_affine_integration():
+    """The same photons integrated in coordinate time and in the affine
+    parameter (with the end-time event) end at the same events: positions
+    and v = k^i / k^t agree to the tolerance at t = t_end."""
+    a, incl, r_obs = 0.9, np.radians(60.0), 50.0
+    idx = np.array([3, 20, 27, 36, 45, 60])           # 8 x 8 image, +-12 M: near passes
+    y0 = O.camera_ic(a, incl, r_obs, 12.0, 8, 8, idx)
+    t_end = -70.0                                      # past-directed: t decreases
+    aff = O.trace(a, y0, O.Opts(tol=1e-12, t_end=t_end, r_escape=-1.0))
+    assert np.all(aff.status == O.ENDTIME)
+    w0 = np.concatenate([y0[:, 1:4], y0[:, 5:8] / y0[:, 4:5]], axis=1)
+    ct = O.trace_coordtime(a, y0[:, 0], w0, t_end, O.Opts(tol=1e-12, r_escape=-1.0))
+    assert np.all(ct.status == O.ENDTIME) and np.all(ct.t == t_end)
+    rmin = min(np.min(np.linalg.norm(O.rk4_fixed(a, y, 0.25, 400, stride=4)[:, 1:4], axis=1))
+               for y in y0)
+    assert rmin < 10.0                                 # the window reaches the strong field
+    np.testing.assert_allclose(ct.w[:, :3], aff.y[:, 1:4], rtol=0, atol=1e-7)
+    np.testing.assert_allclose(ct.w[:, 3:], aff.y[:, 5:8] / aff.y[:, 4:5], rtol=0, atol=1e-8)
+
+
+def test_coordtime_circular_orbit():
+    """A prograde circular equatorial orbit in coordinate time: in Cartesian
+    KS coordinates x + i y = (r + i a) e^{i Omega t} with Omega = 1/(r^{3/2} + a)
+    (the KS and BL azimuths differ by a function of r only)."""
+    a, r = 0.5, 8.0
+    Om = C.omega_circular(r, a)
+    w0 = np.array([[r, a, 0.0, -a * Om, r * Om, 0.0]])
+    T = 200.0                                          # ~1.4 orbits
+    z = (r + 1j * a) * np.exp(1j * Om * T)
+    v = 1j * Om * z
+    errs = []
+    for tol in (1e-10, 1e-14):
+        ct = O.trace_coordtime(a, 0.0, w0, T, O.Opts(tol=tol, r_escape=-1.0))
+        assert ct.status[0] == O.ENDTIME and ct.t[0] == T
+        assert abs(ct.w[0, 2]) < 1e-12 and abs(ct.w[0, 5]) < 1e-12
+        errs.append(abs(ct.w[0, 0] + 1j * ct.w[0, 1] - z))
+    # the global error of the local-error controller shrinks like tol^(4/5)
+    assert errs[1] < 2e-9 and errs[0] / errs[1] > 500
+    assert abs(ct.w[0, 3] + 1j * ct.w[0, 4] - v) < 2e-10
+
+
+def test_coordtime_terminations():
+    """Capture, escape and the exact end time in coordinate time."""
+    a = 0.7
+    # radial infall from rest at r = 6 on the axis: captured
+    cap = O.trace_coordtime(a, 0.0, [[0.0, 0.0, 6.0, 0.0, 0.0, 0.0]], 1e4, O.Opts(tol=1e-9))
+    assert cap.status[0] == O.CAPTURED
+    # outgoing photon far away: escapes beyond its start radius (r_escape = 0)
+    esc = O.trace_coordtime(a, 0.0, [[30.0, 0.0, 0.0, 1.0, 0.0, 0.0]], 1e4,
+                            O.Opts(tol=1e-9, r_escape=0.0))
+    assert esc.status[0] == O.ESCAPED
+    # zero-length interval and attempt cap
+    z = O.trace_coordtime(a, 5.0, [[30.0, 0.0, 0.0, 0.5, 0.0, 0.0]], 5.0, O.Opts())
+    assert z.status[0] == O.ENDTIME and z.attempts[0] == 0
+    m = O.trace_coordtime(a, 0.0, [[30.0, 0.0, 0.0, 0.0, 0.1, 0.0]], 1e6,
+                          O.Opts(tol=1e-9, max_steps=3, r_escape=-1.0))
+    assert m.status[0] == O.MAXSTEPS and m.attempts[0] == 3
