@@ -367,6 +367,28 @@ int kerr_surrogate_render(kerr_ctx *ctx, kerr_surrogate *s, const kerr_camera *c
                           const kerr_opts *opts, float p_lo, float p_hi, float crit_dist,
                           float *out, uint8_t *fallback, int64_t *n_fallback, void *stream);
 
+/* Integrates n geodesics in the coordinate time t (Sec. 2.2, eq. geo_t):
+ * state (x, y, z, v^x, v^y, v^z) with v = dx/dt, right-hand side
+ * dv^i/dt = A^i(u) - v^i A^t(u) for u = (1, v), A the affine acceleration of
+ * eqs. opt0/opti (the same function eq. geo_t writes in split-metric form).
+ * Works for null and time-like geodesics alike.  x0: [4][n] start events
+ * (t0, x, y, z), v0: [3][n] coordinate velocities; each geodesic runs from
+ * its t0 to t_end[i] (t_end may be NULL: opts.t_end for all), forward or
+ * backward in t.  Step control as for kerr_trace_rays on the six components;
+ * a trial step never passes the end time, so the last step lands on it
+ * exactly (no clipping needed).  Statuses: KERR_ENDTIME (t = t_end),
+ * KERR_CAPTURED (r < 1.01 r_h after a step), KERR_ESCAPED (r > r_esc while
+ * moving outward in the direction of integration), KERR_MAXSTEPS,
+ * KERR_NONFINITE.  Outputs: x_out [4][n] end events, v_out [3][n], status[n],
+ * steps[n] (attempts).  opts: prec KERR_FP64, or KERR_FP32_KAHAN (FP32
+ * arithmetic with compensated state updates everywhere: this entry point has
+ * no FP64 zone), tol, h0, max_steps, r_escape, t_end.  All buffers device
+ * memory (KERR_EINVAL otherwise); asynchronous on `stream`; statistics in
+ * kerr_get_stats. */
+int kerr_trace_coordtime(kerr_ctx *ctx, const double *x0, const double *v0,
+                         const double *t_end, int64_t n, const kerr_opts *opts, double *x_out,
+                         double *v_out, int32_t *status, int32_t *steps, void *stream);
+
 /* Paper-mode integration (Sec. 3, the timing setting of Sec. 4.2 and
  * Tables 2-3): every geodesic of `state` takes exactly nsteps classic RK4
  * steps of length h in place, with the right-hand side of eqs. opt0/opti,

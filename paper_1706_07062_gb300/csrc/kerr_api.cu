@@ -568,6 +568,76 @@ extern "C" int kerr_trace_particles(kerr_ctx *c, const double *x0, const double 
                         steps, diag, cross, stream);
 }
 
+static bool on_device(const void *p)
+{
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+}
+
+extern "C" int kerr_trace_coordtime(kerr_ctx *c, const double *x0, const double *v0,
+                                    const double *t_end, int64_t n, const kerr_opts *o,
+                                    double *x_out, double *v_out, int32_t *status,
+                                    int32_t *steps, void *stream)
+{
+    if (!c)
+        return fail(KERR_EINVAL, "kerr_trace_coordtime: NULL context");
+    int rc = check_opts(o);
+    if (rc)
+        return rc;
+    if (n < 0)
+        return fail(KERR_EINVAL, "kerr_trace_coordtime: n = %lld < 0", (long long)n);
+    if (n == 0)
+        return KERR_OK;
+    if (!x0 || !v0 || !x_out || !v_out || !status || !steps)
+        return fail(KERR_EINVAL, "kerr_trace_coordtime: NULL buffer");
+    if (!on_device(x0) || !on_device(v0) || !on_device(x_out) || !on_device(v_out) ||
+        !on_device(status) || !on_device(steps) || (t_end && !on_device(t_end)))
+        return fail(KERR_EINVAL, "kerr_trace_coordtime: buffers must be device memory");
+    if (!t_end && std::isnan(o->t_end))
+        return fail(KERR_EINVAL, "kerr_trace_coordtime: no end time (t_end NULL, opts.t_end NaN)");
+    CoordParams P;
+    std::memset(&P, 0, sizeof P);
+    P.n = n;
+    P.a = c->a;
+    P.x0 = x0;
+    P.v0 = v0;
+    P.t_end_each = t_end;
+    P.t_end = o->t_end;
+    P.x_out = x_out;
+    P.v_out = v_out;
+    P.status = status;
+    P.steps = steps;
+    P.tol = o->tol;
+    P.h0 = o->h0;
+    P.r_escape = o->r_escape;
+    P.max_steps = o->max_steps;
+    P.head = c->d_scratch;
+    P.stats = c->d_scratch + 1;
+    cudaStream_t us = (cudaStream_t)stream;
+    KERR_CUDA(cudaEventRecord(c->ev_in, us));
+    KERR_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+    KERR_CUDA(cudaMemsetAsync(c->d_scratch, 0, kScratchWords * sizeof(unsigned long long),
+                              c->stream));
+    KERR_CUDA(cudaEventRecord(c->ev_k0, c->stream));
+    const cudaError_t e = launch_coordtime(P, o->prec == KERR_FP32_KAHAN ? 1 : 0, c->sms,
+                                           c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KERR_ECUDA, "kerr_trace_coordtime: launch failed: %s", cudaGetErrorString(e));
+    }
+    KERR_CUDA(cudaEventRecord(c->ev_k1, c->stream));
+    KERR_CUDA(cudaEventRecord(c->ev_out, c->stream));
+    KERR_CUDA(cudaStreamWaitEvent(us, c->ev_out, 0));
+    c->have_stats = true;
+    c->last_f32 = 0;
+    c->last_variant = -1;
+    return KERR_OK;
+}
+
 static int build_cams(const kerr_camera *cams, int32_t ncam, std::vector<CamDev> &out, int64_t &n)
 {
     if (!cams || ncam <= 0)

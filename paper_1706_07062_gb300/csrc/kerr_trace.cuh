@@ -119,6 +119,23 @@ struct TraceParams {
     unsigned long long *zpush;  // zone phase: re-queued geodesics, zero at launch
 };
 
+// Coordinate-time integration (Sec. 2.2, eq. geo_t): launch parameters.
+struct CoordParams {
+    int64_t n;
+    double a;
+    const double *x0;           // [4][n] start events (t, x, y, z)
+    const double *v0;           // [3][n] coordinate velocities dx^i/dt
+    const double *t_end_each;   // [n] end times, or null: t_end
+    double t_end;
+    double *x_out;              // [4][n] end events
+    double *v_out;              // [3][n] end velocities
+    int32_t *status, *steps;    // [n]
+    double tol, h0, r_escape;
+    int64_t max_steps;
+    unsigned long long *head;   // work-queue counter, zero at launch
+    unsigned long long *stats;  // SC_COUNT counters, zero at launch
+};
+
 #ifndef KERR_TYPES_ONLY
 
 // Per-geodesic constants fixed at set-up.

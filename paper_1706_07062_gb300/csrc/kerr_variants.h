@@ -46,6 +46,11 @@ cudaError_t launch_zone_phase(const TraceParams &P, int zv, int sms, cudaStream_
 cudaError_t launch_setup_f32(const TraceParams &P, int sms, cudaStream_t s);
 cudaError_t launch_finish_f32(const TraceParams &P, int sms, cudaStream_t s);
 
+struct CoordParams;
+// Coordinate-time integration in FP64 (fp32 = 0) or FP32 with compensated
+// state updates (fp32 = 1), persistent grid over `sms` SMs.
+cudaError_t launch_coordtime(const CoordParams &P, int fp32, int sms, cudaStream_t s);
+
 // Records `msg` as this thread's kerr_last_error() and returns `code`.
 int kerr_set_error(int code, const char *msg);
 

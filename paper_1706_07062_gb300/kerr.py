@@ -117,6 +117,8 @@ def lib():
         L.kerr_autotune.argtypes = [vp, c.POINTER(Camera), c.POINTER(Opts), i64, c.POINTER(i32), vp]
         L.kerr_check_fp64_math.argtypes = [vp, i64, vp, vp]
         L.kerr_rk4_fixed.argtypes = [c.c_double, i32, i32, vp, i64, i32, c.c_double, vp]
+        L.kerr_trace_coordtime.argtypes = [vp, vp, vp, vp, i64, c.POINTER(Opts), vp, vp, vp, vp,
+                                           vp]
         L.kerr_last_error.restype = c.c_char_p
         for name in ("kerr_init", "kerr_destroy", "kerr_trace_rays", "kerr_trace_particles",
                      "kerr_trace_camera", "kerr_trace_camera_static", "kerr_get_stats",
@@ -127,7 +129,8 @@ def lib():
                      "kerr_surrogate_get_grad", "kerr_surrogate_targets",
                      "kerr_surrogate_forward", "kerr_surrogate_grad", "kerr_surrogate_train",
                      "kerr_surrogate_render", "kerr_check_fp64_math",
-                     "kerr_surrogate_forward_impl", "kerr_rk4_fixed"):
+                     "kerr_surrogate_forward_impl", "kerr_rk4_fixed",
+                     "kerr_trace_coordtime"):
             getattr(L, name).restype = c.c_int
         _lib = L
     return _lib
@@ -516,3 +519,32 @@ def kerr_rk4_fixed(a: float, state, nsteps: int, h: float, layout: int = LAYOUT_
                                 _ptr(state), n, int(nsteps), float(h),
                                 _stream_ptr(stream, state)), "kerr_rk4_fixed")
     return state
+
+
+@dataclass
+class CoordTimeOut:
+    x: object            # (4, n) end events (t, x, y, z)
+    v: object            # (3, n) end velocities dx/dt
+    status: object
+    steps: object
+
+
+def kerr_trace_coordtime(ctx: Context, x0, v0, t_end=None, opts: Opts | None = None,
+                         stream=None) -> CoordTimeOut:
+    """Coordinate-time integration of device tensors x0 (4, n), v0 (3, n)
+    (float64) to t_end ((n,) tensor, or opts.t_end)."""
+    import torch
+    n = int(x0.shape[1])
+    if tuple(x0.shape) != (4, n) or tuple(v0.shape) != (3, n):
+        raise KerrError("x0 must have shape (4, n) and v0 shape (3, n)")
+    opts = opts or default_opts()
+    dev = x0.device
+    out = CoordTimeOut(torch.empty((4, n), dtype=torch.float64, device=dev),
+                       torch.empty((3, n), dtype=torch.float64, device=dev),
+                       torch.empty(n, dtype=torch.int32, device=dev),
+                       torch.empty(n, dtype=torch.int32, device=dev))
+    _check(lib().kerr_trace_coordtime(ctx.handle, _ptr(x0), _ptr(v0), _ptr(t_end), n,
+                                      ctypes.byref(opts), _ptr(out.x), _ptr(out.v),
+                                      _ptr(out.status), _ptr(out.steps),
+                                      _stream_ptr(stream, x0)), "kerr_trace_coordtime")
+    return out
