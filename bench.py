@@ -528,10 +528,12 @@ def run_particles(K, W, dev, stream):
     return res
 
 
-# The paper's best KS-coordinate entries of its Table 2 (ns per RK4 step per
-# ray, Titan Black, OpenCL; other hardware: context, not a target).
-PAPER_NS_PER_STEP = {("f32", "soa"): 0.309, ("f32", "aos"): 0.297,
-                     ("f64", "soa"): 1.15, ("f64", "aos"): 1.15}
+# The paper's Titan Black entries of its Table 2 (ns per RK4 step per ray,
+# OpenCL; other hardware: context, not a target).
+PAPER_NS_PER_STEP = {("KS", "f32", "soa"): 0.309, ("KS", "f32", "aos"): 0.297,
+                     ("KS", "f64", "soa"): 1.15, ("KS", "f64", "aos"): 1.15,
+                     ("BL", "f32", "soa"): 0.175, ("BL", "f32", "aos"): 0.167,
+                     ("BL", "f64", "soa"): 1.66, ("BL", "f64", "aos"): 1.65}
 
 
 def run_paper_mode(K, dev, stream):
@@ -539,13 +541,14 @@ def run_paper_mode(K, dev, stream):
     a = 0.999 (inclination 60 deg and image plane +-20 M: this reading), each
     ray 1024 fixed RK4 steps of h = 1 in one launch, no termination; ns per
     RK4 step per ray = launch time / (1024 N), best over the image sizes, for
-    FP32 / FP64 and SoA / AoS state layouts.  Initial states are built on the
+    KS / BL coordinates, FP32 / FP64 and SoA / AoS state layouts.  Initial states are built on the
     device (a zero-step camera trace); each timed launch starts from them
     (restored outside the events)."""
     import torch
 
     a, nsteps, h = 0.999, 1024, 1.0
     ctx = K.kerr_init(a)
+    coords_rows = (("ks", "KS"), ("bl", "BL"))
     o0 = K.default_opts(prec=K.FP64, max_steps=0)
     rows = []
     best = {}
@@ -555,36 +558,43 @@ def run_paper_mode(K, dev, stream):
         out = K.alloc_out(n, dev, diag=False)
         K.kerr_trace_camera(ctx, cam, o0, out=out, stream=stream)
         torch.cuda.synchronize(dev)
-        y0 = torch.cat([out.x, out.k], 0).contiguous()          # (8, n) float64
-        for prec, dt in (("f32", torch.float32), ("f64", torch.float64)):
-            for lay, lid in (("soa", K.LAYOUT_SOA), ("aos", K.LAYOUT_AOS)):
-                init = y0.to(dt) if lid == K.LAYOUT_SOA else y0.T.contiguous().to(dt)
-                work = init.clone()
-                K.kerr_rk4_fixed(a, work, nsteps, h, layout=lid, stream=stream)   # warm-up
-                times = []
-                for _ in range(2):
-                    work.copy_(init)
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    K.kerr_rk4_fixed(a, work, nsteps, h, layout=lid, stream=stream)
-                    e1.record(stream)
-                    torch.cuda.synchronize(dev)
-                    times.append(e0.elapsed_time(e1))
-                ns = min(times) * 1e6 / (nsteps * n)
-                rows.append({"side": side, "prec": prec, "layout": lay, "ns_per_step": round(ns, 5)})
-                key = (prec, lay)
-                if key not in best or ns < best[key]["ns_per_step"]:
-                    best[key] = {"ns_per_step": round(ns, 5), "side": side}
-        del out, y0
+        y_ks = torch.cat([out.x, out.k], 0).contiguous()        # (8, n) float64
+        y_bl = K.kerr_bl_camera_states(cam, device=dev, stream=stream)
+        torch.cuda.synchronize(dev)
+        for coords, cname in coords_rows:
+            y0 = y_ks if coords == "ks" else y_bl
+            for prec, dt in (("f32", torch.float32), ("f64", torch.float64)):
+                for lay, lid in (("soa", K.LAYOUT_SOA), ("aos", K.LAYOUT_AOS)):
+                    init = y0.to(dt) if lid == K.LAYOUT_SOA else y0.T.contiguous().to(dt)
+                    work = init.clone()
+                    K.kerr_rk4_fixed(a, work, nsteps, h, layout=lid, stream=stream,
+                                     coords=coords)                              # warm-up
+                    times = []
+                    for _ in range(2):
+                        work.copy_(init)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        K.kerr_rk4_fixed(a, work, nsteps, h, layout=lid, stream=stream,
+                                         coords=coords)
+                        e1.record(stream)
+                        torch.cuda.synchronize(dev)
+                        times.append(e0.elapsed_time(e1))
+                    ns = min(times) * 1e6 / (nsteps * n)
+                    rows.append({"side": side, "coords": cname, "prec": prec, "layout": lay,
+                                 "ns_per_step": round(ns, 5)})
+                    key = (cname, prec, lay)
+                    if key not in best or ns < best[key]["ns_per_step"]:
+                        best[key] = {"ns_per_step": round(ns, 5), "side": side}
+        del out, y_ks, y_bl
     ctx.close()
     summary = {}
-    for (prec, lay), b in sorted(best.items()):
-        paper = PAPER_NS_PER_STEP[(prec, lay)]
-        summary[f"{prec}_{lay}"] = {"ns_per_step": b["ns_per_step"], "best_side": b["side"],
-                                    "ray_steps_per_s": round(1e9 / b["ns_per_step"], 1),
-                                    "paper_titan_black_ns": paper,
-                                    "ratio_vs_paper": round(paper / b["ns_per_step"], 2)}
+    for (cname, prec, lay), b in sorted(best.items()):
+        paper = PAPER_NS_PER_STEP[(cname, prec, lay)]
+        summary[f"{cname}_{prec}_{lay}"] = {
+            "ns_per_step": b["ns_per_step"], "best_side": b["side"],
+            "ray_steps_per_s": round(1e9 / b["ns_per_step"], 1),
+            "paper_titan_black_ns": paper, "ratio_vs_paper": round(paper / b["ns_per_step"], 2)}
     return {"workload": "a=0.999, r_obs=1024M, i=60deg, +-20M, images 64^2..1024^2, "
                         "1024 fixed RK4 steps of h=1 per launch, no termination",
             "unit": "ns per RK4 step per ray (best over image sizes)",

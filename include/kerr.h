@@ -404,6 +404,24 @@ int kerr_trace_coordtime(kerr_ctx *ctx, const double *x0, const double *v0,
 int kerr_rk4_fixed(double a, int32_t fp64, int32_t layout, void *state, int64_t n,
                    int32_t nsteps, double h, void *stream);
 
+/* Paper mode in Boyer-Lindquist coordinates (eq. 1; the BL rows of the
+ * paper's Tables 2-3, whose BL equations it does not print).  This library's
+ * reading: the Hamiltonian form H = N / (2 Sigma) of the BL geodesic
+ * equations, state (t, r, theta, phi, p_t, p_r, p_theta, p_phi) with covariant
+ * momenta (p_t and p_phi stay constant).  Same arguments and behaviour as
+ * kerr_rk4_fixed; |a| < 1. */
+int kerr_rk4_fixed_bl(double a, int32_t fp64, int32_t layout, void *state, int64_t n,
+                      int32_t nsteps, double h, void *stream);
+
+/* BL start states of a camera's rays for kerr_rk4_fixed_bl (this library's
+ * reading of a distant observer at (r_obs, theta = incl, phi = 0, t = 0):
+ * E = 1, L = -alpha sin(incl), Q = beta^2 + cos^2(incl) (alpha^2 - a^2),
+ * p_theta = sign(beta) sqrt(Theta), p_r < 0 from H = 0), nx * ny states into
+ * device `state` (float or double, SoA or AoS as for kerr_rk4_fixed).
+ * |a| < 1, 0 < incl < pi, r_obs > 2.  Asynchronous on `stream`. */
+int kerr_bl_camera_states(const kerr_camera *cam, int32_t fp64, int32_t layout, void *state,
+                          void *stream);
+
 /* Check of the integrator's FP64 reciprocal, reciprocal square root and
  * square root (Newton-refined hardware approximations, see the FP64 steps;
  * this library's own primitives, with no counterpart in the paper): for

@@ -119,6 +119,8 @@ def lib():
         L.kerr_rk4_fixed.argtypes = [c.c_double, i32, i32, vp, i64, i32, c.c_double, vp]
         L.kerr_trace_coordtime.argtypes = [vp, vp, vp, vp, i64, c.POINTER(Opts), vp, vp, vp, vp,
                                            vp]
+        L.kerr_rk4_fixed_bl.argtypes = [c.c_double, i32, i32, vp, i64, i32, c.c_double, vp]
+        L.kerr_bl_camera_states.argtypes = [c.POINTER(Camera), i32, i32, vp, vp]
         L.kerr_last_error.restype = c.c_char_p
         for name in ("kerr_init", "kerr_destroy", "kerr_trace_rays", "kerr_trace_particles",
                      "kerr_trace_camera", "kerr_trace_camera_static", "kerr_get_stats",
@@ -130,7 +132,8 @@ def lib():
                      "kerr_surrogate_forward", "kerr_surrogate_grad", "kerr_surrogate_train",
                      "kerr_surrogate_render", "kerr_check_fp64_math",
                      "kerr_surrogate_forward_impl", "kerr_rk4_fixed",
-                     "kerr_trace_coordtime"):
+                     "kerr_trace_coordtime", "kerr_rk4_fixed_bl",
+                     "kerr_bl_camera_states"):
             getattr(L, name).restype = c.c_int
         _lib = L
     return _lib
@@ -508,17 +511,34 @@ LAYOUT_SOA, LAYOUT_AOS = 0, 1
 
 
 def kerr_rk4_fixed(a: float, state, nsteps: int, h: float, layout: int = LAYOUT_SOA,
-                   stream=None):
+                   stream=None, coords: str = "ks"):
     """Paper-mode fixed-step RK4 in place on a device tensor: float32 or
-    float64, shape (8, n) for LAYOUT_SOA or (n, 8) for LAYOUT_AOS."""
+    float64, shape (8, n) for LAYOUT_SOA or (n, 8) for LAYOUT_AOS; coords
+    "ks" (Cartesian Kerr-Schild, (x, k)) or "bl" (Boyer-Lindquist, (x, p))."""
     import torch
     if state.dtype not in (torch.float32, torch.float64):
         raise KerrError("state must be float32 or float64")
+    if coords not in ("ks", "bl"):
+        raise KerrError("coords must be 'ks' or 'bl'")
     n = int(state.shape[1] if layout == LAYOUT_SOA else state.shape[0])
-    _check(lib().kerr_rk4_fixed(float(a), int(state.dtype == torch.float64), int(layout),
-                                _ptr(state), n, int(nsteps), float(h),
-                                _stream_ptr(stream, state)), "kerr_rk4_fixed")
+    fn = lib().kerr_rk4_fixed if coords == "ks" else lib().kerr_rk4_fixed_bl
+    _check(fn(float(a), int(state.dtype == torch.float64), int(layout), _ptr(state), n,
+              int(nsteps), float(h), _stream_ptr(stream, state)), "kerr_rk4_fixed")
     return state
+
+
+def kerr_bl_camera_states(cam: Camera, dtype=None, layout: int = LAYOUT_SOA, device="cuda",
+                          stream=None):
+    """BL start states (t, r, th, ph, p_t, p_r, p_th, p_ph) of a camera's rays."""
+    import torch
+    dtype = dtype or torch.float64
+    n = cam.nx * cam.ny
+    shape = (8, n) if layout == LAYOUT_SOA else (n, 8)
+    st = torch.empty(shape, dtype=dtype, device=device)
+    _check(lib().kerr_bl_camera_states(ctypes.byref(cam), int(dtype == torch.float64),
+                                       int(layout), _ptr(st), _stream_ptr(stream, st)),
+           "kerr_bl_camera_states")
+    return st
 
 
 @dataclass

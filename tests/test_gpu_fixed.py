@@ -74,3 +74,65 @@ def test_fixed_rk4_arguments():
         K.kerr_rk4_fixed(A, st, 1, H, layout=7)
     with pytest.raises(K.KerrError):
         K.kerr_rk4_fixed(A, torch.zeros((8, 4), dtype=torch.float64), 1, H)   # host memory
+
+
+# ---------------------------------------------------------------------------
+# Boyer-Lindquist paper mode (Hamiltonian form) against the oracle's BL
+# integration (Christoffel form of eq. 1, complex-step derivatives)
+# ---------------------------------------------------------------------------
+import closed_forms as Cf  # noqa: E402
+
+
+def bl_states(a, n=24, seed=5):
+    """Null BL states at r = 25 M heading inward at various angles: oracle
+    form (x, k) and the GPU's (x, p = g k)."""
+    rng = np.random.default_rng(seed)
+    ys, ps = [], []
+    for _ in range(n):
+        r, th, ph = 25.0, rng.uniform(0.6, 2.5), rng.uniform(0, 2 * np.pi)
+        g = Cf.bl_metric(r, th, a)
+        kr, kth, kph = -1.0, rng.uniform(-0.02, 0.02), rng.uniform(-0.01, 0.01)
+        # null condition for k^t (past-directed root not needed: k^t > 0)
+        A = g[0, 0]
+        B = 2 * g[0, 3] * kph
+        Cc = g[1, 1] * kr ** 2 + g[2, 2] * kth ** 2 + g[3, 3] * kph ** 2
+        kt = (-B - np.sqrt(B * B - 4 * A * Cc)) / (2 * A)
+        k = np.array([kt, kr, kth, kph])
+        y = np.array([0.0, r, th, ph, *k])
+        ys.append(y)
+        ps.append(np.array([0.0, r, th, ph, *(g @ k)]))
+    return np.array(ys), np.array(ps)
+
+
+@pytest.mark.parametrize("layout", [K.LAYOUT_SOA, K.LAYOUT_AOS])
+def test_fixed_rk4_bl_matches_oracle(layout):
+    a, h, nsteps = 0.9, 0.02, 1000                      # 20 M of path toward the hole
+    ys, ps = bl_states(a)
+    ref = np.stack([O.rk4_fixed(a, y, h, nsteps, stride=nsteps, coords=O.BL)[-1] for y in ys])
+    st = torch.tensor(ps.T if layout == K.LAYOUT_SOA else ps, dtype=torch.float64,
+                      device=DEV).contiguous()
+    K.kerr_rk4_fixed(a, st, nsteps, h, layout=layout, coords="bl")
+    torch.cuda.synchronize()
+    got = st.cpu().numpy()
+    got = got.T if layout == K.LAYOUT_SOA else got
+    # positions: the same geodesic through different formulations of the same
+    # equations; fixed-step truncation differs at O(h^4)
+    e = np.abs(got[:, :4] - ref[:, :4]) / (1 + np.abs(ref[:, :4]))
+    assert e.max() < 1e-8, e.max()
+    # momenta: p = g k at the end point
+    for j in range(len(ys)):
+        g = Cf.bl_metric(ref[j, 1], ref[j, 2], a)
+        np.testing.assert_allclose(got[j, 4:], g @ ref[j, 4:], rtol=1e-7, atol=1e-9)
+    # p_t and p_phi are constants of the Hamiltonian form
+    assert np.all(got[:, 4] == ps[:, 4]) and np.all(got[:, 7] == ps[:, 7])
+
+
+def test_bl_camera_states_are_null_and_inward():
+    a = 0.9
+    cam = K.camera(a, np.radians(60.0), 1024.0, 20.0, 16, 16)
+    st = K.kerr_bl_camera_states(cam).cpu().numpy().T       # (n, 8)
+    assert np.all(st[:, 5] < 0)                                # p_r < 0: moving inward
+    for y in st[::17]:
+        g = Cf.bl_metric(y[1], y[2], a)
+        p = y[4:]
+        assert abs(p @ np.linalg.solve(g, p)) < 1e-9         # g^{ab} p_a p_b = 0
