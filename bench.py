@@ -322,6 +322,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- learned surrogate: train on integrator rays, render with fallback
     if rank == 0 and not args.skip_surrogate:
         result["surrogate"] = run_surrogate(args, K, W, dev, stream)
+        result["_surr_img"] = result["surrogate"].pop("_img0")
 
     # ---- the other workloads: 64 uneven images in one launch, 2^20 particles
     if rank == 0 and not args.skip_batch:
@@ -336,11 +337,13 @@ def run_ours(args, rank, world, local_rank):
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.skip_cpu:
         result["cpu_baseline"], acc = cpu_baseline(spec, W, out, result.get("_fp64_out"),
-                                                   result.get("_nz_out"))
+                                                   result.get("_nz_out"),
+                                                   result.get("_surr_img"))
         if acc:
             result["accuracy"] = acc
     result.pop("_fp64_out", None)
     result.pop("_nz_out", None)
+    result.pop("_surr_img", None)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist is not None:
@@ -391,6 +394,7 @@ def run_surrogate(args, K, W, dev, stream):
     n_tot = n_fb = 0
     dis = dis_n = 0
     errs = {k: [] for k in ("r1", "phi1", "r2", "phi2", "g1")}
+    img0 = None
     for cs in W.surrogate_eval_cameras():
         cam = K.camera(*cs.as_tuple())
         n = cs.n
@@ -425,6 +429,8 @@ def run_surrogate(args, K, W, dev, stream):
             else:
                 e = (a_[ok] - b_[ok]).abs()
             errs[key].append(e.double().cpu().numpy())
+        if img0 is None:      # kept for the CPU leg's comparison with the oracle
+            img0 = {"spec": cs, "out": out.cpu().numpy(), "fallback": fb.cpu().numpy()}
         del out, fb, ref, ref32
     err = {}
     for key, v in errs.items():
@@ -438,7 +444,7 @@ def run_surrogate(args, K, W, dev, stream):
     v_sur = n_tot / t_sur
     v_int = n_tot / t_int
     ep = args.surrogate_epochs
-    return {"value": round(v_sur, 1), "unit": UNIT,
+    return {"_img0": img0, "value": round(v_sur, 1), "unit": UNIT,
             "workload": "8 images 2048x2048 (seeded a ~ U[0,0.998], i ~ U[5,85] deg), "
                         "r_obs 1000M, +-25M; fallback: p in [0.05,0.95] or within 0.5M of "
                         "the critical curve; integrator FP32+Kahan tol 1e-6",
@@ -601,7 +607,7 @@ def run_paper_mode(K, dev, stream):
             "best": summary, "all": rows}
 
 
-def cpu_baseline(spec, W, out_gpu, out64, out_nz=None):
+def cpu_baseline(spec, W, out_gpu, out64, out_nz=None, surr_img=None):
     """Time the FP64 CPU oracle on a bounded seeded sample of the same image
     (all host cores), and use that same sample to state the GPU path's
     end-point error against it."""
@@ -628,6 +634,11 @@ def cpu_baseline(spec, W, out_gpu, out64, out_nz=None):
     base = {"value": round(n_done / dt, 1), "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"{n_done} rays of the 1024x1024 image (seeded 4096-ray subset plus "
                       f"{extra} seeded random rays), FP64 oracle, tol 1e-6, {dt:.1f} s"}
+    # one core, on the first 512 rays of the seeded subset
+    t1 = time.perf_counter()
+    O.trace(spec.a, y0[:512], oo, nthreads=1)
+    base["single_core"] = {"value": round(512 / (time.perf_counter() - t1), 1), "unit": UNIT,
+                           "sample": "first 512 rays of the seeded 4096-ray subset"}
     # accuracy of the GPU paths on the seeded subset
     acc = None
     try:
@@ -656,7 +667,39 @@ def cpu_baseline(spec, W, out_gpu, out64, out_nz=None):
             acc["fp32_no_zone"] = errs(out_nz)
     except Exception as exc:  # accuracy is a report, not the measurement
         acc = {"error": repr(exc)}
+    if surr_img is not None:
+        try:
+            acc = acc or {}
+            acc["surrogate"] = surrogate_vs_oracle(O, W, surr_img, nthreads)
+        except Exception as exc:
+            acc["surrogate"] = {"error": repr(exc)}
     return base, acc
+
+
+def surrogate_vs_oracle(O, W, img, nthreads):
+    """The surrogate's answers on a seeded 4096-pixel subset of the first
+    evaluation image against the FP64 oracle (tol 1e-6, crossings on): capture
+    disagreement and label errors on the pixels the network answered."""
+    cs, out, fb = img["spec"], img["out"], img["fallback"]
+    idx = W.camera_subset(cs, 4096, seed=1709)
+    y0 = O.camera_ic(cs.a, cs.incl, cs.r_obs, cs.half_width, cs.nx, cs.ny, idx)
+    ref = O.trace(cs.a, y0, O.Opts(tol=1e-6), nthreads=nthreads, crossings=True)
+    net = fb[idx] == 0
+    o = out[:, idx]
+    res = {"sample": int(len(idx)), "network_pixels": int(net.sum()),
+           "capture_disagreement": float(np.mean((o[0][net] >= 0.5) != (ref.status[net] == 2)))}
+    for j, key in enumerate(("r1", "phi1", "r2", "phi2", "g1")):
+        a_, b_ = o[1 + j], ref.cross[:, j]
+        ok = net & ~np.isnan(a_) & ~np.isnan(b_)
+        if key.startswith("phi"):
+            e = np.abs(np.remainder(a_[ok] - b_[ok] + np.pi, 2 * np.pi) - np.pi)
+        elif key.startswith("r"):
+            e = np.abs(a_[ok] - b_[ok]) / b_[ok]
+        else:
+            e = np.abs(a_[ok] - b_[ok])
+        res[key] = {"n": int(ok.sum()), "median": float(np.median(e)) if e.size else None,
+                    "p99": float(np.percentile(e, 99)) if e.size else None}
+    return res
 
 
 # ---------------------------------------------------------------------------

@@ -727,3 +727,27 @@ def test_coordtime_terminations():
     m = O.trace_coordtime(a, 0.0, [[30.0, 0.0, 0.0, 0.0, 0.1, 0.0]], 1e6,
                           O.Opts(tol=1e-9, max_steps=3, r_escape=-1.0))
     assert m.status[0] == O.MAXSTEPS and m.attempts[0] == 3
+
+
+def test_redshift_label_sign_convention():
+    """g1 = 1 / (u^t (1 - Omega xi)) with xi = L_z / E of the ray, for a
+    prograde Keplerian emitter (a = 0: u^t = 1/sqrt(1 - 3/r), Omega = r^{-3/2}):
+    photons moving with the disk's rotation (xi > 0) are blueshifted relative
+    to those moving against it.  Checked at the oracle's own first crossing
+    radius, with xi from the start state's constants."""
+    a, incl, r_obs = 0.0, np.radians(60.0), 1000.0
+    pts = [(12.0, 4.0), (-12.0, 4.0), (9.0, -6.0), (-9.0, -6.0)]
+    y0 = np.stack([camera_ic_at(a, incl, r_obs, al, be) for al, be in pts])
+    res = O.trace(a, y0, O.Opts(tol=1e-10), crossings=True)
+    gs = []
+    for j in range(len(pts)):
+        E, Lz, Q, u2 = O.constants(a, y0[j])
+        xi = Lz / E
+        r1 = res.cross[j, 0]
+        assert r1 > 6.0
+        want = np.sqrt(1 - 3 / r1) / (1 - r1 ** -1.5 * xi)
+        assert abs(res.cross[j, 4] - want) < 1e-7, (j, res.cross[j, 4], want)
+        gs.append((xi, res.cross[j, 4]))
+    # the two mirror-image pairs: the sign of xi decides blue- or redshift
+    for (x1, g1), (x2, g2) in ((gs[0], gs[1]), (gs[2], gs[3])):
+        assert np.sign(x1) == -np.sign(x2) and (g1 - g2) * (x1 - x2) > 0
