@@ -389,6 +389,31 @@ int kerr_trace_coordtime(kerr_ctx *ctx, const double *x0, const double *v0,
                          const double *t_end, int64_t n, const kerr_opts *opts, double *x_out,
                          double *v_out, int32_t *status, int32_t *steps, void *stream);
 
+/* kerr_trace_rays on the FP64 path (opts->prec must be KERR_FP64) that also
+ * stores the solution: for geodesic i, records (lambda, t, x, y, z, k^t, k^x,
+ * k^y, k^z) of the start state and after every accepted step (the last one
+ * on the termination surface) into traj[i][0 .. cap-1][9] (device memory,
+ * n * cap * 9 doubles; lambda counted from 0), with the number stored in
+ * traj_count[i] (device; recording stops at cap).  Other arguments and
+ * outputs as kerr_trace_rays (no diagnostics or crossings). */
+int kerr_trace_rays_dense(kerr_ctx *ctx, const double *x0, const double *k0, int64_t n,
+                          const kerr_opts *opts, int32_t cap, double *traj, int32_t *traj_count,
+                          double *x_out, double *k_out, int32_t *status, int32_t *steps,
+                          void *stream);
+
+/* Root finding on a stored solution (Sec. 2.2, the second way of matching a
+ * target time): for each geodesic, the first stored step across which t
+ * passes t_target[i]; on it the state is the cubic Hermite interpolant of
+ * both ends and their derivatives (dx/dlambda = k, dk/dlambda from eqs.
+ * opt0/opti at spin a), and t(lambda) = t_target[i] is solved on it by a
+ * bracketed Newton iteration (|t - t_target| <= 1e-13 (1 + |t_target|)).
+ * Outputs (device): y_out [8][n] = (t, x, y, z, k^t, k^x, k^y, k^z),
+ * lam_out [n], found [n] (1, or 0 with NaN outputs when the stored part of
+ * the solution does not reach the target).  Asynchronous on `stream`. */
+int kerr_dense_find_time(double a, const double *traj, int32_t cap, const int32_t *traj_count,
+                         int64_t n, const double *t_target, double *y_out, double *lam_out,
+                         int32_t *found, void *stream);
+
 /* Paper-mode integration (Sec. 3, the timing setting of Sec. 4.2 and
  * Tables 2-3): every geodesic of `state` takes exactly nsteps classic RK4
  * steps of length h in place, with the right-hand side of eqs. opt0/opti,

@@ -18,7 +18,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libkerr.so")
 UNITS = ["kerr_api.cu", "kerr_trace_f32.cu", "kerr_trace_f32b.cu", "kerr_trace_zone.cu",
          "kerr_trace_f64.cu", "kerr_static.cu", "kerr_surrogate.cu", "kerr_mlp_tc.cu",
-         "kerr_fixed.cu", "kerr_coordtime.cu"]
+         "kerr_fixed.cu", "kerr_coordtime.cu",
+         "kerr_dense.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

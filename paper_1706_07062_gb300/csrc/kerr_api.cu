@@ -359,6 +359,9 @@ struct TraceExtra {
     double r_obs = 0.0;
     const int64_t *index = nullptr;                 // device
     const unsigned long long *n_dev = nullptr;      // device
+    double *traj = nullptr;                         // device, FP64 path: stored solution
+    int32_t traj_cap = 0;
+    int32_t *traj_count = nullptr;                  // device
 };
 
 static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k0,
@@ -463,6 +466,9 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
     P.r_obs = X.r_obs;
     P.index = X.index;
     P.n_dev = X.n_dev;
+    P.traj = X.traj;
+    P.traj_cap = X.traj_cap;
+    P.traj_count = X.traj_count;
     if (mode == MODE_POINTS && !is_device_ptr(X.points))
         st.push_back({X.points, (void **)&P.points, 4 * nn * sizeof(double), true, 0});
     if (mode == MODE_RAYS || mode == MODE_PARTICLES) {
@@ -557,6 +563,27 @@ extern "C" int kerr_trace_rays(kerr_ctx *c, const double *x0, const double *k0, 
 {
     return trace_common(c, MODE_RAYS, x0, k0, nullptr, n, nullptr, 0, o, x_out, k_out, status,
                         steps, diag, cross, stream);
+}
+
+extern "C" int kerr_trace_rays_dense(kerr_ctx *c, const double *x0, const double *k0, int64_t n,
+                                     const kerr_opts *o, int32_t cap, double *traj,
+                                     int32_t *traj_count, double *x_out, double *k_out,
+                                     int32_t *status, int32_t *steps, void *stream)
+{
+    if (!o || o->prec != KERR_FP64)
+        return fail(KERR_EINVAL, "kerr_trace_rays_dense: the stored solution needs the FP64 path");
+    if (cap < 1)
+        return fail(KERR_EINVAL, "kerr_trace_rays_dense: cap = %d < 1", cap);
+    if (n > 0 && (!traj || !traj_count))
+        return fail(KERR_EINVAL, "kerr_trace_rays_dense: NULL stored-solution buffer");
+    if (n > 0 && (!is_device_ptr(traj) || !is_device_ptr(traj_count)))
+        return fail(KERR_EINVAL, "kerr_trace_rays_dense: stored-solution buffers must be device memory");
+    TraceExtra X;
+    X.traj = traj;
+    X.traj_cap = cap;
+    X.traj_count = traj_count;
+    return trace_common(c, MODE_RAYS, x0, k0, nullptr, n, nullptr, 0, o, x_out, k_out, status,
+                        steps, nullptr, nullptr, stream, X);
 }
 
 extern "C" int kerr_trace_particles(kerr_ctx *c, const double *x0, const double *v0,

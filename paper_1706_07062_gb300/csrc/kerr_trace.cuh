@@ -117,6 +117,9 @@ struct TraceParams {
     unsigned long long *zcount; // entries appended, zero at launch
     unsigned long long *zhead;  // zone-phase work-queue counter, zero at launch
     unsigned long long *zpush;  // zone phase: re-queued geodesics, zero at launch
+    double *traj;               // FP64 path: stored solution [n][traj_cap][9] (lambda, y)
+    int32_t traj_cap;           // records per geodesic (the start state is the first)
+    int32_t *traj_count;        // [n] records stored
 };
 
 // Coordinate-time integration (Sec. 2.2, eq. geo_t): launch parameters.
@@ -570,7 +573,8 @@ template <> __device__ __forceinline__ dfloat from_d<dfloat>(double d) { return 
 template <bool KAHAN, typename T, bool FAST_FACTOR = false, int RM = RHS_INLINE>
 __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &P, int64_t id,
                                          const T tol, T y[8], T c[8], T &h, T &rn,
-                                         uint32_t &nrhs, uint32_t &nacc, int &since_renorm)
+                                         uint32_t &nrhs, uint32_t &nacc, int &since_renorm,
+                                         T *h_taken = nullptr)
 {
     const T a = RC<T>::a(rc);
     const T a2 = a * a;
@@ -666,6 +670,8 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
         y[i] = yn[i];
         c[i] = cn[i];
     }
+    if (h_taken)
+        *h_taken = h_used;
     if (st != ST_NONE)
         return st;
     if (P.renorm_every > 0 && ++since_renorm >= P.renorm_every) {
@@ -1105,6 +1111,21 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f64_kernel(const TraceParam
     Counters C;
     const unsigned long long t_start = global_ns();
     uint32_t iter = 0;
+    // stored solution (dense output): affine parameter and state after every
+    // accepted step, up to traj_cap records per geodesic
+    double lam = 0.0;
+    int32_t ntraj = 0;
+    auto record = [&](double l, const double s[8]) {
+        if (P.traj && ntraj < P.traj_cap) {
+            double *dst = P.traj + ((size_t)id * P.traj_cap + ntraj) * 9;
+            dst[0] = l;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                dst[1 + i] = s[i];
+            ++ntraj;
+            P.traj_count[id] = ntraj;
+        }
+    };
     for (;;) {
         const unsigned need = __ballot_sync(FULL, !has);
         if (need && !drained) {
@@ -1115,6 +1136,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f64_kernel(const TraceParam
                 const unsigned long long my = base + __popc(need & lt_mask);
                 if (my < n_items) {
                     id = (int64_t)my;
+                    if (P.traj)
+                        P.traj_count[id] = 0;
                     const int st0 = init_geodesic(P, id, y, rc);
                     clear_cross(P, id);
                     ++C.geo;
@@ -1129,6 +1152,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f64_kernel(const TraceParam
                         h = P.h0;
                         nsteps = 0;
                         since_renorm = 0;
+                        lam = 0.0;
+                        ntraj = 0;
+                        record(lam, y);
                         has = true;
                     }
                 }
@@ -1150,11 +1176,16 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f64_kernel(const TraceParam
                 ++C.att;
                 ++C.att64;
                 uint32_t r = 0;
+                double taken = 0.0;
                 // right-hand sides out of line: one copy keeps the kernel in
                 // the instruction cache (same arithmetic as inline)
                 st = step_once<false, double, false, RHS_CALL>(rc, P, id, P.tol, y, c, h, rnow,
-                                                               r, C.acc, since_renorm);
+                                                               r, C.acc, since_renorm, &taken);
                 C.rhs64 += r;
+                if (taken != 0.0) {
+                    lam += taken;
+                    record(lam, y);
+                }
             }
             if (st != ST_NONE) {
                 write_out(P, id, y, st, nsteps, rc.a, rc.xi);

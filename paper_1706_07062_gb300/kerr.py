@@ -121,6 +121,9 @@ def lib():
                                            vp]
         L.kerr_rk4_fixed_bl.argtypes = [c.c_double, i32, i32, vp, i64, i32, c.c_double, vp]
         L.kerr_bl_camera_states.argtypes = [c.POINTER(Camera), i32, i32, vp, vp]
+        L.kerr_trace_rays_dense.argtypes = [vp, vp, vp, i64, c.POINTER(Opts), i32, vp, vp, vp,
+                                            vp, vp, vp, vp]
+        L.kerr_dense_find_time.argtypes = [c.c_double, vp, i32, vp, i64, vp, vp, vp, vp, vp]
         L.kerr_last_error.restype = c.c_char_p
         for name in ("kerr_init", "kerr_destroy", "kerr_trace_rays", "kerr_trace_particles",
                      "kerr_trace_camera", "kerr_trace_camera_static", "kerr_get_stats",
@@ -133,7 +136,8 @@ def lib():
                      "kerr_surrogate_render", "kerr_check_fp64_math",
                      "kerr_surrogate_forward_impl", "kerr_rk4_fixed",
                      "kerr_trace_coordtime", "kerr_rk4_fixed_bl",
-                     "kerr_bl_camera_states"):
+                     "kerr_bl_camera_states", "kerr_trace_rays_dense",
+                     "kerr_dense_find_time"):
             getattr(L, name).restype = c.c_int
         _lib = L
     return _lib
@@ -568,3 +572,35 @@ def kerr_trace_coordtime(ctx: Context, x0, v0, t_end=None, opts: Opts | None = N
                                       _ptr(out.status), _ptr(out.steps),
                                       _stream_ptr(stream, x0)), "kerr_trace_coordtime")
     return out
+
+
+def kerr_trace_rays_dense(ctx: Context, x0, k0, cap: int, opts: Opts | None = None,
+                          stream=None):
+    """FP64 trace of device tensors x0, k0 (4, n) that also stores the solution.
+    Returns (TraceOut, traj (n, cap, 9), traj_count (n,))."""
+    import torch
+    n = int(x0.shape[1])
+    opts = opts or default_opts(prec=FP64)
+    dev = x0.device
+    out = alloc_out(n, dev, diag=False)
+    traj = torch.empty((n, cap, 9), dtype=torch.float64, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev)
+    _check(lib().kerr_trace_rays_dense(ctx.handle, _ptr(x0), _ptr(k0), n, ctypes.byref(opts),
+                                       int(cap), _ptr(traj), _ptr(cnt), _ptr(out.x), _ptr(out.k),
+                                       _ptr(out.status), _ptr(out.steps),
+                                       _stream_ptr(stream, x0)), "kerr_trace_rays_dense")
+    return out, traj, cnt
+
+
+def kerr_dense_find_time(a: float, traj, traj_count, t_target, stream=None):
+    """(y (8, n), lam (n,), found (n,)) at t = t_target on stored solutions."""
+    import torch
+    n, cap = int(traj.shape[0]), int(traj.shape[1])
+    dev = traj.device
+    y = torch.empty((8, n), dtype=torch.float64, device=dev)
+    lam = torch.empty(n, dtype=torch.float64, device=dev)
+    found = torch.empty(n, dtype=torch.int32, device=dev)
+    _check(lib().kerr_dense_find_time(float(a), _ptr(traj), cap, _ptr(traj_count), n,
+                                      _ptr(t_target), _ptr(y), _ptr(lam), _ptr(found),
+                                      _stream_ptr(stream, traj)), "kerr_dense_find_time")
+    return y, lam, found
