@@ -133,6 +133,26 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def reduce_step_time(ms: float, device=None) -> float:
+    """The job's time per step: the maximum over ranks when a process group
+    is up (one rank per GPU; replicas, so this is the only collective), else
+    the local time.  `device`: where the reduction tensor lives (the rank's
+    GPU for NCCL, the CPU for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job units per second: every rank processes its own units
+    (weak scaling) in at most ms_per_step."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -197,12 +217,8 @@ def run_ours(args, rank, world, local_rank):
     t_wall = time.perf_counter() - t_wall0
     clocks = sampler.stop() if sampler else None
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(step_ms) / len(step_ms)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n / (ms * 1e-3)
+    ms = reduce_step_time(sum(step_ms) / len(step_ms), dev if dist is not None else None)
+    value = job_throughput(n, world, ms)
     stats = K.kerr_get_stats(ctx)
 
     # ---- rooflines (algorithmic FLOPs from the counted right-hand sides)
