@@ -55,6 +55,19 @@ struct Layout {
 };
 const Layout kL;
 
+struct WOffsets {
+    int64_t w[kLayers];
+    int64_t end;
+};
+WOffsets woffsets()
+{
+    WOffsets o;
+    for (int l = 0; l < kLayers; ++l)
+        o.w[l] = (int64_t)kL.w[l];
+    o.end = (int64_t)kL.total;
+    return o;
+}
+
 // ---------------------------------------------------------------------------
 // elementwise kernels
 // ---------------------------------------------------------------------------
@@ -150,6 +163,49 @@ __global__ void colsum_kernel(const bf16 *__restrict__ X, int64_t n, int w, floa
 }
 
 // Adam on the whole parameter vector; refreshes the bf16 copy of each weight.
+// dst [cols][ld] = src [rows][cols] transposed (bf16); columns rows .. ld-1
+// of dst are zero (ld a multiple of 8, so that the GEMM's 16-byte loads of
+// dst rows stay inside them).  32 x 32 tiles through shared memory.
+__global__ void transpose_bf16_kernel(const bf16 *__restrict__ src, int64_t rows, int cols,
+                                      int64_t ld, bf16 *__restrict__ dst)
+{
+    __shared__ bf16 tile[32][34];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    for (int j = ty; j < 32; j += 8) {
+        const int64_t r = r0 + j;
+        const int c = c0 + tx;
+        tile[j][tx] = (r < rows && c < cols) ? src[r * cols + c] : __float2bfloat16(0.0f);
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        const int c = c0 + j;
+        const int64_t r = r0 + tx;
+        if (c < cols && r < ld)
+            dst[(int64_t)c * ld + r] = tile[tx][j];
+    }
+}
+
+// Transposed bf16 copy of every weight matrix: layer l's W [out][in] at the
+// same offset as [in][out] (the B operand of the input-gradient GEMMs).
+__global__ void transpose_weights_kernel(const bf16 *__restrict__ wbf, bf16 *__restrict__ wt,
+                                         WOffsets o)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < o.end;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int l = 0;
+        while (l + 1 < kLayers && i >= o.w[l + 1])
+            ++l;
+        const int64_t j = i - o.w[l];
+        if (j >= (int64_t)out_dim(l) * in_dim(l))
+            continue;                               // bias entries
+        const int K = in_dim(l), N = out_dim(l);
+        const int nrow = (int)(j / K), k = (int)(j % K);
+        wt[o.w[l] + (int64_t)k * N + nrow] = wbf[i];
+    }
+}
+
 __global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g,
                             float *__restrict__ m, float *__restrict__ v, bf16 *__restrict__ wbf,
                             int64_t n, float lr, float b1, float b2, float c1, float c2, float eps)
@@ -238,6 +294,9 @@ struct kerr_surrogate {
     bf16 *dOut = nullptr;         // [cap][64]
     float *dA = nullptr;          // [cap][256]
     bf16 *dZ = nullptr;           // [cap][256]
+    bf16 *T1 = nullptr, *T2 = nullptr;   // transposed batch operands [256][ldT]
+    int64_t ldT = 0;
+    bf16 *wbfT = nullptr;         // transposed bf16 weights (same offsets)
     float *loss = nullptr;        // [1]
     RenderScratch *render = nullptr;   // kerr_surrogate_render's scratch
     bf16 *wpk = nullptr;          // weights in the tensor-core operand layout
@@ -255,6 +314,10 @@ static void free_batch(kerr_surrogate *s)
     cudaFree(s->dOut);
     cudaFree(s->dA);
     cudaFree(s->dZ);
+    cudaFree(s->T1);
+    cudaFree(s->T2);
+    s->T1 = s->T2 = nullptr;
+    s->ldT = 0;
     s->out = s->dA = nullptr;
     s->dOut = s->dZ = nullptr;
     s->cap = 0;
@@ -279,6 +342,13 @@ static int ensure_batch(kerr_surrogate *s, int64_t rows, bool training)
             e = cudaMalloc(&s->dA, (size_t)rows * kHidden * sizeof(float));
         if (e == cudaSuccess)
             e = cudaMalloc(&s->dZ, (size_t)rows * kHidden * sizeof(bf16));
+        const int64_t ldT = (rows + 7) / 8 * 8;
+        if (e == cudaSuccess)
+            e = cudaMalloc(&s->T1, (size_t)kHidden * ldT * sizeof(bf16));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&s->T2, (size_t)kHidden * ldT * sizeof(bf16));
+        if (e == cudaSuccess)
+            s->ldT = ldT;
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -302,6 +372,7 @@ extern "C" int kerr_surrogate_destroy(kerr_surrogate *s)
     cudaFree(s->m);
     cudaFree(s->v);
     cudaFree(s->wbf);
+    cudaFree(s->wbfT);
     cudaFree(s->loss);
     cudaFree(s->wpk);
     cudaFree(s->tc_err);
@@ -339,6 +410,8 @@ extern "C" int kerr_surrogate_create(const float *init, kerr_surrogate **out)
     if (e == cudaSuccess)
         e = cudaMalloc(&s->wbf, n * sizeof(bf16));
     if (e == cudaSuccess)
+        e = cudaMalloc(&s->wbfT, n * sizeof(bf16));
+    if (e == cudaSuccess)
         e = cudaMalloc(&s->loss, sizeof(float));
     if (e == cudaSuccess)
         e = cudaMalloc(&s->wpk, packed_weight_elems() * sizeof(bf16));
@@ -358,6 +431,7 @@ extern "C" int kerr_surrogate_create(const float *init, kerr_surrogate **out)
         e = cudaMemset(s->v, 0, n * sizeof(float));
     if (e == cudaSuccess) {
         to_bf16_kernel<<<grid_1d(n), 256>>>(s->w, s->wbf, n);
+        transpose_weights_kernel<<<grid_1d(n), 256>>>(s->wbf, s->wbfT, woffsets());
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)
@@ -426,48 +500,62 @@ static cudaError_t backward_rows(kerr_surrogate *s, int64_t rows, cudaStream_t s
 {
     cudaError_t e = cudaMemsetAsync(s->g, 0, kL.total * sizeof(float), st);
     const int R = (int)rows;
+    const int LT = (int)s->ldT;
     const int ygrid = (int)std::min<int64_t>(rows, 512);
-    // output layer
-    {
-        const int l = kLayers - 1, K = in_dim(l), N = out_dim(l);
+    const dim3 tb(32, 8);
+    // dst [cols][ldT] = src [rows][cols]^T: batch rows become the contiguous
+    // contraction dimension of the weight-gradient GEMMs
+    auto transpose = [&](const bf16 *src, int cols, bf16 *dst) {
+        transpose_bf16_kernel<<<dim3((unsigned)((LT + 31) / 32), (unsigned)((cols + 31) / 32)),
+                                tb, 0, st>>>(src, rows, cols, LT, dst);
+        return cudaGetLastError();
+    };
+    // dW_l [N][K] += D^T A_l over the batch, D = dOut or dZ ([R][N])
+    auto weight_grad = [&](const bf16 *D, int l) {
+        const int K = in_dim(l), N = out_dim(l);
+        cudaError_t r = transpose(D, N, s->T1);
+        if (r == cudaSuccess)
+            r = transpose(s->A[l], K, s->T2);
         EpiArgs ea;
         std::memset(&ea, 0, sizeof ea);
         ea.C = s->g + kL.w[l];
         ea.ldc = K;
-        if (e == cudaSuccess)   // dW_l [N][K] += dOut^T A_l
-            e = gemm<true, true, EPI_F32_ATOMIC>(s->dOut, N, s->A[l], K, N, K, R, ea, st,
-                                                 wsplits(rows));
+        if (r == cudaSuccess)
+            r = gemm<false, false, EPI_F32_ATOMIC>(s->T1, LT, s->T2, LT, N, K, LT, ea, st,
+                                                   wsplits(rows));
+        return r;
+    };
+    // dA [R][K] = D W_l, with W_l^T [K][N] as the B operand
+    auto input_grad = [&](const bf16 *D, int l) {
+        const int K = in_dim(l), N = out_dim(l);
+        EpiArgs eb;
+        std::memset(&eb, 0, sizeof eb);
+        eb.C = s->dA;
+        eb.ldc = K;
+        return gemm<false, false, EPI_F32>(D, N, s->wbfT + kL.w[l], N, R, K, N, eb, st);
+    };
+    // output layer
+    {
+        const int l = kLayers - 1, N = out_dim(l);
+        if (e == cudaSuccess)
+            e = weight_grad(s->dOut, l);
         if (e == cudaSuccess) {
             colsum_kernel<<<dim3((N + 127) / 128, ygrid), 128, 0, st>>>(s->dOut, rows, N,
                                                                         s->g + kL.b[l]);
             e = cudaGetLastError();
         }
-        EpiArgs eb;
-        std::memset(&eb, 0, sizeof eb);
-        eb.C = s->dA;
-        eb.ldc = K;
-        if (e == cudaSuccess)   // dA_l [R][K] = dOut W_l
-            e = gemm<false, true, EPI_F32>(s->dOut, N, s->wbf + kL.w[l], K, R, K, N, eb, st);
+        if (e == cudaSuccess)
+            e = input_grad(s->dOut, l);
     }
     for (int l = kLayers - 2; l >= 0 && e == cudaSuccess; --l) {
-        const int K = in_dim(l), N = out_dim(l);
+        const int N = out_dim(l);
         silu_back_kernel<<<dim3((N + 127) / 128, ygrid), 128, 0, st>>>(s->dA, s->Z[l], s->dZ, rows,
                                                                        N, s->g + kL.b[l]);
         e = cudaGetLastError();
-        EpiArgs ea;
-        std::memset(&ea, 0, sizeof ea);
-        ea.C = s->g + kL.w[l];
-        ea.ldc = K;
         if (e == cudaSuccess)
-            e = gemm<true, true, EPI_F32_ATOMIC>(s->dZ, N, s->A[l], K, N, K, R, ea, st,
-                                                 wsplits(rows));
-        if (l > 0 && e == cudaSuccess) {
-            EpiArgs eb;
-            std::memset(&eb, 0, sizeof eb);
-            eb.C = s->dA;
-            eb.ldc = K;
-            e = gemm<false, true, EPI_F32>(s->dZ, N, s->wbf + kL.w[l], K, R, K, N, eb, st);
-        }
+            e = weight_grad(s->dZ, l);
+        if (l > 0 && e == cudaSuccess)
+            e = input_grad(s->dZ, l);
     }
     return e;
 }
@@ -622,6 +710,8 @@ extern "C" int kerr_surrogate_train(kerr_surrogate *s, const float *in, const fl
                 const float c2 = (float)(1.0 / (1.0 - std::pow(b2, (double)s->step)));
                 adam_kernel<<<grid_1d(kL.total), 256, 0, st>>>(s->w, s->g, s->m, s->v, s->wbf,
                                                                kL.total, lr_k, b1, b2, c1, c2, eps);
+                transpose_weights_kernel<<<grid_1d(kL.total), 256, 0, st>>>(s->wbf, s->wbfT,
+                                                                            woffsets());
                 e = cudaGetLastError();
             }
             if (e != cudaSuccess) {
