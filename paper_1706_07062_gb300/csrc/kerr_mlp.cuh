@@ -68,15 +68,29 @@ __device__ __forceinline__ void mma_bf16_16x8x16(float d[4], const uint32_t a[4]
 // Tiles: 64 x 64 per block of 128 threads (2 x 2 warps of 32 x 32), K step 32.
 // Out-of-range rows/columns/k are read as zero and not written.  Split-K:
 // block z covers k in [z kchunk, (z + 1) kchunk) (kchunk a multiple of 32).
+// With both operands K-contiguous (K, lda, ldb multiples of 8) the tiles are
+// staged by 16-byte cp.async copies into a double buffer, so that the next
+// k-step's loads overlap this one's MMAs; transposed operands are staged
+// element by element.
 constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
 
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(128) gemm_bf16(const __nv_bfloat16 *__restrict__ A, int lda,
                                                  const __nv_bfloat16 *__restrict__ B, int ldb,
                                                  int M, int N, int K, int kchunk, EpiArgs e)
 {
-    __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
-    __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];
+    constexpr bool ASYNC = !TA && !TB;
+    constexpr int NBUF = ASYNC ? 2 : 1;
+    __shared__ __align__(16) __nv_bfloat16 As[NBUF][GBM][GBK + GPAD];
+    __shared__ __align__(16) __nv_bfloat16 Bs[NBUF][GBN][GBK + GPAD];
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t = lane & 3;
@@ -95,58 +109,41 @@ __global__ void __launch_bounds__(128) gemm_bf16(const __nv_bfloat16 *__restrict
 
     const int kb = blockIdx.z * kchunk;
     const int ke = min(K, kb + kchunk);
-    for (int k0 = kb; k0 < ke; k0 += GBK) {
-        // ---- stage the A and B tiles (canonical [row][k] layout in shared)
-        if (!TA) {
-            // 64 rows x 32 k = 256 chunks of 8 bf16 (16 B); K, lda multiples of 8
-            for (int c = tid; c < GBM * GBK / 8; c += 128) {
-                const int m = c / (GBK / 8), kc = (c % (GBK / 8)) * 8;
-                const int gm = m0 + m, gk = k0 + kc;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (gm < M && gk < ke)
-                    v = *reinterpret_cast<const uint4 *>(A + (size_t)gm * lda + gk);
-                *reinterpret_cast<uint4 *>(&As[m][kc]) = v;
-            }
-        } else {
-            for (int i = tid; i < GBM * GBK; i += 128) {
-                const int k = i / GBM, m = i % GBM;   // consecutive threads: consecutive m
-                const int gm = m0 + m, gk = k0 + k;
-                As[m][k] = (gm < M && gk < ke) ? A[(size_t)gk * lda + gm] : zero;
-            }
+
+    // 16-byte asynchronous staging of one k-tile into buffer `buf`
+    auto stage_async = [&](int k0, int buf) {
+        for (int c = tid; c < GBM * GBK / 8; c += 128) {
+            const int m = c / (GBK / 8), kc = (c % (GBK / 8)) * 8;
+            const int gm = m0 + m, gk = k0 + kc;
+            const bool ok = gm < M && gk < ke;
+            cp_async16(&As[buf][m][kc], ok ? A + (size_t)gm * lda + gk : A, ok);
         }
-        if (!TB) {
-            for (int c = tid; c < GBN * GBK / 8; c += 128) {
-                const int n = c / (GBK / 8), kc = (c % (GBK / 8)) * 8;
-                const int gn = n0 + n, gk = k0 + kc;
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (gn < N && gk < ke)
-                    v = *reinterpret_cast<const uint4 *>(B + (size_t)gn * ldb + gk);
-                *reinterpret_cast<uint4 *>(&Bs[n][kc]) = v;
-            }
-        } else {
-            for (int i = tid; i < GBN * GBK; i += 128) {
-                const int k = i / GBN, n = i % GBN;
-                const int gn = n0 + n, gk = k0 + k;
-                Bs[n][k] = (gn < N && gk < ke) ? B[(size_t)gk * ldb + gn] : zero;
-            }
+        for (int c = tid; c < GBN * GBK / 8; c += 128) {
+            const int n = c / (GBK / 8), kc = (c % (GBK / 8)) * 8;
+            const int gn = n0 + n, gk = k0 + kc;
+            const bool ok = gn < N && gk < ke;
+            cp_async16(&Bs[buf][n][kc], ok ? B + (size_t)gn * ldb + gk : B, ok);
         }
-        __syncthreads();
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    auto compute = [&](int buf) {
 #pragma unroll
         for (int kk = 0; kk < GBK; kk += 16) {
             uint32_t a[2][4], b[4][2];
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
                 const int r = wm + mt * 16 + g;
-                a[mt][0] = ld_b32(&As[r][kk + 2 * t]);
-                a[mt][1] = ld_b32(&As[r + 8][kk + 2 * t]);
-                a[mt][2] = ld_b32(&As[r][kk + 2 * t + 8]);
-                a[mt][3] = ld_b32(&As[r + 8][kk + 2 * t + 8]);
+                a[mt][0] = ld_b32(&As[buf][r][kk + 2 * t]);
+                a[mt][1] = ld_b32(&As[buf][r + 8][kk + 2 * t]);
+                a[mt][2] = ld_b32(&As[buf][r][kk + 2 * t + 8]);
+                a[mt][3] = ld_b32(&As[buf][r + 8][kk + 2 * t + 8]);
             }
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
                 const int cidx = wn + nt * 8 + g;
-                b[nt][0] = ld_b32(&Bs[cidx][kk + 2 * t]);
-                b[nt][1] = ld_b32(&Bs[cidx][kk + 2 * t + 8]);
+                b[nt][0] = ld_b32(&Bs[buf][cidx][kk + 2 * t]);
+                b[nt][1] = ld_b32(&Bs[buf][cidx][kk + 2 * t + 8]);
             }
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt)
@@ -154,7 +151,43 @@ __global__ void __launch_bounds__(128) gemm_bf16(const __nv_bfloat16 *__restrict
                 for (int nt = 0; nt < 4; ++nt)
                     mma_bf16_16x8x16(acc[mt][nt], a[mt], b[nt]);
         }
-        __syncthreads();
+    };
+
+    if constexpr (ASYNC) {
+        if (kb < ke)
+            stage_async(kb, 0);
+        int buf = 0;
+        for (int k0 = kb; k0 < ke; k0 += GBK, buf ^= 1) {
+            if (k0 + GBK < ke) {
+                stage_async(k0 + GBK, buf ^ 1);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+            __syncthreads();
+            compute(buf);
+            __syncthreads();
+        }
+    } else {
+        for (int k0 = kb; k0 < ke; k0 += GBK) {
+            for (int i = tid; i < GBM * GBK; i += 128) {
+                const int k = TA ? i / GBM : i % GBK, m = TA ? i % GBM : i / GBK;
+                const int gm = m0 + m, gk = k0 + k;
+                As[0][m][k] = (gm < M && gk < ke)
+                                  ? (TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk])
+                                  : zero;
+            }
+            for (int i = tid; i < GBN * GBK; i += 128) {
+                const int k = TB ? i / GBN : i % GBK, n = TB ? i % GBN : i / GBK;
+                const int gn = n0 + n, gk = k0 + k;
+                Bs[0][n][k] = (gn < N && gk < ke)
+                                  ? (TB ? B[(size_t)gk * ldb + gn] : B[(size_t)gn * ldb + gk])
+                                  : zero;
+            }
+            __syncthreads();
+            compute(0);
+            __syncthreads();
+        }
     }
 
     // ---- epilogue: accumulator (row g / g+8, columns 2t, 2t+1) of each tile
