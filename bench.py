@@ -585,12 +585,15 @@ def run_paper_mode(K, dev, stream):
         torch.cuda.synchronize(dev)
         for coords, cname in coords_rows:
             y0 = y_ks if coords == "ks" else y_bl
-            for prec, dt in (("f32", torch.float32), ("f64", torch.float64)):
+            precs = [("f32", torch.float32, False), ("f64", torch.float64, False)]
+            if coords == "ks":
+                precs.append(("f32x2", torch.float32, True))   # two geodesics per thread
+            for prec, dt, paired in precs:
                 for lay, lid in (("soa", K.LAYOUT_SOA), ("aos", K.LAYOUT_AOS)):
                     init = y0.to(dt) if lid == K.LAYOUT_SOA else y0.T.contiguous().to(dt)
                     work = init.clone()
                     K.kerr_rk4_fixed(a, work, nsteps, h, layout=lid, stream=stream,
-                                     coords=coords)                              # warm-up
+                                     coords=coords, paired=paired)               # warm-up
                     times = []
                     for _ in range(2):
                         work.copy_(init)
@@ -598,7 +601,7 @@ def run_paper_mode(K, dev, stream):
                         e1 = torch.cuda.Event(enable_timing=True)
                         e0.record(stream)
                         K.kerr_rk4_fixed(a, work, nsteps, h, layout=lid, stream=stream,
-                                         coords=coords)
+                                         coords=coords, paired=paired)
                         e1.record(stream)
                         torch.cuda.synchronize(dev)
                         times.append(e0.elapsed_time(e1))
@@ -612,7 +615,7 @@ def run_paper_mode(K, dev, stream):
     ctx.close()
     summary = {}
     for (cname, prec, lay), b in sorted(best.items()):
-        paper = PAPER_NS_PER_STEP[(cname, prec, lay)]
+        paper = PAPER_NS_PER_STEP[(cname, prec.replace("x2", ""), lay)]
         summary[f"{cname}_{prec}_{lay}"] = {
             "ns_per_step": b["ns_per_step"], "best_side": b["side"],
             "ray_steps_per_s": round(1e9 / b["ns_per_step"], 1),

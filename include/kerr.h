@@ -228,6 +228,14 @@ int kerr_num_variants(void);
  * (which sets the register cap). */
 int kerr_variant_info(int v, int32_t *block, int32_t *min_blocks);
 
+/* The same plus the geodesics each thread advances (1, or 2: the FP32
+ * stepping phase runs two geodesics per thread on packed f32x2 instructions;
+ * such variants are FP32-only, and KERR_FP64 calls reject them) and how the
+ * FP32 steps evaluate their right-hand sides (0 inline, 1 one out-of-line
+ * copy).  Any output pointer may be NULL.  KERR_EINVAL for v out of range. */
+int kerr_variant_shape(int v, int32_t *block, int32_t *min_blocks, int32_t *rays_per_thread,
+                       int32_t *rhs_mode);
+
 /* Launch shapes of the FP32 path's zone phase (threads per block, blocks per
  * SM); fewer threads than deferred geodesics lets lanes refill. */
 int kerr_num_zone_variants(void);
@@ -419,13 +427,19 @@ int kerr_dense_find_time(double a, const double *traj, int32_t cap, const int32_
  * steps of length h in place, with the right-hand side of eqs. opt0/opti,
  * no error control and no termination test (a geodesic that reaches the
  * singularity turns non-finite and keeps costing the same).  state: device
- * memory, n states (t, x, y, z, k^t, k^x, k^y, k^z) of float (fp64 = 0, plain
- * FP32 arithmetic) or double (fp64 = 1), in layout KERR_LAYOUT_SOA ([8][n])
- * or KERR_LAYOUT_AOS ([n][8], 16-byte aligned).  Spin a, |a| <= 1.
- * Asynchronous on `stream`.  KERR_EINVAL for bad arguments or host memory;
- * n == 0 or nsteps == 0 is a no-op. */
+ * memory, n states (t, x, y, z, k^t, k^x, k^y, k^z) of float (fp64 =
+ * KERR_FIXED_FP32: plain FP32 arithmetic, one geodesic per thread;
+ * KERR_FIXED_FP32X2: the same FP32 steps for two geodesics per thread on
+ * packed f32x2 instructions, equal to the one-per-thread results up to the
+ * compiler's fusing of multiply-adds) or double (KERR_FIXED_FP64), in layout
+ * KERR_LAYOUT_SOA ([8][n]) or KERR_LAYOUT_AOS ([n][8], 16-byte aligned).
+ * Spin a, |a| <= 1.  Asynchronous on `stream`.  KERR_EINVAL for bad
+ * arguments or host memory; n == 0 or nsteps == 0 is a no-op. */
 #define KERR_LAYOUT_SOA 0
 #define KERR_LAYOUT_AOS 1
+#define KERR_FIXED_FP32 0
+#define KERR_FIXED_FP64 1
+#define KERR_FIXED_FP32X2 2
 int kerr_rk4_fixed(double a, int32_t fp64, int32_t layout, void *state, int64_t n,
                    int32_t nsteps, double h, void *stream);
 
@@ -434,7 +448,7 @@ int kerr_rk4_fixed(double a, int32_t fp64, int32_t layout, void *state, int64_t 
  * reading: the Hamiltonian form H = N / (2 Sigma) of the BL geodesic
  * equations, state (t, r, theta, phi, p_t, p_r, p_theta, p_phi) with covariant
  * momenta (p_t and p_phi stay constant).  Same arguments and behaviour as
- * kerr_rk4_fixed; |a| < 1. */
+ * kerr_rk4_fixed (KERR_FIXED_FP32 or KERR_FIXED_FP64 only); |a| < 1. */
 int kerr_rk4_fixed_bl(double a, int32_t fp64, int32_t layout, void *state, int64_t n,
                       int32_t nsteps, double h, void *stream);
 

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libkerr.so")
-UNITS = ["kerr_api.cu", "kerr_trace_f32.cu", "kerr_trace_f32b.cu", "kerr_trace_zone.cu",
+UNITS = ["kerr_api.cu", "kerr_trace_f32.cu", "kerr_trace_f32b.cu", "kerr_trace_f32x2.cu", "kerr_trace_zone.cu",
          "kerr_trace_f64.cu", "kerr_static.cu", "kerr_surrogate.cu", "kerr_mlp_tc.cu",
          "kerr_fixed.cu", "kerr_coordtime.cu",
          "kerr_dense.cu"]

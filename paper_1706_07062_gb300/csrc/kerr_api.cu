@@ -133,6 +133,22 @@ extern "C" int kerr_variant_info(int v, int32_t *block, int32_t *min_blocks)
     return KERR_OK;
 }
 
+extern "C" int kerr_variant_shape(int v, int32_t *block, int32_t *min_blocks,
+                                  int32_t *rays_per_thread, int32_t *rhs_mode)
+{
+    if (v < 0 || v >= kNumVariants)
+        return fail(KERR_EINVAL, "variant %d out of range [0, %d)", v, kNumVariants);
+    if (block)
+        *block = kVariants[v].block;
+    if (min_blocks)
+        *min_blocks = kVariants[v].min_blocks;
+    if (rays_per_thread)
+        *rays_per_thread = kVariantRays[v];
+    if (rhs_mode)
+        *rhs_mode = kVariantRhs[v];
+    return KERR_OK;
+}
+
 extern "C" int kerr_num_zone_variants(void) { return kNumZoneVariants; }
 
 extern "C" int kerr_zone_variant_info(int v, int32_t *block, int32_t *blocks_per_sm)
@@ -240,6 +256,9 @@ static int check_opts(const kerr_opts *o)
                     o->zone_prec);
     if (o->variant < -1 || o->variant >= kNumVariants)
         return fail(KERR_EINVAL, "opts.variant = %d outside [-1, %d)", o->variant, kNumVariants);
+    if (o->prec == KERR_FP64 && o->variant >= 0 && kVariantRays[o->variant] != 1)
+        return fail(KERR_EINVAL, "opts.variant = %d (two geodesics per thread) is FP32-only",
+                    o->variant);
     if (o->zone_quantum < 0)
         return fail(KERR_EINVAL, "opts.zone_quantum = %d < 0", o->zone_quantum);
     if (o->zone_variant < -1 || o->zone_variant >= kNumZoneVariants)
@@ -811,6 +830,8 @@ extern "C" int kerr_autotune(kerr_ctx *c, const kerr_camera *cam, const kerr_opt
     float best_ms = 1e30f;
     int best_v = 0;
     for (int v = 0; v < kNumVariants && rc == KERR_OK; ++v) {
+        if (o->prec == KERR_FP64 && kVariantRays[v] != 1)
+            continue;                            // FP32-only launch shapes
         oo.variant = v;
         float ms_min = 1e30f;
         for (int rep = 0; rep < 3 && rc == KERR_OK; ++rep) {

@@ -5,6 +5,7 @@
 // registers, one geodesic per thread; the state array is read once and
 // written once per launch, in SoA ([8][n]) or AoS ([n][8]) layout.
 #include "kerr_trace.cuh"
+#include "kerr_f2.cuh"
 #include "kerr_variants.h"
 #include "kerr.h"
 
@@ -90,6 +91,46 @@ __global__ void __launch_bounds__(128) rk4_fixed_kernel(T *__restrict__ state, i
             y[j] = y[j] + d[j];
     }
     store_state<T, AOS>(state, n, i, y);
+}
+
+// The same steps for two geodesics per thread on packed FP32 instructions:
+// thread i advances geodesics i and i + ceil(n/2) (for odd n the last thread
+// repeats geodesic i in its second half and stores it once).
+template <bool AOS>
+__global__ void __launch_bounds__(128) rk4_fixed_x2_kernel(float *__restrict__ state, int64_t n,
+                                                           int nsteps, float h, float a)
+{
+    const int64_t half = (n + 1) / 2;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= half)
+        return;
+    const int64_t j = i + half < n ? i + half : i;
+    float u[8], w[8];
+    load_state<float, AOS>(state, n, i, u);
+    load_state<float, AOS>(state, n, j, w);
+    f2 y[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        y[q] = f2(u[q], w[q]);
+    const f2 av(a, a), hv(h, h);
+    const f2 a2 = av * av;
+#pragma unroll 1
+    for (int s = 0; s < nsteps; ++s) {
+        f2 A0[4], d[8];
+        rhs<RHS_CALL>(av, a2, y[1], y[2], y[3], y[4], y[5], y[6], y[7], A0);
+        rk4_incr<RHS_CALL>(av, a2, y, A0, hv, d);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            y[q] = y[q] + d[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        u[q] = y[q].v.x;
+        w[q] = y[q].v.y;
+    }
+    store_state<float, AOS>(state, n, i, u);
+    if (j != i)
+        store_state<float, AOS>(state, n, j, w);
 }
 
 // ---------------------------------------------------------------------------
@@ -212,6 +253,15 @@ cudaError_t launch_bl(void *state, int64_t n, int nsteps, double h, double a, cu
     return cudaGetLastError();
 }
 
+template <bool AOS>
+cudaError_t launch_x2(void *state, int64_t n, int nsteps, double h, double a, cudaStream_t s)
+{
+    const int64_t blocks = ((n + 1) / 2 + 127) / 128;
+    rk4_fixed_x2_kernel<AOS><<<(unsigned)blocks, 128, 0, s>>>(static_cast<float *>(state), n,
+                                                             nsteps, (float)h, (float)a);
+    return cudaGetLastError();
+}
+
 template <typename T, bool AOS>
 cudaError_t launch(void *state, int64_t n, int nsteps, double h, double a, cudaStream_t s)
 {
@@ -226,7 +276,8 @@ cudaError_t launch(void *state, int64_t n, int nsteps, double h, double a, cudaS
 static int fixed_common(int coords, double a, int32_t fp64, int32_t layout, void *state,
                         int64_t n, int32_t nsteps, double h, void *stream)
 {
-    if (!(std::fabs(a) <= 1.0) || (fp64 != 0 && fp64 != 1) ||
+    if (!(std::fabs(a) <= 1.0) || fp64 < KERR_FIXED_FP32 || fp64 > KERR_FIXED_FP32X2 ||
+        (coords != 0 && fp64 == KERR_FIXED_FP32X2) ||
         (layout != KERR_LAYOUT_SOA && layout != KERR_LAYOUT_AOS) || n < 0 || nsteps < 0 ||
         !std::isfinite(h) || (n > 0 && !state))
         return kerr::kerr_set_error(KERR_EINVAL, "kerr_rk4_fixed: invalid arguments");
@@ -244,7 +295,9 @@ static int fixed_common(int coords, double a, int32_t fp64, int32_t layout, void
     const cudaStream_t s = (cudaStream_t)stream;
     const bool aos = layout == KERR_LAYOUT_AOS;
     cudaError_t e;
-    if (coords == 0) {
+    if (coords == 0 && fp64 == KERR_FIXED_FP32X2) {
+        e = aos ? launch_x2<true>(state, n, nsteps, h, a, s) : launch_x2<false>(state, n, nsteps, h, a, s);
+    } else if (coords == 0) {
         if (fp64)
             e = aos ? launch<double, true>(state, n, nsteps, h, a, s)
                     : launch<double, false>(state, n, nsteps, h, a, s);

@@ -104,7 +104,8 @@ extern "C" int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam,
         o->renorm_every < 0 || !(o->fp64_zone >= 0.0) || o->variant < -1 ||
         (o->zone_prec != KERR_ZONE_FP64 && o->zone_prec != KERR_ZONE_F32X2) ||
         o->zone_variant < -1 || o->zone_variant >= kNumZoneVariants ||
-        o->zone_quantum < 0 || o->variant >= kNumVariants)
+        o->zone_quantum < 0 || o->variant >= kNumVariants ||
+        (o->prec == KERR_FP64 && o->variant >= 0 && kVariantRays[o->variant] != 1))
         return fail(KERR_EINVAL, "kerr_trace_camera_static: invalid options");
     CamDev cd[kMaxCams];
     int64_t n = 0;

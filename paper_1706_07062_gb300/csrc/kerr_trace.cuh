@@ -216,8 +216,7 @@ template <int RM, typename T>
 __device__ __forceinline__ void rhs(const T a, const T a2, const T x, const T y, const T z,
                                     const T kt, const T kx, const T ky, const T kz, T A[4])
 {
-    if constexpr (RM != RHS_INLINE &&
-                  (std::is_same<T, double>::value || std::is_same<T, float>::value)) {
+    if constexpr (RM != RHS_INLINE) {
         const Acc<T> r = accel_call<T>(a, a2, x, y, z, kt, kx, ky, kz);
         A[0] = r.t;
         A[1] = r.x;
@@ -252,9 +251,9 @@ __device__ __forceinline__ void rhs2(const T a, const T a2, const T p[7], const 
 
 // Increments d = y(lambda + h) - y(lambda) of one classic RK4 step (Sec. 3)
 // from y, with A0 = accel(y) already known: 3 right-hand sides.
-template <int RM = RHS_INLINE, typename T>
-__device__ __forceinline__ void rk4_incr(const T a, const T a2, const T y[8], const T A0[4],
-                                         const T h, T d[8])
+template <int RM, typename T>
+__device__ __forceinline__ void rk4_incr_body(const T a, const T a2, const T y[8], const T A0[4],
+                                              const T h, T d[8])
 {
     const T hh = T(0.5) * h;
     T Sk[4], SA[4];
@@ -289,6 +288,45 @@ __device__ __forceinline__ void rk4_incr(const T a, const T a2, const T y[8], co
     for (int j = 0; j < 4; ++j) {
         d[j] = h6 * (Sk[j] + m[j]);
         d[4 + j] = h6 * (SA[j] + A[j]);
+    }
+}
+
+template <typename T> struct Incr8 {
+    T v[8];
+};
+
+// One out-of-line copy of the RK4 step for float-float: each float-float
+// operation expands to several FP32 instructions, and with every step inlined
+// the attempt's code no longer fits the instruction cache (warps then stall
+// on instruction fetch).  y[0] (t) does not enter the step.
+template <typename T>
+static __device__ __noinline__ Incr8<T> rk4_incr_call(const T a, const T a2, const T y1,
+                                                      const T y2, const T y3, const T y4,
+                                                      const T y5, const T y6, const T y7,
+                                                      const T A00, const T A01, const T A02,
+                                                      const T A03, const T h)
+{
+    const T y[8] = {T(0), y1, y2, y3, y4, y5, y6, y7};
+    const T A0[4] = {A00, A01, A02, A03};
+    Incr8<T> r;
+    rk4_incr_body<RHS_CALL>(a, a2, y, A0, h, r.v);
+    return r;
+}
+
+// RK4 increments: inline, or (float-float with out-of-line right-hand sides)
+// through the one out-of-line copy above.
+template <int RM = RHS_INLINE, typename T>
+__device__ __forceinline__ void rk4_incr(const T a, const T a2, const T y[8], const T A0[4],
+                                         const T h, T d[8])
+{
+    if constexpr (RM == RHS_CALL && std::is_same<T, dfloat>::value) {
+        const Incr8<T> r = rk4_incr_call<T>(a, a2, y[1], y[2], y[3], y[4], y[5], y[6], y[7],
+                                            A0[0], A0[1], A0[2], A0[3], h);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            d[i] = r.v[i];
+    } else {
+        rk4_incr_body<RM>(a, a2, y, A0, h, d);
     }
 }
 
@@ -376,6 +414,24 @@ __device__ __forceinline__ void two_halves(const T a, const T a2, const T y[8], 
         d[i] = d1[i] + d[i];
 }
 
+// Error measure of an FP32 step-doubling attempt: the largest over the
+// components i >= 1 of |d_i - df_i| / 15 relative to tol (1 + max(|y_i|,
+// |y_i + d_i|)), with d the two-half-step and df the full-step increment
+// (Richardson's estimate of the local error of the more accurate solution).
+__device__ __forceinline__ float err_norm_f(const float y[8], const float d[8], const float df[8],
+                                            const float tol)
+{
+    float err = 0.f;
+#pragma unroll
+    for (int i = 1; i < 8; ++i) {
+        const float delta = (d[i] - df[i]) * (float)(1.0 / 15.0);
+        const float sc = tol * (1.f + fmaxf(fabsf(y[i]), fabsf(y[i] + d[i])));
+        const float e = fabsf(delta) / sc;
+        err = (e <= err) ? err : e;    // NaN propagates
+    }
+    return err;
+}
+
 // One step-doubling attempt: returns the error measure and the increment of
 // the two-half-step solution (10 RHS beyond A0).  With paired right-hand
 // sides the full step and the first half step run in lockstep.
@@ -401,15 +457,7 @@ __device__ __forceinline__ T attempt(const T a, const T a2, const T y[8], const 
         two_halves<RM>(a, a2, y, A0, h, d);
     }
     if constexpr (std::is_same<T, float>::value) {
-        T err = T(0);
-#pragma unroll
-        for (int i = 1; i < 8; ++i) {
-            const T delta = (d[i] - df[i]) * T(1.0 / 15.0);
-            const T sc = tol * (T(1) + fmax(fabs(y[i]), fabs(y[i] + d[i])));
-            const T e = fabs(delta) / sc;
-            err = (e <= err) ? err : e;    // NaN propagates
-        }
-        return err;
+        return err_norm_f(y, d, df, tol);
     } else {
         // FP64 / float-float: the max over i of |delta_i| / sc_i is kept as
         // one fraction num / den, each comparison cross-multiplied (sc_i,
@@ -458,6 +506,7 @@ __device__ __forceinline__ double step_factor_f(double err)
 {
     return (double)step_factor((float)err);
 }
+__device__ __forceinline__ dfloat step_factor_f(dfloat err) { return step_factor(err); }
 
 template <bool KAHAN, typename T>
 __device__ __forceinline__ void add_incr(T &y, T &c, T d)
@@ -567,22 +616,22 @@ __device__ __forceinline__ double to_d(dfloat x) { return (double)x.hi + (double
 template <typename T> __device__ __forceinline__ T from_d(double d) { return (T)d; }
 template <> __device__ __forceinline__ dfloat from_d<dfloat>(double d) { return dfloat(d); }
 
-// One attempted step with events.  (y, c) is the lane state; h the trial
-// step; rn receives r of the new state when a step is accepted.  Returns a
-// status code when the geodesic terminates, ST_NONE otherwise.
-template <bool KAHAN, typename T, bool FAST_FACTOR = false, int RM = RHS_INLINE>
-__device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &P, int64_t id,
-                                         const T tol, T y[8], T c[8], T &h, T &rn,
+// The rest of an attempt once its error measure err and the increment d of
+// the two-half-step solution are known (A0 = accel(y), a2 = a^2): step-size
+// control, the compensated update, the termination events, the equatorial
+// crossings and the periodic renormalisation.
+__device__ __forceinline__ void load_const_full(const TraceParams &P, int64_t id, RayConst &rc);
+
+// LAZY: rc holds the FP32 fields only; the renormalisation loads the FP64
+// ones when it runs.
+template <bool KAHAN, typename T, bool FAST_FACTOR = false, int RM = RHS_INLINE,
+          bool LAZY = false>
+__device__ __forceinline__ int step_post(const RayConst &rc, const TraceParams &P, int64_t id,
+                                         const T a, const T a2, const T A0[4], const T d[8],
+                                         const T err, T y[8], T c[8], T &h, T &rn,
                                          uint32_t &nrhs, uint32_t &nacc, int &since_renorm,
                                          T *h_taken = nullptr)
 {
-    const T a = RC<T>::a(rc);
-    const T a2 = a * a;
-    T A0[4];
-    rhs<RM>(a, a2, y[1], y[2], y[3], y[4], y[5], y[6], y[7], A0);
-    T d[8];
-    const T err = attempt<RM>(a, a2, y, A0, h, tol, d);
-    nrhs += 11;
     T fac;
     if constexpr (FAST_FACTOR)
         fac = step_factor_f(err);
@@ -680,16 +729,39 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             k[j] = to_d(y[4 + j]) + (KAHAN ? to_d(c[4 + j]) : 0.0);
-        const KSPoint p = ks_point(rc.a, to_d(y[1]) + (KAHAN ? to_d(c[1]) : 0.0),
+        RayConst rf = rc;
+        if (LAZY)
+            load_const_full(P, id, rf);
+        const KSPoint p = ks_point(rf.a, to_d(y[1]) + (KAHAN ? to_d(c[1]) : 0.0),
                                    to_d(y[2]) + (KAHAN ? to_d(c[2]) : 0.0),
                                    to_d(y[3]) + (KAHAN ? to_d(c[3]) : 0.0));
-        if (solve_kt(p, k, rc.u2_0, 0)) {
+        if (solve_kt(p, k, rf.u2_0, 0)) {
             y[4] = from_d<T>(k[0]);
             c[4] = KAHAN ? from_d<T>(k[0] - to_d(y[4])) : T(0);
         }
     }
     h *= fac;
     return ST_NONE;
+}
+
+// One attempted step with events.  (y, c) is the lane state; h the trial
+// step; rn receives r of the new state when a step is accepted.  Returns a
+// status code when the geodesic terminates, ST_NONE otherwise.
+template <bool KAHAN, typename T, bool FAST_FACTOR = false, int RM = RHS_INLINE>
+__device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &P, int64_t id,
+                                         const T tol, T y[8], T c[8], T &h, T &rn,
+                                         uint32_t &nrhs, uint32_t &nacc, int &since_renorm,
+                                         T *h_taken = nullptr)
+{
+    const T a = RC<T>::a(rc);
+    const T a2 = a * a;
+    T A0[4];
+    rhs<RM>(a, a2, y[1], y[2], y[3], y[4], y[5], y[6], y[7], A0);
+    T d[8];
+    const T err = attempt<RM>(a, a2, y, A0, h, tol, d);
+    nrhs += 11;
+    return step_post<KAHAN, T, FAST_FACTOR, RM>(rc, P, id, a, a2, A0, d, err, y, c, h, rn, nrhs,
+                                                nacc, since_renorm, h_taken);
 }
 
 // ---------------------------------------------------------------------------
@@ -912,6 +984,7 @@ static __device__ __noinline__ ZoneResult zone_step(const RayConst rc, const Tra
 
 // The same step in float-float arithmetic: the compensated pair (y, c) is
 // already a float-float number, so no FP64 instruction is needed.
+template <int RM>
 static __device__ __noinline__ ZoneResult zone_step_df(const RayConst rc, const TraceParams &P,
                                                        int64_t id, LaneF s, int since_renorm)
 {
@@ -925,9 +998,8 @@ static __device__ __noinline__ ZoneResult zone_step_df(const RayConst rc, const 
     ZoneResult R;
     R.nrhs = 0;
     R.nacc = 0;
-    R.st = step_once<false, dfloat>(rc, P, id, dfloat((float)P.tol), yd, cd, hd, rd, R.nrhs,
-                                    R.nacc,
-                                    since_renorm);
+    R.st = step_once<false, dfloat, true, RM>(rc, P, id, dfloat((float)P.tol), yd, cd, hd, rd,
+                                              R.nrhs, R.nacc, since_renorm);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         R.s.y[i] = yd[i].hi;
@@ -1504,7 +1576,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     ls.rnow = rnow;
                     ZoneResult R;
                     if (PHASE == 2 || (PHASE == 0 && P.zone_df))
-                        R = zone_step_df(rc, P, id, ls, since_renorm);
+                        R = zone_step_df<PHASE == 2 ? RM : RHS_INLINE>(rc, P, id, ls, since_renorm);
                     else
                         R = zone_step<RM>(rc, P, id, ls, since_renorm);
 #pragma unroll

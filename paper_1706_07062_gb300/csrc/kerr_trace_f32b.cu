@@ -35,7 +35,7 @@ cudaError_t launch_trace_f32_hi(const TraceParams &P, int v, int sms, cudaStream
         KERR_VARIANT_LIST_HI(KERR_CASE)
 #undef KERR_CASE
     default:
-        return cudaErrorInvalidValue;
+        return launch_trace_f32x2(P, v, sms, s);
     }
 }
 

@@ -23,7 +23,7 @@ cudaError_t launch_zone_phase(const TraceParams &P, int zv, int sms, cudaStream_
     switch (zv) {
 #define KERR_ZCASE(i, b, m, rm)                                                        \
     case i:                                                                            \
-        return P.zone_df ? launch_zone<2, 128, 2, RHS_INLINE>(P, sms, s)                 \
+        return P.zone_df ? launch_zone<2, 128, 2, RHS_CALL>(P, sms, s)                   \
                          : launch_zone<1, b, m, rm>(P, sms, s);
         KERR_ZONE_VARIANT_LIST(KERR_ZCASE)
 #undef KERR_ZCASE

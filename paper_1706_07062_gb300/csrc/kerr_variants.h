@@ -17,13 +17,23 @@ struct Variant {
 #define KERR_VARIANT_LIST_HI(X) X(5, 128, 2, 0) X(6, 64, 8, 0) X(7, 128, 5, 0) X(8, 256, 2, 1) \
     X(9, 128, 5, 1)
 #define KERR_VARIANT_LIST(X) KERR_VARIANT_LIST_LO(X) KERR_VARIANT_LIST_HI(X)
+// FP32 stepping with two geodesics per thread (packed f32x2 right-hand sides,
+// always out of line): (index, threads per block, minimum blocks per SM).
+// FP32+Kahan path only.
+#define KERR_VARIANT_LIST_X2(X) X(10, 128, 2) X(11, 128, 3) X(12, 64, 4) X(13, 64, 6)
 
-constexpr int kNumVariants = 10;
+constexpr int kNumVariants = 14;
+constexpr int kFirstX2Variant = 10;
 // Defaults before autotuning, per precision (KERR_FP64, KERR_FP32_KAHAN):
 // the fastest on the 1024 x 1024, a = 0.99 camera.
 constexpr int kDefaultVariant[2] = {1, 3};
 constexpr Variant kVariants[kNumVariants] = {{128, 4}, {128, 3}, {256, 2}, {128, 4}, {128, 3},
-                                             {128, 2}, {64, 8},  {128, 5}, {256, 2}, {128, 5}};
+                                             {128, 2}, {64, 8},  {128, 5}, {256, 2}, {128, 5},
+                                             {128, 2}, {128, 3}, {64, 4},  {64, 6}};
+// Geodesics per thread of each variant.
+constexpr int kVariantRays[kNumVariants] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2};
+// Right-hand-side mode of each variant's FP32 steps (RHS_INLINE = 0, RHS_CALL = 1).
+constexpr int kVariantRhs[kNumVariants] = {0, 0, 0, 1, 1, 0, 0, 0, 1, 1, 1, 1, 1, 1};
 
 // Zone-phase variants: (threads per block, blocks per SM, how FP64 steps
 // evaluate their right-hand sides: 0 inline, 1 one out-of-line copy, 2
@@ -41,6 +51,7 @@ struct TraceParams;
 // Launch the persistent kernel for variant v on a grid of `blocks_per_sm *
 // sms` blocks (0 = as many as fit).  Returns the CUDA error of the launch.
 cudaError_t launch_trace_f32(const TraceParams &P, int v, int sms, cudaStream_t s);
+cudaError_t launch_trace_f32x2(const TraceParams &P, int v, int sms, cudaStream_t s);
 cudaError_t launch_trace_f64(const TraceParams &P, int v, int sms, cudaStream_t s);
 cudaError_t launch_zone_phase(const TraceParams &P, int zv, int sms, cudaStream_t s);
 cudaError_t launch_setup_f32(const TraceParams &P, int sms, cudaStream_t s);

@@ -112,6 +112,8 @@ def lib():
                                             c.c_float, c.c_float, vp, vp, c.POINTER(i64), vp]
         L.kerr_num_variants.argtypes = []
         L.kerr_variant_info.argtypes = [c.c_int, c.POINTER(i32), c.POINTER(i32)]
+        L.kerr_variant_shape.argtypes = [c.c_int, c.POINTER(i32), c.POINTER(i32),
+                                         c.POINTER(i32), c.POINTER(i32)]
         L.kerr_num_zone_variants.argtypes = []
         L.kerr_zone_variant_info.argtypes = [c.c_int, c.POINTER(i32), c.POINTER(i32)]
         L.kerr_autotune.argtypes = [vp, c.POINTER(Camera), c.POINTER(Opts), i64, c.POINTER(i32), vp]
@@ -348,6 +350,15 @@ def kerr_variant_info(v: int) -> tuple[int, int]:
     return b.value, m.value
 
 
+def kerr_variant_shape(v: int) -> tuple[int, int, int, int]:
+    """(threads per block, minimum blocks per SM, geodesics per thread,
+    right-hand-side mode of the FP32 steps) of stepping variant v."""
+    b, m, r, h = (ctypes.c_int32() for _ in range(4))
+    _check(lib().kerr_variant_shape(v, ctypes.byref(b), ctypes.byref(m), ctypes.byref(r),
+                                    ctypes.byref(h)), "kerr_variant_shape")
+    return b.value, m.value, r.value, h.value
+
+
 def kerr_num_zone_variants() -> int:
     return lib().kerr_num_zone_variants()
 
@@ -512,13 +523,16 @@ def kerr_check_fp64_math(x, stream=None):
 
 
 LAYOUT_SOA, LAYOUT_AOS = 0, 1
+FIXED_FP32, FIXED_FP64, FIXED_FP32X2 = 0, 1, 2
 
 
 def kerr_rk4_fixed(a: float, state, nsteps: int, h: float, layout: int = LAYOUT_SOA,
-                   stream=None, coords: str = "ks"):
+                   stream=None, coords: str = "ks", paired: bool = False):
     """Paper-mode fixed-step RK4 in place on a device tensor: float32 or
     float64, shape (8, n) for LAYOUT_SOA or (n, 8) for LAYOUT_AOS; coords
-    "ks" (Cartesian Kerr-Schild, (x, k)) or "bl" (Boyer-Lindquist, (x, p))."""
+    "ks" (Cartesian Kerr-Schild, (x, k)) or "bl" (Boyer-Lindquist, (x, p)).
+    paired: float32 KS only, two geodesics per thread on packed f32x2
+    instructions (KERR_FIXED_FP32X2)."""
     import torch
     if state.dtype not in (torch.float32, torch.float64):
         raise KerrError("state must be float32 or float64")
@@ -526,7 +540,12 @@ def kerr_rk4_fixed(a: float, state, nsteps: int, h: float, layout: int = LAYOUT_
         raise KerrError("coords must be 'ks' or 'bl'")
     n = int(state.shape[1] if layout == LAYOUT_SOA else state.shape[0])
     fn = lib().kerr_rk4_fixed if coords == "ks" else lib().kerr_rk4_fixed_bl
-    _check(fn(float(a), int(state.dtype == torch.float64), int(layout), _ptr(state), n,
+    prec = FIXED_FP64 if state.dtype == torch.float64 else FIXED_FP32
+    if paired:
+        if prec != FIXED_FP32:
+            raise KerrError("paired steps are FP32 only")
+        prec = FIXED_FP32X2
+    _check(fn(float(a), int(prec), int(layout), _ptr(state), n,
               int(nsteps), float(h), _stream_ptr(stream, state)), "kerr_rk4_fixed")
     return state
 

@@ -70,11 +70,19 @@ def test_defaults_and_variants_without_gpu(libpath):
     assert o.zone_quantum == 32 and o.zone_variant == -1
     n = K.kerr_num_variants()
     assert n >= 1
+    rays = []
     for v in range(n):
         b, m = K.kerr_variant_info(v)
         assert b % 32 == 0 and m >= 1
+        b2, m2, r, rm = K.kerr_variant_shape(v)
+        assert (b2, m2) == (b, m) and r in (1, 2) and rm in (0, 1)
+        assert r == 1 or rm == 1          # paired steps always call their right-hand side
+        rays.append(r)
+    assert 1 in rays and 2 in rays
     with pytest.raises(K.KerrError):
         K.kerr_variant_info(n)
+    with pytest.raises(K.KerrError):
+        K.kerr_variant_shape(-1)
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):

@@ -65,6 +65,42 @@ def test_layouts_agree_bit_for_bit(rays, dtype):
     assert torch.equal(soa.T.contiguous(), aos)
 
 
+@pytest.mark.parametrize("layout", [K.LAYOUT_SOA, K.LAYOUT_AOS])
+@pytest.mark.parametrize("n", [1, 2, 7, 193])
+def test_paired_fp32_matches_one_per_thread(rays, layout, n):
+    """Two geodesics per thread on packed f32x2 instructions: the same IEEE
+    operations per geodesic as one per thread (odd n: the last thread's second
+    half repeats a geodesic and stores nothing), and within the FP32 gate of
+    the oracle."""
+    y0, ref = rays
+    idx = np.arange(n) % len(y0)
+    ys = y0[idx]
+    mk = lambda: torch.tensor(ys.T if layout == K.LAYOUT_SOA else ys, dtype=torch.float32,
+                              device=DEV).contiguous()
+    one, two = mk(), mk()
+    K.kerr_rk4_fixed(A, one, NSTEPS, H, layout=layout)
+    K.kerr_rk4_fixed(A, two, NSTEPS, H, layout=layout, paired=True)
+    torch.cuda.synchronize()
+    g1, g2 = one.double().cpu().numpy(), two.double().cpu().numpy()
+    # fused multiply-adds are explicit in both forms; allow a few ulps in case
+    # a compiler contracts the scalar form differently
+    assert np.allclose(g1, g2, rtol=1e-6, atol=0.0), np.abs(g1 - g2).max()
+    got = g2.T if layout == K.LAYOUT_SOA else g2
+    e = rel(got, ref[idx])
+    assert e.max() < 2e-3 and np.median(e) < 3e-5
+
+
+def test_paired_arguments():
+    st = torch.zeros((8, 4), dtype=torch.float64, device=DEV)
+    with pytest.raises(K.KerrError):
+        K.kerr_rk4_fixed(A, st, 1, H, paired=True)            # FP64 state
+    st32 = torch.zeros((8, 4), dtype=torch.float32, device=DEV)
+    with pytest.raises(K.KerrError):
+        K.kerr_rk4_fixed(0.5, st32, 1, H, coords="bl", paired=True)   # KS only
+    # an unknown precision code is rejected at the C boundary
+    assert K.lib().kerr_rk4_fixed(A, 3, K.LAYOUT_SOA, st32.data_ptr(), 4, 1, H, None) != 0
+
+
 def test_fixed_rk4_arguments():
     st = torch.zeros((8, 4), dtype=torch.float64, device=DEV)
     K.kerr_rk4_fixed(A, st, 0, H)                       # no-op

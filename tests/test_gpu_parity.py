@@ -255,16 +255,22 @@ def test_invalid_arguments_are_rejected(ctx):
 
 
 # FP32-phase right-hand-side mode of each stepping variant (0 inline, 1 call)
-VARIANT_RHS_MODE = [0, 0, 0, 1, 1, 0, 0, 0, 1, 1]
+def variant_family(v):
+    """(geodesics per thread, right-hand-side mode): variants of one family
+    run the same arithmetic per geodesic."""
+    _, _, rays, rhs_mode = K.kerr_variant_shape(v)
+    return rays, rhs_mode
 
 
 def test_every_variant_and_autotune(ctx):
     """Variants with the same right-hand-side code agree bit for bit (the
     launch shape only moves geodesics between lanes).  Inline and
     out-of-line FP32 right-hand sides may fuse multiply-adds differently, and
-    FP32 rounding differences grow along a trajectory: each mode is checked
-    against the oracle at the FP32 gate instead."""
-    assert K.kerr_num_variants() == len(VARIANT_RHS_MODE)
+    so may the packed two-per-thread steps; FP32 rounding differences grow
+    along a trajectory: each family is checked against the oracle at the FP32
+    gate instead."""
+    fams = {variant_family(v) for v in range(K.kerr_num_variants())}
+    assert fams == {(1, 0), (1, 1), (2, 1)}
     spec = W.CameraSpec(0.9, 1.0, 1000.0, 20.0, 48, 48)
     outs = []
     for v in range(K.kerr_num_variants()):
@@ -273,7 +279,7 @@ def test_every_variant_and_autotune(ctx):
         outs.append(o)
     first = {}
     for v, o in enumerate(outs):
-        m = VARIANT_RHS_MODE[v]
+        m = variant_family(v)
         if m not in first:
             first[m] = v
             continue
@@ -290,6 +296,59 @@ def test_every_variant_and_autotune(ctx):
         assert s["max_err_good"] < 1e-4, s
     best = K.kerr_autotune(ctx, cam(spec), K.default_opts(), sample=2048)
     assert 0 <= best < K.kerr_num_variants()
+    # two geodesics per thread is an FP32-only launch shape
+    best64 = K.kerr_autotune(ctx, cam(spec), K.default_opts(prec=K.FP64), sample=1024)
+    assert variant_family(best64)[0] == 1
+    x2 = next(v for v in range(K.kerr_num_variants()) if variant_family(v)[0] == 2)
+    with pytest.raises(K.KerrError):
+        K.kerr_trace_camera(ctx, cam(spec), K.default_opts(prec=K.FP64, variant=x2), device=DEV)
+
+
+def test_two_per_thread_edge_cases(ctx):
+    """Two geodesics per thread with ragged counts (a last thread holding one
+    geodesic, fewer geodesics than one warp's slots), particles with end
+    times and crossing labels: the same end states, statuses, step counts
+    and labels in every two-per-thread launch shape, and within the FP32 gate
+    of the one-per-thread kernel with out-of-line right-hand sides."""
+    x2 = [v for v in range(K.kerr_num_variants()) if variant_family(v)[0] == 2]
+    ref_v = next(v for v in range(K.kerr_num_variants()) if variant_family(v) == (1, 1))
+    for nx, ny in ((1, 1), (7, 5), (33, 31)):
+        spec = W.CameraSpec(0.9, 1.0, 1000.0, 12.0, nx, ny)
+        outs = []
+        for v in x2 + [ref_v]:
+            o = K.alloc_out(spec.n, DEV, cross=True)
+            K.kerr_trace_camera(ctx, cam(spec), K.default_opts(variant=v), out=o)
+            torch.cuda.synchronize()
+            outs.append(o)
+        for o in outs[1:-1]:
+            for f in ("x", "k", "status", "steps"):
+                assert torch.equal(getattr(o, f), getattr(outs[0], f)), (nx, ny, f)
+            assert torch.equal(torch.nan_to_num(o.cross, 7.0), torch.nan_to_num(outs[0].cross, 7.0))
+        r = outs[-1]
+        assert torch.equal(r.status, outs[0].status)
+        ex, ek, _ = rel_errors(to_np(outs[0].x), to_np(outs[0].k),
+                               np.concatenate([to_np(r.x).T, to_np(r.k).T], 1))
+        # two FP32 roundings of one method; end points on the capture sphere
+        # amplify differences near the horizon
+        assert np.median(np.maximum(ex, ek)) < 1e-4
+    ps = W.particles(n=999, periods=3)
+    c2 = K.kerr_init(ps.a)
+    x0 = torch.tensor(ps.x0, device=DEV)
+    v0 = torch.tensor(ps.v0, device=DEV)
+    te = torch.tensor(ps.t_end, device=DEV)
+    res = []
+    for v in x2 + [ref_v]:
+        o = K.default_opts(tol=1e-6, r_escape=-1.0, max_steps=10_000_000, variant=v)
+        res.append(K.kerr_trace_particles(c2, x0, v0, te, o))
+        torch.cuda.synchronize()
+    for o in res[1:-1]:
+        for f in ("x", "k", "status", "steps"):
+            assert torch.equal(getattr(o, f), getattr(res[0], f)), f
+    assert torch.equal(res[0].status, res[-1].status)
+    ended = to_np(res[0].status) == K.ENDTIME
+    # end-time clip tolerance of the FP32 steps: 2e-6 relative
+    assert ended.any() and np.allclose(to_np(res[0].x)[0][ended], ps.t_end[ended], rtol=5e-6)
+    c2.close()
 
 
 # ---------------------------------------------------------------------------
