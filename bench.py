@@ -316,6 +316,30 @@ def run_ours(args, rank, world, local_rank):
                                   "note": "same path with fp64_zone = 0 (every step FP32+Kahan)"}
         result["_nz_out"] = outnz
 
+    # ---- FP32+Kahan with float-float zone steps (comparison leg): the zone's
+    # steps in ~48-bit float-float arithmetic on the FP32 pipe instead of FP64
+    if rank == 0 and prec == K.FP32_KAHAN and not args.skip_fp64:
+        odf = K.default_opts(prec=K.FP32_KAHAN, tol=W.TOL_1024, zone_prec=K.ZONE_F32X2)
+        outdf = K.alloc_out(n, dev)
+        K.kerr_trace_camera(ctx, cam, odf, out=outdf, stream=stream)
+        torch.cuda.synchronize(dev)
+        tdf, zdf = [], []
+        for _ in range(3):
+            flush.zero_()
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            K.kerr_trace_camera(ctx, cam, odf, out=outdf, stream=stream)
+            b_.record(stream)
+            torch.cuda.synchronize(dev)
+            tdf.append(a_.elapsed_time(b_))
+            zdf.append(K.kerr_get_stats(ctx).phase_ms[2])
+        result["fp32_zone_float_float"] = {
+            "value": round(n / (min(tdf) * 1e-3), 1), "unit": UNIT,
+            "ms_per_step": round(min(tdf), 3), "zone_phase_ms": round(min(zdf), 3),
+            "note": "same path with zone_prec = KERR_ZONE_F32X2: steps inside 1.5 r_h in "
+                    "float-float (~48-bit) arithmetic on the FP32 pipe instead of FP64"}
+        result["_df_out"] = outdf
+
     # ---- plain FP64 GPU path on the same workload (comparison leg)
     if rank == 0 and prec == K.FP32_KAHAN and not args.skip_fp64:
         o64 = K.default_opts(prec=K.FP64, tol=W.TOL_1024)
@@ -354,11 +378,13 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.skip_cpu:
         result["cpu_baseline"], acc = cpu_baseline(spec, W, out, result.get("_fp64_out"),
                                                    result.get("_nz_out"),
-                                                   result.get("_surr_img"))
+                                                   result.get("_surr_img"),
+                                                   result.get("_df_out"))
         if acc:
             result["accuracy"] = acc
     result.pop("_fp64_out", None)
     result.pop("_nz_out", None)
+    result.pop("_df_out", None)
     result.pop("_surr_img", None)
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -626,7 +652,7 @@ def run_paper_mode(K, dev, stream):
             "best": summary, "all": rows}
 
 
-def cpu_baseline(spec, W, out_gpu, out64, out_nz=None, surr_img=None):
+def cpu_baseline(spec, W, out_gpu, out64, out_nz=None, surr_img=None, out_df=None):
     """Time the FP64 CPU oracle on a bounded seeded sample of the same image
     (all host cores), and use that same sample to state the GPU path's
     end-point error against it."""
@@ -684,6 +710,8 @@ def cpu_baseline(spec, W, out_gpu, out64, out_nz=None, surr_img=None):
             acc["fp64"] = errs(out64)
         if out_nz is not None:
             acc["fp32_no_zone"] = errs(out_nz)
+        if out_df is not None:
+            acc["fp32_zone_float_float"] = errs(out_df)
     except Exception as exc:  # accuracy is a report, not the measurement
         acc = {"error": repr(exc)}
     if surr_img is not None:

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libkerr.so")
 UNITS = ["kerr_api.cu", "kerr_trace_f32.cu", "kerr_trace_f32b.cu", "kerr_trace_f32x2.cu", "kerr_trace_zone.cu",
-         "kerr_trace_f64.cu", "kerr_static.cu", "kerr_surrogate.cu", "kerr_mlp_tc.cu",
+         "kerr_trace_f64.cu", "kerr_static.cu", "kerr_surrogate.cu", "kerr_mlp_tc.cu", "kerr_gemm_tc.cu",
          "kerr_fixed.cu", "kerr_coordtime.cu",
          "kerr_dense.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -78,14 +78,51 @@ __global__ void to_bf16_kernel(const float *__restrict__ src, bf16 *__restrict__
         dst[i] = __float2bfloat16(src[i]);
 }
 
-// Network input rows [n][16] (bf16, 4 live) from in [n][4].
-__global__ void input_kernel(const float *__restrict__ in, bf16 *__restrict__ A0, int64_t n)
+// Per-step values of a training run, computed on the device by
+// train_step_kernel at the start of each step (so that every step is the
+// same captured graph): the batch's first row, its epoch, the scheduled
+// learning rate and Adam's bias corrections.
+struct StepCtl {
+    long long k;       // steps taken in this run
+    long long r0;      // first row of this step's batch
+    int ep;            // epoch of this step
+    float lr, c1, c2;
+};
+
+// Step k's values; sched[k] = (learning rate, Adam bias corrections) from
+// the host (cosine schedule, 1 / (1 - beta^t)).
+__global__ void train_step_kernel(StepCtl *ctl, const float3 *__restrict__ sched,
+                                  long long steps_per_epoch, long long batch)
 {
+    if (threadIdx.x != 0 || blockIdx.x != 0)
+        return;
+    const long long k = ctl->k;
+    ctl->r0 = (k % steps_per_epoch) * batch;
+    ctl->ep = (int)(k / steps_per_epoch);
+    const float3 v = sched[k];
+    ctl->lr = v.x;
+    ctl->c1 = v.y;
+    ctl->c2 = v.z;
+    ctl->k = k + 1;
+}
+
+// Network input rows [n][16] (bf16, 4 live) from in [n][4]; with A0T also
+// the transposed copy [16][ldT] (training: the batch-contracted operand of
+// the first layer's weight gradient).
+__global__ void input_kernel(const float *__restrict__ in, bf16 *__restrict__ A0, int64_t n,
+                             bf16 *__restrict__ A0T = nullptr, int64_t ldT = 0,
+                             const StepCtl *__restrict__ ctl = nullptr)
+{
+    if (ctl)
+        in += ctl->r0 * kIn;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * kInPad;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i / kInPad;
         const int c = (int)(i % kInPad);
-        A0[i] = __float2bfloat16(c < kIn ? in[r * kIn + c] : 0.0f);
+        const bf16 v = __float2bfloat16(c < kIn ? in[r * kIn + c] : 0.0f);
+        A0[i] = v;
+        if (A0T)
+            A0T[c * ldT + r] = v;
     }
 }
 
@@ -94,28 +131,44 @@ __global__ void input_kernel(const float *__restrict__ in, bf16 *__restrict__ A0
 // gradient of the batch mean goes to dOut [n][64] (bf16, padding zero).
 __global__ void loss_kernel(const float *__restrict__ out, const float *__restrict__ tgt,
                             const float *__restrict__ msk, int64_t n, float inv_n,
-                            bf16 *__restrict__ dOut, float *__restrict__ loss_sum)
+                            bf16 *__restrict__ dOut, float *__restrict__ loss_sum,
+                            bf16 *__restrict__ dOutT, int64_t ldT,
+                            const StepCtl *__restrict__ ctl = nullptr)
 {
+    if (ctl) {
+        tgt += ctl->r0 * kOut;
+        msk += ctl->r0 * kOut;
+        loss_sum += ctl->ep;
+    }
     float local = 0.0f;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x) {
         const float *o = out + r * kOutPad;
         const float *y = tgt + r * kOut;
         const float *m = msk + r * kOut;
-        bf16 *d = dOut + r * kOutPad;
         const float z = o[0];
         const float sp = z > 0.f ? z + log1pf(__expf(-z)) : log1pf(__expf(z));
         local += sp - y[0] * z;
         const float sig = 1.0f / (1.0f + __expf(-z));
-        d[0] = __float2bfloat16((sig - y[0]) * inv_n);
+        __align__(16) bf16 dv[kOut];
+        dv[0] = __float2bfloat16((sig - y[0]) * inv_n);
 #pragma unroll
         for (int j = 1; j < kOut; ++j) {
             const float e = m[j] * (o[j] - y[j]);
             local += e * (o[j] - y[j]);
-            d[j] = __float2bfloat16(2.0f * e * inv_n);
+            dv[j] = __float2bfloat16(2.0f * e * inv_n);
         }
-        for (int j = kOut; j < kOutPad; ++j)
-            d[j] = __float2bfloat16(0.0f);
+        // the row's 64 gradient entries (8 live) as eight 16-byte stores
+        uint4 *d = reinterpret_cast<uint4 *>(dOut + r * kOutPad);
+        d[0] = *reinterpret_cast<const uint4 *>(dv);
+#pragma unroll
+        for (int q = 1; q < kOutPad / 8; ++q)
+            d[q] = make_uint4(0u, 0u, 0u, 0u);
+        if (dOutT) {
+#pragma unroll
+            for (int j = 0; j < kOut; ++j)
+                dOutT[j * ldT + r] = dv[j];     // rows 8..63 of dOutT stay zero
+        }
     }
     // block reduction
     __shared__ float red[32];
@@ -133,23 +186,6 @@ __global__ void loss_kernel(const float *__restrict__ out, const float *__restri
     }
 }
 
-// dZ = dA * silu'(Z) (bf16 out) for [n][w]; column sums of dZ added to db.
-__global__ void silu_back_kernel(const float *__restrict__ dA, const float *__restrict__ Z,
-                                 bf16 *__restrict__ dZ, int64_t n, int w, float *__restrict__ db)
-{
-    // one thread per column, rows strided over blockIdx.y
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= w)
-        return;
-    float s = 0.0f;
-    for (int64_t r = blockIdx.y; r < n; r += gridDim.y) {
-        const float g = dA[r * w + c] * silu_grad(Z[r * w + c]);
-        dZ[r * w + c] = __float2bfloat16(g);
-        s += g;
-    }
-    atomicAdd(&db[c], s);
-}
-
 // Column sums of a bf16 [n][w] matrix into db (output-layer bias gradient).
 __global__ void colsum_kernel(const bf16 *__restrict__ X, int64_t n, int w, float *__restrict__ db)
 {
@@ -160,31 +196,6 @@ __global__ void colsum_kernel(const bf16 *__restrict__ X, int64_t n, int w, floa
     for (int64_t r = blockIdx.y; r < n; r += gridDim.y)
         s += __bfloat162float(X[r * w + c]);
     atomicAdd(&db[c], s);
-}
-
-// Adam on the whole parameter vector; refreshes the bf16 copy of each weight.
-// dst [cols][ld] = src [rows][cols] transposed (bf16); columns rows .. ld-1
-// of dst are zero (ld a multiple of 8, so that the GEMM's 16-byte loads of
-// dst rows stay inside them).  32 x 32 tiles through shared memory.
-__global__ void transpose_bf16_kernel(const bf16 *__restrict__ src, int64_t rows, int cols,
-                                      int64_t ld, bf16 *__restrict__ dst)
-{
-    __shared__ bf16 tile[32][34];
-    const int64_t r0 = (int64_t)blockIdx.x * 32;
-    const int c0 = blockIdx.y * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
-    for (int j = ty; j < 32; j += 8) {
-        const int64_t r = r0 + j;
-        const int c = c0 + tx;
-        tile[j][tx] = (r < rows && c < cols) ? src[r * cols + c] : __float2bfloat16(0.0f);
-    }
-    __syncthreads();
-    for (int j = ty; j < 32; j += 8) {
-        const int c = c0 + j;
-        const int64_t r = r0 + tx;
-        if (c < cols && r < ld)
-            dst[(int64_t)c * ld + r] = tile[tx][j];
-    }
 }
 
 // Transposed bf16 copy of every weight matrix: layer l's W [out][in] at the
@@ -206,10 +217,15 @@ __global__ void transpose_weights_kernel(const bf16 *__restrict__ wbf, bf16 *__r
     }
 }
 
+// Adam on the whole parameter vector; refreshes the bf16 copy of each weight.
+// The transposed bf16 copy (see transpose_weights_kernel) is written in the
+// same pass; learning rate and bias corrections come from the step control.
 __global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g,
                             float *__restrict__ m, float *__restrict__ v, bf16 *__restrict__ wbf,
-                            int64_t n, float lr, float b1, float b2, float c1, float c2, float eps)
+                            bf16 *__restrict__ wbfT, WOffsets o, int64_t n,
+                            const StepCtl *__restrict__ ctl, float b1, float b2, float eps)
 {
+    const float lr = ctl->lr, c1 = ctl->c1, c2 = ctl->c2;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -219,7 +235,16 @@ __global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g,
         v[i] = vi;
         const float wi = w[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
         w[i] = wi;
-        wbf[i] = __float2bfloat16(wi);
+        const bf16 wb = __float2bfloat16(wi);
+        wbf[i] = wb;
+        int l = 0;
+        while (l + 1 < kLayers && i >= o.w[l + 1])
+            ++l;
+        const int64_t j = i - o.w[l];
+        if (j < (int64_t)out_dim(l) * in_dim(l)) {            // weights, not biases
+            const int K = in_dim(l), N = out_dim(l);
+            wbfT[o.w[l] + (j % K) * N + j / K] = wb;
+        }
     }
 }
 
@@ -229,19 +254,20 @@ int grid_1d(int64_t n, int block = 256)
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
 }
 
-template <bool TA, bool TB, int EPI>
+// C = A B^T with epilogue EPI on the tensor cores (kerr_gemm_tc.cu); a
+// pipeline wait that gives up sets *err (checked after the call).
+template <int EPI>
 cudaError_t gemm(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K, EpiArgs e,
-                 cudaStream_t s, int splits = 1)
+                 unsigned *err, cudaStream_t s, int splits = 1)
 {
-    const int kchunk = ((K + splits - 1) / splits + GBK - 1) / GBK * GBK;
-    splits = (K + kchunk - 1) / kchunk;
-    dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, splits);
-    gemm_bf16<TA, TB, EPI><<<grid, 128, 0, s>>>(A, lda, B, ldb, M, N, K, kchunk, e);
-    return cudaGetLastError();
+    return gemm_tc(A, lda, B, ldb, M, N, K, EPI, e, splits, err, s);
 }
 
-// Split count for a weight gradient contracted over `rows` batch rows.
-int wsplits(int64_t rows) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, rows / 512)); }
+// Split count for a weight gradient contracted over `rows` batch rows: about
+// four 64-row slices per CTA, so that the four 128 x 128 output tiles of a
+// hidden layer spread over ~128 CTAs (each adds its partial tile with
+// coalesced atomics).
+int wsplits(int64_t rows) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, rows / 256)); }
 
 } // namespace
 
@@ -292,9 +318,13 @@ struct kerr_surrogate {
     float *Z[kLayers - 1] = {};   // hidden pre-activations [cap][256]
     float *out = nullptr;         // [cap][64]
     bf16 *dOut = nullptr;         // [cap][64]
-    float *dA = nullptr;          // [cap][256]
-    bf16 *dZ = nullptr;           // [cap][256]
-    bf16 *T1 = nullptr, *T2 = nullptr;   // transposed batch operands [256][ldT]
+    bf16 *dZ[2] = {};             // [cap][256] hidden-layer gradients (two layers in flight)
+    // transposed batch operands of the weight gradients (row stride ldT,
+    // columns >= the batch's rows kept zero): AT[l] = A[l]^T [in_dim(l)][ldT],
+    // DT[i] = dZ[i]^T [256][ldT], OT = dOut^T [64][ldT]
+    bf16 *AT[kLayers] = {};
+    bf16 *DT[2] = {};
+    bf16 *OT = nullptr;
     int64_t ldT = 0;
     bf16 *wbfT = nullptr;         // transposed bf16 weights (same offsets)
     float *loss = nullptr;        // [1]
@@ -312,14 +342,17 @@ static void free_batch(kerr_surrogate *s)
         cudaFree(s->Z[l]), s->Z[l] = nullptr;
     cudaFree(s->out);
     cudaFree(s->dOut);
-    cudaFree(s->dA);
-    cudaFree(s->dZ);
-    cudaFree(s->T1);
-    cudaFree(s->T2);
-    s->T1 = s->T2 = nullptr;
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(s->dZ[i]), s->dZ[i] = nullptr;
+        cudaFree(s->DT[i]), s->DT[i] = nullptr;
+    }
+    for (int l = 0; l < kLayers; ++l)
+        cudaFree(s->AT[l]), s->AT[l] = nullptr;
+    cudaFree(s->OT);
+    s->OT = nullptr;
     s->ldT = 0;
-    s->out = s->dA = nullptr;
-    s->dOut = s->dZ = nullptr;
+    s->out = nullptr;
+    s->dOut = nullptr;
     s->cap = 0;
 }
 
@@ -338,15 +371,21 @@ static int ensure_batch(kerr_surrogate *s, int64_t rows, bool training)
             e = cudaMalloc(&s->Z[l], (size_t)rows * kHidden * sizeof(float));
         if (e == cudaSuccess)
             e = cudaMalloc(&s->dOut, (size_t)rows * kOutPad * sizeof(bf16));
-        if (e == cudaSuccess)
-            e = cudaMalloc(&s->dA, (size_t)rows * kHidden * sizeof(float));
-        if (e == cudaSuccess)
-            e = cudaMalloc(&s->dZ, (size_t)rows * kHidden * sizeof(bf16));
+        for (int i = 0; i < 2; ++i)
+            if (e == cudaSuccess)
+                e = cudaMalloc(&s->dZ[i], (size_t)rows * kHidden * sizeof(bf16));
         const int64_t ldT = (rows + 7) / 8 * 8;
-        if (e == cudaSuccess)
-            e = cudaMalloc(&s->T1, (size_t)kHidden * ldT * sizeof(bf16));
-        if (e == cudaSuccess)
-            e = cudaMalloc(&s->T2, (size_t)kHidden * ldT * sizeof(bf16));
+        auto zalloc = [&](bf16 **p, int64_t h) {
+            if (e == cudaSuccess)
+                e = cudaMalloc(p, (size_t)h * ldT * sizeof(bf16));
+            if (e == cudaSuccess)
+                e = cudaMemset(*p, 0, (size_t)h * ldT * sizeof(bf16));
+        };
+        for (int l = 0; l < kLayers; ++l)
+            zalloc(&s->AT[l], in_dim(l));
+        zalloc(&s->DT[0], kHidden);
+        zalloc(&s->DT[1], kHidden);
+        zalloc(&s->OT, kOutPad);
         if (e == cudaSuccess)
             s->ldT = ldT;
     }
@@ -422,6 +461,8 @@ extern "C" int kerr_surrogate_create(const float *init, kerr_surrogate **out)
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
     if (e == cudaSuccess)
+        e = gemm_tc_prepare();
+    if (e == cudaSuccess)
         e = cudaMemcpy(s->w, init, n * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemset(s->g, 0, n * sizeof(float));
@@ -480,82 +521,96 @@ static cudaError_t forward_rows(kerr_surrogate *s, int64_t rows, bool training, 
             if (training) {
                 ea.C = s->Z[l];
                 ea.ldc = N;
-                e = gemm<false, false, EPI_BIAS_SILU>(s->A[l], K, W, K, (int)rows, N, K, ea, st);
+                ea.AoutT = s->AT[l + 1];     // transposed activations for the weight gradient
+                ea.ldT = s->ldT;
+                e = gemm<EPI_BIAS_SILU>(s->A[l], K, W, K, (int)rows, N, K, ea, s->tc_err, st);
             } else {
-                e = gemm<false, false, EPI_BIAS_SILU_BF16>(s->A[l], K, W, K, (int)rows, N, K, ea,
-                                                          st);
+                e = gemm<EPI_BIAS_SILU_BF16>(s->A[l], K, W, K, (int)rows, N, K, ea, s->tc_err,
+                                             st);
             }
         } else {
             ea.C = s->out;
             ea.ldc = N;
-            e = gemm<false, false, EPI_BIAS_F32>(s->A[l], K, W, K, (int)rows, N, K, ea, st);
+            e = gemm<EPI_BIAS_F32>(s->A[l], K, W, K, (int)rows, N, K, ea, s->tc_err, st);
         }
     }
     return e;
 }
 
 // Backward pass after forward_rows(training) and loss_kernel: gradients of
-// the batch accumulate into s->g (zeroed first).
+// the batch accumulate into s->g (zeroed first).  Each hidden layer's
+// gradient comes out of the previous GEMM's epilogue already multiplied by
+// the SiLU derivative, with its transpose and bias gradient.  The weight gradients
+// contract over the batch rows, rounded up to a multiple of 8 (the
+// transposed operands are zero from `rows` on).
 static cudaError_t backward_rows(kerr_surrogate *s, int64_t rows, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(s->g, 0, kL.total * sizeof(float), st);
     const int R = (int)rows;
-    const int LT = (int)s->ldT;
-    const int ygrid = (int)std::min<int64_t>(rows, 512);
-    const dim3 tb(32, 8);
-    // dst [cols][ldT] = src [rows][cols]^T: batch rows become the contiguous
-    // contraction dimension of the weight-gradient GEMMs
-    auto transpose = [&](const bf16 *src, int cols, bf16 *dst) {
-        transpose_bf16_kernel<<<dim3((unsigned)((LT + 31) / 32), (unsigned)((cols + 31) / 32)),
-                                tb, 0, st>>>(src, rows, cols, LT, dst);
-        return cudaGetLastError();
-    };
-    // dW_l [N][K] += D^T A_l over the batch, D = dOut or dZ ([R][N])
-    auto weight_grad = [&](const bf16 *D, int l) {
+    const int R8 = (R + 7) / 8 * 8;
+    const int64_t LT = s->ldT;
+    if (R8 > R) {
+        // columns R .. R8-1 of the transposed operands may hold an earlier,
+        // larger batch's values
+        auto clear_tail = [&](bf16 *p, int h) {
+            if (e == cudaSuccess)
+                e = cudaMemset2DAsync(p + R, LT * sizeof(bf16), 0, (R8 - R) * sizeof(bf16), h,
+                                      st);
+        };
+        for (int l = 0; l < kLayers; ++l)
+            clear_tail(s->AT[l], in_dim(l));
+        clear_tail(s->DT[0], kHidden);
+        clear_tail(s->DT[1], kHidden);
+        clear_tail(s->OT, kOutPad);
+    }
+    // dW_l [N][K] += D^T A_l over the batch, with DT = D^T [N][LT] and
+    // AT[l] = A_l^T [K][LT] written by the producers
+    auto weight_grad = [&](const bf16 *DT, int l) {
         const int K = in_dim(l), N = out_dim(l);
-        cudaError_t r = transpose(D, N, s->T1);
-        if (r == cudaSuccess)
-            r = transpose(s->A[l], K, s->T2);
         EpiArgs ea;
         std::memset(&ea, 0, sizeof ea);
         ea.C = s->g + kL.w[l];
         ea.ldc = K;
-        if (r == cudaSuccess)
-            r = gemm<false, false, EPI_F32_ATOMIC>(s->T1, LT, s->T2, LT, N, K, LT, ea, st,
-                                                   wsplits(rows));
-        return r;
+        return gemm<EPI_F32_ATOMIC>(DT, (int)LT, s->AT[l], (int)LT, N, K, R8, ea, s->tc_err, st,
+                                    wsplits(rows));
     };
-    // dA [R][K] = D W_l, with W_l^T [K][N] as the B operand
-    auto input_grad = [&](const bf16 *D, int l) {
+    // gradient into layer l's input through the previous layer's SiLU:
+    // dZ_{l-1} = (D W_l) * silu'(Z_{l-1}) with W_l^T [K][N] as the B operand,
+    // written to dZ[i] and DT[i] with the bias gradient of layer l - 1
+    auto input_grad = [&](const bf16 *D, int l, int i) {
         const int K = in_dim(l), N = out_dim(l);
         EpiArgs eb;
         std::memset(&eb, 0, sizeof eb);
-        eb.C = s->dA;
+        eb.Zin = s->Z[l - 1];
         eb.ldc = K;
-        return gemm<false, false, EPI_F32>(D, N, s->wbfT + kL.w[l], N, R, K, N, eb, st);
+        eb.Aout = s->dZ[i];
+        eb.lda_out = K;
+        eb.AoutT = s->DT[i];
+        eb.ldT = LT;
+        eb.dbias = s->g + kL.b[l - 1];
+        return gemm<EPI_DSILU>(D, N, s->wbfT + kL.w[l], N, R, K, N, eb, s->tc_err, st);
     };
+    const int ygrid = (int)std::min<int64_t>(rows, 512);
     // output layer
+    int cur = 0;
     {
         const int l = kLayers - 1, N = out_dim(l);
         if (e == cudaSuccess)
-            e = weight_grad(s->dOut, l);
+            e = weight_grad(s->OT, l);
         if (e == cudaSuccess) {
             colsum_kernel<<<dim3((N + 127) / 128, ygrid), 128, 0, st>>>(s->dOut, rows, N,
                                                                         s->g + kL.b[l]);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess)
-            e = input_grad(s->dOut, l);
+            e = input_grad(s->dOut, l, cur);
     }
+    // hidden layers: dZ[cur] / DT[cur] hold layer l's output gradient
     for (int l = kLayers - 2; l >= 0 && e == cudaSuccess; --l) {
-        const int N = out_dim(l);
-        silu_back_kernel<<<dim3((N + 127) / 128, ygrid), 128, 0, st>>>(s->dA, s->Z[l], s->dZ, rows,
-                                                                       N, s->g + kL.b[l]);
-        e = cudaGetLastError();
-        if (e == cudaSuccess)
-            e = weight_grad(s->dZ, l);
+        e = weight_grad(s->DT[cur], l);
         if (l > 0 && e == cudaSuccess)
-            e = input_grad(s->dZ, l);
+            e = input_grad(s->dZ[cur], l, cur ^ 1);
+        cur ^= 1;
     }
     return e;
 }
@@ -587,7 +642,7 @@ static int check_tc(kerr_surrogate *s)
     SURR_CUDA(cudaMemcpy(&h, s->tc_err, sizeof h, cudaMemcpyDeviceToHost));
     if (h) {
         cudaMemset(s->tc_err, 0, sizeof h);
-        return fail(KERR_ECUDA, "surrogate forward: tensor-core pipeline wait timed out");
+        return fail(KERR_ECUDA, "surrogate: tensor-core pipeline wait timed out");
     }
     return KERR_OK;
 }
@@ -629,8 +684,13 @@ extern "C" int kerr_surrogate_forward_impl(kerr_surrogate *s, const float *in, i
     if (rc || n == 0)
         return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    if (impl == KERR_SURR_FWD_GEMM)
-        return forward_gemm(s, in, n, out, st);
+    if (impl == KERR_SURR_FWD_GEMM) {
+        rc = forward_gemm(s, in, n, out, st);
+        if (rc)
+            return rc;
+        SURR_CUDA(cudaStreamSynchronize(st));
+        return check_tc(s);
+    }
     rc = forward_fused(s, in, n, out, st);
     if (rc)
         return rc;
@@ -650,17 +710,20 @@ extern "C" int kerr_surrogate_grad(kerr_surrogate *s, const float *in, const flo
     rc = ensure_batch(s, n, true);
     if (rc)
         return rc;
-    input_kernel<<<grid_1d(n * kInPad), 256, 0, st>>>(in, s->A[0], n);
+    input_kernel<<<grid_1d(n * kInPad), 256, 0, st>>>(in, s->A[0], n, s->AT[0], s->ldT);
     SURR_CUDA(cudaGetLastError());
     SURR_CUDA(forward_rows(s, n, true, st));
     SURR_CUDA(cudaMemsetAsync(s->loss, 0, sizeof(float), st));
-    loss_kernel<<<grid_1d(n), 256, 0, st>>>(s->out, targets, mask, n, 1.0f / (float)n, s->dOut,
-                                            s->loss);
+    loss_kernel<<<grid_1d(n, 64), 64, 0, st>>>(s->out, targets, mask, n, 1.0f / (float)n,
+                                               s->dOut, s->loss, s->OT, s->ldT);
     SURR_CUDA(cudaGetLastError());
     SURR_CUDA(backward_rows(s, n, st));
     float h = 0.f;
     SURR_CUDA(cudaMemcpyAsync(&h, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st));
     SURR_CUDA(cudaStreamSynchronize(st));
+    rc = check_tc(s);
+    if (rc)
+        return rc;
     if (loss)
         *loss = h;
     return KERR_OK;
@@ -682,55 +745,129 @@ extern "C" int kerr_surrogate_train(kerr_surrogate *s, const float *in, const fl
         return rc;
     const int64_t steps_per_epoch = n / B;
     const int64_t total = std::max<int64_t>(1, steps_per_epoch * epochs);
-    float *d_epoch = nullptr;
-    SURR_CUDA(cudaMalloc(&d_epoch, sizeof(float) * epochs));
-    SURR_CUDA(cudaMemsetAsync(d_epoch, 0, sizeof(float) * epochs, st));
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-    int64_t k = 0;
-    for (int ep = 0; ep < epochs; ++ep) {
-        for (int64_t bi = 0; bi < steps_per_epoch; ++bi, ++k) {
-            const int64_t r0 = bi * B;
-            input_kernel<<<grid_1d(B * kInPad), 256, 0, st>>>(in + r0 * kIn, s->A[0], B);
-            cudaError_t e = cudaGetLastError();
-            if (e == cudaSuccess)
-                e = forward_rows(s, B, true, st);
-            if (e == cudaSuccess) {
-                loss_kernel<<<grid_1d(B), 256, 0, st>>>(s->out, targets + r0 * kOut,
-                                                        mask + r0 * kOut, B, 1.0f / (float)B,
-                                                        s->dOut, d_epoch + ep);
-                e = cudaGetLastError();
-            }
-            if (e == cudaSuccess)
-                e = backward_rows(s, B, st);
-            if (e == cudaSuccess) {
-                ++s->step;
-                const double frac = (double)k / (double)total;
-                const float lr_k = (float)(lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(M_PI * frac))));
-                const float c1 = (float)(1.0 / (1.0 - std::pow(b1, (double)s->step)));
-                const float c2 = (float)(1.0 / (1.0 - std::pow(b2, (double)s->step)));
-                adam_kernel<<<grid_1d(kL.total), 256, 0, st>>>(s->w, s->g, s->m, s->v, s->wbf,
-                                                               kL.total, lr_k, b1, b2, c1, c2, eps);
-                transpose_weights_kernel<<<grid_1d(kL.total), 256, 0, st>>>(s->wbf, s->wbfT,
-                                                                            woffsets());
-                e = cudaGetLastError();
-            }
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                cudaFree(d_epoch);
-                return fail(KERR_ECUDA, "kerr_surrogate_train: launch failed");
-            }
-        }
+    // One training step = one fixed sequence of launches whose per-step values
+    // (batch rows, epoch, learning rate, bias corrections) are computed on the
+    // device: it is captured once as a CUDA graph of U steps and replayed, on
+    // a private stream ordered after the caller's.
+    float *d_epoch = nullptr;
+    StepCtl *ctl = nullptr;
+    float3 *sched = nullptr;
+    // cosine learning-rate schedule from lr down to 0.05 lr over the run, and
+    // Adam's bias corrections 1 / (1 - beta^t) at t = step0 + k + 1
+    std::vector<float3> hs((size_t)total);
+    for (int64_t k = 0; k < total; ++k) {
+        const double frac = (double)k / (double)total;
+        const double t = (double)(s->step + k + 1);
+        hs[k] = make_float3((float)(lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(M_PI * frac)))),
+                            (float)(1.0 / (1.0 - std::pow((double)b1, t))),
+                            (float)(1.0 / (1.0 - std::pow((double)b2, t))));
     }
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaGraph_t gU = nullptr, g1 = nullptr;
+    cudaGraphExec_t xU = nullptr, x1 = nullptr;
+    auto enqueue_step = [&](cudaStream_t q) -> cudaError_t {
+        train_step_kernel<<<1, 32, 0, q>>>(ctl, sched, steps_per_epoch, B);
+        input_kernel<<<grid_1d(B * kInPad), 256, 0, q>>>(in, s->A[0], B, s->AT[0], s->ldT, ctl);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = forward_rows(s, B, true, q);
+        if (e == cudaSuccess) {
+            loss_kernel<<<grid_1d(B, 64), 64, 0, q>>>(s->out, targets, mask, B, 1.0f / (float)B,
+                                                      s->dOut, d_epoch, s->OT, s->ldT, ctl);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            e = backward_rows(s, B, q);
+        if (e == cudaSuccess) {
+            adam_kernel<<<grid_1d(kL.total), 256, 0, q>>>(s->w, s->g, s->m, s->v, s->wbf, s->wbfT,
+                                                          woffsets(), kL.total, ctl, b1, b2, eps);
+            e = cudaGetLastError();
+        }
+        return e;
+    };
+    auto capture = [&](int steps, cudaGraph_t *g, cudaGraphExec_t *x) -> cudaError_t {
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        for (int u = 0; u < steps && e == cudaSuccess; ++u)
+            e = enqueue_step(cs);
+        cudaGraph_t gg = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &gg);
+        if (e == cudaSuccess)
+            e = e2;
+        *g = gg;
+        if (e == cudaSuccess)
+            e = cudaGraphInstantiate(x, gg, 0);
+        return e;
+    };
+    const int U = (int)std::min<int64_t>(8, total);
+    cudaError_t e = cudaMalloc(&d_epoch, sizeof(float) * epochs);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&ctl, sizeof(StepCtl));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&sched, sizeof(float3) * (size_t)total);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sched, hs.data(), sizeof(float3) * (size_t)total,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&ev1, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(d_epoch, 0, sizeof(float) * epochs, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(ctl, 0, sizeof(StepCtl), st);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(ev0, st);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(cs, ev0, 0);
+    if (e == cudaSuccess)
+        e = capture(U, &gU, &xU);
+    if (e == cudaSuccess && total % U)
+        e = capture(1, &g1, &x1);
+    for (int64_t i = 0; i < total / U && e == cudaSuccess; ++i)
+        e = cudaGraphLaunch(xU, cs);
+    for (int64_t i = 0; i < total % U && e == cudaSuccess; ++i)
+        e = cudaGraphLaunch(x1, cs);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(ev1, cs);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(st, ev1, 0);
     std::vector<float> h(epochs);
-    cudaError_t e = cudaMemcpyAsync(h.data(), d_epoch, sizeof(float) * epochs,
-                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), d_epoch, sizeof(float) * epochs, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess)
+        s->step += total;
+    if (xU)
+        cudaGraphExecDestroy(xU);
+    if (x1)
+        cudaGraphExecDestroy(x1);
+    if (gU)
+        cudaGraphDestroy(gU);
+    if (g1)
+        cudaGraphDestroy(g1);
+    if (cs) {
+        cudaStreamSynchronize(cs);
+        cudaStreamDestroy(cs);
+    }
+    if (ev0)
+        cudaEventDestroy(ev0);
+    if (ev1)
+        cudaEventDestroy(ev1);
     cudaFree(d_epoch);
+    cudaFree(ctl);
+    cudaFree(sched);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(KERR_ECUDA, "kerr_surrogate_train: synchronisation failed");
+        return fail(KERR_ECUDA, "kerr_surrogate_train: launch failed");
     }
+    rc = check_tc(s);
+    if (rc)
+        return rc;
     if (loss_per_epoch)
         for (int ep = 0; ep < epochs; ++ep)
             loss_per_epoch[ep] = h[ep] / (float)std::max<int64_t>(1, steps_per_epoch);

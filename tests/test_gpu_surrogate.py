@@ -39,8 +39,8 @@ def dev(a):
 @pytest.mark.parametrize("impl", [K.SURR_FWD_TENSOR_CORE, K.SURR_FWD_GEMM])
 @pytest.mark.parametrize("n", [1, 128, 129, 3000])
 def test_forward_matches_reference_network(impl, n):
-    """Both forward implementations (the fused tcgen05 kernel, 128-row tiles;
-    the layer-by-layer GEMMs, 64-row tiles) against the FP64 reference
+    """Both forward implementations (the fused tcgen05 kernel; the
+    layer-by-layer tcgen05 GEMMs of the training path) against the FP64 reference
     network with the same bfloat16 rounding points, on ragged row counts."""
     p = M.init_params(11)
     p[M.B_OFF[1]:M.B_OFF[1] + 256] = np.random.default_rng(2).normal(size=256) * 0.2
@@ -78,10 +78,15 @@ def test_fused_forward_many_tiles_per_cta():
     s.close()
 
 
-def test_gradient_matches_reference_network():
+@pytest.mark.parametrize("n", [4096, 1000, 37])
+def test_gradient_matches_reference_network(n):
+    """Weight, bias and loss gradients of the tensor-core training GEMMs
+    against the FP64 reference network, on batches that fill whole tiles and
+    on ragged ones (partial row tiles, a partial last K slice of the
+    batch-contracted weight gradients, split-K)."""
     p = M.init_params(12)
     s = K.Surrogate(p)
-    x, y, m = random_batch(4096, 6)
+    x, y, m = random_batch(n, 6)
     loss = K.kerr_surrogate_grad(s, dev(x), dev(y), dev(m))
     g = s.grad().astype(np.float64)
     Lq, gq = M.grad(p.astype(np.float64), x, y, m, quantize=True)
