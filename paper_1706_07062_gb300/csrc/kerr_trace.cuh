@@ -665,18 +665,23 @@ __device__ __forceinline__ int step_post(const RayConst &rc, const TraceParams &
     const T rcap = RC<T>::rcap(rc);
     const T resc = RC<T>::resc(rc);
     const int maxit = P.clip_maxit;
+    // event surfaces to stol x scale; an FP64 (or float-float) zone step of
+    // the FP32+Kahan path (FAST_FACTOR), whose end points are good to ~1e-6,
+    // places them to 1e-10, which the regula falsi reaches in fewer
+    // single-lane iterations than the FP64 path's 1e-12
+    const T stol = FAST_FACTOR ? T(1e-10) : Prec<T>::stol();
     int st = ST_NONE;
     T h_used = h;
     if (rn < rcap) {
         const T s_lo = event_value<KAHAN>(0, a2, y, c, rcap, T(0));
         h_used = clip<KAHAN, T, RM>(a, a2, y, c, A0, h, 0, rcap, T(0), s_lo, rn - rcap,
-                             Prec<T>::stol() * rcap, Prec<T>::eps(), maxit, yn, cn, nrhs);
+                             stol * rcap, Prec<T>::eps(), maxit, yn, cn, nrhs);
         st = ST_CAPTURED;
     } else if (rn > resc && k_fma(yn[1], yn[5], k_fma(yn[2], yn[6], yn[3] * yn[7])) > T(0)) {
         const T s_lo = event_value<KAHAN>(0, a2, y, c, resc, T(0));
         if (s_lo <= T(0))
             h_used = clip<KAHAN, T, RM>(a, a2, y, c, A0, h, 0, resc, T(0), s_lo, rn - resc,
-                                 Prec<T>::stol() * resc, Prec<T>::eps(), maxit, yn, cn, nrhs);
+                                 stol * resc, Prec<T>::eps(), maxit, yn, cn, nrhs);
         st = ST_ESCAPED;
     } else if (rc.use_t) {
         const T tend = RC<T>::tend(rc), tlo = RC<T>::tendlo(rc);
@@ -685,7 +690,7 @@ __device__ __forceinline__ int step_post(const RayConst &rc, const TraceParams &
             const T s_lo = event_value<KAHAN>(1, a2, y, c, tend, tlo);
             const T sc = fmax(T(1), fabs(tend));
             h_used = clip<KAHAN, T, RM>(a, a2, y, c, A0, h, 1, tend, tlo, s_lo, s_hi,
-                                 Prec<T>::stol() * sc, Prec<T>::eps(), maxit, yn, cn, nrhs);
+                                 stol * sc, Prec<T>::eps(), maxit, yn, cn, nrhs);
             st = ST_ENDTIME;
         }
     }
