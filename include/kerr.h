@@ -338,9 +338,10 @@ int kerr_surrogate_forward(kerr_surrogate *s, const float *in, int64_t n, float 
 
 /* The same forward on a chosen implementation: KERR_SURR_FWD_TENSOR_CORE
  * (as kerr_surrogate_forward) or KERR_SURR_FWD_GEMM (the layer-by-layer
- * mma.sync GEMM kernels of the training path; asynchronous).  Both compute
- * bf16 operands with fp32 accumulation; results differ by accumulation
- * order only. */
+ * tcgen05 GEMM kernels of the training path, one launch per layer).  Both
+ * compute bf16 operands with fp32 accumulation; results differ by
+ * accumulation order only.  Both synchronise `stream` and return KERR_ECUDA
+ * if a tensor-core pipeline wait timed out. */
 #define KERR_SURR_FWD_TENSOR_CORE 0
 #define KERR_SURR_FWD_GEMM 1
 int kerr_surrogate_forward_impl(kerr_surrogate *s, const float *in, int64_t n, float *out,
@@ -356,7 +357,11 @@ int kerr_surrogate_grad(kerr_surrogate *s, const float *in, const float *targets
 /* Trains with Adam (beta1 0.9, beta2 0.999, eps 1e-8) on n rows for `epochs`
  * passes in order, `batch` rows per step, learning rate lr decayed by cosine
  * to lr/20 over all steps.  loss_per_epoch (host, `epochs` floats, or NULL)
- * receives the mean batch loss of each epoch.  Synchronises `stream`. */
+ * receives the mean batch loss of each epoch.  The steps run on a private
+ * stream ordered after `stream`, replayed from a CUDA graph captured by the
+ * call (the per-step batch offset, schedule and bias corrections are read on
+ * the device).  Synchronises `stream`; KERR_ECUDA if a launch failed or a
+ * tensor-core pipeline wait timed out. */
 int kerr_surrogate_train(kerr_surrogate *s, const float *in, const float *targets,
                          const float *mask, int64_t n, int32_t epochs, int32_t batch, float lr,
                          float *loss_per_epoch, void *stream);
