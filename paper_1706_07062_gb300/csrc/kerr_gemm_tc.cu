@@ -247,8 +247,6 @@ __global__ void __launch_bounds__(TTHREADS)
                         float *cp = e.C + (size_t)grow * e.ldc + col;
                         if (EPI == EPI_F32_ATOMIC)
                             atomicAdd(cp, z);
-                        else if (EPI == EPI_F32_ACC)
-                            *cp += z;
                         else
                             *cp = z;
                     }
@@ -282,8 +280,6 @@ template <int BN, int EPI> cudaError_t set_smem_attr()
 template <int BN> cudaError_t set_smem_attrs()
 {
     cudaError_t e = set_smem_attr<BN, EPI_F32>();
-    if (e == cudaSuccess)
-        e = set_smem_attr<BN, EPI_F32_ACC>();
     if (e == cudaSuccess)
         e = set_smem_attr<BN, EPI_BIAS_SILU>();
     if (e == cudaSuccess)
@@ -347,8 +343,6 @@ cudaError_t gemm_tc(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N
     switch (epi) {
     case EPI_F32:
         return launch_bn<EPI_F32>(bn, A, lda, B, ldb, M, N, K, splits, e, err, s);
-    case EPI_F32_ACC:
-        return launch_bn<EPI_F32_ACC>(bn, A, lda, B, ldb, M, N, K, splits, e, err, s);
     case EPI_BIAS_SILU:
         return launch_bn<EPI_BIAS_SILU>(bn, A, lda, B, ldb, M, N, K, splits, e, err, s);
     case EPI_BIAS_F32:

@@ -25,7 +25,6 @@ __host__ __device__ constexpr int out_dim(int l) { return l == kLayers - 1 ? kOu
 // Epilogues of the GEMM.
 enum Epi : int {
     EPI_F32 = 0,         // C (fp32) = acc
-    EPI_F32_ACC = 1,     // C (fp32) += acc
     EPI_BIAS_SILU = 2,   // Z (fp32) = acc + b;  Aout (bf16) = silu(Z)
     EPI_BIAS_F32 = 3,    // C (fp32) = acc + b
     EPI_BIAS_SILU_BF16 = 4,  // Aout (bf16) = silu(acc + b)  (inference: no Z kept)
