@@ -435,6 +435,9 @@ def run_surrogate(args, K, W, dev, stream):
     t_sur = t_int = 0.0
     n_tot = n_fb = 0
     dis = dis_n = 0
+    # the same renders with the fallback rays' zone steps in float-float
+    opts_df = K.default_opts(zone_prec=K.ZONE_F32X2)
+    t_sur_df = 0.0
     errs = {k: [] for k in ("r1", "phi1", "r2", "phi2", "g1")}
     img0 = None
     for cs in W.surrogate_eval_cameras():
@@ -447,6 +450,9 @@ def run_surrogate(args, K, W, dev, stream):
         (out, fb, nfb), dt = timed(lambda: K.kerr_surrogate_render(ctx, net, cam, opts,
                                                                    stream=stream))
         torch.cuda.nvtx.range_pop()
+        K.kerr_surrogate_render(ctx, net, cam, opts_df, stream=stream)   # warm
+        _, dtd = timed(lambda: K.kerr_surrogate_render(ctx, net, cam, opts_df, stream=stream))
+        t_sur_df += dtd
         _, dti = timed(lambda: K.kerr_trace_camera(ctx, cam, opts, out=ref32, stream=stream))
         ref = K.alloc_out(n, dev, diag=False, cross=True)
         K.kerr_trace_camera(ctx, cam, o64, out=ref, stream=stream)
@@ -491,6 +497,7 @@ def run_surrogate(args, K, W, dev, stream):
                         "r_obs 1000M, +-25M; fallback: p in [0.05,0.95] or within 0.5M of "
                         "the critical curve; integrator FP32+Kahan tol 1e-6",
             "integrator_only": round(v_int, 1), "gain": round(v_sur / v_int, 3),
+            "value_fallback_float_float_zone": round(n_tot / t_sur_df, 1),
             "fallback_frac": round(n_fb / n_tot, 5),
             "capture_disagreement": dis / max(dis_n, 1),
             "reference": "GPU FP64 integrator, tol 1e-6, same images",
