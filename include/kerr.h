@@ -242,9 +242,10 @@ int kerr_num_zone_variants(void);
 int kerr_zone_variant_info(int v, int32_t *block, int32_t *blocks_per_sm);
 
 /* Times every launch configuration for the given precision on `sample`
- * camera rays of cams[0] (spread over the image) and remembers the fastest
- * for later calls with variant == -1 on this context.  Writes the chosen
- * variant to *best. */
+ * camera rays of cams[0] (spread over the image; the two-geodesics-per-thread
+ * variants for KERR_FP32_KAHAN only) and remembers the fastest for later
+ * calls with variant == -1 on this context.  Writes the chosen variant to
+ * *best. */
 int kerr_autotune(kerr_ctx *ctx, const kerr_camera *cam, const kerr_opts *opts,
                   int64_t sample, int32_t *best, void *stream);
 
