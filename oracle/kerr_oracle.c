@@ -415,7 +415,41 @@ typedef struct {
     int32_t renorm_every;/* > 0: every n accepted steps re-solve k^t so that     */
                          /* g k k keeps its initial value; 0: off               */
     int32_t clip_maxit;  /* iterations of the surface root-find                 */
+    /* Conditioning test only (0 = off, the plain integration): every accepted
+     * step that starts at r >= noise_zone * r_h has each component of its
+     * increment y_new - y scaled by (1 + noise * u), u uniform in [-1, 1)
+     * drawn per geodesic, step and component -- a model of the rounding that
+     * FP32 arithmetic leaves in each step of the FP32+Kahan path outside its
+     * FP64 zone.                                                             */
+    double noise;
+    double noise_zone;
+    uint64_t noise_seed;
 } oracle_opts;
+
+/* SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014): the output function applied to a counter.     */
+static uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+/* Uniform in [-1, 1) from 53 random bits. */
+static double uniform_pm1(uint64_t bits) { return (double)(bits >> 11) * 0x1p-52 - 1.0; }
+
+/* Per-geodesic stream of the noise: FNV-1a over the bytes of its start state. */
+static uint64_t state_seed(const double y0[8], uint64_t seed)
+{
+    const unsigned char *p = (const unsigned char *)y0;
+    uint64_t h = 1469598103934665603ull ^ seed;
+    for (int i = 0; i < 64; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
 
 typedef struct {
     int64_t attempts;
@@ -626,6 +660,8 @@ int oracle_trace_one(double a, const double y0[8], const oracle_opts *o, double 
     memcpy(y, y0, sizeof y);
     double h = o->h0;
     int64_t since_renorm = 0;
+    const uint64_t nseed = o->noise > 0.0 ? state_seed(y0, o->noise_seed) : 0;
+    const double noise_r = o->noise_zone * rh;
     int status = ST_MAXSTEPS;
     for (;;) {
         if (cnt->attempts >= o->max_steps) {
@@ -642,6 +678,12 @@ int oracle_trace_one(double a, const double y0[8], const oracle_opts *o, double 
             continue;
         }
         cnt->accepted++;
+        if (o->noise > 0.0 && oracle_ks_r(a, y[1], y[2], y[3]) >= noise_r) {
+            for (int i = 0; i < 8; ++i) {
+                const uint64_t ctr = nseed + 8u * (uint64_t)cnt->accepted + (uint64_t)i;
+                yh[i] = y[i] + (yh[i] - y[i]) * (1.0 + o->noise * uniform_pm1(splitmix64(ctr)));
+            }
+        }
         if (!all_finite(yh)) {
             memcpy(y, yh, sizeof y);
             status = ST_NONFINITE;

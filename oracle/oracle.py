@@ -42,7 +42,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("h0", ctypes.c_double),
                 ("max_steps", ctypes.c_int64), ("r_escape", ctypes.c_double),
                 ("t_end", ctypes.c_double), ("renorm_every", ctypes.c_int32),
-                ("clip_maxit", ctypes.c_int32)]
+                ("clip_maxit", ctypes.c_int32), ("noise", ctypes.c_double),
+                ("noise_zone", ctypes.c_double), ("noise_seed", ctypes.c_uint64)]
 
 
 class _Counts(ctypes.Structure):
@@ -109,10 +110,16 @@ class Opts:
     t_end: float = float("inf")
     renorm_every: int = 0
     clip_maxit: int = 40
+    # conditioning test only: relative perturbation of every accepted
+    # increment that starts outside noise_zone * r_h (0 = off)
+    noise: float = 0.0
+    noise_zone: float = 0.0
+    noise_seed: int = 0
 
     def c(self) -> _Opts:
         return _Opts(self.tol, self.h0, self.max_steps, self.r_escape, self.t_end,
-                     self.renorm_every, self.clip_maxit)
+                     self.renorm_every, self.clip_maxit, self.noise, self.noise_zone,
+                     self.noise_seed)
 
 
 # ---------------------------------------------------------------------------
@@ -244,32 +251,51 @@ def trace(a, y0, opts: Opts, nthreads: int | None = None, t_end=None,
     return TraceResult(yend, status, att, ev, cr)
 
 
+# FP32 rounding model of the conditioning test: each component of each
+# accepted increment outside the FP64 zone perturbed by up to 8 units of FP32
+# roundoff (an increment combines eleven right-hand sides of ~100 FP32
+# operations each), in three independent draws.
+FP32_NOISE = 2.0 ** -21
+FP32_NOISE_SEEDS = (1, 2, 3)
+
+
 def ill_conditioned(a, y0, opts: Opts, ref: TraceResult | None = None,
-                    rel: float = 1e-5, nthreads: int | None = None, t_end=None) -> np.ndarray:
+                    rel: float = 1e-5, nthreads: int | None = None, t_end=None,
+                    noise_zone: float | None = 1.5) -> np.ndarray:
     """Flag rays whose endpoint is not determined to `rel` by the integration.
 
     A ray is ill-conditioned if its end state moves by more than `rel`
-    (relative, in x^i and in k) when (i) the tolerance is tightened 100x, or
-    (ii) the initial spatial position is perturbed by 1e-7 relative, or if
-    its status changes under either.  Rays close to the photon ring amplify
-    perturbations exponentially, so their endpoints are not comparable
+    (relative, in x^i and in k), or its status changes, when (i) the
+    tolerance is tightened 100x, (ii) the initial spatial position is
+    perturbed by 1e-7 relative, or (iii) every accepted step that starts
+    outside noise_zone * r_h carries FP32-sized rounding in its increment
+    (FP32_NOISE, three seeded draws; None skips this test).  Rays close to
+    the photon ring, or spiralling into the horizon, amplify perturbations
+    exponentially -- a perturbation made along the way can matter far more
+    than one made at the start -- so their endpoints are not comparable
     between two correct integrators."""
     y0 = _f64(y0).reshape(-1, 8)
     if ref is None:
         ref = trace(a, y0, opts, nthreads, t_end=t_end)
     tight = Opts(**{**opts.__dict__, "tol": opts.tol / 100.0})
-    r_tight = trace(a, y0, tight, nthreads, t_end=t_end)
+    runs = [trace(a, y0, tight, nthreads, t_end=t_end)]
     yp = y0.copy()
     yp[:, 1:4] *= (1.0 + 1e-7)
-    r_pert = trace(a, yp, opts, nthreads, t_end=t_end)
+    runs.append(trace(a, yp, opts, nthreads, t_end=t_end))
+    if noise_zone is not None:
+        for seed in FP32_NOISE_SEEDS:
+            noisy = Opts(**{**opts.__dict__, "noise": FP32_NOISE, "noise_zone": noise_zone,
+                            "noise_seed": seed})
+            runs.append(trace(a, y0, noisy, nthreads, t_end=t_end))
 
     def rel_err(u, v):
         ex = np.linalg.norm(u[:, 1:4] - v[:, 1:4], axis=1) / np.linalg.norm(v[:, 1:4], axis=1)
         ek = np.linalg.norm(u[:, 4:8] - v[:, 4:8], axis=1) / np.linalg.norm(v[:, 4:8], axis=1)
         return np.maximum(ex, ek)
 
-    bad = (rel_err(r_tight.y, ref.y) > rel) | (r_tight.status != ref.status)
-    bad |= (rel_err(r_pert.y, ref.y) > rel) | (r_pert.status != ref.status)
+    bad = np.zeros(len(y0), dtype=bool)
+    for r in runs:
+        bad |= (rel_err(r.y, ref.y) > rel) | (r.status != ref.status)
     return bad
 
 

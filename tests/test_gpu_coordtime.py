@@ -34,25 +34,66 @@ def run(ctx, y0, w0, t_end, opts):
     return out
 
 
-@pytest.mark.parametrize("prec,tol,gate", [(K.FP64, 1e-10, 1e-8), (K.FP32_KAHAN, 1e-6, 2e-4)])
+def coordtime_err(w, ref_w):
+    """Per-geodesic end-state error max_i |w_i - ref_i| / (1 + |ref_i|) over
+    (x, y, z, v^x, v^y, v^z)."""
+    return np.max(np.abs(w - ref_w) / (1 + np.abs(ref_w)), axis=1)
+
+
+def coordtime_flags(a, y0, w0, t_end, opts, ref, gate, fp32):
+    """Geodesics whose coordinate-time end state is not determined to `gate`:
+    it moves by more than the gate, or the status changes, when the start
+    position is perturbed (1e-12 relative for the FP64 comparison, which
+    follows the oracle's step sequence; 1e-7 for FP32) or, for FP32, when the
+    tolerance is tightened 100x.  Captured geodesics stop at the first step
+    inside 1.01 r_h without clipping, so their end states depend on the step
+    sequence and are flagged whenever it matters."""
+    wp = w0.copy()
+    wp[:, :3] *= 1 + (1e-7 if fp32 else 1e-12)
+    runs = [O.trace_coordtime(a, y0[:, 0], wp, t_end, opts)]
+    if fp32:
+        runs.append(O.trace_coordtime(a, y0[:, 0], w0, t_end,
+                                      O.Opts(**{**opts.__dict__, "tol": opts.tol / 100})))
+    bad = np.zeros(len(w0), dtype=bool)
+    for r in runs:
+        bad |= (coordtime_err(r.w, ref.w) > gate) | (r.status != ref.status)
+    return bad
+
+
+@pytest.mark.parametrize("prec,tol,gate", [(K.FP64, 1e-10, 1e-9), (K.FP32_KAHAN, 1e-8, 1e-5)])
 def test_coordtime_matches_oracle(prec, tol, gate):
+    """End states against the oracle's coordinate-time integrator on every
+    geodesic that reaches the end time and that the oracle finds determined
+    to the gate, and the same status on every well-conditioned geodesic (at
+    most 12 % are not).  Captures are compared by status only: the
+    coordinate-time integrator stops at the first accepted step inside
+    1.01 r_h without clipping, where rounding differences of the two
+    right-hand-side forms, grown along the plunge, move the state by 1e-8 even
+    in FP64 with identical step sequences.  FP32 runs at tol 1e-8: at 1e-6
+    the oracle's own end states move by more than 1e-5 between tol and
+    tol/100."""
     a = 0.9
     ctx = K.kerr_init(a)
     y0, w0 = photons(a)
     t_end = -100.0
     out = run(ctx, y0, w0, t_end, K.default_opts(prec=prec, tol=tol))
-    ref = O.trace_coordtime(a, y0[:, 0], w0, t_end, O.Opts(tol=tol))
+    oo = O.Opts(tol=tol)
+    ref = O.trace_coordtime(a, y0[:, 0], w0, t_end, oo)
+    flags = coordtime_flags(a, y0, w0, t_end, oo, ref, gate, prec == K.FP32_KAHAN)
+    assert flags.mean() <= 0.12, flags.sum()
+    good = ~flags
     st = out.status.cpu().numpy()
     x = out.x.cpu().numpy().T
     v = out.v.cpu().numpy().T
     assert set(np.unique(ref.status)) >= {O.CAPTURED, O.ENDTIME}
-    same = st == ref.status
-    assert same.mean() > 0.98                      # flips only at a termination boundary
-    end = same & (ref.status == O.ENDTIME)
+    assert np.array_equal(st[good], ref.status[good])
+    end = good & (ref.status == O.ENDTIME)
+    assert end.sum() > 200
     assert np.all(x[end, 0] == t_end)              # lands on the end time exactly
-    gpu = np.concatenate([x[:, 1:], v], axis=1)
-    e = np.abs(gpu - ref.w) / (1 + np.abs(ref.w))
-    assert np.median(e[end]) < gate / 10 and np.max(e[end]) < gate, (np.median(e[end]), e[end].max())
+    e = coordtime_err(np.concatenate([x[:, 1:], v], axis=1), ref.w)
+    assert np.all(e[end] <= gate), (np.sort(e[end])[-5:], int(flags.sum()))
+    print(dict(prec=prec, ill_conditioned=int(flags.sum()), max_err_endtime=float(e[end].max()),
+               median_err_endtime=float(np.median(e[end]))))
     s = K.kerr_get_stats(ctx)
     assert s.geodesics == len(y0) and sum(s.status_count) == len(y0)
     ctx.close()

