@@ -38,6 +38,8 @@ FP32_LANES_PER_SM = 128      # FP32 FMA lanes per SM (one FMA = 2 FLOPs)
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (non-tensor) nominal rate
 WORKLOAD = ("camera 1024x1024, a=0.99, i=17deg, r_obs=1000M, +-25M, tol 1e-6, "
             "FP32+Kahan persistent kernel")
+# The autotuner's cache file (per machine; a fresh GPU machine starts empty).
+TUNE_CACHE = os.path.join(os.environ.get("TMPDIR", "/tmp"), "kerr_tune_cache.txt")
 
 
 # Sources of the integrator kernels (the surrogate's files are left out:
@@ -147,6 +149,41 @@ def reduce_step_time(ms: float, device=None) -> float:
     return float(t.item())
 
 
+def measure_alu_peaks(K, dev, stream, target_ms: float = 150.0) -> dict:
+    """Measured FP32 and FP64 pipe rates of this GPU: the FMA-chain kernel
+    (kerr_fma_chain) timed with CUDA events on `stream`, best of three
+    launches of ~target_ms each, with the SM clock sampled meanwhile."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    bps = 4
+    sink = torch.empty(props.multi_processor_count * bps * 256, dtype=torch.float32, device=dev)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(props.uuid)
+    except Exception:
+        uuid = None
+    out = {}
+    for name, kind, guess in (("fp32", K.PEAK_FP32, 70.0), ("fp32x2", K.PEAK_FP32X2, 70.0),
+                              ("fp64", K.PEAK_FP64, 1.2)):
+        # size the launch from a nominal guess, then from a first measurement
+        rounds = max(16, int(guess * 1e12 * target_ms * 1e-3
+                             / (2 * props.multi_processor_count * bps * 256 * 128)))
+        K.kerr_fma_chain(kind, 16, sink, bps, stream=stream)
+        sampler = ClockSampler(uuid)
+        best = None
+        for _ in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fl = K.kerr_fma_chain(kind, rounds, sink, bps, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            tf = fl / (e0.elapsed_time(e1) * 1e-3) / 1e12
+            best = tf if best is None else max(best, tf)
+        clk = sampler.stop()
+        out[name] = {"tflops": round(best, 3), "clocks": clk}
+    return out
+
+
 def job_throughput(units_per_rank: int, world: int, ms_per_step: float) -> float:
     """Whole-job units per second: every rank processes its own units
     (weak scaling) in at most ms_per_step."""
@@ -166,20 +203,33 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
+    from paper_1706_07062_gb300 import shard
+
     spec = W.CAMERA_1024
     cam = K.camera(*spec.as_tuple())
-    n = spec.n
+    n_total = spec.n
     prec = K.FP64 if args.prec == "fp64" else K.FP32_KAHAN
     ctx = K.kerr_init(spec.a)
     opts = K.default_opts(prec=prec, tol=W.TOL_1024)
     if args.autotune:
         opts.variant = K.kerr_autotune(ctx, cam, opts, sample=1 << 16)
-    out = K.alloc_out(n, dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    # one image; with several ranks each traces its interleaved rows of it
+    # (the outputs would be concatenated on the host; no exchange on the GPU)
+    if world > 1:
+        my_pix = torch.from_numpy(shard.row_partition(spec.nx, spec.ny, world, rank)).to(dev)
+        n = int(my_pix.numel())
+    else:
+        my_pix, n = None, n_total
+    out = K.alloc_out(n, dev)
 
-    def step():
-        K.kerr_trace_camera(ctx, cam, opts, out=out, stream=stream)
+    def step(o=None):
+        o = o or out
+        if my_pix is None:
+            K.kerr_trace_camera(ctx, cam, opts, out=o, stream=stream)
+        else:
+            K.kerr_trace_camera_pixels(ctx, cam, my_pix, opts, out=o, stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -189,6 +239,7 @@ def run_ours(args, rank, world, local_rank):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     kern_ms, phase_ms, rhs32, rhs64, att, att64 = [], [], 0, 0, 0, 0
+    rhs32z, att32z = 0, 0
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -211,6 +262,8 @@ def run_ours(args, rank, world, local_rank):
         rhs64 += s.rhs_fp64
         att += s.attempts
         att64 += s.attempts_fp64
+        rhs32z += s.rhs_fp32_zone_phase
+        att32z += s.attempts_fp32_zone_phase
     torch.cuda.synchronize(dev)
     if dist is not None:
         dist.barrier()
@@ -218,12 +271,15 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.stop() if sampler else None
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = reduce_step_time(sum(step_ms) / len(step_ms), dev if dist is not None else None)
-    value = job_throughput(n, world, ms)
+    value = n_total / (ms * 1e-3)
     stats = K.kerr_get_stats(ctx)
 
-    # ---- rooflines (algorithmic FLOPs from the counted right-hand sides)
+    # ---- rooflines (algorithmic FLOPs from the counted right-hand sides),
+    # each phase's FLOPs divided by that phase's own time
     att32 = att - att64
     fl32 = rhs32 * FLOPS_PER_RHS + att32 * FLOPS_PER_ATTEMPT
+    fl32z = rhs32z * FLOPS_PER_RHS + att32z * FLOPS_PER_ATTEMPT   # FP32 steps of the zone phase
+    fl32s = fl32 - fl32z                                          # FP32 stepping phase
     fl64 = rhs64 * FLOPS_PER_RHS + att64 * FLOPS_PER_ATTEMPT
     kms = sum(kern_ms) / len(kern_ms)
     ph = [sum(p[i] for p in phase_ms) / len(phase_ms) for i in range(4)]
@@ -231,24 +287,35 @@ def run_ours(args, rank, world, local_rank):
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak32 = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    peak64 = FP64_NOMINAL_TFLOPS
+    nominal32 = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    alu = measure_alu_peaks(K, dev, stream) if rank == 0 else None
+    if alu:
+        peak32 = max(alu["fp32"]["tflops"], alu["fp32x2"]["tflops"])
+        peak64 = alu["fp64"]["tflops"]
+        src32 = (f"measured: FMA-chain kernel (kerr_fma_chain) in this run, best of fma.f32 "
+                 f"and fma.f32x2 (of measured; nominal {sms} SMs x {FP32_LANES_PER_SM} lanes "
+                 f"x 2 x {sm_max:.0f} MHz = {nominal32:.1f})")
+        src64 = "measured: FMA-chain kernel (kerr_fma_chain, fma.f64) in this run (of measured)"
+    else:
+        peak32, peak64 = nominal32, FP64_NOMINAL_TFLOPS
+        src32 = f"nominal {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz"
+        src64 = "nominal GB300 FP64 rate"
     traffic = load_traffic()
     if prec == K.FP32_KAHAN:
         t32, t64 = ph[1], ph[2]
-        ach32 = fl32 / args.steps / (t32 * 1e-3) / 1e12 if t32 > 0 else 0.0
+        ach32 = fl32s / args.steps / (t32 * 1e-3) / 1e12 if t32 > 0 else 0.0
         ach64 = fl64 / args.steps / (t64 * 1e-3) / 1e12 if t64 > 0 else 0.0
         fp32_roof = {"kernel": "trace_f32_kernel (FP32 stepping phase)", "bound": "alu",
                      "achieved": round(ach32, 3), "peak": round(peak32, 2), "unit": "TFLOP/s",
                      "frac": round(ach32 / peak32, 4), "kernel_ms": round(t32, 4),
-                     "traffic": traffic.get("fp32_stepping"),
-                     "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
-                                    f"{sm_max:.0f} MHz ({peak_src} sm_max_mhz)"}
+                     "traffic": traffic.get("fp32_stepping"), "peak_source": src32,
+                     "frac_of_nominal": round(ach32 / nominal32, 4)}
         zone_roof = {"kernel": "trace_f32_kernel (FP64 zone phase)", "bound": "alu",
-                     "achieved": round(ach64, 4), "peak": peak64, "unit": "TFLOP/s",
+                     "achieved": round(ach64, 4), "peak": round(peak64, 4), "unit": "TFLOP/s",
                      "frac": round(ach64 / peak64, 4), "kernel_ms": round(t64, 4),
-                     "traffic": traffic.get("fp64_zone"),
-                     "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)"}
+                     "traffic": traffic.get("fp64_zone"), "peak_source": src64,
+                     "frac_of_nominal": round(ach64 / FP64_NOMINAL_TFLOPS, 4),
+                     "fp32_flops_of_zone_phase": fl32z // args.steps}
         dominant = zone_roof if t64 > t32 else fp32_roof
         roofline = dict(dominant)
         roofline["phase_ms"] = {"setup": round(ph[0], 4), "fp32_stepping": round(ph[1], 4),
@@ -258,48 +325,58 @@ def run_ours(args, rank, world, local_rank):
     else:
         ach64 = fl64 / args.steps / (kms * 1e-3) / 1e12
         roofline = {"kernel": "trace_f64_kernel", "bound": "alu", "achieved": round(ach64, 4),
-                    "peak": peak64, "unit": "TFLOP/s", "frac": round(ach64 / peak64, 4),
+                    "peak": round(peak64, 4), "unit": "TFLOP/s", "frac": round(ach64 / peak64, 4),
                     "kernel_ms": round(kms, 4), "traffic": traffic.get("fp64_path"),
-                    "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)"}
+                    "peak_source": src64}
     roofline["attempts_per_ray"] = round(att / args.steps / n, 2)
     roofline["fp64_attempt_share"] = round(att64 / max(att, 1), 4)
     roofline["fp32_flops_per_step"] = fl32 // args.steps
+    if alu:
+        roofline["alu_peaks_measured"] = alu
     roofline["fp64_flops_per_step"] = fl64 // args.steps
 
     result = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
-              "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+              "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
               "dtype": "f32" if prec == K.FP32_KAHAN else "f64", "data": "synthetic",
               "config": {"workload": WORKLOAD if prec == K.FP32_KAHAN else
                          WORKLOAD.replace("FP32+Kahan", "FP64"),
-                         "rays_per_gpu": n, "parallelism": f"replicas x{world}",
+                         "rays": n_total, "rays_per_gpu": n,
+                         "parallelism": ("one image" if world == 1 else
+                                         f"image rows interleaved over {world} processes"),
                          "l2": "flushed between steps (512 MiB write, outside the events)",
                          "variant": stats.variant},
               "gpu_launches": args.steps * (4 if prec == K.FP32_KAHAN else 1),
               "roofline": roofline, "clocks": clocks,
               "timed_wall_s": round(t_wall, 3)}
 
-    # ---- end to end through the C ABI with host (pinned) buffers
-    if rank == 0 and not args.skip_e2e:
+    # ---- end to end through the C ABI with host (pinned) buffers: every rank
+    # its share, the job's time the slowest rank's
+    if not args.skip_e2e:
         host = K.alloc_out(n, device="cpu", pinned=True)
         for _ in range(2):
-            K.kerr_trace_camera(ctx, cam, opts, out=host, stream=stream)
+            step(host)
         e2e_t = []
         for _ in range(max(3, min(args.steps, 10))):
             flush.zero_()
             torch.cuda.synchronize(dev)
+            if dist is not None:
+                dist.barrier()
             t0 = time.perf_counter()
-            K.kerr_trace_camera(ctx, cam, opts, out=host, stream=stream)
+            step(host)                     # returns once the host buffers hold the results
             e2e_t.append(time.perf_counter() - t0)
-        e2e_s = sum(e2e_t) / len(e2e_t)
-        result["e2e"] = {"value": round(n / e2e_s, 1), "unit": UNIT,
-                         "h2d_bytes_per_step": 56,
+        e2e_ms = reduce_step_time(1e3 * sum(e2e_t) / len(e2e_t),
+                                  dev if dist is not None else None)
+        # inputs: the camera (56 bytes) and, split across ranks, the pixel list
+        h2d = 56 + (8 * n if my_pix is not None else 0)
+        result["e2e"] = {"value": round(n_total / (e2e_ms * 1e-3), 1), "unit": UNIT,
+                         "h2d_bytes_per_step": h2d,
                          "d2h_bytes_per_step": n * (8 * 8 + 4 + 4 + 4 * 4)}
 
     # ---- FP32+Kahan without the FP64 zone (comparison leg)
     if rank == 0 and prec == K.FP32_KAHAN and not args.skip_fp64:
         onz = K.default_opts(prec=K.FP32_KAHAN, tol=W.TOL_1024, fp64_zone=0.0)
-        outnz = K.alloc_out(n, dev)
+        outnz = K.alloc_out(n_total, dev)
         K.kerr_trace_camera(ctx, cam, onz, out=outnz, stream=stream)
         torch.cuda.synchronize(dev)
         tnz = []
@@ -311,7 +388,7 @@ def run_ours(args, rank, world, local_rank):
             b_.record(stream)
             torch.cuda.synchronize(dev)
             tnz.append(a_.elapsed_time(b_))
-        result["fp32_no_zone"] = {"value": round(n / (min(tnz) * 1e-3), 1), "unit": UNIT,
+        result["fp32_no_zone"] = {"value": round(n_total / (min(tnz) * 1e-3), 1), "unit": UNIT,
                                   "ms_per_step": round(min(tnz), 3),
                                   "note": "same path with fp64_zone = 0 (every step FP32+Kahan)"}
         result["_nz_out"] = outnz
@@ -320,7 +397,7 @@ def run_ours(args, rank, world, local_rank):
     # steps in ~48-bit float-float arithmetic on the FP32 pipe instead of FP64
     if rank == 0 and prec == K.FP32_KAHAN and not args.skip_fp64:
         odf = K.default_opts(prec=K.FP32_KAHAN, tol=W.TOL_1024, zone_prec=K.ZONE_F32X2)
-        outdf = K.alloc_out(n, dev)
+        outdf = K.alloc_out(n_total, dev)
         K.kerr_trace_camera(ctx, cam, odf, out=outdf, stream=stream)
         torch.cuda.synchronize(dev)
         tdf, zdf = [], []
@@ -334,7 +411,7 @@ def run_ours(args, rank, world, local_rank):
             tdf.append(a_.elapsed_time(b_))
             zdf.append(K.kerr_get_stats(ctx).phase_ms[2])
         result["fp32_zone_float_float"] = {
-            "value": round(n / (min(tdf) * 1e-3), 1), "unit": UNIT,
+            "value": round(n_total / (min(tdf) * 1e-3), 1), "unit": UNIT,
             "ms_per_step": round(min(tdf), 3), "zone_phase_ms": round(min(zdf), 3),
             "note": "same path with zone_prec = KERR_ZONE_F32X2: steps inside 1.5 r_h in "
                     "float-float (~48-bit) arithmetic on the FP32 pipe instead of FP64"}
@@ -343,7 +420,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- plain FP64 GPU path on the same workload (comparison leg)
     if rank == 0 and prec == K.FP32_KAHAN and not args.skip_fp64:
         o64 = K.default_opts(prec=K.FP64, tol=W.TOL_1024)
-        out64 = K.alloc_out(n, dev)
+        out64 = K.alloc_out(n_total, dev)
         K.kerr_trace_camera(ctx, cam, o64, out=out64, stream=stream)
         torch.cuda.synchronize(dev)
         t64 = []
@@ -355,7 +432,7 @@ def run_ours(args, rank, world, local_rank):
             b_.record(stream)
             torch.cuda.synchronize(dev)
             t64.append(a_.elapsed_time(b_))
-        result["fp64_path"] = {"value": round(n / (min(t64) * 1e-3), 1), "unit": UNIT,
+        result["fp64_path"] = {"value": round(n_total / (min(t64) * 1e-3), 1), "unit": UNIT,
                                "ms_per_step": round(min(t64), 3)}
         result["_fp64_out"] = out64
 
@@ -521,6 +598,12 @@ def run_batch64(K, W, dev, stream):
     n = sum(c.n for c in specs)
     ctx = K.kerr_init(0.0)
     opts = K.default_opts(tol=1e-6)
+    # the autotuner picks the launch configuration on a 2^18-ray sample of the
+    # batch (kept for the context's later calls; cached per GPU and workload)
+    t0 = time.perf_counter()
+    tuning = K.kerr_autotune_cameras(ctx, cams, opts, sample=1 << 18, cache_path=TUNE_CACHE,
+                                     stream=stream)
+    tune_s = time.perf_counter() - t0
     out = K.alloc_out(n, dev, diag=False)
     K.kerr_trace_camera(ctx, cams, opts, out=out, stream=stream)      # warm (graph, buffers)
     torch.cuda.synchronize(dev)
@@ -540,29 +623,45 @@ def run_batch64(K, W, dev, stream):
                         "r_obs 1000M, +-25M, seed 1708, one launch, FP32+Kahan tol 1e-6",
             "rays": n, "latency_ms": round(ms, 2), "value": round(n / (ms * 1e-3), 1),
             "unit": UNIT, "phase_ms": [round(x, 2) for x in s.phase_ms],
-            "attempts_per_ray": round(s.attempts / n, 2), "status_count": st}
+            "attempts_per_ray": round(s.attempts / n, 2), "status_count": st,
+            "autotune": dict(tuning.as_dict(), seconds=round(tune_s, 2), used=s.variant)}
 
 
 def run_particles(K, W, dev, stream):
     """2^20 bound particles, a = 0.7 (seed 1707): semi-major axes log-uniform
     in [10, 1000] M, e ~ U[0, 0.9], isotropic planes, 100 Newtonian radial
-    periods each (or capture); FP32+Kahan on all of them, the FP64 path on
-    the first 2^16 (its time is set by the longest particles).  Particles/s
-    and attempted steps/s."""
+    periods each (or capture); FP32+Kahan and the FP64 path on all of them,
+    tol 1e-6, with the launch configuration picked by the autotuner (on a
+    2^15-particle sample run for a tenth of the time).  Particles/s,
+    attempted steps/s, and the drift of the constants of motion E, L_z and
+    Carter's Q between start and end (end points after 100 periods are not
+    determined to 1e-5 by the method: orbital phase error grows with every
+    period, so the constants are the accuracy measure here)."""
     import torch
 
     ps = W.particles()
+    m = ps.x0.shape[1]
     ctx = K.kerr_init(ps.a)
+    x0 = torch.tensor(ps.x0, device=dev).contiguous()
+    v0 = torch.tensor(ps.v0, device=dev).contiguous()
+    te = torch.tensor(ps.t_end, device=dev).contiguous()
+    # constants of motion at the start (zero-step trace)
+    start = K.alloc_out(m, dev)
+    K.kerr_trace_particles(ctx, x0, v0, te, K.default_opts(prec=K.FP64, max_steps=0,
+                                                           r_escape=-1.0),
+                           out=start, stream=stream)
+    torch.cuda.synchronize(dev)
+    c0 = start.diag.double()
+    scale = torch.stack([c0[0].abs(), c0[1].abs() + 1e-3,
+                         c0[2] + (c0[1] - ps.a * c0[0]) ** 2])      # E, L_z, Carter's K
     res = {}
-    for name, prec, m in (("fp32_kahan", K.FP32_KAHAN, ps.x0.shape[1]), ("fp64", K.FP64, 1 << 16)):
-        x0 = torch.tensor(ps.x0[:, :m], device=dev).contiguous()
-        v0 = torch.tensor(ps.v0[:, :m], device=dev).contiguous()
-        te = torch.tensor(ps.t_end[:m], device=dev).contiguous()
+    for name, prec in (("fp32_kahan", K.FP32_KAHAN), ("fp64", K.FP64)):
         opts = K.default_opts(prec=prec, tol=1e-6, r_escape=-1.0)
-        out = K.alloc_out(m, dev, diag=False)
-        if prec == K.FP32_KAHAN:                  # warm (graph, buffers)
-            K.kerr_trace_particles(ctx, x0, v0, te, opts, out=out, stream=stream)
-            torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        tuning = K.kerr_autotune_particles(ctx, x0, v0, te * 0.1, opts, sample=1 << 15,
+                                           cache_path=TUNE_CACHE, stream=stream)
+        tune_s = time.perf_counter() - t0
+        out = K.alloc_out(m, dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         K.kerr_trace_particles(ctx, x0, v0, te, opts, out=out, stream=stream)
@@ -571,15 +670,27 @@ def run_particles(K, W, dev, stream):
         ms = e0.elapsed_time(e1)
         s = K.kerr_get_stats(ctx)
         steps = out.steps.double()
+        ended = out.status == K.ENDTIME
+        drift = {}
+        for j, key in enumerate(("E", "Lz", "Q")):
+            d = ((out.diag[j].double() - c0[j]).abs() / scale[j])[ended]
+            q = torch.quantile(d, torch.tensor([0.5, 0.9, 0.99], dtype=torch.float64, device=dev))
+            drift[key] = {"median": float(q[0]), "p90": float(q[1]), "p99": float(q[2])}
         res[name] = {"particles": m, "ms": round(ms, 2),
                      "value": round(m / (ms * 1e-3), 1), "unit": "particles/s",
                      "attempts_per_s": round(s.attempts / (ms * 1e-3), 1),
                      "steps_min_median_max": [int(steps.min()), float(steps.median()),
                                               int(steps.max())],
-                     "status_count": list(s.status_count)}
+                     "status_count": list(s.status_count),
+                     "drift_of_constants": drift,
+                     "autotune": dict(tuning.as_dict(), seconds=round(tune_s, 2),
+                                      used=s.variant)}
     ctx.close()
     res["workload"] = ("2^20 particles, a=0.7, A log-uniform [10,1000]M, e ~ U[0,0.9], isotropic, "
                        "100 radial periods, tol 1e-6, seed 1707")
+    res["drift_note"] = ("|constant(end) - constant(start)| / scale over particles that reach "
+                         "their end time; scale |E|, |L_z| + 1e-3, and Carter's K = Q + "
+                         "(L_z - a E)^2 for Q")
     return res
 
 
@@ -817,8 +928,15 @@ def main():
     ap.add_argument("--surrogate-rays", type=int, default=10_000_000)
     ap.add_argument("--surrogate-epochs", type=int, default=16)
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: start them under torch.distributed.run
+        launch = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+                  f"--nproc-per-node={args.gpus}", "--master-addr=127.0.0.1",
+                  f"--master-port={29500 + os.getpid() % 1000}", os.path.abspath(__file__),
+                  *sys.argv[1:]]
+        os.execv(sys.executable, launch)
     rank = int(os.environ.get("RANK", 0))
-    world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
+    world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.warmup < 3:
         args.warmup = 3

@@ -88,8 +88,10 @@ typedef struct kerr_ctx kerr_ctx;
  *   end time  t - t_end changed sign from its initial value (t_end finite).
  * The crossing step is then clipped onto the surface: the step as a function
  * of its length (two RK4 half steps from the last accepted state) is solved
- * for the surface by Illinois regula falsi, to |r - r_stop| <= 1e-12 r_stop in
- * FP64 (2e-6 r_stop in FP32; the same factors for t with scale max(1,|t_end|))
+ * for the surface by Illinois regula falsi, to |r - r_stop| <= 1e-12 r_stop on
+ * the FP64 path, 2e-6 r_stop for FP32 steps and 1e-10 r_stop for the FP64 (or
+ * float-float) zone steps of the FP32+Kahan path, whose end points are only
+ * good to ~1e-6 anyway (the same factors for t with scale max(1, |t_end|)),
  * or clip_maxit iterations.  A geodesic that starts inside 1.01 r_h is
  * captured with no step; one that reaches max_steps attempts is MAXSTEPS. */
 typedef struct {
@@ -159,6 +161,11 @@ typedef struct {
     int64_t queue_errors;     /* zone-phase queue hand-overs that timed out (the */
                               /* geodesic is then lost); 0 unless the library is */
                               /* faulty                                          */
+    int64_t rhs_fp32_zone_phase;      /* FP32 path: of rhs_fp32, those evaluated */
+    int64_t attempts_fp32_zone_phase; /* (and FP32 attempts taken) by the zone   */
+                                      /* phase for geodesics outside the zone    */
+    int64_t clips;            /* end points clipped onto an event surface        */
+    int64_t clip_rhs;         /* right-hand sides evaluated by those clips       */
 } kerr_stats;
 
 /* Fills *opts with: prec FP32_KAHAN, tol 1e-6, h0 1, max_steps 1e6,
@@ -205,6 +212,16 @@ int kerr_trace_camera(kerr_ctx *ctx, const kerr_camera *cams, int32_t ncam,
                       const kerr_opts *opts, double *x_out, double *k_out, int32_t *status,
                       int32_t *steps, float *diag, float *cross, void *stream);
 
+/* Integrates the pixels index[0 .. n-1] (device memory, flat indices q*nx + p
+ * in [0, nx*ny)) of one camera; outputs as for kerr_trace_rays, entry i for
+ * pixel index[i].  The same rays as kerr_trace_camera, for any subset and
+ * order: a share of one image per process when an image is split across
+ * GPUs (the only exchange is the host-side concatenation of the outputs). */
+int kerr_trace_camera_pixels(kerr_ctx *ctx, const kerr_camera *cam, const int64_t *index,
+                             int64_t n, const kerr_opts *opts, double *x_out, double *k_out,
+                             int32_t *status, int32_t *steps, float *diag, float *cross,
+                             void *stream);
+
 /* Integrates n massive particles (Sec. 3.2: time-like geodesics with the same
  * integrator).  x0: [4][n] plane of start events; v0: [3][n] plane of
  * coordinate velocities dx^i/dt.  u^t is solved in FP64 from g_ab u^a u^b = -1
@@ -241,11 +258,69 @@ int kerr_variant_shape(int v, int32_t *block, int32_t *min_blocks, int32_t *rays
 int kerr_num_zone_variants(void);
 int kerr_zone_variant_info(int v, int32_t *block, int32_t *blocks_per_sm);
 
-/* Times every launch configuration for the given precision on `sample`
- * camera rays of cams[0] (spread over the image; the two-geodesics-per-thread
- * variants for KERR_FP32_KAHAN only) and remembers the fastest for later
- * calls with variant == -1 on this context.  Writes the chosen variant to
- * *best. */
+/* Autotuning (the counterpart of the paper's run-time tuning of the OpenCL
+ * work-group size for each image size, Sec. 4).  The search space is the
+ * stepping variants -- threads per block x register cap (the minimum
+ * resident blocks per SM, which caps registers at 65536 / (block x blocks))
+ * x geodesics per thread (1, or 2 on packed f32x2 instructions, FP32 only) x
+ * right-hand-side mode -- and, for the FP32+Kahan path with an FP64 zone, the
+ * zone-phase launch shapes.  Coordinate search: every stepping variant with
+ * the default zone shape, then every zone shape with the best stepping
+ * variant; each candidate is traced once untimed (graph capture, buffers) and
+ * then timed (device time of the whole call, minimum over repetitions) on a
+ * sample of the workload.  The choice is kept by the context for its later
+ * calls with variant == -1 / zone_variant == -1 in that precision.
+ *
+ * cache_path (NULL = no cache): a text file of lines
+ *   <gpu>\t<workload key>\t<variant>\t<zone variant>\t<ms>\n
+ * where <gpu> is the device name with its SM count ("NVIDIA GB300 (152
+ * SMs)") and the key describes the workload's shape and options, including
+ * the precision (kerr_tune_key_cameras / kerr_tune_key_particles).  When the
+ * file holds the (gpu, key) pair (the last matching line wins) nothing is
+ * timed and the stored choice is applied (out->from_cache = 1); otherwise the
+ * result is appended. */
+typedef struct {
+    int32_t variant;       /* chosen stepping variant                           */
+    int32_t zone_variant;  /* chosen zone-phase variant, -1 without a zone phase */
+    float ms;              /* device time of the chosen configuration (sample)  */
+    int32_t from_cache;    /* 1: read from the cache file, nothing was timed    */
+    int32_t timed;         /* configurations timed                              */
+} kerr_tuning;
+
+/* Tunes on `sample` rays of the camera list: each camera at a resolution
+ * lowered in proportion to its share of the rays, over the same field of
+ * view, so the sample has the batch's mix of images. */
+int kerr_autotune_cameras(kerr_ctx *ctx, const kerr_camera *cams, int32_t ncam,
+                          const kerr_opts *opts, int64_t sample, const char *cache_path,
+                          kerr_tuning *out, void *stream);
+
+/* Tunes on every (n / sample)-th of n particles (inputs as for
+ * kerr_trace_particles, host or device memory; pass shortened end times to
+ * tune a long run on a shorter one). */
+int kerr_autotune_particles(kerr_ctx *ctx, const double *x0, const double *v0,
+                            const double *t_end, int64_t n, const kerr_opts *opts, int64_t sample,
+                            const char *cache_path, kerr_tuning *out, void *stream);
+
+/* Workload keys of the cache (host only): the camera list's size, a hash of
+ * its geometry (spins, inclinations, distances, widths, pixel counts) and the
+ * options that change the work (precision, tol, zone radius and arithmetic,
+ * renormalisation); for particles their number, max_steps and the same
+ * options.  KERR_EINVAL if `cap` bytes do not hold the key. */
+int kerr_tune_key_cameras(const kerr_camera *cams, int32_t ncam, const kerr_opts *opts, char *buf,
+                          int32_t cap);
+int kerr_tune_key_particles(int64_t n, const kerr_opts *opts, char *buf, int32_t cap);
+
+/* The cache file itself (host only; no GPU needed): lookup returns KERR_OK
+ * and fills *out when (gpu, key) is present, 1 when it is not (or the file
+ * does not exist), KERR_EINVAL for a malformed file; store appends one line
+ * (KERR_EINVAL for empty fields or fields holding a tab or newline). */
+int kerr_tune_cache_lookup(const char *path, const char *gpu, const char *key, kerr_tuning *out);
+int kerr_tune_cache_store(const char *path, const char *gpu, const char *key,
+                          const kerr_tuning *t);
+
+/* The single-camera form: tunes on `sample` rays of cams[0] (no cache) and
+ * writes the chosen stepping variant to *best (the zone shape is chosen and
+ * kept too). */
 int kerr_autotune(kerr_ctx *ctx, const kerr_camera *cam, const kerr_opts *opts,
                   int64_t sample, int32_t *best, void *stream);
 
@@ -255,30 +330,55 @@ int kerr_autotune(kerr_ctx *ctx, const kerr_camera *cam, const kerr_opts *opts,
  * synchronise the device and have unbounded latency), or hosts whose device
  * memory is owned and budgeted by another framework's pool.
  *
- * Same computation and outputs as kerr_trace_camera (either precision), with
- * no context: each camera carries its spin.  All scratch lives in one
- * file-scope device array of KERR_STATIC_SCRATCH_BYTES that every GPU that
- * loads the library holds until the process exits; the call performs no
- * allocation of any kind.  Limits: at most KERR_STATIC_MAX_GEODESICS rays and
- * KERR_STATIC_MAX_CAMERAS cameras per call (KERR_EINVAL beyond); outputs must
- * be device memory (KERR_EINVAL otherwise, since host buffers would need
- * staging).  Geodesics entering the FP64 zone beyond the array's zone buffer
- * (a quarter of the maximum) take their zone steps in place.
+ * Same computation and outputs as kerr_trace_camera (either precision, the
+ * same argument checks), with no context: each camera carries its spin.  All
+ * scratch lives in one file-scope device array of KERR_STATIC_SCRATCH_BYTES
+ * that every GPU that loads the library holds until the process exits.
+ * Limits: at most KERR_STATIC_MAX_GEODESICS rays and KERR_STATIC_MAX_CAMERAS
+ * cameras per call (KERR_EINVAL beyond); outputs must be device memory
+ * (KERR_EINVAL otherwise, since host buffers would need staging).  Geodesics
+ * entering the FP64 zone beyond the array's zone buffer (a quarter of the
+ * maximum) take their zone steps in place.
  *
- * The call is asynchronous on `stream`.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current
- * and caches it; make that first call before any stream capture.  Every call
- * shares the array and leaves its contents there (the counters are cleared at
- * the start of each call), so calls that overlap on the GPU -- on other
- * streams or from other host threads -- race and must be serialised by the
- * caller.  Counters of the call are not reported (kerr_get_stats needs a
- * context). */
+ * The first call on a device is the set-up: it looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current and caches it, and
+ * the CUDA runtime loads the library's kernels on their first use (lazy
+ * module loading) and places the array in device memory then -- driver
+ * allocations that may synchronise the device.  Make that first call, in each
+ * precision that will be used, during start-up and before any stream
+ * capture; later calls allocate nothing.  The call is asynchronous on
+ * `stream`.  Every call shares the array and leaves its contents there (the
+ * counters are cleared at the start of each call), so calls that overlap on
+ * the GPU -- on other streams or from other host threads -- race and must be
+ * serialised by the caller.  Counters of the call are not reported
+ * (kerr_get_stats needs a context). */
 #define KERR_STATIC_MAX_GEODESICS 131072
 #define KERR_STATIC_MAX_CAMERAS 64
-#define KERR_STATIC_SCRATCH_BYTES 16256256
+#define KERR_STATIC_SCRATCH_BYTES 18877696
 int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam, const kerr_opts *opts,
                              double *x_out, double *k_out, int32_t *status, int32_t *steps,
                              float *diag, float *cross, void *stream);
+
+/* Host-writable abort flag of the context (a stop request with no
+ * counterpart in the paper; the host side of its failure detection).  *flag
+ * receives the address of an int32 in mapped pinned host memory, allocated
+ * by the first call and owned by the context (freed by kerr_destroy).  While
+ * it holds a non-zero value, every launch of this context's trace calls --
+ * including one already running -- stops within a few dozen steps: lanes
+ * poll the flag, warp by warp, every 32 iterations (the same place as the
+ * budget_ns check); unfinished geodesics end with KERR_TIMEOUT and the state
+ * reached, which kerr_trace_rays accepts to resume them.  No wait is
+ * involved: a kernel that sees the flag finishes its current steps and
+ * returns.  Write 0 to re-arm.  KERR_ENOMEM / KERR_ECUDA if the mapped
+ * allocation fails. */
+int kerr_abort_flag(kerr_ctx *ctx, int32_t **flag);
+
+/* Allocation-failure injection for tests (host-side only; nothing on the GPU
+ * faults): the n-th device allocation the library makes from now on (n >= 1)
+ * reports cudaErrorMemoryAllocation without allocating, so the call that
+ * needed it returns KERR_ENOMEM and leaves its context usable; n = 0
+ * disarms.  Process-wide.  KERR_EINVAL for n < 0. */
+int kerr_debug_fail_alloc(int32_t n);
 
 /* Integrates rays from n image-plane points, each with its own camera:
  * points[4 * i + 0..3] = (alpha, beta, spin a, inclination) as in
@@ -320,6 +420,23 @@ int kerr_surrogate_destroy(kerr_surrogate *s);
 /* Copies the FP32 parameters (or the last computed gradient) to host. */
 int kerr_surrogate_get_params(kerr_surrogate *s, float *host_out);
 int kerr_surrogate_get_grad(kerr_surrogate *s, float *host_out);
+
+/* Parameter files (host code only; no GPU needed): a 96-byte little-endian
+ * header -- magic "KERRSURR", version 1, header size, number of parameters,
+ * layer count, the padded input and output widths of the five layers, the
+ * live input and output widths, KERR_SURR_INPUT_SCALE, an FNV-1a checksum of
+ * the parameter bytes, 12 reserved zero bytes -- followed by the
+ * kerr_surrogate_num_params() FP32 parameters in the order described above.
+ * kerr_params_write writes n == kerr_surrogate_num_params() host floats;
+ * kerr_params_read checks every header field, the length and the checksum
+ * (KERR_EINVAL naming what differs) before filling `params`.  Save/load
+ * move a surrogate's FP32 master parameters through such a file (load
+ * creates a new surrogate on the current device; optimizer moments are not
+ * stored). */
+int kerr_params_write(const char *path, const float *params, int64_t n);
+int kerr_params_read(const char *path, float *params, int64_t n);
+int kerr_surrogate_save(kerr_surrogate *s, const char *path);
+int kerr_surrogate_load(const char *path, kerr_surrogate **out);
 
 /* Network inputs and training targets from points (device, [n][4] doubles as
  * for kerr_trace_points): in [n][4] = (alpha/s, beta/s, a, cos i); the rays
@@ -475,6 +592,23 @@ int kerr_bl_camera_states(const kerr_camera *cam, int32_t fp64, int32_t layout, 
  * negative x gives NaN).  Asynchronous on `stream`.  KERR_EINVAL for
  * n < 0 or NULL buffers with n > 0; n == 0 is a no-op. */
 int kerr_check_fp64_math(const double *x, int64_t n, double *out, void *stream);
+
+/* Arithmetic peak of this GPU's FP32 or FP64 pipe (a measurement aid with no
+ * counterpart in the paper: the integrator is bound by these pipes, and its
+ * roofline fraction is taken against the rate this kernel reaches).  Launches
+ * SMs x blocks_per_sm blocks of 256 threads, each thread running 8 independent
+ * fused multiply-add chains for 16 x rounds steps: kind KERR_PEAK_FP32 (fma.f32),
+ * KERR_PEAK_FP64 (fma.f64) or KERR_PEAK_FP32X2 (packed fma.f32x2, two per
+ * instruction).  *flops (host, or NULL) receives the FLOPs the launch performs
+ * (2 per fused multiply-add); the caller times the launch on `stream`.  sink:
+ * device memory of at least SMs x blocks_per_sm x 256 floats (never written in
+ * practice; it keeps the chains from being optimised away).  KERR_EINVAL for
+ * an unknown kind, rounds < 1 or blocks_per_sm outside 1..8. */
+#define KERR_PEAK_FP32 0
+#define KERR_PEAK_FP64 1
+#define KERR_PEAK_FP32X2 2
+int kerr_fma_chain(int32_t kind, int64_t rounds, int32_t blocks_per_sm, float *sink,
+                   double *flops, void *stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *kerr_last_error(void);

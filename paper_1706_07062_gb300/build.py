@@ -1,6 +1,6 @@
 """Build libkerr.so (CUDA, sm_103a) in-tree with nvcc.
 
-The three translation units compile in parallel; the shared library links
+The translation units compile in parallel; the shared library links
 the CUDA runtime statically, so it loads next to any PyTorch build.
 """
 from __future__ import annotations
@@ -19,7 +19,7 @@ LIB = os.path.join(OUT, "libkerr.so")
 UNITS = ["kerr_api.cu", "kerr_trace_f32.cu", "kerr_trace_f32b.cu", "kerr_trace_f32x2.cu", "kerr_trace_zone.cu",
          "kerr_trace_f64.cu", "kerr_static.cu", "kerr_surrogate.cu", "kerr_mlp_tc.cu", "kerr_gemm_tc.cu",
          "kerr_fixed.cu", "kerr_coordtime.cu",
-         "kerr_dense.cu"]
+         "kerr_dense.cu", "kerr_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

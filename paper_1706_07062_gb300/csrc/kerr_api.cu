@@ -4,11 +4,15 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/kerr.h"
@@ -74,7 +78,7 @@ struct kerr_ctx {
                                                  // [17] zone count, [18] zone-phase head
     ZoneEntry *d_zone = nullptr;                 // deferred FP64-zone geodesics
     int64_t zone_cap = 0;
-    float *d_work = nullptr;                     // FP32 path: state and constant planes
+    char *d_work = nullptr;                      // FP32 path: state, constants, clip queue
     int64_t work_cap = 0;                        // geodesics d_work can hold
     CamDev *d_cams = nullptr;
     int cam_cap = 0;
@@ -83,13 +87,16 @@ struct kerr_ctx {
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey;
     bool gvalid = false;
+    int32_t *h_abort = nullptr;                  // abort flag: mapped pinned host memory
+    int32_t *d_abort = nullptr;                  // ... and its device address
     int tuned[2] = {-1, -1};                     // autotuned variant per precision
+    int tuned_zone[2] = {-1, -1};                // autotuned zone-phase variant per precision
     int last_variant = -1;
     int last_f32 = 0;
     bool have_stats = false;
 };
 
-static const int kScratchWords = 1 + SC_COUNT + 3;
+static const int kScratchWords = kCounterWords(SC_COUNT);
 
 extern "C" void kerr_opts_default(kerr_opts *o)
 {
@@ -118,6 +125,54 @@ int kerr::kerr_set_error(int code, const char *msg)
 {
     g_err = msg;
     return code;
+}
+
+// Injected allocation failure: the n-th next library allocation fails.
+static std::atomic<int> g_fail_alloc{0};
+
+cudaError_t kerr::dev_alloc_bytes(void **p, size_t bytes)
+{
+    int n = g_fail_alloc.load();
+    while (n > 0) {
+        if (g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+            if (n == 1) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
+extern "C" int kerr_debug_fail_alloc(int32_t n)
+{
+    if (n < 0)
+        return fail(KERR_EINVAL, "kerr_debug_fail_alloc: n = %d < 0", n);
+    g_fail_alloc.store(n);
+    return KERR_OK;
+}
+
+cudaError_t kerr::blocks_per_sm(const void *fn, int block, int *out)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> cache;   // (kernel, device) -> blocks
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    const auto key = std::make_pair(fn, dev * 4096 + block);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, 0);
+        if (e != cudaSuccess)
+            return e;
+        it = cache.emplace(key, n < 1 ? 1 : n).first;
+    }
+    *out = it->second;
+    return cudaSuccess;
 }
 
 extern "C" int kerr_num_variants(void) { return kNumVariants; }
@@ -189,7 +244,7 @@ extern "C" int kerr_init(double a, kerr_ctx **out)
     for (int i = 0; i < 3 && e == cudaSuccess; ++i)
         e = cudaEventCreate(&c->ev_ph[i]);
     if (e == cudaSuccess)
-        e = cudaMalloc(&c->d_scratch, kScratchWords * sizeof(unsigned long long));
+        e = dev_alloc(&c->d_scratch, kScratchWords * sizeof(unsigned long long));
     if (e == cudaSuccess)
         e = cudaMemset(c->d_scratch, 0, kScratchWords * sizeof(unsigned long long));
     if (e != cudaSuccess) {
@@ -214,6 +269,8 @@ extern "C" int kerr_destroy(kerr_ctx *c)
     cudaFree(c->d_work);
     cudaFree(c->d_cams);
     cudaFree(c->d_stage);
+    if (c->h_abort)
+        cudaFreeHost(c->h_abort);
     if (c->ev_in)
         cudaEventDestroy(c->ev_in);
     if (c->ev_out)
@@ -231,7 +288,7 @@ extern "C" int kerr_destroy(kerr_ctx *c)
     return KERR_OK;
 }
 
-static int check_opts(const kerr_opts *o)
+int kerr::check_opts(const kerr_opts *o)
 {
     if (!o)
         return fail(KERR_EINVAL, "opts is NULL");
@@ -285,7 +342,7 @@ static int ensure_stage(kerr_ctx *c, size_t bytes)
     c->d_stage = nullptr;
     c->stage_cap = 0;
     size_t cap = std::max(bytes, (size_t)1 << 20);
-    cudaError_t e = cudaMalloc(&c->d_stage, cap);
+    cudaError_t e = dev_alloc(&c->d_stage, cap);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(KERR_ENOMEM, "staging allocation of %zu bytes failed: %s", cap,
@@ -326,6 +383,8 @@ static int launch_integration(kerr_ctx *c, const TraceParams &P, int prec, int v
                 e2 = launch_zone_phase(P, zone_variant, c->sms, c->stream);
             if (e2 == cudaSuccess)
                 e2 = cudaEventRecordWithFlags(c->ev_ph[2], c->stream, cudaEventRecordExternal);
+            if (e2 == cudaSuccess && P.clipq)
+                e2 = launch_clip_f32(P, c->sms, c->stream);
             if (e2 == cudaSuccess)
                 e2 = launch_finish_f32(P, c->sms, c->stream);
         } else if (e2 == cudaSuccess) {
@@ -422,19 +481,21 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
     P.zone_df = o->zone_prec == KERR_ZONE_F32X2 ? 1 : 0;
     P.zone_quantum = o->zone_quantum;
     P.budget_ns = o->budget_ns;
+    P.abort = c->d_abort;
     P.head = c->d_scratch;
     P.stats = c->d_scratch + 1;
     P.zcount = c->d_scratch + 1 + SC_COUNT;
     P.zhead = c->d_scratch + 2 + SC_COUNT;
     P.zpush = c->d_scratch + 3 + SC_COUNT;
     if (o->prec == KERR_FP32_KAHAN) {
-        // state [16][n] and constant [KC_COUNT][n] float planes
+        // state [16][n] and constant [KC_COUNT][n] float planes, deferred-clip
+        // planes and queue
         if (n > c->work_cap) {
             cudaStreamSynchronize(c->stream);
             cudaFree(c->d_work);
             c->d_work = nullptr;
             c->work_cap = 0;
-            cudaError_t e = cudaMalloc(&c->d_work, (size_t)n * (16 + KC_COUNT) * sizeof(float));
+            cudaError_t e = dev_alloc(&c->d_work, (size_t)n * kWorkBytesPerGeodesic);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 return fail(KERR_ENOMEM, "work buffer allocation (%lld geodesics) failed",
@@ -442,8 +503,7 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
             }
             c->work_cap = n;
         }
-        P.s_state = c->d_work;
-        P.s_const = c->d_work + (size_t)16 * n;
+        bind_f32_scratch(P, c->d_work, c->d_scratch, n);
     }
     if (o->prec == KERR_FP32_KAHAN && o->fp64_zone > 0.0) {
         // Deferred-zone buffer: a quarter of the geodesics (at least 64 Ki);
@@ -454,7 +514,7 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
             cudaFree(c->d_zone);
             c->d_zone = nullptr;
             c->zone_cap = 0;
-            cudaError_t e = cudaMalloc(&c->d_zone, (size_t)want * sizeof(ZoneEntry));
+            cudaError_t e = dev_alloc(&c->d_zone, (size_t)want * sizeof(ZoneEntry));
             if (e == cudaSuccess)    // queue slots start empty (seq = 0)
                 e = cudaMemset(c->d_zone, 0, (size_t)want * sizeof(ZoneEntry));
             if (e != cudaSuccess) {
@@ -533,7 +593,7 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
             cudaFree(c->d_cams);
             c->d_cams = nullptr;
             c->cam_cap = 0;
-            cudaError_t e = cudaMalloc(&c->d_cams, (size_t)ncam * sizeof(CamDev));
+            cudaError_t e = dev_alloc(&c->d_cams, (size_t)ncam * sizeof(CamDev));
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 return fail(KERR_ENOMEM, "camera table allocation failed");
@@ -555,7 +615,9 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
     int prec = o->prec;
     int variant = o->variant >= 0 ? o->variant
                                    : (c->tuned[prec] >= 0 ? c->tuned[prec] : kDefaultVariant[prec]);
-    const int zvar = o->zone_variant >= 0 ? o->zone_variant : kDefaultZoneVariant;
+    const int zvar = o->zone_variant >= 0
+                         ? o->zone_variant
+                         : (c->tuned_zone[prec] >= 0 ? c->tuned_zone[prec] : kDefaultZoneVariant);
     rc = launch_integration(c, P, prec, variant, zvar);
     if (rc)
         return rc;
@@ -573,6 +635,33 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
     KERR_CUDA(cudaStreamWaitEvent(us, c->ev_out, 0));
     if (any_host)
         KERR_CUDA(cudaStreamSynchronize(c->stream));
+    return KERR_OK;
+}
+
+extern "C" int kerr_abort_flag(kerr_ctx *c, int32_t **flag)
+{
+    if (!c || !flag)
+        return fail(KERR_EINVAL, "kerr_abort_flag: NULL argument");
+    if (!c->h_abort) {
+        void *h = nullptr;
+        cudaError_t e = cudaHostAlloc(&h, sizeof(int32_t), cudaHostAllocMapped);
+        void *d = nullptr;
+        if (e == cudaSuccess) {
+            *(volatile int32_t *)h = 0;
+            e = cudaHostGetDevicePointer(&d, h, 0);
+        }
+        if (e != cudaSuccess) {
+            if (h)
+                cudaFreeHost(h);
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? KERR_ENOMEM : KERR_ECUDA,
+                        "kerr_abort_flag: mapped host allocation failed: %s",
+                        cudaGetErrorString(e));
+        }
+        c->h_abort = (int32_t *)h;
+        c->d_abort = (int32_t *)d;
+    }
+    *flag = c->h_abort;
     return KERR_OK;
 }
 
@@ -684,12 +773,11 @@ extern "C" int kerr_trace_coordtime(kerr_ctx *c, const double *x0, const double 
     return KERR_OK;
 }
 
-static int build_cams(const kerr_camera *cams, int32_t ncam, std::vector<CamDev> &out, int64_t &n)
+int kerr::build_cams(const kerr_camera *cams, int32_t ncam, CamDev *out, int64_t *n_out)
 {
     if (!cams || ncam <= 0)
         return fail(KERR_EINVAL, "need at least one camera (ncam = %d)", ncam);
-    out.resize(ncam);
-    n = 0;
+    int64_t n = 0;
     for (int i = 0; i < ncam; ++i) {
         const kerr_camera &k = cams[i];
         if (!(std::fabs(k.a) <= 1.0))
@@ -704,6 +792,7 @@ static int build_cams(const kerr_camera *cams, int32_t ncam, std::vector<CamDev>
         out[i] = CamDev{k.a, k.incl, k.r_obs, k.half_width, k.nx, k.ny, n};
         n += (int64_t)k.nx * k.ny;
     }
+    *n_out = n;
     return KERR_OK;
 }
 
@@ -711,9 +800,9 @@ extern "C" int kerr_trace_camera(kerr_ctx *c, const kerr_camera *cams, int32_t n
                                  const kerr_opts *o, double *x_out, double *k_out, int32_t *status,
                                  int32_t *steps, float *diag, float *cross, void *stream)
 {
-    std::vector<CamDev> cd;
+    std::vector<CamDev> cd(std::max(ncam, 1));
     int64_t n = 0;
-    int rc = build_cams(cams, ncam, cd, n);
+    int rc = build_cams(cams, ncam, cd.data(), &n);
     if (rc)
         return rc;
     return trace_common(c, MODE_CAMERA, nullptr, nullptr, nullptr, n, cd.data(), ncam, o, x_out,
@@ -742,16 +831,29 @@ int kerr_trace_camera_list(kerr_ctx *c, const kerr_camera *cam, const int64_t *i
                            double *x_out, double *k_out, int32_t *status, int32_t *steps,
                            float *diag, float *cross, void *stream)
 {
-    std::vector<CamDev> cd;
+    CamDev cd[1];
     int64_t n = 0;
-    int rc = build_cams(cam, 1, cd, n);
+    int rc = build_cams(cam, 1, cd, &n);
     if (rc)
         return rc;
     TraceExtra X;
     X.index = index;
     X.n_dev = n_dev;
-    return trace_common(c, MODE_CAMERA, nullptr, nullptr, nullptr, capacity, cd.data(), 1, o,
+    return trace_common(c, MODE_CAMERA, nullptr, nullptr, nullptr, capacity, cd, 1, o,
                         x_out, k_out, status, steps, diag, cross, stream, X);
+}
+
+extern "C" int kerr_trace_camera_pixels(kerr_ctx *c, const kerr_camera *cam, const int64_t *index,
+                                        int64_t n, const kerr_opts *o, double *x_out,
+                                        double *k_out, int32_t *status, int32_t *steps,
+                                        float *diag, float *cross, void *stream)
+{
+    if (n < 0)
+        return fail(KERR_EINVAL, "kerr_trace_camera_pixels: n = %lld < 0", (long long)n);
+    if (n > 0 && (!index || !is_device_ptr(index)))
+        return fail(KERR_EINVAL, "kerr_trace_camera_pixels: index must be device memory");
+    return kerr_trace_camera_list(c, cam, index, nullptr, n, o, x_out, k_out, status, steps, diag,
+                                  cross, stream);
 }
 
 extern "C" int kerr_get_stats(kerr_ctx *c, kerr_stats *out)
@@ -774,6 +876,10 @@ extern "C" int kerr_get_stats(kerr_ctx *c, kerr_stats *out)
     out->deferred = (int64_t)s[SC_DEFERRED];
     out->requeued = (int64_t)s[SC_REQUEUED];
     out->queue_errors = (int64_t)s[SC_STATUS + ST_NONE];
+    out->rhs_fp32_zone_phase = (int64_t)s[SC_RHS32_ZONE];
+    out->attempts_fp32_zone_phase = (int64_t)s[SC_ATT32_ZONE];
+    out->clips = (int64_t)s[SC_CLIPS];
+    out->clip_rhs = (int64_t)s[SC_CLIP_RHS];
     for (int j = 0; j < 8; ++j)
         out->status_count[j] = (int64_t)s[SC_STATUS + j];
     float ms = 0.f;
@@ -794,68 +900,444 @@ extern "C" int kerr_get_stats(kerr_ctx *c, kerr_stats *out)
     return KERR_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner (the analogue of the paper's run-time tuning of the work-group
+// size, Sec. 4): stepping variants (block size x register cap x geodesics
+// per thread x right-hand-side mode), then zone-phase variants with the
+// chosen stepping variant, each timed on a sample of the workload; results
+// optionally kept in a cache file keyed by GPU, workload shape and precision.
+// ---------------------------------------------------------------------------
+namespace {
+
+uint32_t fnv1a_bytes(const void *data, size_t bytes, uint32_t h = 2166136261u)
+{
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < bytes; ++i) {
+        h ^= p[i];
+        h *= 16777619u;
+    }
+    return h;
+}
+
+// Name of the current GPU with its SM count, e.g. "NVIDIA GB300 (152 SMs)".
+int gpu_label(char *buf, size_t cap)
+{
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KERR_ECUDA, "autotune: cannot query the device");
+    }
+    std::snprintf(buf, cap, "%s (%d SMs)", prop.name, prop.multiProcessorCount);
+    return KERR_OK;
+}
+
+void options_key(const kerr_opts *o, char *buf, size_t cap)
+{
+    std::snprintf(buf, cap, "prec=%d:tol=%.3g:zone=%.3g:zprec=%d:renorm=%d", o->prec, o->tol,
+                  o->prec == KERR_FP32_KAHAN ? o->fp64_zone : 0.0, o->zone_prec, o->renorm_every);
+}
+
+// Field separators of the cache file must not occur inside a field.
+bool clean_field(const char *s)
+{
+    for (; *s; ++s)
+        if (*s == '\t' || *s == '\n' || *s == '\r')
+            return false;
+    return true;
+}
+
+// Times the candidates with `run(variant, zone_variant)` (which traces the
+// sample and returns KERR_OK) and the stats' kernel_ms: one untimed call per
+// candidate (graph capture, buffers), then the minimum of `reps` timed ones.
+template <typename Run>
+int sweep(kerr_ctx *c, const kerr_opts *o, int reps, Run run, kerr_tuning *t)
+{
+    const int prec = o->prec;
+    auto time_one = [&](int v, int zv, float *ms) -> int {
+        float best = 1e30f;
+        for (int rep = 0; rep <= reps; ++rep) {
+            int rc = run(v, zv);
+            if (rc)
+                return rc;
+            kerr_stats st;
+            rc = kerr_get_stats(c, &st);
+            if (rc)
+                return rc;
+            if (rep > 0)
+                best = std::min(best, st.kernel_ms);
+        }
+        *ms = best;
+        return KERR_OK;
+    };
+    const bool zone = prec == KERR_FP32_KAHAN && o->fp64_zone > 0.0;
+    const int zdef = zone ? kDefaultZoneVariant : -1;
+    int best_v = kDefaultVariant[prec];
+    float best_ms = 1e30f;
+    t->timed = 0;
+    for (int v = 0; v < kNumVariants; ++v) {
+        if (prec == KERR_FP64 && kVariantRays[v] != 1)
+            continue;                       // two geodesics per thread: FP32 only
+        float ms = 0.f;
+        int rc = time_one(v, zdef, &ms);
+        if (rc)
+            return rc;
+        ++t->timed;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_v = v;
+        }
+    }
+    int best_z = zdef;
+    if (zone) {
+        for (int zv = 0; zv < kNumZoneVariants; ++zv) {
+            if (zv == zdef)
+                continue;                   // timed with the stepping variants
+            float ms = 0.f;
+            int rc = time_one(best_v, zv, &ms);
+            if (rc)
+                return rc;
+            ++t->timed;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_z = zv;
+            }
+        }
+    }
+    t->variant = best_v;
+    t->zone_variant = best_z;
+    t->ms = best_ms;
+    t->from_cache = 0;
+    c->tuned[prec] = best_v;
+    c->tuned_zone[prec] = best_z;
+    return KERR_OK;
+}
+
+struct DevBufs {
+    std::vector<void *> p;
+    ~DevBufs()
+    {
+        for (void *q : p)
+            cudaFree(q);
+    }
+    template <typename T> cudaError_t get(T **out, size_t bytes)
+    {
+        void *q = nullptr;
+        cudaError_t e = dev_alloc(&q, bytes);
+        if (e == cudaSuccess)
+            p.push_back(q);
+        *out = (T *)q;
+        return e;
+    }
+};
+
+// Looks the workload up in the cache (when a path is given); on a hit applies
+// the stored choice to the context.
+int cache_hit(kerr_ctx *c, const kerr_opts *o, const char *path, const char *key,
+              kerr_tuning *out, bool *hit)
+{
+    *hit = false;
+    if (!path)
+        return KERR_OK;
+    char gpu[256];
+    int rc = gpu_label(gpu, sizeof gpu);
+    if (rc)
+        return rc;
+    rc = kerr_tune_cache_lookup(path, gpu, key, out);
+    if (rc < 0)
+        return rc;
+    if (rc == KERR_OK) {
+        const bool zone = o->prec == KERR_FP32_KAHAN && o->fp64_zone > 0.0;
+        if (out->variant < 0 || out->variant >= kNumVariants ||
+            (o->prec == KERR_FP64 && kVariantRays[out->variant] != 1) ||
+            out->zone_variant >= kNumZoneVariants || (zone && out->zone_variant < 0))
+            return fail(KERR_EINVAL, "autotune cache: stored configuration is out of range");
+        c->tuned[o->prec] = out->variant;
+        c->tuned_zone[o->prec] = zone ? out->zone_variant : -1;
+        out->from_cache = 1;
+        *hit = true;
+    }
+    return KERR_OK;
+}
+
+int cache_store(const char *path, const char *key, const kerr_tuning *t)
+{
+    if (!path)
+        return KERR_OK;
+    char gpu[256];
+    int rc = gpu_label(gpu, sizeof gpu);
+    if (rc)
+        return rc;
+    return kerr_tune_cache_store(path, gpu, key, t);
+}
+
+} // namespace
+
+extern "C" int kerr_tune_cache_lookup(const char *path, const char *gpu, const char *key,
+                                      kerr_tuning *out)
+{
+    if (!path || !gpu || !key || !out)
+        return fail(KERR_EINVAL, "kerr_tune_cache_lookup: NULL argument");
+    FILE *f = std::fopen(path, "r");
+    if (!f)
+        return 1;                           // no cache yet: a miss
+    char line[1024];
+    bool found = false;
+    kerr_tuning t;
+    std::memset(&t, 0, sizeof t);
+    int lineno = 0;
+    while (std::fgets(line, sizeof line, f)) {
+        ++lineno;
+        const size_t len = std::strlen(line);
+        if (len == 0 || line[0] == '#' || line[0] == '\n')
+            continue;
+        if (line[len - 1] != '\n' && !std::feof(f)) {
+            std::fclose(f);
+            return fail(KERR_EINVAL, "kerr_tune_cache_lookup: line %d too long", lineno);
+        }
+        // gpu \t key \t variant \t zone_variant \t ms
+        char *fields[5];
+        int nf = 0;
+        char *p = line;
+        fields[nf++] = p;
+        for (; *p && nf < 5; ++p)
+            if (*p == '\t') {
+                *p = '\0';
+                fields[nf++] = p + 1;
+            }
+        int v = 0, zv = 0;
+        float ms = 0.f;
+        if (nf != 5 || std::sscanf(fields[2], "%d", &v) != 1 ||
+            std::sscanf(fields[3], "%d", &zv) != 1 || std::sscanf(fields[4], "%f", &ms) != 1) {
+            std::fclose(f);
+            return fail(KERR_EINVAL, "kerr_tune_cache_lookup: malformed line %d", lineno);
+        }
+        if (std::strcmp(fields[0], gpu) == 0 && std::strcmp(fields[1], key) == 0) {
+            t.variant = v;                  // the last matching line wins
+            t.zone_variant = zv;
+            t.ms = ms;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    if (!found)
+        return 1;
+    t.from_cache = 1;
+    *out = t;
+    return KERR_OK;
+}
+
+extern "C" int kerr_tune_cache_store(const char *path, const char *gpu, const char *key,
+                                     const kerr_tuning *t)
+{
+    if (!path || !gpu || !key || !t)
+        return fail(KERR_EINVAL, "kerr_tune_cache_store: NULL argument");
+    if (!clean_field(gpu) || !clean_field(key) || !*gpu || !*key)
+        return fail(KERR_EINVAL, "kerr_tune_cache_store: empty field or tab/newline in a field");
+    FILE *f = std::fopen(path, "a");
+    if (!f)
+        return fail(KERR_EINVAL, "kerr_tune_cache_store: cannot open the cache file");
+    const int n = std::fprintf(f, "%s\t%s\t%d\t%d\t%.6g\n", gpu, key, t->variant,
+                               t->zone_variant, (double)t->ms);
+    const bool closed = std::fclose(f) == 0;
+    if (n < 0 || !closed)
+        return fail(KERR_EINVAL, "kerr_tune_cache_store: write failed");
+    return KERR_OK;
+}
+
+extern "C" int kerr_tune_key_cameras(const kerr_camera *cams, int32_t ncam, const kerr_opts *o,
+                                     char *buf, int32_t cap)
+{
+    if (!cams || ncam < 1 || !o || !buf || cap < 1)
+        return fail(KERR_EINVAL, "kerr_tune_key_cameras: bad argument");
+    int64_t n = 0;
+    uint32_t h = 2166136261u;
+    for (int i = 0; i < ncam; ++i) {
+        const kerr_camera &k = cams[i];
+        n += (int64_t)k.nx * k.ny;
+        const double d[4] = {k.a, k.incl, k.r_obs, k.half_width};
+        const int32_t w[2] = {k.nx, k.ny};
+        h = fnv1a_bytes(d, sizeof d, h);
+        h = fnv1a_bytes(w, sizeof w, h);
+    }
+    char ok[160];
+    options_key(o, ok, sizeof ok);
+    const int m = std::snprintf(buf, (size_t)cap, "cameras:ncam=%d:rays=%lld:geom=%08x:%s", ncam,
+                                (long long)n, h, ok);
+    if (m < 0 || m >= cap)
+        return fail(KERR_EINVAL, "kerr_tune_key_cameras: buffer too small");
+    return KERR_OK;
+}
+
+extern "C" int kerr_tune_key_particles(int64_t n, const kerr_opts *o, char *buf, int32_t cap)
+{
+    if (n < 1 || !o || !buf || cap < 1)
+        return fail(KERR_EINVAL, "kerr_tune_key_particles: bad argument");
+    char ok[160];
+    options_key(o, ok, sizeof ok);
+    const int m = std::snprintf(buf, (size_t)cap, "particles:n=%lld:max_steps=%lld:%s",
+                                (long long)n, (long long)o->max_steps, ok);
+    if (m < 0 || m >= cap)
+        return fail(KERR_EINVAL, "kerr_tune_key_particles: buffer too small");
+    return KERR_OK;
+}
+
+extern "C" int kerr_autotune_cameras(kerr_ctx *c, const kerr_camera *cams, int32_t ncam,
+                                     const kerr_opts *o, int64_t sample, const char *cache_path,
+                                     kerr_tuning *out, void *stream)
+{
+    if (!c || !cams || !out)
+        return fail(KERR_EINVAL, "kerr_autotune_cameras: NULL argument");
+    int rc = check_opts(o);
+    if (rc)
+        return rc;
+    std::vector<CamDev> cd(std::max(ncam, 1));
+    int64_t n = 0;
+    rc = build_cams(cams, ncam, cd.data(), &n);
+    if (rc)
+        return rc;
+    char key[512];
+    rc = kerr_tune_key_cameras(cams, ncam, o, key, sizeof key);
+    if (rc)
+        return rc;
+    bool hit = false;
+    rc = cache_hit(c, o, cache_path, key, out, &hit);
+    if (rc || hit)
+        return rc;
+    if (sample < 1024)
+        sample = 1024;
+    // each camera at a lower resolution over the same field of view, its
+    // share of the sample in proportion to its rays
+    std::vector<kerr_camera> sub(cams, cams + ncam);
+    int64_t m = 0;
+    for (auto &k : sub) {
+        const double share = (double)sample * ((double)k.nx * k.ny) / (double)n;
+        const double f = std::min(1.0, std::sqrt(share / ((double)k.nx * k.ny)));
+        k.nx = std::max(1, std::min(k.nx, (int)std::lround(k.nx * f)));
+        k.ny = std::max(1, std::min(k.ny, (int)std::lround(k.ny * f)));
+        m += (int64_t)k.nx * k.ny;
+    }
+    DevBufs B;
+    double *xo = nullptr, *ko = nullptr;
+    int32_t *so = nullptr, *no = nullptr;
+    cudaError_t e = B.get(&xo, 4 * m * sizeof(double));
+    if (e == cudaSuccess)
+        e = B.get(&ko, 4 * m * sizeof(double));
+    if (e == cudaSuccess)
+        e = B.get(&so, m * sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = B.get(&no, m * sizeof(int32_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KERR_ENOMEM, "kerr_autotune_cameras: allocation failed");
+    }
+    kerr_opts oo = *o;
+    rc = sweep(c, o, 2,
+               [&](int v, int zv) {
+                   oo.variant = v;
+                   oo.zone_variant = zv;
+                   return kerr_trace_camera(c, sub.data(), ncam, &oo, xo, ko, so, no, nullptr,
+                                            nullptr, stream);
+               },
+               out);
+    cudaStreamSynchronize(c->stream);
+    if (rc)
+        return rc;
+    return cache_store(cache_path, key, out);
+}
+
+extern "C" int kerr_autotune_particles(kerr_ctx *c, const double *x0, const double *v0,
+                                       const double *t_end, int64_t n, const kerr_opts *o,
+                                       int64_t sample, const char *cache_path, kerr_tuning *out,
+                                       void *stream)
+{
+    if (!c || !x0 || !v0 || !out)
+        return fail(KERR_EINVAL, "kerr_autotune_particles: NULL argument");
+    int rc = check_opts(o);
+    if (rc)
+        return rc;
+    if (n < 1)
+        return fail(KERR_EINVAL, "kerr_autotune_particles: n = %lld < 1", (long long)n);
+    char key[512];
+    rc = kerr_tune_key_particles(n, o, key, sizeof key);
+    if (rc)
+        return rc;
+    bool hit = false;
+    rc = cache_hit(c, o, cache_path, key, out, &hit);
+    if (rc || hit)
+        return rc;
+    if (sample < 256)
+        sample = 256;
+    const int64_t stride = std::max<int64_t>(1, n / sample);
+    const int64_t m = std::min<int64_t>(sample, (n + stride - 1) / stride);
+    DevBufs B;
+    double *xs = nullptr, *vs = nullptr, *ts = nullptr, *xo = nullptr, *ko = nullptr;
+    int32_t *so = nullptr, *no = nullptr;
+    cudaError_t e = B.get(&xs, 4 * m * sizeof(double));
+    if (e == cudaSuccess)
+        e = B.get(&vs, 3 * m * sizeof(double));
+    if (e == cudaSuccess && t_end)
+        e = B.get(&ts, m * sizeof(double));
+    if (e == cudaSuccess)
+        e = B.get(&xo, 4 * m * sizeof(double));
+    if (e == cudaSuccess)
+        e = B.get(&ko, 4 * m * sizeof(double));
+    if (e == cudaSuccess)
+        e = B.get(&so, m * sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = B.get(&no, m * sizeof(int32_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KERR_ENOMEM, "kerr_autotune_particles: allocation failed");
+    }
+    // every stride-th particle of each plane (the planes may be host or
+    // device memory)
+    auto gather = [&](double *dst, const double *src, int planes) -> cudaError_t {
+        for (int j = 0; j < planes; ++j) {
+            cudaError_t ee = cudaMemcpy2DAsync(dst + j * m, sizeof(double), src + j * n,
+                                               (size_t)stride * sizeof(double), sizeof(double),
+                                               (size_t)m, cudaMemcpyDefault, c->stream);
+            if (ee != cudaSuccess)
+                return ee;
+        }
+        return cudaSuccess;
+    };
+    e = gather(xs, x0, 4);
+    if (e == cudaSuccess)
+        e = gather(vs, v0, 3);
+    if (e == cudaSuccess && t_end)
+        e = gather(ts, t_end, 1);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KERR_ECUDA, "kerr_autotune_particles: sample gather failed: %s",
+                    cudaGetErrorString(e));
+    }
+    kerr_opts oo = *o;
+    rc = sweep(c, o, 1,
+               [&](int v, int zv) {
+                   oo.variant = v;
+                   oo.zone_variant = zv;
+                   return kerr_trace_particles(c, xs, vs, ts, m, &oo, xo, ko, so, no, nullptr,
+                                               nullptr, stream);
+               },
+               out);
+    cudaStreamSynchronize(c->stream);
+    if (rc)
+        return rc;
+    return cache_store(cache_path, key, out);
+}
+
 extern "C" int kerr_autotune(kerr_ctx *c, const kerr_camera *cam, const kerr_opts *o,
                              int64_t sample, int32_t *best, void *stream)
 {
     if (!c || !cam || !best)
         return fail(KERR_EINVAL, "kerr_autotune: NULL argument");
-    int rc = check_opts(o);
+    kerr_tuning t;
+    const int rc = kerr_autotune_cameras(c, cam, 1, o, sample, nullptr, &t, stream);
     if (rc)
         return rc;
-    if (sample < 1024)
-        sample = 1024;
-    kerr_camera sub = *cam;
-    int side = (int)std::lround(std::sqrt((double)sample));
-    sub.nx = std::min(cam->nx, side);
-    sub.ny = std::min(cam->ny, side);
-    const size_t n = (size_t)sub.nx * sub.ny;
-    double *xo = nullptr, *ko = nullptr;
-    int32_t *so = nullptr, *no = nullptr;
-    cudaError_t e = cudaMalloc(&xo, 4 * n * sizeof(double));
-    if (e == cudaSuccess)
-        e = cudaMalloc(&ko, 4 * n * sizeof(double));
-    if (e == cudaSuccess)
-        e = cudaMalloc(&so, n * sizeof(int32_t));
-    if (e == cudaSuccess)
-        e = cudaMalloc(&no, n * sizeof(int32_t));
-    if (e != cudaSuccess) {
-        cudaFree(xo);
-        cudaFree(ko);
-        cudaFree(so);
-        cudaFree(no);
-        cudaGetLastError();
-        return fail(KERR_ENOMEM, "kerr_autotune: allocation failed");
-    }
-    kerr_opts oo = *o;
-    float best_ms = 1e30f;
-    int best_v = 0;
-    for (int v = 0; v < kNumVariants && rc == KERR_OK; ++v) {
-        if (o->prec == KERR_FP64 && kVariantRays[v] != 1)
-            continue;                            // FP32-only launch shapes
-        oo.variant = v;
-        float ms_min = 1e30f;
-        for (int rep = 0; rep < 3 && rc == KERR_OK; ++rep) {
-            rc = kerr_trace_camera(c, &sub, 1, &oo, xo, ko, so, no, nullptr, nullptr, stream);
-            if (rc)
-                break;
-            kerr_stats s;
-            rc = kerr_get_stats(c, &s);
-            if (rep > 0)
-                ms_min = std::min(ms_min, s.kernel_ms);
-        }
-        if (ms_min < best_ms) {
-            best_ms = ms_min;
-            best_v = v;
-        }
-    }
-    cudaStreamSynchronize(c->stream);
-    cudaFree(xo);
-    cudaFree(ko);
-    cudaFree(so);
-    cudaFree(no);
-    if (rc)
-        return rc;
-    c->tuned[o->prec] = best_v;
-    *best = best_v;
+    *best = t.variant;
     return KERR_OK;
 }

@@ -209,15 +209,10 @@ __global__ void __launch_bounds__(128) coordtime_kernel(const CoordParams P)
 template <typename T, bool KAHAN>
 cudaError_t launch(const CoordParams &P, int sms, cudaStream_t s)
 {
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, coordtime_kernel<T, KAHAN>, 128, 0);
-        if (e != cudaSuccess)
-            return e;
-        if (per_sm < 1)
-            per_sm = 1;
-    }
+    int per_sm = 0;
+    const cudaError_t eo = blocks_per_sm((const void *)coordtime_kernel<T, KAHAN>, 128, &per_sm);
+    if (eo != cudaSuccess)
+        return eo;
     long long grid = (long long)per_sm * sms;
     const long long need = (P.n + 127) / 128;
     if (need < grid)

@@ -8,8 +8,8 @@
 // that a library allocating behind their back breaks their accounting.  For
 // them this entry point keeps
 // every byte of its scratch -- work-queue and statistics counters, the camera
-// table, the per-geodesic state and constant planes and the FP64-zone buffer
-// -- in one file-scope device array of fixed size.  The caller still passes
+// table, the per-geodesic state and constant planes, the deferred-clip queue
+// and the FP64-zone buffer -- in one file-scope device array of fixed size.  The caller still passes
 // the output buffers, which must be device memory.
 //
 // The array is a static __device__ symbol, so every GPU that loads the library
@@ -39,11 +39,11 @@ constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 // Layout of the scratch array (byte offsets, each part 256-byte aligned).
-constexpr size_t kCountersWords = 1 + SC_COUNT + 3;     // queue head, stats, zone count/head/push
+constexpr size_t kCountersWords = kCounterWords(SC_COUNT);   // queue, stats, zone and clip counts
 constexpr size_t kOffCounters = 0;
 constexpr size_t kOffCams = align_up(kOffCounters + kCountersWords * sizeof(unsigned long long));
 constexpr size_t kOffWork = align_up(kOffCams + kMaxCams * sizeof(CamDev));
-constexpr size_t kOffZone = align_up(kOffWork + (size_t)kMaxGeo * (16 + KC_COUNT) * sizeof(float));
+constexpr size_t kOffZone = align_up(kOffWork + (size_t)kMaxGeo * kWorkBytesPerGeodesic);
 constexpr size_t kBytes = align_up(kOffZone + (size_t)kZoneCap * sizeof(ZoneEntry));
 static_assert(kBytes == KERR_STATIC_SCRATCH_BYTES, "kerr.h states the scratch size");
 
@@ -87,6 +87,21 @@ int scratch_ptr(int dev, char **out)
     return KERR_OK;
 }
 
+// The camera table travels to the device as a kernel argument (captured by
+// value when the kernel is launched), so no host copy of it has to outlive
+// the call and no pageable-memory copy is involved.
+struct CamTable {
+    CamDev c[kMaxCams];
+};
+static_assert(sizeof(CamTable) <= 4000, "kernel argument size");
+
+__global__ void upload_cams_kernel(const CamTable t, int ncam, CamDev *dst)
+{
+    const int i = threadIdx.x;
+    if (i < ncam)
+        dst[i] = t.c[i];
+}
+
 } // namespace
 
 extern "C" int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam,
@@ -96,28 +111,15 @@ extern "C" int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam,
 {
     if (!cams || ncam < 1 || ncam > kMaxCams)
         return fail(KERR_EINVAL, "kerr_trace_camera_static: need 1..KERR_STATIC_MAX_CAMERAS cameras");
-    if (!o)
-        return fail(KERR_EINVAL, "kerr_trace_camera_static: opts is NULL");
-    if (o->prec != KERR_FP64 && o->prec != KERR_FP32_KAHAN)
-        return fail(KERR_EINVAL, "kerr_trace_camera_static: unknown precision");
-    if (!(o->tol > 0.0) || !(o->h0 > 0.0) || o->max_steps < 0 || o->clip_maxit < 1 ||
-        o->renorm_every < 0 || !(o->fp64_zone >= 0.0) || o->variant < -1 ||
-        (o->zone_prec != KERR_ZONE_FP64 && o->zone_prec != KERR_ZONE_F32X2) ||
-        o->zone_variant < -1 || o->zone_variant >= kNumZoneVariants ||
-        o->zone_quantum < 0 || o->variant >= kNumVariants ||
-        (o->prec == KERR_FP64 && o->variant >= 0 && kVariantRays[o->variant] != 1))
-        return fail(KERR_EINVAL, "kerr_trace_camera_static: invalid options");
-    CamDev cd[kMaxCams];
+    // the same checks as kerr_trace_camera
+    int rc = check_opts(o);
+    if (rc)
+        return rc;
+    CamTable table;
     int64_t n = 0;
-    for (int i = 0; i < ncam; ++i) {
-        const kerr_camera &k = cams[i];
-        const double rh = 1.0 + std::sqrt(std::fmax(0.0, 1.0 - k.a * k.a));
-        if (!(std::fabs(k.a) <= 1.0) || k.nx <= 0 || k.ny <= 0 || !(k.half_width > 0.0) ||
-            !(k.r_obs > 1.01 * rh) || !std::isfinite(k.r_obs) || !std::isfinite(k.incl))
-            return fail(KERR_EINVAL, "kerr_trace_camera_static: invalid camera");
-        cd[i] = CamDev{k.a, k.incl, k.r_obs, k.half_width, k.nx, k.ny, n};
-        n += (int64_t)k.nx * k.ny;
-    }
+    rc = build_cams(cams, ncam, table.c, &n);
+    if (rc)
+        return rc;
     if (n > kMaxGeo)
         return fail(KERR_EINVAL, "kerr_trace_camera_static: more rays than "
                                  "KERR_STATIC_MAX_GEODESICS; use kerr_trace_camera");
@@ -137,19 +139,21 @@ extern "C" int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam,
         return fail(KERR_ECUDA, "kerr_trace_camera_static: cudaDeviceGetAttribute failed");
     }
     char *base = nullptr;
-    int rc = scratch_ptr(dev, &base);
+    rc = scratch_ptr(dev, &base);
     if (rc)
         return rc;
     cudaStream_t s = (cudaStream_t)stream;
     unsigned long long *ctr = (unsigned long long *)(base + kOffCounters);
     CamDev *dcams = (CamDev *)(base + kOffCams);
-    float *work = (float *)(base + kOffWork);
+    char *work = base + kOffWork;
     ZoneEntry *zone = (ZoneEntry *)(base + kOffZone);
 
     // the previous call's counters are still in the array: clear them
     cudaError_t e = cudaMemsetAsync(ctr, 0, kCountersWords * sizeof(unsigned long long), s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dcams, cd, (size_t)ncam * sizeof(CamDev), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        upload_cams_kernel<<<1, kMaxCams, 0, s>>>(table, ncam, dcams);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(KERR_ECUDA, "kerr_trace_camera_static: clearing the scratch failed");
@@ -185,8 +189,7 @@ extern "C" int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam,
     P.zpush = ctr + 3 + SC_COUNT;
     const int variant = o->variant >= 0 ? o->variant : kDefaultVariant[o->prec == KERR_FP32_KAHAN];
     if (o->prec == KERR_FP32_KAHAN) {
-        P.s_state = work;
-        P.s_const = work + (size_t)16 * n;
+        bind_f32_scratch(P, work, ctr, n);
         if (P.fp64_zone > 0.0) {
             P.zbuf = zone;
             P.zcap = kZoneCap;
@@ -197,6 +200,8 @@ extern "C" int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam,
         if (e == cudaSuccess && P.zbuf)
             e = launch_zone_phase(P, o->zone_variant >= 0 ? o->zone_variant : kDefaultZoneVariant,
                                   sms, s);
+        if (e == cudaSuccess)
+            e = launch_clip_f32(P, sms, s);
         if (e == cudaSuccess)
             e = launch_finish_f32(P, sms, s);
     } else {

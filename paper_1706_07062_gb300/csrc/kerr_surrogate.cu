@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -363,21 +364,21 @@ static int ensure_batch(kerr_surrogate *s, int64_t rows, bool training)
     free_batch(s);
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < kLayers && e == cudaSuccess; ++l)
-        e = cudaMalloc(&s->A[l], (size_t)rows * in_dim(l) * sizeof(bf16));
+        e = dev_alloc(&s->A[l], (size_t)rows * in_dim(l) * sizeof(bf16));
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->out, (size_t)rows * kOutPad * sizeof(float));
+        e = dev_alloc(&s->out, (size_t)rows * kOutPad * sizeof(float));
     if (training) {
         for (int l = 0; l < kLayers - 1 && e == cudaSuccess; ++l)
-            e = cudaMalloc(&s->Z[l], (size_t)rows * kHidden * sizeof(float));
+            e = dev_alloc(&s->Z[l], (size_t)rows * kHidden * sizeof(float));
         if (e == cudaSuccess)
-            e = cudaMalloc(&s->dOut, (size_t)rows * kOutPad * sizeof(bf16));
+            e = dev_alloc(&s->dOut, (size_t)rows * kOutPad * sizeof(bf16));
         for (int i = 0; i < 2; ++i)
             if (e == cudaSuccess)
-                e = cudaMalloc(&s->dZ[i], (size_t)rows * kHidden * sizeof(bf16));
+                e = dev_alloc(&s->dZ[i], (size_t)rows * kHidden * sizeof(bf16));
         const int64_t ldT = (rows + 7) / 8 * 8;
         auto zalloc = [&](bf16 **p, int64_t h) {
             if (e == cudaSuccess)
-                e = cudaMalloc(p, (size_t)h * ldT * sizeof(bf16));
+                e = dev_alloc(p, (size_t)h * ldT * sizeof(bf16));
             if (e == cudaSuccess)
                 e = cudaMemset(*p, 0, (size_t)h * ldT * sizeof(bf16));
         };
@@ -439,23 +440,23 @@ extern "C" int kerr_surrogate_create(const float *init, kerr_surrogate **out)
     const size_t n = kL.total;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->w, n * sizeof(float));
+        e = dev_alloc(&s->w, n * sizeof(float));
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->g, n * sizeof(float));
+        e = dev_alloc(&s->g, n * sizeof(float));
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->m, n * sizeof(float));
+        e = dev_alloc(&s->m, n * sizeof(float));
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->v, n * sizeof(float));
+        e = dev_alloc(&s->v, n * sizeof(float));
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->wbf, n * sizeof(bf16));
+        e = dev_alloc(&s->wbf, n * sizeof(bf16));
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->wbfT, n * sizeof(bf16));
+        e = dev_alloc(&s->wbfT, n * sizeof(bf16));
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->loss, sizeof(float));
+        e = dev_alloc(&s->loss, sizeof(float));
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->wpk, packed_weight_elems() * sizeof(bf16));
+        e = dev_alloc(&s->wpk, packed_weight_elems() * sizeof(bf16));
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->tc_err, sizeof(unsigned));
+        e = dev_alloc(&s->tc_err, sizeof(unsigned));
     if (e == cudaSuccess)
         e = cudaMemset(s->tc_err, 0, sizeof(unsigned));
     if (e == cudaSuccess)
@@ -801,11 +802,11 @@ extern "C" int kerr_surrogate_train(kerr_surrogate *s, const float *in, const fl
         return e;
     };
     const int U = (int)std::min<int64_t>(8, total);
-    cudaError_t e = cudaMalloc(&d_epoch, sizeof(float) * epochs);
+    cudaError_t e = dev_alloc(&d_epoch, sizeof(float) * epochs);
     if (e == cudaSuccess)
-        e = cudaMalloc(&ctl, sizeof(StepCtl));
+        e = dev_alloc(&ctl, sizeof(StepCtl));
     if (e == cudaSuccess)
-        e = cudaMalloc(&sched, sizeof(float3) * (size_t)total);
+        e = dev_alloc(&sched, sizeof(float3) * (size_t)total);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sched, hs.data(), sizeof(float3) * (size_t)total,
                             cudaMemcpyHostToDevice, st);
@@ -921,15 +922,15 @@ extern "C" int kerr_surrogate_targets(kerr_ctx *ctx, const double *points, int64
     double *x = nullptr, *k = nullptr;
     int32_t *stat = nullptr, *nst = nullptr;
     float *cr = nullptr;
-    cudaError_t e = cudaMalloc(&x, (size_t)n * 4 * sizeof(double));
+    cudaError_t e = dev_alloc(&x, (size_t)n * 4 * sizeof(double));
     if (e == cudaSuccess)
-        e = cudaMalloc(&k, (size_t)n * 4 * sizeof(double));
+        e = dev_alloc(&k, (size_t)n * 4 * sizeof(double));
     if (e == cudaSuccess)
-        e = cudaMalloc(&stat, (size_t)n * sizeof(int32_t));
+        e = dev_alloc(&stat, (size_t)n * sizeof(int32_t));
     if (e == cudaSuccess)
-        e = cudaMalloc(&nst, (size_t)n * sizeof(int32_t));
+        e = dev_alloc(&nst, (size_t)n * sizeof(int32_t));
     if (e == cudaSuccess)
-        e = cudaMalloc(&cr, (size_t)n * 5 * sizeof(float));
+        e = dev_alloc(&cr, (size_t)n * 5 * sizeof(float));
     int rc = KERR_OK;
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1222,13 +1223,13 @@ static int ensure_render(RenderScratch &r, int64_t n, cudaStream_t st)
 {
     cudaError_t e = cudaSuccess;
     if (!r.curve) {
-        e = cudaMalloc(&r.curve, (size_t)2 * kCurveSamples * sizeof(float2));
+        e = dev_alloc(&r.curve, (size_t)2 * kCurveSamples * sizeof(float2));
         if (e == cudaSuccess)
-            e = cudaMalloc(&r.rint, 2 * sizeof(double));
+            e = dev_alloc(&r.rint, 2 * sizeof(double));
         if (e == cudaSuccess)
-            e = cudaMalloc(&r.bounds, sizeof(float4));
+            e = dev_alloc(&r.bounds, sizeof(float4));
         if (e == cudaSuccess)
-            e = cudaMalloc(&r.cnt, sizeof(unsigned long long));
+            e = dev_alloc(&r.cnt, sizeof(unsigned long long));
     }
     if (e == cudaSuccess && n > r.cap_n) {
         cudaStreamSynchronize(st);
@@ -1238,11 +1239,11 @@ static int ensure_render(RenderScratch &r, int64_t n, cudaStream_t st)
         r.in = r.o = nullptr;
         r.idx = nullptr;
         r.cap_n = 0;
-        e = cudaMalloc(&r.in, (size_t)n * kIn * sizeof(float));
+        e = dev_alloc(&r.in, (size_t)n * kIn * sizeof(float));
         if (e == cudaSuccess)
-            e = cudaMalloc(&r.o, (size_t)n * kOut * sizeof(float));
+            e = dev_alloc(&r.o, (size_t)n * kOut * sizeof(float));
         if (e == cudaSuccess)
-            e = cudaMalloc(&r.idx, (size_t)n * sizeof(int64_t));
+            e = dev_alloc(&r.idx, (size_t)n * sizeof(int64_t));
         if (e == cudaSuccess)
             r.cap_n = n;
     }
@@ -1269,15 +1270,15 @@ static int ensure_fallback(RenderScratch &r, int64_t m, cudaStream_t st)
     r.crs = nullptr;
     r.cap_m = 0;
     const int64_t want = std::max<int64_t>(m, 1 << 16);
-    cudaError_t e = cudaMalloc(&r.x, (size_t)want * 4 * sizeof(double));
+    cudaError_t e = dev_alloc(&r.x, (size_t)want * 4 * sizeof(double));
     if (e == cudaSuccess)
-        e = cudaMalloc(&r.k, (size_t)want * 4 * sizeof(double));
+        e = dev_alloc(&r.k, (size_t)want * 4 * sizeof(double));
     if (e == cudaSuccess)
-        e = cudaMalloc(&r.stat, (size_t)want * sizeof(int32_t));
+        e = dev_alloc(&r.stat, (size_t)want * sizeof(int32_t));
     if (e == cudaSuccess)
-        e = cudaMalloc(&r.nst, (size_t)want * sizeof(int32_t));
+        e = dev_alloc(&r.nst, (size_t)want * sizeof(int32_t));
     if (e == cudaSuccess)
-        e = cudaMalloc(&r.crs, (size_t)want * 5 * sizeof(float));
+        e = dev_alloc(&r.crs, (size_t)want * 5 * sizeof(float));
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_render(r);
@@ -1364,3 +1365,134 @@ extern "C" int kerr_surrogate_render(kerr_ctx *ctx, kerr_surrogate *s, const ker
     return rc;
 }
 
+
+// ---------------------------------------------------------------------------
+// Parameter files: a 96-byte header and the FP32 parameter vector, both
+// little-endian (the byte order of every host this library builds for).
+// Host code only; the checksum is FNV-1a over the parameter bytes.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct ParamFileHeader {
+    char magic[8];          // "KERRSURR"
+    uint32_t version;       // 1
+    uint32_t header_bytes;  // 96
+    int64_t num_params;
+    int32_t layers;
+    int32_t in_width[kLayers];
+    int32_t out_width[kLayers];
+    int32_t live_in, live_out;
+    float input_scale;
+    uint32_t checksum;
+    uint8_t reserved[12];
+};
+static_assert(sizeof(ParamFileHeader) == 96, "parameter file header layout");
+
+const char kParamMagic[8] = {'K', 'E', 'R', 'R', 'S', 'U', 'R', 'R'};
+
+uint32_t fnv1a(const void *data, size_t bytes)
+{
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    uint32_t h = 2166136261u;
+    for (size_t i = 0; i < bytes; ++i) {
+        h ^= p[i];
+        h *= 16777619u;
+    }
+    return h;
+}
+
+ParamFileHeader expected_header()
+{
+    ParamFileHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, kParamMagic, sizeof h.magic);
+    h.version = 1;
+    h.header_bytes = sizeof(ParamFileHeader);
+    h.num_params = (int64_t)kL.total;
+    h.layers = kLayers;
+    for (int l = 0; l < kLayers; ++l) {
+        h.in_width[l] = in_dim(l);
+        h.out_width[l] = out_dim(l);
+    }
+    h.live_in = kIn;
+    h.live_out = kOut;
+    h.input_scale = KERR_SURR_INPUT_SCALE;
+    return h;
+}
+
+} // namespace
+
+extern "C" int kerr_params_write(const char *path, const float *params, int64_t n)
+{
+    if (!path || !params)
+        return fail(KERR_EINVAL, "kerr_params_write: NULL argument");
+    if (n != (int64_t)kL.total)
+        return fail(KERR_EINVAL, "kerr_params_write: n is not kerr_surrogate_num_params()");
+    ParamFileHeader h = expected_header();
+    const size_t bytes = (size_t)n * sizeof(float);
+    h.checksum = fnv1a(params, bytes);
+    FILE *f = std::fopen(path, "wb");
+    if (!f)
+        return fail(KERR_EINVAL, "kerr_params_write: cannot open the file for writing");
+    const bool ok = std::fwrite(&h, sizeof h, 1, f) == 1 &&
+                    std::fwrite(params, 1, bytes, f) == bytes;
+    const bool closed = std::fclose(f) == 0;
+    if (!ok || !closed)
+        return fail(KERR_EINVAL, "kerr_params_write: write failed");
+    return KERR_OK;
+}
+
+extern "C" int kerr_params_read(const char *path, float *params, int64_t n)
+{
+    if (!path || !params)
+        return fail(KERR_EINVAL, "kerr_params_read: NULL argument");
+    if (n != (int64_t)kL.total)
+        return fail(KERR_EINVAL, "kerr_params_read: n is not kerr_surrogate_num_params()");
+    FILE *f = std::fopen(path, "rb");
+    if (!f)
+        return fail(KERR_EINVAL, "kerr_params_read: cannot open the file");
+    ParamFileHeader h;
+    const size_t bytes = (size_t)n * sizeof(float);
+    bool ok = std::fread(&h, sizeof h, 1, f) == 1;
+    const ParamFileHeader want = expected_header();
+    // every field but the checksum must be this network's
+    ParamFileHeader cmp = h;
+    if (ok)
+        cmp.checksum = 0;
+    if (!ok || std::memcmp(&cmp, &want, sizeof want) != 0) {
+        std::fclose(f);
+        return fail(KERR_EINVAL, "kerr_params_read: not a parameter file of this network "
+                                 "(magic, version or layer widths differ)");
+    }
+    ok = std::fread(params, 1, bytes, f) == bytes;
+    const bool extra = ok && std::fgetc(f) != EOF;
+    std::fclose(f);
+    if (!ok || extra)
+        return fail(KERR_EINVAL, "kerr_params_read: the file has the wrong length");
+    if (fnv1a(params, bytes) != h.checksum)
+        return fail(KERR_EINVAL, "kerr_params_read: checksum mismatch (corrupted file)");
+    return KERR_OK;
+}
+
+extern "C" int kerr_surrogate_save(kerr_surrogate *s, const char *path)
+{
+    if (!s || !path)
+        return fail(KERR_EINVAL, "kerr_surrogate_save: NULL argument");
+    std::vector<float> p(kL.total);
+    int rc = kerr_surrogate_get_params(s, p.data());
+    if (rc)
+        return rc;
+    return kerr_params_write(path, p.data(), (int64_t)p.size());
+}
+
+extern "C" int kerr_surrogate_load(const char *path, kerr_surrogate **out)
+{
+    if (!path || !out)
+        return fail(KERR_EINVAL, "kerr_surrogate_load: NULL argument");
+    *out = nullptr;
+    std::vector<float> p(kL.total);
+    int rc = kerr_params_read(path, p.data(), (int64_t)p.size());
+    if (rc)
+        return rc;
+    return kerr_surrogate_create(p.data(), out);
+}

@@ -52,7 +52,11 @@ enum : int {
     SC_REQUEUED = 7, // zone phase: geodesics put back behind waiting ones
     SC_STATUS = 8,   // 8 slots: geodesics per status code; slot 0 (no status)
                      // counts zone-queue hand-overs that timed out (never expected)
-    SC_COUNT = 16
+    SC_RHS32_ZONE = 16,  // zone phase: FP32 right-hand sides (steps outside the zone)
+    SC_ATT32_ZONE = 17,  // zone phase: FP32 attempts
+    SC_CLIPS = 18,       // end points clipped onto an event surface
+    SC_CLIP_RHS = 19,    // right-hand sides of those clips
+    SC_COUNT = 20
 };
 
 // State of one geodesic handed from the FP32 phase to the FP64-zone phase
@@ -108,6 +112,7 @@ struct TraceParams {
     int32_t zone_quantum;       // zone phase: attempts before a geodesic yields its
                                 // lane to a waiting one (0: run to the end)
     uint64_t budget_ns;
+    const int32_t *abort;       // host-writable stop flag (mapped pinned memory), or null
     unsigned long long *head;   // work-queue counter, zero at launch
     unsigned long long *stats;  // SC_COUNT counters, zero at launch
     float *s_state;             // FP32 path: [16][n] planes y[0..7], c[0..7]
@@ -120,6 +125,16 @@ struct TraceParams {
     double *traj;               // FP64 path: stored solution [n][traj_cap][9] (lambda, y)
     int32_t traj_cap;           // records per geodesic (the start state is the first)
     int32_t *traj_count;        // [n] records stored
+    // FP32 path, deferred clipping (all null: clip in place).  A geodesic whose
+    // accepted step crosses an event surface keeps its state from before the
+    // step in s_state, the step length in clip_h and the event value at the
+    // unclipped end in clip_shi, and is queued in clipq: geodesics whose last
+    // step ran in FP32 from the front (count *cq32), those whose last step
+    // ran in the zone's arithmetic from the back (count *cq64).
+    float *clip_h;              // [n]
+    double *clip_shi;           // [n]
+    int64_t *clipq;             // [n]
+    unsigned long long *cq32, *cq64;
 };
 
 // Coordinate-time integration (Sec. 2.2, eq. geo_t): launch parameters.
@@ -418,18 +433,25 @@ __device__ __forceinline__ void two_halves(const T a, const T a2, const T y[8], 
 // components i >= 1 of |d_i - df_i| / 15 relative to tol (1 + max(|y_i|,
 // |y_i + d_i|)), with d the two-half-step and df the full-step increment
 // (Richardson's estimate of the local error of the more accurate solution).
+// The running maximum is kept as one fraction num / den: each candidate
+// e_i / sc_i is compared by cross-multiplying (sc_i, den > 0, products far
+// from overflow), and one division by den remains at the end instead of one
+// per component.  A NaN component makes the measure NaN (a rejected step).
 __device__ __forceinline__ float err_norm_f(const float y[8], const float d[8], const float df[8],
                                             const float tol)
 {
-    float err = 0.f;
+    float num = 0.f, den = 1.f;
+    bool bad = false;
 #pragma unroll
     for (int i = 1; i < 8; ++i) {
-        const float delta = (d[i] - df[i]) * (float)(1.0 / 15.0);
+        const float e = fabsf((d[i] - df[i]) * (float)(1.0 / 15.0));
         const float sc = tol * (1.f + fmaxf(fabsf(y[i]), fabsf(y[i] + d[i])));
-        const float e = fabsf(delta) / sc;
-        err = (e <= err) ? err : e;    // NaN propagates
+        const bool take = e * den > num * sc;
+        num = take ? e : num;
+        den = take ? sc : den;
+        bad = bad || !(e == e);
     }
-    return err;
+    return bad ? __int_as_float(0x7fc00000) : __fdiv_rn(num, den);
 }
 
 // One step-doubling attempt: returns the error measure and the increment of
@@ -624,13 +646,20 @@ __device__ __forceinline__ void load_const_full(const TraceParams &P, int64_t id
 
 // LAZY: rc holds the FP32 fields only; the renormalisation loads the FP64
 // ones when it runs.
+// A step that ended on an event surface whose clipping is left to the clip
+// pass: the state stays the one before the step, h its length.
+struct ClipRec {
+    bool pending = false;
+    double s_hi = 0.0;          // event value at the unclipped end of the step
+};
+
 template <bool KAHAN, typename T, bool FAST_FACTOR = false, int RM = RHS_INLINE,
           bool LAZY = false>
 __device__ __forceinline__ int step_post(const RayConst &rc, const TraceParams &P, int64_t id,
                                          const T a, const T a2, const T A0[4], const T d[8],
                                          const T err, T y[8], T c[8], T &h, T &rn,
                                          uint32_t &nrhs, uint32_t &nacc, int &since_renorm,
-                                         T *h_taken = nullptr)
+                                         T *h_taken = nullptr, ClipRec *defer = nullptr)
 {
     T fac;
     if constexpr (FAST_FACTOR)
@@ -670,29 +699,55 @@ __device__ __forceinline__ int step_post(const RayConst &rc, const TraceParams &
     // places them to 1e-10, which the regula falsi reaches in fewer
     // single-lane iterations than the FP64 path's 1e-12
     const T stol = FAST_FACTOR ? T(1e-10) : Prec<T>::stol();
+    // clipping left to the clip pass (not with crossing labels: a crossing in
+    // the last step is located on the clipped step)
+    const bool defer_ok = defer != nullptr && P.cross == nullptr;
     int st = ST_NONE;
     T h_used = h;
+    bool pending = false;
+    T s_pend = T(0);
     if (rn < rcap) {
-        const T s_lo = event_value<KAHAN>(0, a2, y, c, rcap, T(0));
-        h_used = clip<KAHAN, T, RM>(a, a2, y, c, A0, h, 0, rcap, T(0), s_lo, rn - rcap,
-                             stol * rcap, Prec<T>::eps(), maxit, yn, cn, nrhs);
         st = ST_CAPTURED;
+        if (defer_ok) {
+            pending = true;
+            s_pend = rn - rcap;
+        } else {
+            const T s_lo = event_value<KAHAN>(0, a2, y, c, rcap, T(0));
+            h_used = clip<KAHAN, T, RM>(a, a2, y, c, A0, h, 0, rcap, T(0), s_lo, rn - rcap,
+                                        stol * rcap, Prec<T>::eps(), maxit, yn, cn, nrhs);
+        }
     } else if (rn > resc && k_fma(yn[1], yn[5], k_fma(yn[2], yn[6], yn[3] * yn[7])) > T(0)) {
         const T s_lo = event_value<KAHAN>(0, a2, y, c, resc, T(0));
-        if (s_lo <= T(0))
-            h_used = clip<KAHAN, T, RM>(a, a2, y, c, A0, h, 0, resc, T(0), s_lo, rn - resc,
-                                 stol * resc, Prec<T>::eps(), maxit, yn, cn, nrhs);
+        if (s_lo <= T(0)) {
+            if (defer_ok) {
+                pending = true;
+                s_pend = rn - resc;
+            } else {
+                h_used = clip<KAHAN, T, RM>(a, a2, y, c, A0, h, 0, resc, T(0), s_lo, rn - resc,
+                                            stol * resc, Prec<T>::eps(), maxit, yn, cn, nrhs);
+            }
+        }
         st = ST_ESCAPED;
     } else if (rc.use_t) {
         const T tend = RC<T>::tend(rc), tlo = RC<T>::tendlo(rc);
         const T s_hi = event_value<KAHAN>(1, a2, yn, cn, tend, tlo);
         if ((s_hi > T(0)) != (rc.tpos != 0)) {
-            const T s_lo = event_value<KAHAN>(1, a2, y, c, tend, tlo);
-            const T sc = fmax(T(1), fabs(tend));
-            h_used = clip<KAHAN, T, RM>(a, a2, y, c, A0, h, 1, tend, tlo, s_lo, s_hi,
-                                 stol * sc, Prec<T>::eps(), maxit, yn, cn, nrhs);
+            if (defer_ok) {
+                pending = true;
+                s_pend = s_hi;
+            } else {
+                const T s_lo = event_value<KAHAN>(1, a2, y, c, tend, tlo);
+                const T sc = fmax(T(1), fabs(tend));
+                h_used = clip<KAHAN, T, RM>(a, a2, y, c, A0, h, 1, tend, tlo, s_lo, s_hi,
+                                            stol * sc, Prec<T>::eps(), maxit, yn, cn, nrhs);
+            }
             st = ST_ENDTIME;
         }
+    }
+    if (pending) {
+        defer->pending = true;
+        defer->s_hi = to_d(s_pend);
+        return st;
     }
     // equatorial crossings within [y, end point]
     if (P.cross) {
@@ -756,7 +811,7 @@ template <bool KAHAN, typename T, bool FAST_FACTOR = false, int RM = RHS_INLINE>
 __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &P, int64_t id,
                                          const T tol, T y[8], T c[8], T &h, T &rn,
                                          uint32_t &nrhs, uint32_t &nacc, int &since_renorm,
-                                         T *h_taken = nullptr)
+                                         T *h_taken = nullptr, ClipRec *defer = nullptr)
 {
     const T a = RC<T>::a(rc);
     const T a2 = a * a;
@@ -766,7 +821,7 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
     const T err = attempt<RM>(a, a2, y, A0, h, tol, d);
     nrhs += 11;
     return step_post<KAHAN, T, FAST_FACTOR, RM>(rc, P, id, a, a2, A0, d, err, y, c, h, rn, nrhs,
-                                                nacc, since_renorm, h_taken);
+                                                nacc, since_renorm, h_taken, defer);
 }
 
 // ---------------------------------------------------------------------------
@@ -943,6 +998,21 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
+// A stop request: the launch's wall-time budget ran out, or the host set the
+// context's abort flag (mapped pinned memory, read at system scope so that a
+// host write made while the kernel runs becomes visible).
+__device__ __forceinline__ bool stop_requested(const TraceParams &P, unsigned long long t_start)
+{
+    if (P.budget_ns && (global_ns() - t_start) > P.budget_ns)
+        return true;
+    if (P.abort) {
+        int32_t v;
+        asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(P.abort) : "memory");
+        return v != 0;
+    }
+    return false;
+}
+
 // One attempted step of an FP32+Kahan geodesic taken in FP64 (inside the
 // zone r < fp64_zone r_h, where f l l is large): the compensated pair is
 // folded into one FP64 state, stepped, and split back.  Kept out of line so
@@ -958,6 +1028,7 @@ struct ZoneResult {
     int st;
     uint32_t nrhs, nacc;
     int since_renorm;
+    ClipRec clip;               // the step's clipping was deferred (state before it)
 };
 
 template <int RM>
@@ -975,7 +1046,8 @@ static __device__ __noinline__ ZoneResult zone_step(const RayConst rc, const Tra
     R.nrhs = 0;
     R.nacc = 0;
     R.st = step_once<false, double, true, RM>(rc, P, id, P.tol, yd, cd, hd, rd, R.nrhs,
-                                              R.nacc, since_renorm);
+                                              R.nacc, since_renorm, nullptr,
+                                              P.clipq ? &R.clip : nullptr);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         R.s.y[i] = (float)yd[i];
@@ -1004,7 +1076,8 @@ static __device__ __noinline__ ZoneResult zone_step_df(const RayConst rc, const 
     R.nrhs = 0;
     R.nacc = 0;
     R.st = step_once<false, dfloat, true, RM>(rc, P, id, dfloat((float)P.tol), yd, cd, hd, rd,
-                                              R.nrhs, R.nacc, since_renorm);
+                                              R.nrhs, R.nacc, since_renorm, nullptr,
+                                              P.clipq ? &R.clip : nullptr);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         R.s.y[i] = yd[i].hi;
@@ -1039,6 +1112,7 @@ __device__ __forceinline__ double geodesic_spin(const TraceParams &P, int64_t id
 struct Counters {
     uint32_t geo = 0, att = 0, acc = 0, rhs32 = 0, rhs64 = 0, att64 = 0, def = 0, req = 0;
     uint32_t st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t r32z = 0, a32z = 0, clips = 0, clip_rhs = 0;
     __device__ __forceinline__ void status(int s)
     {
 #pragma unroll
@@ -1061,6 +1135,7 @@ struct Counters {
 #pragma unroll
         for (int j = 0; j < 8; ++j)
             w[j] = wsum(st[j]);
+        const unsigned long long u[4] = {wsum(r32z), wsum(a32z), wsum(clips), wsum(clip_rhs)};
         if ((threadIdx.x & 31) == 0) {
             const int slot[8] = {SC_GEODESICS, SC_ATTEMPTS, SC_ACCEPTED, SC_RHS32,
                                  SC_RHS64,     SC_ATT64,    SC_DEFERRED, SC_REQUEUED};
@@ -1072,6 +1147,10 @@ struct Counters {
             for (int j = 0; j < 8; ++j)
                 if (w[j])
                     atomicAdd(stats + SC_STATUS + j, w[j]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (u[j])
+                    atomicAdd(stats + SC_RHS32_ZONE + j, u[j]);
         }
     }
 };
@@ -1270,10 +1349,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f64_kernel(const TraceParam
                 has = false;
             }
         }
-        if (P.budget_ns && ((++iter & 31u) == 0) && !timed_out) {
+        if ((P.budget_ns || P.abort) && ((++iter & 31u) == 0) && !timed_out) {
             bool over = false;
             if (lane == 0)
-                over = (global_ns() - t_start) > P.budget_ns;
+                over = stop_requested(P, t_start);
             timed_out = __shfl_sync(FULL, over, 0);
         }
     }
@@ -1291,6 +1370,29 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f64_kernel(const TraceParam
 //   f32_finish_kernel  folds the compensated pairs into FP64 outputs and
 //                      computes the FP64 diagnostics (whole warps).
 // ===========================================================================
+// Appends the geodesics of the warp whose clipping was deferred to the clip
+// queue (warp-aggregated; every lane of the warp calls this): FP32 clips from
+// the front, zone-arithmetic clips from the back.  Each geodesic ends once,
+// so the two ends never meet.
+__device__ __forceinline__ void enqueue_clips(const TraceParams &P, bool pend32, bool pend64,
+                                              int64_t id)
+{
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lt_mask = (1u << (threadIdx.x & 31)) - 1u;
+    const unsigned m32 = __ballot_sync(FULL, pend32);
+    if (m32) {
+        const unsigned long long b = warp_claim(P.cq32, m32);
+        if (pend32)
+            P.clipq[b + __popc(m32 & lt_mask)] = id;
+    }
+    const unsigned m64 = __ballot_sync(FULL, pend64);
+    if (m64) {
+        const unsigned long long b = warp_claim(P.cq64, m64);
+        if (pend64)
+            P.clipq[P.n - 1 - (int64_t)(b + __popc(m64 & lt_mask))] = id;
+    }
+}
+
 // Number of geodesics of a launch: n, or the device-side count when given.
 __device__ __forceinline__ int64_t live_count(const TraceParams &P)
 {
@@ -1366,6 +1468,143 @@ static __global__ void __launch_bounds__(256) f32_finish_kernel(const TraceParam
                 P.diag[j * n + id] = cst[j];
         }
     }
+}
+
+// Event surface of a geodesic that ended with status st: kind (0: r, 1: t),
+// target value, its low part (float-pair end time) and the scale of the
+// clipping tolerance -- as chosen by step_post.
+template <typename T>
+__device__ __forceinline__ void event_of(const RayConst &rc, int st, int &kind, T &target, T &tlo,
+                                         T &scale)
+{
+    tlo = T(0);
+    if (st == ST_CAPTURED) {
+        kind = 0;
+        target = RC<T>::rcap(rc);
+        scale = target;
+    } else if (st == ST_ESCAPED) {
+        kind = 0;
+        target = RC<T>::resc(rc);
+        scale = target;
+    } else {
+        kind = 1;
+        target = RC<T>::tend(rc);
+        tlo = RC<T>::tendlo(rc);
+        scale = fmax(T(1), fabs(target));
+    }
+}
+
+__device__ __forceinline__ void load_const_f32(const TraceParams &P, int64_t id, RayConst &rc);
+
+// The deferred clip of a geodesic whose last step was an FP32 step: the same
+// Illinois iteration step_post runs in place (FP32, compensated state).
+__device__ __forceinline__ void clip_end_f32(const TraceParams &P, int64_t id, int st, float y[8],
+                                             float c[8], uint32_t &nrhs)
+{
+    RayConst rc;
+    load_const_f32(P, id, rc);
+    const float a = rc.af, a2 = a * a;
+    float A0[4];
+    rhs<RHS_CALL>(a, a2, y[1], y[2], y[3], y[4], y[5], y[6], y[7], A0);
+    ++nrhs;
+    int kind = 0;
+    float target, tlo, scale;
+    event_of<float>(rc, st, kind, target, tlo, scale);
+    const float s_lo = event_value<true>(kind, a2, y, c, target, tlo);
+    float ye[8], ce[8];
+    clip<true, float, RHS_CALL>(a, a2, y, c, A0, P.clip_h[id], kind, target, tlo, s_lo,
+                                (float)P.clip_shi[id], Prec<float>::stol() * scale,
+                                Prec<float>::eps(), P.clip_maxit, ye, ce, nrhs);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        y[i] = ye[i];
+        c[i] = ce[i];
+    }
+}
+
+__device__ __forceinline__ double zfold(float y, float c, double) { return (double)y + (double)c; }
+__device__ __forceinline__ dfloat zfold(float y, float c, dfloat) { return quick_two_sum(y, c); }
+__device__ __forceinline__ void zsplit(double v, float &y, float &c)
+{
+    y = (float)v;
+    c = (float)(v - (double)y);
+}
+__device__ __forceinline__ void zsplit(dfloat v, float &y, float &c)
+{
+    y = v.hi;
+    c = v.lo;
+}
+
+// The deferred clip of a geodesic whose last step was a zone step (FP64 or
+// float-float): the zone step's arithmetic and its 1e-10 tolerance.
+template <typename T>
+__device__ void clip_end_zone(const TraceParams &P, int64_t id, int st, float y[8], float c[8],
+                              uint32_t &nrhs)
+{
+    RayConst rc;
+    load_const_full(P, id, rc);
+    T yd[8], cd[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        yd[i] = zfold(y[i], c[i], T(0));
+        cd[i] = T(0);
+    }
+    const T a = RC<T>::a(rc), a2 = a * a;
+    T A0[4];
+    rhs<RHS_CALL>(a, a2, yd[1], yd[2], yd[3], yd[4], yd[5], yd[6], yd[7], A0);
+    ++nrhs;
+    int kind = 0;
+    T target, tlo, scale;
+    event_of<T>(rc, st, kind, target, tlo, scale);
+    const T s_lo = event_value<false>(kind, a2, yd, cd, target, tlo);
+    T ye[8], ce[8];
+    clip<false, T, RHS_CALL>(a, a2, yd, cd, A0, T(P.clip_h[id]), kind, target, tlo, s_lo,
+                             from_d<T>(P.clip_shi[id]), T(1e-10) * scale, Prec<T>::eps(),
+                             P.clip_maxit, ye, ce, nrhs);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        zsplit(ye[i], y[i], c[i]);
+}
+
+// Clip pass of the FP32 path: finishes, with whole warps, the geodesics whose
+// last step crossed an event surface -- work that ran for one lane at a time
+// while the rest of its warp waited when it was done inside the stepping
+// loops.  Threads below the FP32 count take FP32 clips, the others zone
+// clips, so a warp mixes the two at most once.
+static __global__ void __launch_bounds__(128) f32_clip_kernel(const TraceParams P)
+{
+    const int64_t n = P.n;
+    const unsigned long long n32 = *P.cq32, n64 = *P.cq64;
+    const unsigned long long total = n32 + n64;
+    Counters C;
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+         k < total; k += (unsigned long long)gridDim.x * blockDim.x) {
+        const bool fp32 = k < n32;
+        const int64_t id = fp32 ? P.clipq[k] : P.clipq[n - 1 - (int64_t)(k - n32)];
+        const int st = P.status[id];
+        float y[8], c[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            y[i] = P.s_state[i * n + id];
+            c[i] = P.s_state[(8 + i) * n + id];
+        }
+        uint32_t nrhs = 0;
+        if (fp32)
+            clip_end_f32(P, id, st, y, c, nrhs);
+        else if (P.zone_df)
+            clip_end_zone<dfloat>(P, id, st, y, c, nrhs);
+        else
+            clip_end_zone<double>(P, id, st, y, c, nrhs);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            P.s_state[i * n + id] = y[i];
+            P.s_state[(8 + i) * n + id] = c[i];
+        }
+        ++C.clips;
+        C.clip_rhs += nrhs;
+    }
+    // every thread of the grid reaches here (grid-stride loop above)
+    C.flush(P.stats);
 }
 
 // FP32 lane constants from the planes (PHASE 0) -- no FP64 arithmetic.
@@ -1558,8 +1797,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                 }
             }
         }
+        // clipping deferred to the clip pass: the last step ran in FP32 (front
+        // of the clip queue) or in the zone's arithmetic (back)
+        bool pend32 = false, pend64 = false;
         if (has) {
             int st = ST_NONE;
+            ClipRec cr;
+            bool zone_step_taken = false;
             if (timed_out) {
                 st = ST_TIMEOUT;
             } else if ((int64_t)nsteps >= P.max_steps) {
@@ -1593,6 +1837,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     rnow = R.s.rnow;
                     since_renorm = R.since_renorm;
                     st = R.st;
+                    cr = R.clip;
+                    zone_step_taken = true;
                     C.rhs64 += R.nrhs;
                     C.acc += R.nacc;
                     ++C.att64;
@@ -1603,8 +1849,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     // default stepping variant, so that a geodesic's FP32
                     // steps are the same arithmetic in either launch)
                     st = step_once<true, float, false, PHASE == 0 ? RM : RHS_CALL>(
-                        rc, P, id, tol, y, c, h, rnow, r, C.acc, since_renorm);
+                        rc, P, id, tol, y, c, h, rnow, r, C.acc, since_renorm, nullptr,
+                        P.clipq ? &cr : nullptr);
                     C.rhs32 += r;
+                    if (PHASE != 0) {
+                        C.r32z += r;
+                        ++C.a32z;
+                    }
                 }
             }
             if (st != ST_NONE) {
@@ -1615,10 +1866,18 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                 }
                 P.status[id] = st;
                 P.steps[id] = (int32_t)nsteps;
+                if (cr.pending) {
+                    P.clip_h[id] = h;
+                    P.clip_shi[id] = cr.s_hi;
+                    pend64 = zone_step_taken;
+                    pend32 = !zone_step_taken;
+                }
                 C.status(st);
                 has = false;
             }
         }
+        if (P.clipq)
+            enqueue_clips(P, pend32, pend64, id);
         // ---- zone phase: after zone_quantum attempts a geodesic yields its
         // lane to one that waits in the queue (processor sharing), so that
         // the phase is not left with a second, partly filled wave of lanes
@@ -1660,11 +1919,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                 }
             }
         }
-        // ---- wall-time budget (warp-uniform decision)
-        if (P.budget_ns && ((++iter & 31u) == 0) && !timed_out) {
+        // ---- wall-time budget or abort flag (warp-uniform decision)
+        if ((P.budget_ns || P.abort) && ((++iter & 31u) == 0) && !timed_out) {
             bool over = false;
             if (lane == 0)
-                over = (global_ns() - t_start) > P.budget_ns;
+                over = stop_requested(P, t_start);
             timed_out = __shfl_sync(FULL, over, 0);
         }
     }

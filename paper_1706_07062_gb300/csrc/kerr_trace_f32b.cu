@@ -8,16 +8,10 @@ namespace kerr {
 template <int PH, int B, int M, int RM>
 static cudaError_t launch_one(const TraceParams &P, int sms, cudaStream_t s, bool clamp_to_n)
 {
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaError_t e =
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_f32_kernel<PH, B, M, RM>, B,
-                                                          0);
-        if (e != cudaSuccess)
-            return e;
-        if (per_sm < 1)
-            per_sm = 1;
-    }
+    int per_sm = 0;
+    const cudaError_t eo = blocks_per_sm((const void *)trace_f32_kernel<PH, B, M, RM>, B, &per_sm);
+    if (eo != cudaSuccess)
+        return eo;
     long long grid = (long long)per_sm * sms;
     const long long need = (P.n + B - 1) / B;
     if (clamp_to_n && need < grid)

@@ -171,6 +171,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32x2_kernel(const TracePar
         // ---- per-slot checks; in-place zone steps (zone buffer full or absent)
         int st[2] = {ST_NONE, ST_NONE};
         bool fp32_step[2] = {false, false};
+        ClipRec cr[2];
+        bool zstep[2] = {false, false};
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             if (!has[s])
@@ -207,6 +209,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32x2_kernel(const TracePar
                     rnow[s] = R.s.rnow;
                     since_renorm[s] = R.since_renorm;
                     st[s] = R.st;
+                    cr[s] = R.clip;
+                    zstep[s] = true;
                     C.rhs64 += R.nrhs;
                     C.acc += R.nacc;
                     ++C.att64;
@@ -245,7 +249,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32x2_kernel(const TracePar
                 st[s] = step_post<true, float, false, RM, true>(slot_rc(rc[s]), P, id[s], rc[s].af,
                                                                 slot_get(a2, s), A0s, ds, err, ys,
                                                                 cs, h[s], rnow[s], r, C.acc,
-                                                                since_renorm[s]);
+                                                                since_renorm[s], nullptr,
+                                                                P.clipq ? &cr[s] : nullptr);
                 C.rhs32 += r;
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -254,7 +259,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32x2_kernel(const TracePar
                 }
             }
         }
-        // ---- geodesics that ended
+        // ---- geodesics that ended (a deferred clip keeps the state before
+        // the step and goes to the clip queue)
+        bool p32[2] = {false, false}, p64[2] = {false, false};
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             if (st[s] == ST_NONE)
@@ -267,14 +274,25 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32x2_kernel(const TracePar
             }
             P.status[g] = st[s];
             P.steps[g] = (int32_t)nsteps[s];
+            if (cr[s].pending) {
+                P.clip_h[g] = h[s];
+                P.clip_shi[g] = cr[s].s_hi;
+                p64[s] = zstep[s];
+                p32[s] = !zstep[s];
+            }
             C.status(st[s]);
             has[s] = false;
         }
+        if (P.clipq) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+                enqueue_clips(P, p32[s], p64[s], id[s]);
+        }
         // ---- wall-time budget (warp-uniform decision)
-        if (P.budget_ns && ((++iter & 31u) == 0) && !timed_out) {
+        if ((P.budget_ns || P.abort) && ((++iter & 31u) == 0) && !timed_out) {
             bool over = false;
             if (lane == 0)
-                over = (global_ns() - t_start) > P.budget_ns;
+                over = stop_requested(P, t_start);
             timed_out = __shfl_sync(FULL, over, 0);
         }
     }

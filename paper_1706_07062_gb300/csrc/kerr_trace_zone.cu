@@ -18,6 +18,32 @@ static cudaError_t launch_zone(const TraceParams &P, int sms, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_clip_f32(const TraceParams &P, int sms, cudaStream_t s)
+{
+    f32_clip_kernel<<<(unsigned)(4 * sms), 128, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+void bind_f32_scratch(TraceParams &P, void *work, unsigned long long *ctr, int64_t n)
+{
+    static_assert(KC_COUNT == 9, "kWorkBytesPerGeodesic counts 9 constant planes");
+    static_assert(kWorkBytesPerGeodesic == 120, "FP32-path scratch layout");
+    char *w = static_cast<char *>(work);
+    const size_t nn = (size_t)n;
+    P.s_state = reinterpret_cast<float *>(w);
+    P.s_const = P.s_state + 16 * nn;
+    P.clip_h = P.s_const + (size_t)KC_COUNT * nn;
+    P.clip_shi = reinterpret_cast<double *>(w + (16 + KC_COUNT + 1) * sizeof(float) * nn);
+    P.clipq = reinterpret_cast<int64_t *>(P.clip_shi + nn);
+    P.head = ctr;
+    P.stats = ctr + 1;
+    P.zcount = ctr + 1 + SC_COUNT;
+    P.zhead = ctr + 2 + SC_COUNT;
+    P.zpush = ctr + 3 + SC_COUNT;
+    P.cq32 = ctr + 4 + SC_COUNT;
+    P.cq64 = ctr + 5 + SC_COUNT;
+}
+
 cudaError_t launch_zone_phase(const TraceParams &P, int zv, int sms, cudaStream_t s)
 {
     switch (zv) {

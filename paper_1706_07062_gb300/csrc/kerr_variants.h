@@ -1,6 +1,11 @@
 // kerr_variants.h -- launch configurations of the persistent kernel.
 #pragma once
 
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kerr.h"
+
 namespace kerr {
 
 // (threads per block, minimum resident blocks per SM).  The second number
@@ -56,11 +61,47 @@ cudaError_t launch_trace_f64(const TraceParams &P, int v, int sms, cudaStream_t 
 cudaError_t launch_zone_phase(const TraceParams &P, int zv, int sms, cudaStream_t s);
 cudaError_t launch_setup_f32(const TraceParams &P, int sms, cudaStream_t s);
 cudaError_t launch_finish_f32(const TraceParams &P, int sms, cudaStream_t s);
+// Clip pass of the FP32 path (geodesics whose clipping was deferred).
+cudaError_t launch_clip_f32(const TraceParams &P, int sms, cudaStream_t s);
+
+// FP32-path scratch per geodesic: state and constant planes, then the
+// deferred-clip step length (float), event value (double) and queue (int64).
+constexpr size_t kWorkBytesPerGeodesic = (16 + 9) * sizeof(float) + sizeof(float) +
+                                         sizeof(double) + sizeof(int64_t);
+// Counters ahead of the FP32 path's scratch: queue head, statistics, zone
+// count / head / re-queue count, clip-queue counts (FP32 front, zone back).
+constexpr int kCounterWords(int sc_count) { return 1 + sc_count + 3 + 2; }
+
+// Points the FP32 path's scratch pointers of P into `work` (n geodesics,
+// kWorkBytesPerGeodesic each, 8-byte aligned) and `ctr` (kCounterWords).
+void bind_f32_scratch(TraceParams &P, void *work, unsigned long long *ctr, int64_t n);
 
 struct CoordParams;
 // Coordinate-time integration in FP64 (fp32 = 0) or FP32 with compensated
 // state updates (fp32 = 1), persistent grid over `sms` SMs.
 cudaError_t launch_coordtime(const CoordParams &P, int fp32, int sms, cudaStream_t s);
+
+// Resident blocks per SM (at least 1) of kernel `fn` launched with `block`
+// threads and no dynamic shared memory on the current device.  Looked up once
+// per (kernel, device) and cached under a lock, so that a process that drives
+// several GPUs, or calls from several host threads, gets each device's value.
+cudaError_t blocks_per_sm(const void *fn, int block, int *out);
+
+// Checks shared by the trace entry points (KERR_OK, or the error code with
+// kerr_last_error() set): the options, and a camera list, which is converted
+// to the kernels' table out[0 .. ncam-1] with *n = the total number of rays.
+int check_opts(const kerr_opts *o);
+struct CamDev;
+int build_cams(const kerr_camera *cams, int32_t ncam, CamDev *out, int64_t *n);
+
+// Device allocation used by every library-owned buffer: cudaMalloc, unless
+// an injected failure is armed (kerr_debug_fail_alloc), in which case the
+// chosen allocation reports cudaErrorMemoryAllocation without allocating.
+cudaError_t dev_alloc_bytes(void **p, size_t bytes);
+template <typename T> inline cudaError_t dev_alloc(T **p, size_t bytes)
+{
+    return dev_alloc_bytes(reinterpret_cast<void **>(p), bytes);
+}
 
 // Records `msg` as this thread's kerr_last_error() and returns `code`.
 int kerr_set_error(int code, const char *msg);

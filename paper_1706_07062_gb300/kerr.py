@@ -58,7 +58,10 @@ class Stats(ctypes.Structure):
                 ("deferred", ctypes.c_int64),
                 ("status_count", ctypes.c_int64 * 8), ("kernel_ms", ctypes.c_float),
                 ("variant", ctypes.c_int32), ("phase_ms", ctypes.c_float * 4),
-                ("requeued", ctypes.c_int64), ("queue_errors", ctypes.c_int64)]
+                ("requeued", ctypes.c_int64), ("queue_errors", ctypes.c_int64),
+                ("rhs_fp32_zone_phase", ctypes.c_int64),
+                ("attempts_fp32_zone_phase", ctypes.c_int64),
+                ("clips", ctypes.c_int64), ("clip_rhs", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_
@@ -66,6 +69,16 @@ class Stats(ctypes.Structure):
         d["status_count"] = list(self.status_count)
         d["phase_ms"] = list(self.phase_ms)
         return d
+
+
+class Tuning(ctypes.Structure):
+    """kerr_tuning."""
+    _fields_ = [("variant", ctypes.c_int32), ("zone_variant", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("from_cache", ctypes.c_int32),
+                ("timed", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _lib = None
@@ -126,6 +139,26 @@ def lib():
         L.kerr_trace_rays_dense.argtypes = [vp, vp, vp, i64, c.POINTER(Opts), i32, vp, vp, vp,
                                             vp, vp, vp, vp]
         L.kerr_dense_find_time.argtypes = [c.c_double, vp, i32, vp, i64, vp, vp, vp, vp, vp]
+        L.kerr_fma_chain.argtypes = [i32, i64, i32, vp, c.POINTER(c.c_double), vp]
+        L.kerr_trace_camera_pixels.argtypes = [vp, c.POINTER(Camera), vp, i64, c.POINTER(Opts),
+                                               vp, vp, vp, vp, vp, vp, vp]
+        L.kerr_abort_flag.argtypes = [vp, c.POINTER(c.POINTER(i32))]
+        L.kerr_debug_fail_alloc.argtypes = [i32]
+        L.kerr_params_write.argtypes = [c.c_char_p, vp, i64]
+        L.kerr_params_read.argtypes = [c.c_char_p, vp, i64]
+        L.kerr_surrogate_save.argtypes = [vp, c.c_char_p]
+        L.kerr_surrogate_load.argtypes = [c.c_char_p, c.POINTER(vp)]
+        L.kerr_autotune_cameras.argtypes = [vp, c.POINTER(Camera), i32, c.POINTER(Opts), i64,
+                                            c.c_char_p, c.POINTER(Tuning), vp]
+        L.kerr_autotune_particles.argtypes = [vp, vp, vp, vp, i64, c.POINTER(Opts), i64,
+                                              c.c_char_p, c.POINTER(Tuning), vp]
+        L.kerr_tune_key_cameras.argtypes = [c.POINTER(Camera), i32, c.POINTER(Opts), c.c_char_p,
+                                            i32]
+        L.kerr_tune_key_particles.argtypes = [i64, c.POINTER(Opts), c.c_char_p, i32]
+        L.kerr_tune_cache_lookup.argtypes = [c.c_char_p, c.c_char_p, c.c_char_p,
+                                             c.POINTER(Tuning)]
+        L.kerr_tune_cache_store.argtypes = [c.c_char_p, c.c_char_p, c.c_char_p,
+                                            c.POINTER(Tuning)]
         L.kerr_last_error.restype = c.c_char_p
         for name in ("kerr_init", "kerr_destroy", "kerr_trace_rays", "kerr_trace_particles",
                      "kerr_trace_camera", "kerr_trace_camera_static", "kerr_get_stats",
@@ -139,7 +172,12 @@ def lib():
                      "kerr_surrogate_forward_impl", "kerr_rk4_fixed",
                      "kerr_trace_coordtime", "kerr_rk4_fixed_bl",
                      "kerr_bl_camera_states", "kerr_trace_rays_dense",
-                     "kerr_dense_find_time"):
+                     "kerr_dense_find_time", "kerr_fma_chain", "kerr_abort_flag",
+                     "kerr_debug_fail_alloc", "kerr_params_write", "kerr_params_read",
+                     "kerr_surrogate_save", "kerr_surrogate_load", "kerr_autotune_cameras",
+                     "kerr_autotune_particles", "kerr_tune_key_cameras",
+                     "kerr_tune_key_particles", "kerr_tune_cache_lookup",
+                     "kerr_tune_cache_store", "kerr_trace_camera_pixels"):
             getattr(L, name).restype = c.c_int
         _lib = L
     return _lib
@@ -308,6 +346,22 @@ def kerr_trace_camera(ctx: Context, cams, opts: Opts | None = None, out: TraceOu
                                    _ptr(out.k), _ptr(out.status), _ptr(out.steps),
                                    _ptr(out.diag), _ptr(out.cross), _stream_ptr(stream, out.x)),
            "kerr_trace_camera")
+    return out
+
+
+def kerr_trace_camera_pixels(ctx: Context, cam: Camera, index, opts: Opts | None = None,
+                             out: TraceOut | None = None, stream=None) -> TraceOut:
+    """Trace the pixels `index` (device int64 tensor of flat indices) of one
+    camera; entry i of the outputs belongs to pixel index[i]."""
+    n = int(index.numel())
+    opts = opts or default_opts()
+    if out is None:
+        out = alloc_out(n, index.device)
+    _check(lib().kerr_trace_camera_pixels(ctx.handle, ctypes.byref(cam), _ptr(index), n,
+                                          ctypes.byref(opts), _ptr(out.x), _ptr(out.k),
+                                          _ptr(out.status), _ptr(out.steps), _ptr(out.diag),
+                                          _ptr(out.cross), _stream_ptr(stream, index)),
+           "kerr_trace_camera_pixels")
     return out
 
 
@@ -623,3 +677,135 @@ def kerr_dense_find_time(a: float, traj, traj_count, t_target, stream=None):
                                       _ptr(t_target), _ptr(y), _ptr(lam), _ptr(found),
                                       _stream_ptr(stream, traj)), "kerr_dense_find_time")
     return y, lam, found
+
+
+PEAK_FP32, PEAK_FP64, PEAK_FP32X2 = 0, 1, 2
+
+
+def kerr_fma_chain(kind: int, rounds: int, sink, blocks_per_sm: int = 4, stream=None) -> float:
+    """Launch the FMA-chain peak kernel on `stream` (the caller times it);
+    returns the FLOPs the launch performs.  sink: device float32 tensor of at
+    least SMs x blocks_per_sm x 256 elements."""
+    flops = ctypes.c_double()
+    _check(lib().kerr_fma_chain(int(kind), int(rounds), int(blocks_per_sm), _ptr(sink),
+                                ctypes.byref(flops), _stream_ptr(stream, sink)), "kerr_fma_chain")
+    return flops.value
+
+
+# ---------------------------------------------------------------------------
+# failure handling, parameter files, autotuning with a cache
+# ---------------------------------------------------------------------------
+class AbortFlag:
+    """The context's host-writable abort flag (kerr_abort_flag): set() makes
+    running and later launches stop (KERR_TIMEOUT), clear() re-arms."""
+
+    def __init__(self, ctx: Context):
+        p = ctypes.POINTER(ctypes.c_int32)()
+        _check(lib().kerr_abort_flag(ctx.handle, ctypes.byref(p)), "kerr_abort_flag")
+        self._p = p
+        self._ctx = ctx          # the flag lives as long as the context
+
+    def set(self, value: int = 1):
+        self._p[0] = int(value)
+
+    def clear(self):
+        self._p[0] = 0
+
+    def value(self) -> int:
+        return int(self._p[0])
+
+
+def kerr_abort_flag(ctx: Context) -> AbortFlag:
+    return AbortFlag(ctx)
+
+
+def kerr_debug_fail_alloc(n: int):
+    _check(lib().kerr_debug_fail_alloc(int(n)), "kerr_debug_fail_alloc")
+
+
+def kerr_params_write(path: str, params: np.ndarray):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib().kerr_params_write(os.fsencode(path), p.ctypes.data, p.size),
+           "kerr_params_write")
+
+
+def kerr_params_read(path: str) -> np.ndarray:
+    out = np.empty(kerr_surrogate_num_params(), np.float32)
+    _check(lib().kerr_params_read(os.fsencode(path), out.ctypes.data, out.size),
+           "kerr_params_read")
+    return out
+
+
+def kerr_surrogate_save(s: "Surrogate", path: str):
+    _check(lib().kerr_surrogate_save(s.handle, os.fsencode(path)), "kerr_surrogate_save")
+
+
+def kerr_surrogate_load(path: str) -> "Surrogate":
+    h = ctypes.c_void_p()
+    _check(lib().kerr_surrogate_load(os.fsencode(path), ctypes.byref(h)), "kerr_surrogate_load")
+    s = Surrogate.__new__(Surrogate)
+    s.handle = h
+    return s
+
+
+def kerr_autotune_cameras(ctx: Context, cams, opts: Opts | None = None, sample: int = 1 << 18,
+                          cache_path: str | None = None, stream=None) -> Tuning:
+    if isinstance(cams, Camera):
+        cams = [cams]
+    arr = (Camera * len(cams))(*cams)
+    t = Tuning()
+    opts = opts or default_opts()
+    _check(lib().kerr_autotune_cameras(ctx.handle, arr, len(cams), ctypes.byref(opts), int(sample),
+                                       os.fsencode(cache_path) if cache_path else None,
+                                       ctypes.byref(t), _stream_ptr(stream)),
+           "kerr_autotune_cameras")
+    return t
+
+
+def kerr_autotune_particles(ctx: Context, x0, v0, t_end=None, opts: Opts | None = None,
+                            sample: int = 1 << 14, cache_path: str | None = None,
+                            stream=None) -> Tuning:
+    n = int(x0.shape[-1])
+    t = Tuning()
+    opts = opts or default_opts()
+    _check(lib().kerr_autotune_particles(ctx.handle, _ptr(x0), _ptr(v0), _ptr(t_end), n,
+                                         ctypes.byref(opts), int(sample),
+                                         os.fsencode(cache_path) if cache_path else None,
+                                         ctypes.byref(t), _stream_ptr(stream, x0)),
+           "kerr_autotune_particles")
+    return t
+
+
+def kerr_tune_key_cameras(cams, opts: Opts | None = None) -> str:
+    if isinstance(cams, Camera):
+        cams = [cams]
+    arr = (Camera * len(cams))(*cams)
+    buf = ctypes.create_string_buffer(512)
+    opts = opts or default_opts()
+    _check(lib().kerr_tune_key_cameras(arr, len(cams), ctypes.byref(opts), buf, len(buf)),
+           "kerr_tune_key_cameras")
+    return buf.value.decode()
+
+
+def kerr_tune_key_particles(n: int, opts: Opts | None = None) -> str:
+    buf = ctypes.create_string_buffer(512)
+    opts = opts or default_opts()
+    _check(lib().kerr_tune_key_particles(int(n), ctypes.byref(opts), buf, len(buf)),
+           "kerr_tune_key_particles")
+    return buf.value.decode()
+
+
+def kerr_tune_cache_lookup(path: str, gpu: str, key: str) -> Tuning | None:
+    """The stored choice for (gpu, key), or None when the cache has none."""
+    t = Tuning()
+    rc = lib().kerr_tune_cache_lookup(os.fsencode(path), gpu.encode(), key.encode(),
+                                      ctypes.byref(t))
+    if rc == 1:
+        return None
+    _check(rc, "kerr_tune_cache_lookup")
+    return t
+
+
+def kerr_tune_cache_store(path: str, gpu: str, key: str, t: Tuning):
+    _check(lib().kerr_tune_cache_store(os.fsencode(path), gpu.encode(), key.encode(),
+                                       ctypes.byref(t)), "kerr_tune_cache_store")

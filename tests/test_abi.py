@@ -50,16 +50,18 @@ def test_library_exports_every_declared_symbol(libpath):
 def test_struct_layout_matches_binding(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "kerr.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(kerr_opts),'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(kerr_opts),'
                     ' sizeof(kerr_camera), sizeof(kerr_stats), offsetof(kerr_opts, budget_ns),'
-                    ' offsetof(kerr_stats, kernel_ms), offsetof(kerr_camera, ny)); return 0;}\n')
+                    ' offsetof(kerr_stats, kernel_ms), offsetof(kerr_camera, ny),'
+                    ' sizeof(kerr_tuning), offsetof(kerr_stats, clip_rhs)); return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)],
                    check=True)
     vals = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True,
                                         check=True).stdout.split()))
     assert vals == [ctypes.sizeof(K.Opts), ctypes.sizeof(K.Camera), ctypes.sizeof(K.Stats),
-                    K.Opts.budget_ns.offset, K.Stats.kernel_ms.offset, K.Camera.ny.offset]
+                    K.Opts.budget_ns.offset, K.Stats.kernel_ms.offset, K.Camera.ny.offset,
+                    ctypes.sizeof(K.Tuning), K.Stats.clip_rhs.offset]
 
 
 def test_defaults_and_variants_without_gpu(libpath):
