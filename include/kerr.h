@@ -91,8 +91,9 @@ typedef struct kerr_ctx kerr_ctx;
  * for the surface by Illinois regula falsi, to |r - r_stop| <= 1e-12 r_stop on
  * the FP64 path, 2e-6 r_stop for FP32 steps and 1e-10 r_stop for the FP64 (or
  * float-float) zone steps of the FP32+Kahan path, whose end points are only
- * good to ~1e-6 anyway (the same factors for t with scale max(1, |t_end|)),
- * or clip_maxit iterations.  A geodesic that starts inside 1.01 r_h is
+ * good to ~1e-6 anyway (for t the same factors times max(1, |t_end|), except
+ * FP32 steps: 2e-6 times max(1, the step's change of t)), or clip_maxit
+ * iterations.  A geodesic that starts inside 1.01 r_h is
  * captured with no step; one that reaches max_steps attempts is MAXSTEPS. */
 typedef struct {
     int32_t prec;          /* KERR_FP64 or KERR_FP32_KAHAN                       */

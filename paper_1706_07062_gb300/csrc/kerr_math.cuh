@@ -108,12 +108,19 @@ __device__ __forceinline__ T ks_r(T a2, T x, T y, T z)
 // parametrised flat-space geodesic) reduce F to -f L^2 (l^i d_i f) / 2.
 // The pieces:
 //   r from eq. CKSr; d_i r = (f/2) (x, y, z (1 + a^2/r^2));
-//   f = 2 r^3 / (r^4 + a^2 z^2);  d_i f = f (3/r - 2f) d_i r - 2 f a^2 z/(r^4 + a^2 z^2) delta_iz;
-//   l_i = ((r x + a y), (r y - a x)) / (r^2 + a^2), z / r;
+//   f = 2 r^3 / q, q = r^4 + a^2 z^2;  d_i f = c1 d_i r + g delta_iz with
+//     c1 = f (3/r - 2f), g = -2 f a^2 z / q;
+//   l_i = (P x + Q y, P y - Q x, z / r), P = r/s, Q = a/s, s = r^2 + a^2;
 //   d_al l_i = (d_al r) e_i + M_{al i}, with
-//     e = ((x - 2 r l_x) / (r^2 + a^2), (y - 2 r l_y) / (r^2 + a^2), -l_z / r),
-//     M_{xx} = M_{yy} = r / (r^2 + a^2), M_{yx} = -M_{xy} = a / (r^2 + a^2),
-//     M_{zz} = 1 / r, all other entries 0.
+//     e = ((x - 2 r l_x) / s, (y - 2 r l_y) / s, -l_z / r),
+//     M_{xx} = M_{yy} = P, M_{yx} = -M_{xy} = Q, M_{zz} = 1 / r, others 0.
+// Contracted as the equations need them (exact rearrangements):
+//   A_al k^al = L (c1 k.grad r + g k_z) + f (k.grad r (e.k) + P (k_x^2 + k_y^2)
+//               + k_z^2 / r)                       (M's antisymmetric part drops),
+//   l.grad f  = c1 + g l_z                         (l.grad r = 1 here),
+//   x_i''     = (L^2/2) d_i f + f L (dL_i - kd_i) + l_i (F - A.k),
+//   with dL_i - kd_i = (d_i r)(e.k) - (k.grad r) e_i - 2Q (k_y, -k_x, 0)_i,
+// where dL_i = (d_i l_ga) k^ga and kd_i = k^al d_al l_i.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void accel(const T a, const T a2, const T x, const T y, const T z,
@@ -126,46 +133,46 @@ __device__ __forceinline__ void accel(const T a, const T a2, const T x, const T 
     const T r2 = T(0.5) * (d + k_sqrt(k_fma(d, d, T(4) * az2)));
     const T ir = k_rsqrt(r2);
     const T r = r2 * ir;
-    T iq, is;                                   // 1/(r^4 + a^2 z^2), 1/(r^2 + a^2)
+    T iq, is;                                   // 1/q, 1/s
     recip2(k_fma(r2, r2, az2), r2 + a2, iq, is);
     const T hf = r * r2 * iq;                   // f / 2
     const T f = hf + hf;
-    const T lx = k_fma(r, x, a * y) * is;
-    const T ly = k_fma(r, y, -(a * x)) * is;
+    const T P = r * is;
+    const T Q = a * is;
+    const T lx = k_fma(P, x, Q * y);
+    const T ly = k_fma(P, y, -(Q * x));
     const T lz = z * ir;
     const T L = k_fma(lx, kx, k_fma(ly, ky, k_fma(lz, kz, kt)));
     // gradient of r and of f
     const T rx = hf * x;
     const T ry = hf * y;
     const T rz = hf * z * k_fma(a2, ir * ir, T(1));
-    const T c1 = f * k_fma(T(3), ir, T(-2) * f);
+    const T c1 = f * k_fma(T(3), ir, -(f + f));
+    const T g = -(f + f) * (a2 * z) * iq;
     const T fx = c1 * rx;
     const T fy = c1 * ry;
-    const T fz = k_fma(c1, rz, T(-2) * f * a2 * z * iq);
-    // d_al l_i = r_al e_i + M_{al i}
-    const T ex = is * k_fma(T(-2) * r, lx, x);
-    const T ey = is * k_fma(T(-2) * r, ly, y);
+    const T fz = k_fma(c1, rz, g);
+    // e of d_al l_i = r_al e_i + M_{al i}
+    const T m2r = -(r + r);
+    const T ex = is * k_fma(m2r, lx, x);
+    const T ey = is * k_fma(m2r, ly, y);
     const T ez = -lz * ir;
     const T ek = k_fma(ex, kx, k_fma(ey, ky, ez * kz));     // e . k
     const T kr = k_fma(rx, kx, k_fma(ry, ky, rz * kz));     // k . grad r
-    const T dLx = k_fma(rx, ek, is * k_fma(r, kx, -(a * ky)));   // (d_x l_ga) k^ga
-    const T dLy = k_fma(ry, ek, is * k_fma(r, ky, a * kx));
-    const T dLz = k_fma(rz, ek, ir * kz);
-    const T kdx = k_fma(kr, ex, is * k_fma(r, kx, a * ky));      // k^al d_al l_x
-    const T kdy = k_fma(kr, ey, is * k_fma(r, ky, -(a * kx)));
-    const T kdz = k_fma(kr, ez, ir * kz);
-    const T Ax = k_fma(fx, L, f * dLx);
-    const T Ay = k_fma(fy, L, f * dLy);
-    const T Az = k_fma(fz, L, f * dLz);
-    const T Ak = k_fma(Ax, kx, k_fma(Ay, ky, Az * kz));          // k^al D_{0 al}
-    const T lf = k_fma(lx, fx, k_fma(ly, fy, lz * fz));          // l . grad f
-    const T F = T(-0.5) * f * (L * L) * lf;
-    const T fL = f * L;
-    const T hL = T(0.5) * L;
+    // A_al k^al and l . grad f
+    const T gk = k_fma(c1, kr, g * kz);
+    const T dLk = k_fma(kr, ek, k_fma(P, k_fma(kx, kx, ky * ky), (ir * kz) * kz));
+    const T Ak = k_fma(L, gk, f * dLk);
+    const T lf = k_fma(g, lz, c1);
+    const T F = -(hf * L * L) * lf;
     at = Ak - F;
-    ax = k_fma(hL, k_fma(f, dLx, Ax), k_fma(F, lx, -k_fma(lx, Ak, fL * kdx)));
-    ay = k_fma(hL, k_fma(f, dLy, Ay), k_fma(F, ly, -k_fma(ly, Ak, fL * kdy)));
-    az = k_fma(hL, k_fma(f, dLz, Az), k_fma(F, lz, -k_fma(lz, Ak, fL * kdz)));
+    const T fL = f * L;
+    const T FmA = F - Ak;
+    const T hLL = T(0.5) * L * L;
+    const T Q2 = Q + Q;
+    ax = k_fma(hLL, fx, k_fma(fL, k_fma(rx, ek, k_fma(-kr, ex, -(Q2 * ky))), lx * FmA));
+    ay = k_fma(hLL, fy, k_fma(fL, k_fma(ry, ek, k_fma(-kr, ey, Q2 * kx)), ly * FmA));
+    az = k_fma(hLL, fz, k_fma(fL, k_fma(rz, ek, -(kr * ez)), lz * FmA));
 }
 
 // ---------------------------------------------------------------------------

@@ -631,6 +631,24 @@ template <> struct Prec<dfloat> {
     static __device__ __forceinline__ dfloat eps() { return dfloat(1e-13); }
 };
 
+// Scale of the end-time clipping tolerance.  FP64 and float-float: max(1,
+// |t_end|).  FP32 steps: max(1, |t change over the step|) -- the compensated
+// time is good to a few units of FP32 roundoff of the step's own increment,
+// while a tolerance relative to t_end would leave an end point hundreds of
+// time units into an orbit off by a visible fraction of a step.
+__device__ __forceinline__ float time_event_scale(float tend, float s_lo, float s_hi)
+{
+    return fmaxf(1.f, fabsf(s_hi - s_lo));
+}
+__device__ __forceinline__ double time_event_scale(double tend, double, double)
+{
+    return fmax(1.0, fabs(tend));
+}
+__device__ __forceinline__ dfloat time_event_scale(dfloat tend, dfloat, dfloat)
+{
+    return fmax(dfloat(1.f), fabs(tend));
+}
+
 // Conversions used by the FP64 renormalisation.
 __device__ __forceinline__ double to_d(float x) { return (double)x; }
 __device__ __forceinline__ double to_d(double x) { return x; }
@@ -737,7 +755,7 @@ __device__ __forceinline__ int step_post(const RayConst &rc, const TraceParams &
                 s_pend = s_hi;
             } else {
                 const T s_lo = event_value<KAHAN>(1, a2, y, c, tend, tlo);
-                const T sc = fmax(T(1), fabs(tend));
+                const T sc = time_event_scale(tend, s_lo, s_hi);
                 h_used = clip<KAHAN, T, RM>(a, a2, y, c, A0, h, 1, tend, tlo, s_lo, s_hi,
                                             stol * sc, Prec<T>::eps(), maxit, yn, cn, nrhs);
             }
@@ -1511,10 +1529,13 @@ __device__ __forceinline__ void clip_end_f32(const TraceParams &P, int64_t id, i
     float target, tlo, scale;
     event_of<float>(rc, st, kind, target, tlo, scale);
     const float s_lo = event_value<true>(kind, a2, y, c, target, tlo);
+    const float s_hi = (float)P.clip_shi[id];
+    if (kind == 1)
+        scale = time_event_scale(target, s_lo, s_hi);
     float ye[8], ce[8];
-    clip<true, float, RHS_CALL>(a, a2, y, c, A0, P.clip_h[id], kind, target, tlo, s_lo,
-                                (float)P.clip_shi[id], Prec<float>::stol() * scale,
-                                Prec<float>::eps(), P.clip_maxit, ye, ce, nrhs);
+    clip<true, float, RHS_CALL>(a, a2, y, c, A0, P.clip_h[id], kind, target, tlo, s_lo, s_hi,
+                                Prec<float>::stol() * scale, Prec<float>::eps(), P.clip_maxit,
+                                ye, ce, nrhs);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         y[i] = ye[i];

@@ -751,3 +751,37 @@ def test_redshift_label_sign_convention():
     # the two mirror-image pairs: the sign of xi decides blue- or redshift
     for (x1, g1), (x2, g2) in ((gs[0], gs[1]), (gs[2], gs[3])):
         assert np.sign(x1) == -np.sign(x2) and (g1 - g2) * (x1 - x2) > 0
+
+
+# ---------------------------------------------------------------------------
+# the conditioning test's FP32 rounding model (test infrastructure of the
+# end-point comparison; the plain integration is unchanged)
+# ---------------------------------------------------------------------------
+def test_noise_mode_is_off_by_default_and_reproducible():
+    y0 = O.camera_ic(0.9, np.radians(60.0), 1000.0, 20.0, 16, 16, np.arange(256))
+    plain = O.trace(0.9, y0, O.Opts(tol=1e-6))
+    zero = O.trace(0.9, y0, O.Opts(tol=1e-6, noise=0.0, noise_zone=1.5, noise_seed=5))
+    assert np.array_equal(plain.y, zero.y) and np.array_equal(plain.attempts, zero.attempts)
+    n1 = O.trace(0.9, y0, O.Opts(tol=1e-6, noise=2.0 ** -21, noise_zone=1.5, noise_seed=1))
+    n1b = O.trace(0.9, y0, O.Opts(tol=1e-6, noise=2.0 ** -21, noise_zone=1.5, noise_seed=1))
+    n2 = O.trace(0.9, y0, O.Opts(tol=1e-6, noise=2.0 ** -21, noise_zone=1.5, noise_seed=2))
+    assert np.array_equal(n1.y, n1b.y)                 # one seed, one draw
+    assert not np.array_equal(n1.y, n2.y)              # another seed, another draw
+    assert not np.array_equal(n1.y, plain.y)
+
+
+def test_noise_mode_stays_outside_its_zone_and_is_small():
+    # a zone radius beyond every step's start: no step is perturbed
+    y0 = O.camera_ic(0.9, np.radians(60.0), 1000.0, 20.0, 8, 8, np.arange(64))
+    plain = O.trace(0.9, y0, O.Opts(tol=1e-8))
+    far = O.trace(0.9, y0, O.Opts(tol=1e-8, noise=1e-3, noise_zone=1e4, noise_seed=3))
+    assert np.array_equal(plain.y, far.y)
+    # a wide ray (b ~ 25 M, far from the photon ring): 8-ulp kicks to every
+    # increment add up, as a random walk over its steps, to a small multiple
+    # of the kick -- far below the 1e-5 gate, but not nothing
+    y1 = O.camera_ic(0.5, np.radians(45.0), 1000.0, 20.0, 2, 2, [0])
+    p = O.trace(0.5, y1, O.Opts(tol=1e-8))
+    n = O.trace(0.5, y1, O.Opts(tol=1e-8, noise=2.0 ** -21, noise_zone=0.0, noise_seed=4))
+    assert p.status[0] == n.status[0] == O.ESCAPED
+    dx = np.linalg.norm(n.y[0, 1:4] - p.y[0, 1:4]) / np.linalg.norm(p.y[0, 1:4])
+    assert 2.0 ** -24 < dx < 2e-6
