@@ -829,7 +829,11 @@ def cpu_baseline(spec, W, out_gpu, out64, out_nz=None, surr_img=None, out_df=Non
         if out64 is not None:
             acc["fp64"] = errs(out64)
         if out_nz is not None:
-            acc["fp32_no_zone"] = errs(out_nz)
+            # without the FP64 zone every step is an FP32 step: FP32 rounding
+            # is modelled on the whole path when deciding what is determined
+            flags = O.ill_conditioned(spec.a, y0, oo, ref=ref, rel=1e-5, nthreads=nthreads,
+                                      noise_zone=0.0)
+            acc["fp32_no_zone"] = dict(errs(out_nz), ill_conditioned=int(flags.sum()))
         if out_df is not None:
             acc["fp32_zone_float_float"] = errs(out_df)
     except Exception as exc:  # accuracy is a report, not the measurement

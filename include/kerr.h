@@ -172,7 +172,8 @@ typedef struct {
 /* Fills *opts with: prec FP32_KAHAN, tol 1e-6, h0 1, max_steps 1e6,
  * r_escape 0, t_end +inf, fp64_zone 1.5, renorm_every 0, clip_maxit 40,
  * variant -1, budget_ns 0, zone_prec KERR_ZONE_FP64, zone_variant -1,
- * zone_quantum 32. */
+ * zone_quantum 48 (measured best of 24..96 on the 1024x1024 image and the
+ * 64-image batch). */
 void kerr_opts_default(kerr_opts *opts);
 
 /* Creates a context for black-hole spin a (|a| <= 1, else KERR_EINVAL) on the

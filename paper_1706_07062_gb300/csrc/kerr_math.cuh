@@ -120,7 +120,8 @@ __device__ __forceinline__ T ks_r(T a2, T x, T y, T z)
 //   l.grad f  = c1 + g l_z                         (l.grad r = 1 here),
 //   x_i''     = (L^2/2) d_i f + f L (dL_i - kd_i) + l_i (F - A.k),
 //   with dL_i - kd_i = (d_i r)(e.k) - (k.grad r) e_i - 2Q (k_y, -k_x, 0)_i,
-// where dL_i = (d_i l_ga) k^ga and kd_i = k^al d_al l_i.
+// where dL_i = (d_i l_ga) k^ga and kd_i = k^al d_al l_i; d_i f and d_i r are
+// expanded in the last line so that neither vector is formed.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void accel(const T a, const T a2, const T x, const T y, const T z,
@@ -143,36 +144,38 @@ __device__ __forceinline__ void accel(const T a, const T a2, const T x, const T 
     const T ly = k_fma(P, y, -(Q * x));
     const T lz = z * ir;
     const T L = k_fma(lx, kx, k_fma(ly, ky, k_fma(lz, kz, kt)));
-    // gradient of r and of f
-    const T rx = hf * x;
-    const T ry = hf * y;
-    const T rz = hf * z * k_fma(a2, ir * ir, T(1));
+    // d_i r = (f/2) (x, y, zt)_i and k . grad r
+    const T zt = z * k_fma(a2, ir * ir, T(1));
+    const T kr = hf * k_fma(x, kx, k_fma(y, ky, zt * kz));
+    // d_i f = c1 d_i r + g delta_iz
     const T c1 = f * k_fma(T(3), ir, -(f + f));
     const T g = -(f + f) * (a2 * z) * iq;
-    const T fx = c1 * rx;
-    const T fy = c1 * ry;
-    const T fz = k_fma(c1, rz, g);
     // e of d_al l_i = r_al e_i + M_{al i}
     const T m2r = -(r + r);
     const T ex = is * k_fma(m2r, lx, x);
     const T ey = is * k_fma(m2r, ly, y);
     const T ez = -lz * ir;
     const T ek = k_fma(ex, kx, k_fma(ey, ky, ez * kz));     // e . k
-    const T kr = k_fma(rx, kx, k_fma(ry, ky, rz * kz));     // k . grad r
     // A_al k^al and l . grad f
     const T gk = k_fma(c1, kr, g * kz);
     const T dLk = k_fma(kr, ek, k_fma(P, k_fma(kx, kx, ky * ky), (ir * kz) * kz));
     const T Ak = k_fma(L, gk, f * dLk);
     const T lf = k_fma(g, lz, c1);
-    const T F = -(hf * L * L) * lf;
+    const T L2 = L * L;
+    const T hLL = T(0.5) * L2;
+    const T F = -(hf * L2) * lf;
     at = Ak - F;
+    // x_i'' with d_i f and d_i r expanded: (f/2)(L^2 c1/2 + f L e.k)(x, y, zt)_i
+    // - f L (k.grad r) e_i - 2 f L Q (k_y, -k_x, 0)_i + (L^2/2) g delta_iz
+    // + l_i (F - A.k)
     const T fL = f * L;
     const T FmA = F - Ak;
-    const T hLL = T(0.5) * L * L;
-    const T Q2 = Q + Q;
-    ax = k_fma(hLL, fx, k_fma(fL, k_fma(rx, ek, k_fma(-kr, ex, -(Q2 * ky))), lx * FmA));
-    ay = k_fma(hLL, fy, k_fma(fL, k_fma(ry, ek, k_fma(-kr, ey, Q2 * kx)), ly * FmA));
-    az = k_fma(hLL, fz, k_fma(fL, k_fma(rz, ek, -(kr * ez)), lz * FmA));
+    const T hw = hf * k_fma(hLL, c1, fL * ek);
+    const T fLkr = fL * kr;
+    const T fLQ2 = fL * (Q + Q);
+    ax = k_fma(x, hw, k_fma(-fLkr, ex, k_fma(-fLQ2, ky, lx * FmA)));
+    ay = k_fma(y, hw, k_fma(-fLkr, ey, k_fma(fLQ2, kx, ly * FmA)));
+    az = k_fma(zt, hw, k_fma(-fLkr, ez, k_fma(hLL, g, lz * FmA)));
 }
 
 // ---------------------------------------------------------------------------
