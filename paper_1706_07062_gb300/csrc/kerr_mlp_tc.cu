@@ -1,18 +1,36 @@
 // kerr_mlp_tc.cu -- the surrogate's inference forward, all five layers fused
 // in one persistent kernel on the 5th-generation tensor cores (tcgen05).
 //
-// Per 128-row tile (one CTA of 256 threads, one tile at a time):
-//   input rows (fp32) -> bf16 tile X [128][16] in shared memory
-//   layer 0: D = X W0^T           (1 MMA, M = 128, N = 256, K = 16)
-//   layers 1-3: D = A W_l^T       (16 MMAs of K = 16, N = 256)
-//   layer 4: D = A W4^T           (16 MMAs, N = 64; 8 outputs used)
-// The accumulator D (128 lanes x 256 fp32 columns) lives in tensor memory;
-// after each layer the eight warps read it back (tcgen05.ld; warps w and
-// w + 4 share TMEM lanes 32 (w % 4) .. + 31 and split the columns), add the
-// bias, apply SiLU, round to bf16 and write the next layer's A operand into
-// shared memory.  Weights are staged per layer by one bulk TMA copy
-// (cp.async.bulk, completion on an mbarrier) from a copy kept in the
-// operand layout below, overlapping the previous layer's epilogue.
+// Each CTA works on a pair of 128-row tiles at a time and keeps one fp32
+// accumulator per tile in tensor memory (2 x 256 of the 512 columns), so that
+// the MMAs of one tile run while the other tile's epilogue reads its
+// accumulator back:
+//
+//   MMA      A0 | B0 | A1 | B1 | A2 | B2 | A3 | B3 | A4 | B4 | (next pair)
+//   epilogue      A0 | B0 | A1 | B1 | A2 | B2 | A3 | B3 | A4 | B4
+//
+// (Xl: layer l of tile X.)  Layer 0 is one MMA (M = 128, N = 256, K = 16)
+// against the resident W0; layers 1-4 stream their weights from global
+// memory in K-slices of 64 columns ([256][64] bf16 = 32 KB, the output layer
+// [64][64]) through two shared-memory slots, each slice consumed by four MMAs
+// (K = 16) and released by a tcgen05.commit on the slot's "empty" barrier.
+// Warp roles (608 threads):
+//   warps 0-1 producers: lane 0 of warp p issues the bulk copies
+//             (cp.async.bulk, completion on the slot's "full" mbarrier) of
+//             every slice that goes through slot p (on GB300 one issuing
+//             warp delivers ~34 B per clock and SM whatever its queue depth,
+//             and each further issuing warp adds about as much);
+//   warp 2    MMA: one elected lane issues every tcgen05.mma and commit;
+//   warps 3-18 epilogue, eight warps per tile of the pair (warps 3-10 the
+//             first, 11-18 the second): read the accumulator (tcgen05.ld; the
+//             two warps of a TMEM lane quarter split the columns), add the
+//             bias, apply SiLU, round to bf16 and write the next layer's A
+//             operand into shared memory (or the 8 outputs to global memory),
+//             and signal the MMA warp; during layer 1 they also fetch the
+//             input rows of the tile's slot in the next pair.  The two tiles' epilogues run at the same
+//             time whenever both accumulators are ready.
+// Every barrier wait is bounded; a wait that gives up sets the error flag,
+// stops its role, and the kernel frees its tensor memory before it exits.
 //
 // Operand layout (K-major, no swizzle): a tile of R rows and K columns is
 // stored as 8 x 8 "core matrices" of 128 contiguous bytes (8 rows of 16 B);
@@ -22,7 +40,8 @@
 // stride-dimension byte offset the distance between 8-row groups (K * 16 B).
 //
 // Same arithmetic as the GEMM path (bf16 operands, fp32 accumulation, bias
-// and SiLU in fp32, bf16 activations); only the accumulation order differs.
+// and SiLU in fp32 with the hardware exp2 and reciprocal approximations, bf16
+// activations); only the accumulation order differs.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -37,66 +56,159 @@ namespace {
 
 using namespace kerr::tc;
 
-constexpr int TM = 128;   // rows per tile (MMA M)
+constexpr int TM = 128;            // rows per tile (MMA M)
+constexpr int KS = 64;             // K columns per weight slice
+constexpr int kSlices = kHidden / KS;                        // slices per layer (1-4)
+constexpr int kSlots = 2;                                    // weight-slice buffers
+constexpr uint32_t kSliceBytes = kHidden * KS * 2;           // 32 KB ([256][64] bf16)
+constexpr uint32_t kOutSliceBytes = kOutPad * KS * 2;        // 8 KB ([64][64] bf16)
 
-// Packed weight offset (bf16 elements) of layer l (l = kLayers: the total),
-// operand layout.
-__host__ __device__ constexpr size_t pack_off(int l)
+// Packed weights (bf16 elements): W0 [256][16] in the K = 16 layout, then for
+// layers 1-4 four K-slices each, every slice [N][64] in the K = 64 layout.
+__host__ __device__ constexpr size_t slice_elems(int l) { return (size_t)out_dim(l) * KS; }
+__host__ __device__ constexpr size_t slice_off(int l, int s)
 {
-    // layer 0: [256][16]; layers 1-3: [256][256]; layer 4: [64][256]
-    return l <= 0 ? 0
-                  : (size_t)kHidden * kInPad + (size_t)(l < kLayers ? l - 1 : kLayers - 2) *
-                                                   kHidden * kHidden +
-                        (l == kLayers ? (size_t)kOutPad * kHidden : 0);
+    return (size_t)kHidden * kInPad +
+           (l <= 1 ? 0 : (size_t)(l - 1 < 3 ? l - 1 : 3) * kSlices * slice_elems(1)) +
+           (size_t)s * slice_elems(l);
 }
-static_assert(pack_off(1) == 4096 && pack_off(2) == 4096 + 65536 && pack_off(4) == 4096 + 3 * 65536,
+constexpr size_t kPackedElems = slice_off(kLayers - 1, kSlices);
+static_assert(slice_off(1, 0) == 4096 && slice_off(2, 0) == 4096 + 65536 &&
+                  slice_off(4, 0) == 4096 + 3 * 65536,
               "packed weight offsets");
-static_assert(pack_off(kLayers) == 217088, "packed weight size");
+static_assert(kPackedElems == 217088, "packed weight size");
 
 // Shared memory (bytes).
-constexpr uint32_t SM_ACT = 0;                               // A operand [128][256]: 64 KB
-constexpr uint32_t SM_W = SM_ACT + TM * kHidden * 2;         // W_l [256][256]: 128 KB
-constexpr uint32_t SM_X = SM_W + kHidden * kHidden * 2;      // X [128][16]: 4 KB
-constexpr uint32_t SM_W0 = SM_X + TM * kInPad * 2;           // W0 [256][16]: 8 KB
-constexpr uint32_t SM_BIAS = SM_W0 + kHidden * kInPad * 2;   // 4 x 256 + 64 floats
+constexpr uint32_t SM_ACT = 0;                                 // 2 x A operand [128][256]: 128 KB
+constexpr uint32_t SM_SLOT = SM_ACT + 2 * TM * kHidden * 2;    // 2 x weight slice: 64 KB
+constexpr uint32_t SM_X = SM_SLOT + kSlots * kSliceBytes;      // 2 x X [128][16]: 8 KB
+constexpr uint32_t SM_W0 = SM_X + 2 * TM * kInPad * 2;         // W0 [256][16]: 8 KB
+constexpr uint32_t SM_BIAS = SM_W0 + kHidden * kInPad * 2;     // 4 x 256 + 64 floats
 constexpr uint32_t SM_BAR = SM_BIAS + (4 * kHidden + kOutPad) * 4;
-constexpr uint32_t SM_TOTAL = SM_BAR + 64;                   // 2 mbarriers, TMEM slot, flag
+// barriers: full[2], empty[2], accfull[2], actready[2], w0, final; TMEM slot; abort flag
+constexpr int kBars = 10;
+constexpr uint32_t SM_TOTAL = SM_BAR + kBars * 8 + 8 + 8;
 static_assert(SM_TOTAL <= 227 * 1024, "shared memory of the fused forward");
-static_assert(SM_W % 16 == 0 && SM_X % 16 == 0 && SM_W0 % 16 == 0 && SM_BAR % 8 == 0,
+static_assert(SM_SLOT % 1024 == 0 && SM_X % 16 == 0 && SM_W0 % 16 == 0 && SM_BAR % 8 == 0,
               "bulk-copy and mbarrier alignment");
 
-constexpr uint32_t kTmemCols = 256;          // fp32 accumulator columns (N <= 256)
+constexpr uint32_t kTmemCols = 512;          // two fp32 accumulators of 256 columns
+constexpr int kThreads = 32 * (kSlots + 1) + 2 * 256;   // 608
+constexpr int kEpiWarp0 = kSlots + 1;          // first epilogue warp
+constexpr int kEpiThreads = 256;
 
 struct Bias {
     const float *b[kLayers];
 };
 
-// Hidden-layer epilogue of one thread: row `row` of the accumulator, columns
-// [32 c0, 32 c1) -> bias + SiLU -> bf16 A operand of the next layer.
+constexpr float kLog2e = 1.4426950408889634f;
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// SiLU of two accumulator values with their biases, rounded to a bf16 pair:
+// z = acc + b, silu(z) = z / (1 + e^-z) with e^-z = 2^(-z log2 e) and the
+// reciprocal from the hardware's approximate exp2 and reciprocal (two MUFU
+// operations per element; the MUFU pipe takes 32 per clock and SM).  The
+// additions and multiplications run on pairs (one f32x2 instruction for two
+// elements).  e^-z beyond the FP32 range gives 1 / inf = 0 and silu = 0 z;
+// below 2^-126 it flushes to 0 and silu = z, as the exact values round.
+__device__ __forceinline__ uint32_t silu2_bf16(uint32_t a0, uint32_t a1, float b0, float b1)
+{
+    const float2 z = __fadd2_rn(make_float2(__uint_as_float(a0), __uint_as_float(a1)),
+                                make_float2(b0, b1));
+    const float2 t = __fmul2_rn(z, make_float2(-kLog2e, -kLog2e));
+    const float2 d = __fadd2_rn(make_float2(ex2_approx(t.x), ex2_approx(t.y)),
+                                make_float2(1.0f, 1.0f));
+    const float2 y = __fmul2_rn(z, make_float2(rcp_approx(d.x), rcp_approx(d.y)));
+    return pack_bf16(y.x, y.y);
+}
+
+// A 16-byte shared store without a compiler memory barrier: the epilogue's
+// stores only write the A operand, which no load of this thread reads, so
+// the bias loads and arithmetic of neighbouring column groups may move across
+// them.  Every store still precedes the fence and mbarrier arrive that
+// publish the operand (volatile asm statements keep their order).
+__device__ __forceinline__ void st_act_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                          uint32_t d)
+{
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+                 "r"(d));
+}
+
+// Hidden-layer epilogue of one thread: accumulator row (TMEM lane) at
+// tmem_row, columns [32 c0, 32 c1) -> bias + SiLU -> bf16 A operand row t.
 __device__ __forceinline__ void epilogue_hidden(uint32_t tmem_row, const float *bias,
                                                 uint32_t act, int t, int c0, int c1)
 {
     const uint32_t row = act + (t >> 3) * (kHidden * 16) + (t & 7) * 16;
 #pragma unroll 1
     for (int c = c0; c < c1; ++c) {
+        float4 b[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            b[i] = *reinterpret_cast<const float4 *>(bias + 32 * c + 4 * i);
         uint32_t v[32];
         tmem_ld32(tmem_row + 32 * c, v);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            uint32_t w[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int col = 32 * c + 8 * q + 2 * j;
-                const float z0 = __uint_as_float(v[8 * q + 2 * j]) + bias[col];
-                const float z1 = __uint_as_float(v[8 * q + 2 * j + 1]) + bias[col + 1];
-                w[j] = pack_bf16(silu(z0), silu(z1));
-            }
-            st_shared_v4(row + (4 * c + q) * 128, w[0], w[1], w[2], w[3]);
+            const float4 lo = b[2 * q], hi = b[2 * q + 1];
+            const uint32_t *u = v + 8 * q;
+            st_act_v4(row + (4 * c + q) * 128, silu2_bf16(u[0], u[1], lo.x, lo.y),
+                      silu2_bf16(u[2], u[3], lo.z, lo.w), silu2_bf16(u[4], u[5], hi.x, hi.y),
+                      silu2_bf16(u[6], u[7], hi.z, hi.w));
         }
     }
 }
 
-constexpr int kThreads = 256;
+// Input rows of tile `tile` (row t of it, for t < 128) as the bf16 X operand:
+// columns 0-3 live, 4-15 zero.  read_x fetches a row from global memory,
+// write_x stores it in the operand layout.
+__device__ __forceinline__ float4 read_x(const float *__restrict__ in, int64_t n, int64_t tile,
+                                         int t)
+{
+    const int64_t r = tile * TM + t;
+    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < n) {
+        x.x = in[r * kIn + 0];
+        x.y = in[r * kIn + 1];
+        x.z = in[r * kIn + 2];
+        x.w = in[r * kIn + 3];
+    }
+    return x;
+}
+
+__device__ __forceinline__ void write_x(float4 x, uint32_t sx, int t)
+{
+    const uint32_t xrow = sx + (t >> 3) * (kInPad * 16) + (t & 7) * 16;
+    st_shared_v4(xrow, pack_bf16(x.x, x.y), pack_bf16(x.z, x.w), 0u, 0u);
+    st_shared_v4(xrow + 128, 0u, 0u, 0u, 0u);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Bounded wait that also gives up early once another role has aborted.
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
+                                              const volatile int *abort_flag)
+{
+    if (*abort_flag)
+        return false;
+    return mbar_wait(bar, parity);
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
     mlp_forward_tc_kernel(const float *__restrict__ in, int64_t n, float *__restrict__ out,
@@ -106,16 +218,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     extern __shared__ __align__(1024) uint8_t smem[];
     const int t = threadIdx.x;
     const int warp = t >> 5;
-    const int row = t & (TM - 1);      // accumulator row (TMEM lane) of this thread
-    const int half = t >> 7;           // column half of the epilogue
+    const int lane = t & 31;
     float *sb = reinterpret_cast<float *>(smem + SM_BIAS);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM_BAR);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM_BAR + 16);
-    int *abort_flag = reinterpret_cast<int *>(smem + SM_BAR + 20);
-    const uint32_t bar_w = smem_u32(&bars[0]);
-    const uint32_t bar_mma = smem_u32(&bars[1]);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + SM_BAR + kBars * 8);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + SM_BAR + kBars * 8 + 8);
+    auto bar = [&](int i) { return smem_u32(&bars[i]); };
+    const int B_FULL = 0, B_EMPTY = 2, B_ACC = 4, B_ACT = 6, B_W0 = 8, B_FIN = 9;
     const uint32_t s_act = smem_u32(smem + SM_ACT);
-    const uint32_t s_w = smem_u32(smem + SM_W);
+    const uint32_t s_slot = smem_u32(smem + SM_SLOT);
     const uint32_t s_x = smem_u32(smem + SM_X);
     const uint32_t s_w0 = smem_u32(smem + SM_W0);
 
@@ -127,8 +238,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (t == 0) {
-        mbar_init(bar_w, 1);
-        mbar_init(bar_mma, 1);
+        for (int i = 0; i < kSlots; ++i) {
+            mbar_init(bar(B_FULL + i), 1);
+            mbar_init(bar(B_EMPTY + i), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(bar(B_ACC + i), 1);
+            mbar_init(bar(B_ACT + i), kEpiThreads);
+        }
+        mbar_init(bar(B_W0), 1);
+        mbar_init(bar(B_FIN), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -139,125 +258,181 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t tmem_row = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
 
-    uint32_t ph_w = 0, ph_mma = 0;
+    const int64_t ntiles = (n + TM - 1) / TM;
+    const int64_t npairs = (ntiles + 1) / 2;
     bool ok = true;
-    // W0 stays resident
-    if (t == 0) {
-        mbar_expect_tx(bar_w, kHidden * kInPad * 2);
-        bulk_load(s_w0, wpk + pack_off(0), kHidden * kInPad * 2, bar_w);
-    }
-    ok = mbar_wait(bar_w, ph_w);
-    ph_w ^= 1;
 
-    const int64_t tiles = (n + TM - 1) / TM;
-    constexpr uint32_t idesc_h = make_idesc(TM, kHidden);
-    constexpr uint32_t idesc_o = make_idesc(TM, kOutPad);
-    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int64_t r0 = tile * TM;
-        if (!ok)
-            *abort_flag = 1;
-        __syncthreads();
-        if (*abort_flag)
-            break;
-        // W1 into the weight buffer (free: the last tile's MMAs completed)
-        if (t == 0 && ok) {
-            mbar_expect_tx(bar_w, kHidden * kHidden * 2);
-            bulk_load(s_w, wpk + pack_off(1), kHidden * kHidden * 2, bar_w);
-        }
-        // input tile: row t, columns 0-3 live, 4-15 zero
-        if (t < TM) {
-            const int64_t r = r0 + t;
-            float x[4] = {0.f, 0.f, 0.f, 0.f};
-            if (r < n) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    x[j] = in[r * kIn + j];
+    if (warp < kSlots) {
+        // ---- producers: warp p streams the slices that go through slot p, in
+        // the MMA's order (W0 once, from warp 0)
+        if (lane == 0) {
+            const int p = warp;
+            if (p == 0) {
+                mbar_expect_tx(bar(B_W0), kHidden * kInPad * 2);
+                bulk_load(s_w0, wpk, kHidden * kInPad * 2, bar(B_W0));
             }
-            const uint32_t xrow = s_x + (t >> 3) * (kInPad * 16) + (t & 7) * 16;
-            st_shared_v4(xrow, pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), 0u, 0u);
-            st_shared_v4(xrow + 128, 0u, 0u, 0u, 0u);
-        }
-        fence_proxy_async();
-        fence_before();
-        __syncthreads();
-        // ---- layer 0 (K = 16): one MMA
-        if (t == 0 && ok) {
-            fence_after();
-            mma_bf16(tmem, make_desc(s_x, 128, kInPad * 16), make_desc(s_w0, 128, kInPad * 16),
-                     idesc_h, 0u);
-            mma_commit(bar_mma);
-        }
-        ok = ok && mbar_wait(bar_mma, ph_mma);
-        ph_mma ^= 1;
-        fence_after();
-        epilogue_hidden(tmem_row, sb, s_act, row, 4 * half, 4 * half + 4);
-        fence_proxy_async();
-        fence_before();
-        __syncthreads();
-        // ---- hidden layers 1-3 and the output layer
-#pragma unroll 1
-        for (int l = 1; l < kLayers; ++l) {
-            ok = ok && mbar_wait(bar_w, ph_w);      // W_l staged
-            ph_w ^= 1;
-            const bool last = l == kLayers - 1;
-            if (t == 0 && ok) {
-                fence_after();
-#pragma unroll 1
-                for (int s = 0; s < kHidden / 16; ++s)
-                    mma_bf16(tmem, make_desc(s_act + s * 256, 128, kHidden * 16),
-                             make_desc(s_w + s * 256, 128, kHidden * 16),
-                             last ? idesc_o : idesc_h, s > 0 ? 1u : 0u);
-                mma_commit(bar_mma);
-            }
-            ok = ok && mbar_wait(bar_mma, ph_mma);
-            ph_mma ^= 1;
-            // the weight buffer is free again: stage the next layer's weights
-            if (t == 0 && ok && l + 1 < kLayers) {
-                const uint32_t bytes = (uint32_t)((pack_off(l + 2) - pack_off(l + 1)) * 2);
-                mbar_expect_tx(bar_w, bytes);
-                bulk_load(s_w, wpk + pack_off(l + 1), bytes, bar_w);
-            }
-            fence_after();
-            if (!last) {
-                epilogue_hidden(tmem_row, sb + l * kHidden, s_act, row, 4 * half,
-                                4 * half + 4);
-                fence_proxy_async();
-            } else if (half == 0) {
-                uint32_t v[8];
-                tmem_ld8(tmem_row, v);
-                const int64_t r = r0 + row;
-                if (r < n) {
-                    const float *b4 = sb + 4 * kHidden;
-                    float4 *o = reinterpret_cast<float4 *>(out + r * kOut);
-                    const float4 lo = make_float4(__uint_as_float(v[0]) + b4[0],
-                                                  __uint_as_float(v[1]) + b4[1],
-                                                  __uint_as_float(v[2]) + b4[2],
-                                                  __uint_as_float(v[3]) + b4[3]);
-                    const float4 hi = make_float4(__uint_as_float(v[4]) + b4[4],
-                                                  __uint_as_float(v[5]) + b4[5],
-                                                  __uint_as_float(v[6]) + b4[6],
-                                                  __uint_as_float(v[7]) + b4[7]);
-                    o[0] = lo;
-                    o[1] = hi;
+            uint32_t k = 0, issued = 0;              // k: slice counter of the MMA's order
+            for (int64_t q = blockIdx.x; q < npairs && ok; q += gridDim.x) {
+                const int ntile = (2 * q + 1 < ntiles) ? 2 : 1;
+                for (int l = 1; l < kLayers && ok; ++l) {
+                    const uint32_t bytes = l == kLayers - 1 ? kOutSliceBytes : kSliceBytes;
+                    for (int tt = 0; tt < ntile && ok; ++tt) {
+                        for (int s = 0; s < kSlices; ++s, ++k) {
+                            if (k % kSlots != (uint32_t)p)
+                                continue;
+                            const uint32_t use = k / kSlots;     // uses of this slot so far
+                            if (use >= 1 &&
+                                !wait_or_abort(bar(B_EMPTY + p), (use - 1) & 1, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            mbar_expect_tx(bar(B_FULL + p), bytes);
+                            bulk_load(s_slot + p * kSliceBytes, wpk + slice_off(l, s), bytes,
+                                      bar(B_FULL + p));
+                            issued = use + 1;
+                        }
+                    }
                 }
             }
-            fence_before();
-            __syncthreads();
+            if (!ok)
+                *abort_flag = 1;
+            // the last copy issued through this slot has landed before the CTA
+            // can exit (already true unless a wait gave up)
+            if (issued > 0)
+                mbar_wait(bar(B_FULL + p), (issued - 1) & 1);
+            if (p == 0)
+                mbar_wait(bar(B_W0), 0);
         }
-    }
-    if (!ok) {
-        // a wait gave up (never expected): flag it, and give whatever this
-        // thread may have left in flight one more bounded wait before the
-        // tensor memory is freed
-        if (err)
-            atomicExch(err, 1u);
-        if (t == 0) {
-            mbar_wait(bar_w, ph_w);
-            mbar_wait(bar_mma, ph_mma);
+    } else if (warp == kSlots) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc_h = make_idesc(TM, kHidden);
+            constexpr uint32_t idesc_o = make_idesc(TM, kOutPad);
+            uint32_t k = 0, ph_act[2] = {0, 0};
+            ok = wait_or_abort(bar(B_W0), 0, abort_flag);
+            for (int64_t q = blockIdx.x; q < npairs && ok; q += gridDim.x) {
+                const int ntile = (2 * q + 1 < ntiles) ? 2 : 1;
+                for (int l = 0; l < kLayers && ok; ++l) {
+                    for (int tt = 0; tt < ntile && ok; ++tt) {
+                        if (!wait_or_abort(bar(B_ACT + tt), ph_act[tt], abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        ph_act[tt] ^= 1;
+                        fence_after();
+                        const uint32_t acc = tmem + 256u * tt;
+                        const uint32_t act = s_act + tt * (TM * kHidden * 2);
+                        if (l == 0) {
+                            mma_bf16(acc, make_desc(s_x + tt * (TM * kInPad * 2), 128,
+                                                    kInPad * 16),
+                                     make_desc(s_w0, 128, kInPad * 16), idesc_h, 0u);
+                        } else {
+                            for (int s = 0; s < kSlices; ++s, ++k) {
+                                const uint32_t slot = k % kSlots;
+                                if (!wait_or_abort(bar(B_FULL + slot), (k / kSlots) & 1,
+                                                   abort_flag)) {
+                                    ok = false;
+                                    break;
+                                }
+                                fence_after();
+                                const uint32_t w = s_slot + slot * kSliceBytes;
+#pragma unroll
+                                for (int j = 0; j < KS / 16; ++j)
+                                    mma_bf16(acc,
+                                             make_desc(act + s * (KS / 8) * 128 + j * 256, 128,
+                                                       kHidden * 16),
+                                             make_desc(w + j * 256, 128, KS * 16),
+                                             l == kLayers - 1 ? idesc_o : idesc_h,
+                                             (s > 0 || j > 0) ? 1u : 0u);
+                                mma_commit(bar(B_EMPTY + slot));   // slot free once these finish
+                            }
+                        }
+                        if (ok)
+                            mma_commit(bar(B_ACC + tt));           // accumulator ready
+                    }
+                }
+            }
+            if (!ok)
+                *abort_flag = 1;
+            // every MMA issued has completed before the tensor memory is freed
+            mma_commit(bar(B_FIN));
+            mbar_wait(bar(B_FIN), 0);
         }
+    } else {
+        // ---- epilogue: warp group g serves tile g of every pair (two warps
+        // per TMEM lane quarter, splitting the columns)
+        const int g = (warp - kEpiWarp0) >> 3;          // tile of the pair
+        const int wg = (warp - kEpiWarp0) & 7;
+        const int et = (t - 32 * kEpiWarp0) & 255;      // thread of the group, 0 .. 255
+        const int quarter = warp & 3;                   // TMEM lanes 32 quarter ..
+        const int half = wg >> 2;                       // column half
+        const int row = 32 * quarter + lane;            // accumulator row of this thread
+        const uint32_t acc_row = tmem + 256u * g + ((uint32_t)(32 * quarter) << 16);
+        const uint32_t act = s_act + g * (TM * kHidden * 2);
+        const uint32_t sx = s_x + g * (TM * kInPad * 2);
+        uint32_t ph_acc = 0;
+        // input rows of the first pair
+        if (blockIdx.x < npairs && 2 * (int64_t)blockIdx.x + g < ntiles) {
+            if (et < TM)
+                write_x(read_x(in, n, 2 * (int64_t)blockIdx.x + g, et), sx, et);
+            fence_proxy_async();
+            mbar_arrive(bar(B_ACT + g));
+        }
+        for (int64_t q = blockIdx.x; q < npairs && ok; q += gridDim.x) {
+            const int64_t tile = 2 * q + g;
+            if (tile >= ntiles)
+                break;                                   // the last pair has one tile
+            const int64_t qn = q + gridDim.x;           // the next pair of this CTA
+            const bool next = qn < npairs && 2 * qn + g < ntiles;
+            float4 xn = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int l = 0; l < kLayers; ++l) {
+                // the input rows of this tile's slot in the next pair: read
+                // while layer 1's accumulator is computed, stored after its
+                // epilogue (layer 0's MMA, the reader of X, has completed)
+                if (l == 1 && next && et < TM)
+                    xn = read_x(in, n, 2 * qn + g, et);
+                if (!wait_or_abort(bar(B_ACC + g), ph_acc, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                ph_acc ^= 1;
+                fence_after();
+                if (l < kLayers - 1) {
+                    epilogue_hidden(acc_row, sb + l * kHidden, act, row, 4 * half, 4 * half + 4);
+                    if (l == 1 && next && et < TM)
+                        write_x(xn, sx, et);
+                } else {
+                    if (half == 0) {
+                        uint32_t v[8];
+                        tmem_ld8(acc_row, v);
+                        const int64_t r = tile * TM + row;
+                        if (r < n) {
+                            const float *b4 = sb + 4 * kHidden;
+                            float4 *o = reinterpret_cast<float4 *>(out + r * kOut);
+                            o[0] = make_float4(__uint_as_float(v[0]) + b4[0],
+                                               __uint_as_float(v[1]) + b4[1],
+                                               __uint_as_float(v[2]) + b4[2],
+                                               __uint_as_float(v[3]) + b4[3]);
+                            o[1] = make_float4(__uint_as_float(v[4]) + b4[4],
+                                               __uint_as_float(v[5]) + b4[5],
+                                               __uint_as_float(v[6]) + b4[6],
+                                               __uint_as_float(v[7]) + b4[7]);
+                        }
+                    }
+                }
+                fence_proxy_async();
+                fence_before();
+                mbar_arrive(bar(B_ACT + g));
+            }
+        }
+        if (!ok)
+            *abort_flag = 1;
     }
+
+    if (!ok && err)
+        atomicExch(err, 1u);
+    fence_before();
     __syncthreads();
     if (warp == 0) {
         fence_after();
@@ -267,7 +442,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// Weights from the bf16 copy ([out][in] per layer) into the operand layout.
+// Weights from the bf16 copy ([out][in] per layer) into the packed operand
+// layout: one thread per source element.
 struct WOff {
     size_t w[kLayers];
 };
@@ -275,24 +451,36 @@ struct WOff {
 __global__ void pack_weights_kernel(const __nv_bfloat16 *__restrict__ wbf, const WOff woff,
                                     __nv_bfloat16 *__restrict__ wpk)
 {
-    const size_t total = pack_off(kLayers);
+    // source elements, layer by layer: [out_dim(l)][in_dim(l)]
+    size_t total = 0;
+    for (int l = 0; l < kLayers; ++l)
+        total += (size_t)out_dim(l) * in_dim(l);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
         int l = 0;
-        while (l + 1 < kLayers && i >= pack_off(l + 1))
+        size_t j = i;
+        while (l + 1 < kLayers && j >= (size_t)out_dim(l) * in_dim(l)) {
+            j -= (size_t)out_dim(l) * in_dim(l);
             ++l;
-        const size_t j = i - pack_off(l);
+        }
         const int K = in_dim(l);
         const int nrow = (int)(j / K), k = (int)(j % K);
-        const size_t dst = pack_off(l) + (size_t)(nrow >> 3) * (K * 8) + (size_t)(k >> 3) * 64 +
-                           (nrow & 7) * 8 + (k & 7);
+        size_t dst;
+        if (l == 0) {
+            dst = (size_t)(nrow >> 3) * (kInPad * 8) + (size_t)(k >> 3) * 64 + (nrow & 7) * 8 +
+                  (k & 7);
+        } else {
+            const int s = k / KS, kk = k % KS;
+            dst = slice_off(l, s) + (size_t)(nrow >> 3) * (KS * 8) + (size_t)(kk >> 3) * 64 +
+                  (nrow & 7) * 8 + (kk & 7);
+        }
         wpk[dst] = wbf[woff.w[l] + j];
     }
 }
 
 } // namespace
 
-size_t packed_weight_elems() { return pack_off(kLayers); }
+size_t packed_weight_elems() { return kPackedElems; }
 int forward_tc_shared_bytes() { return (int)SM_TOTAL; }
 
 cudaError_t pack_weights(const __nv_bfloat16 *wbf, const size_t woff[kLayers],
@@ -310,19 +498,25 @@ cudaError_t forward_tc(const float *in, int64_t n, float *out, const __nv_bfloat
 {
     if (n <= 0)
         return cudaSuccess;
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_TOTAL);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    // the shared-memory opt-in is per device: set it whenever the device is new
+    static int attr_dev = -1;
+    if (attr_dev != dev) {
+        e = cudaFuncSetAttribute(mlp_forward_tc_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_TOTAL);
         if (e != cudaSuccess)
             return e;
-        attr = true;
+        attr_dev = dev;
     }
     Bias b;
     for (int l = 0; l < kLayers; ++l)
         b.b[l] = bias[l];
     const int64_t tiles = (n + TM - 1) / TM;
-    const int grid = (int)(tiles < sms ? tiles : sms);
+    const int64_t pairs = (tiles + 1) / 2;
+    const int grid = (int)(pairs < sms ? pairs : sms);
     mlp_forward_tc_kernel<<<grid, kThreads, SM_TOTAL, s>>>(in, n, out, wpk, b, err);
     return cudaGetLastError();
 }
