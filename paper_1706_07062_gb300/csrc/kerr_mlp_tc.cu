@@ -21,14 +21,16 @@
 //             warp delivers ~34 B per clock and SM whatever its queue depth,
 //             and each further issuing warp adds about as much);
 //   warp 2    MMA: one elected lane issues every tcgen05.mma and commit;
-//   warps 3-18 epilogue, eight warps per tile of the pair (warps 3-10 the
-//             first, 11-18 the second): read the accumulator (tcgen05.ld; the
-//             two warps of a TMEM lane quarter split the columns), add the
-//             bias, apply SiLU, round to bf16 and write the next layer's A
-//             operand into shared memory (or the 8 outputs to global memory),
-//             and signal the MMA warp; during layer 1 they also fetch the
-//             input rows of the tile's slot in the next pair.  The two tiles' epilogues run at the same
-//             time whenever both accumulators are ready.
+//   warps 3-18 epilogue, all sixteen on every accumulator in the MMA's
+//             order (the four warps of a TMEM lane quarter take 64 columns
+//             each): read the accumulator (tcgen05.ld), add the bias, apply
+//             SiLU, round to bf16 and write the next layer's A operand into
+//             shared memory (or the 8 outputs to global memory), and signal
+//             the MMA warp; during layer 1 they also fetch the input rows of
+//             the next pair.  (Two groups of eight warps, one per tile, were
+//             slower: the MMA dependencies keep the two tiles' epilogues
+//             apart in time, so only half the warps worked at once.)
+
 // Every barrier wait is bounded; a wait that gives up sets the error flag,
 // stops its role, and the kernel frees its tensor memory before it exits.
 //
@@ -95,7 +97,7 @@ static_assert(SM_SLOT % 1024 == 0 && SM_X % 16 == 0 && SM_W0 % 16 == 0 && SM_BAR
 constexpr uint32_t kTmemCols = 512;          // two fp32 accumulators of 256 columns
 constexpr int kThreads = 32 * (kSlots + 1) + 2 * 256;   // 608
 constexpr int kEpiWarp0 = kSlots + 1;          // first epilogue warp
-constexpr int kEpiThreads = 256;
+constexpr int kEpiThreads = 512;
 
 struct Bias {
     const float *b[kLayers];
@@ -360,53 +362,61 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_wait(bar(B_FIN), 0);
         }
     } else {
-        // ---- epilogue: warp group g serves tile g of every pair (two warps
-        // per TMEM lane quarter, splitting the columns)
-        const int g = (warp - kEpiWarp0) >> 3;          // tile of the pair
-        const int wg = (warp - kEpiWarp0) & 7;
-        const int et = (t - 32 * kEpiWarp0) & 255;      // thread of the group, 0 .. 255
+        // ---- epilogue: all sixteen warps serve every accumulator, the two
+        // tiles of a pair in the MMA's order (four warps per TMEM lane
+        // quarter, each taking 64 of the 256 columns)
+        const int ew = warp - kEpiWarp0;                // 0 .. 15
+        const int et = t - 32 * kEpiWarp0;              // 0 .. 511
         const int quarter = warp & 3;                   // TMEM lanes 32 quarter ..
-        const int half = wg >> 2;                       // column half
+        const int colq = ew >> 2;                       // column quarter
         const int row = 32 * quarter + lane;            // accumulator row of this thread
-        const uint32_t acc_row = tmem + 256u * g + ((uint32_t)(32 * quarter) << 16);
-        const uint32_t act = s_act + g * (TM * kHidden * 2);
-        const uint32_t sx = s_x + g * (TM * kInPad * 2);
-        uint32_t ph_acc = 0;
+        // input rows: thread et < 256 fetches row et % 128 of tile et / 128
+        const int xt = et >> 7;
+        const int xr = et & (TM - 1);
+        uint32_t ph0 = 0, ph1 = 0;
         // input rows of the first pair
-        if (blockIdx.x < npairs && 2 * (int64_t)blockIdx.x + g < ntiles) {
-            if (et < TM)
-                write_x(read_x(in, n, 2 * (int64_t)blockIdx.x + g, et), sx, et);
+        if (blockIdx.x < npairs) {
+            const int ntile = (2 * (int64_t)blockIdx.x + 1 < ntiles) ? 2 : 1;
+            if (et < 2 * TM && xt < ntile)
+                write_x(read_x(in, n, 2 * (int64_t)blockIdx.x + xt, xr),
+                        s_x + xt * (TM * kInPad * 2), xr);
             fence_proxy_async();
-            mbar_arrive(bar(B_ACT + g));
+            for (int tt = 0; tt < ntile; ++tt)
+                mbar_arrive(bar(B_ACT + tt));
         }
         for (int64_t q = blockIdx.x; q < npairs && ok; q += gridDim.x) {
-            const int64_t tile = 2 * q + g;
-            if (tile >= ntiles)
-                break;                                   // the last pair has one tile
+            const int ntile = (2 * q + 1 < ntiles) ? 2 : 1;
             const int64_t qn = q + gridDim.x;           // the next pair of this CTA
-            const bool next = qn < npairs && 2 * qn + g < ntiles;
+            const bool xnext = et < 2 * TM && qn < npairs && 2 * qn + xt < ntiles;
             float4 xn = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int l = 0; l < kLayers; ++l) {
-                // the input rows of this tile's slot in the next pair: read
-                // while layer 1's accumulator is computed, stored after its
-                // epilogue (layer 0's MMA, the reader of X, has completed)
-                if (l == 1 && next && et < TM)
-                    xn = read_x(in, n, 2 * qn + g, et);
-                if (!wait_or_abort(bar(B_ACC + g), ph_acc, abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                ph_acc ^= 1;
-                fence_after();
-                if (l < kLayers - 1) {
-                    epilogue_hidden(acc_row, sb + l * kHidden, act, row, 4 * half, 4 * half + 4);
-                    if (l == 1 && next && et < TM)
-                        write_x(xn, sx, et);
-                } else {
-                    if (half == 0) {
+            for (int l = 0; l < kLayers && ok; ++l) {
+                // the next pair's input rows: read while layer 1's accumulators
+                // are computed, stored once the tile's layer-1 accumulator is
+                // ready (layer 0's MMA, the reader of X, has then completed)
+                if (l == 1 && xnext)
+                    xn = read_x(in, n, 2 * qn + xt, xr);
+                for (int tt = 0; tt < ntile; ++tt) {
+                    if (!wait_or_abort(bar(B_ACC + tt), tt ? ph1 : ph0, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    if (tt)
+                        ph1 ^= 1;
+                    else
+                        ph0 ^= 1;
+                    fence_after();
+                    const uint32_t acc_row =
+                        tmem + 256u * tt + ((uint32_t)(32 * quarter) << 16);
+                    if (l < kLayers - 1) {
+                        epilogue_hidden(acc_row, sb + l * kHidden,
+                                        s_act + tt * (TM * kHidden * 2), row, 2 * colq,
+                                        2 * colq + 2);
+                        if (l == 1 && xnext && xt == tt)
+                            write_x(xn, s_x + tt * (TM * kInPad * 2), xr);
+                    } else if (colq == 0) {
                         uint32_t v[8];
                         tmem_ld8(acc_row, v);
-                        const int64_t r = tile * TM + row;
+                        const int64_t r = (2 * q + tt) * TM + row;
                         if (r < n) {
                             const float *b4 = sb + 4 * kHidden;
                             float4 *o = reinterpret_cast<float4 *>(out + r * kOut);
@@ -420,10 +430,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                __uint_as_float(v[7]) + b4[7]);
                         }
                     }
+                    fence_proxy_async();
+                    fence_before();
+                    mbar_arrive(bar(B_ACT + tt));
                 }
-                fence_proxy_async();
-                fence_before();
-                mbar_arrive(bar(B_ACT + g));
             }
         }
         if (!ok)
