@@ -474,6 +474,23 @@ int kerr_surrogate_forward_impl(kerr_surrogate *s, const float *in, int64_t n, f
 int kerr_surrogate_grad(kerr_surrogate *s, const float *in, const float *targets,
                         const float *mask, int64_t n, float *loss, void *stream);
 
+/* Training implementations.  KERR_SURR_TRAIN_FUSED (the default of
+ * kerr_surrogate_grad and kerr_surrogate_train): three kernels per step --
+ * one CTA per 128-row tile runs the five forward layers, the loss and the four
+ * backward layers through the hidden weights with every activation in shared
+ * memory and every accumulator in tensor memory; one launch contracts the
+ * stored activations and gradients over the batch into all weight and bias
+ * gradients; one launch applies Adam and refreshes the bf16 weights.
+ * KERR_SURR_TRAIN_GEMM: the layer-by-layer tcgen05 GEMMs (about twenty
+ * launches per step).  Both use bf16 operands with fp32 accumulation, bias
+ * and SiLU in fp32, bf16 activations and backward signals; their gradients
+ * differ by accumulation order only. */
+#define KERR_SURR_TRAIN_FUSED 0
+#define KERR_SURR_TRAIN_GEMM 1
+int kerr_surrogate_grad_impl(kerr_surrogate *s, const float *in, const float *targets,
+                             const float *mask, int64_t n, float *loss, int32_t impl,
+                             void *stream);
+
 /* Trains with Adam (beta1 0.9, beta2 0.999, eps 1e-8) on n rows for `epochs`
  * passes in order, `batch` rows per step, learning rate lr decayed by cosine
  * to lr/20 over all steps.  loss_per_epoch (host, `epochs` floats, or NULL)
@@ -485,6 +502,10 @@ int kerr_surrogate_grad(kerr_surrogate *s, const float *in, const float *targets
 int kerr_surrogate_train(kerr_surrogate *s, const float *in, const float *targets,
                          const float *mask, int64_t n, int32_t epochs, int32_t batch, float lr,
                          float *loss_per_epoch, void *stream);
+/* kerr_surrogate_train on a chosen implementation (KERR_SURR_TRAIN_*). */
+int kerr_surrogate_train_impl(kerr_surrogate *s, const float *in, const float *targets,
+                              const float *mask, int64_t n, int32_t epochs, int32_t batch,
+                              float lr, float *loss_per_epoch, int32_t impl, void *stream);
 
 /* Renders a camera with the surrogate: the network predicts every pixel; a
  * pixel falls back to the integrator (opts, with crossing labels) when its

@@ -19,7 +19,7 @@ LIB = os.path.join(OUT, "libkerr.so")
 UNITS = ["kerr_api.cu", "kerr_trace_f32.cu", "kerr_trace_f32b.cu", "kerr_trace_f32x2.cu", "kerr_trace_zone.cu",
          "kerr_trace_f64.cu", "kerr_static.cu", "kerr_surrogate.cu", "kerr_mlp_tc.cu", "kerr_gemm_tc.cu",
          "kerr_fixed.cu", "kerr_coordtime.cu",
-         "kerr_dense.cu", "kerr_peak.cu"]
+         "kerr_dense.cu", "kerr_peak.cu", "kerr_train_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 
@@ -32,8 +32,10 @@ def _nvcc() -> str:
 
 
 def _sources() -> list[str]:
+    # this file too: a change of the unit list or flags rebuilds
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)
-            if f.endswith((".cu", ".cuh", ".h"))] + [os.path.join(ROOT, "include", "kerr.h")]
+            if f.endswith((".cu", ".cuh", ".h"))] + [os.path.join(ROOT, "include", "kerr.h"),
+                                                      os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:
@@ -64,7 +66,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(len(UNITS)) as ex:
         objs = list(ex.map(compile_unit, UNITS))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+    # every symbol resolved at link time: a unit missing from UNITS fails here
+    # instead of when the library is loaded
+    cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-Xlinker", "--no-undefined", "-o", tmp,
+           *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

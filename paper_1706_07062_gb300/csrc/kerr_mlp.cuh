@@ -77,5 +77,66 @@ cudaError_t forward_tc(const float *in, int64_t n, float *out, const __nv_bfloat
                        const float *const bias[kLayers], unsigned *err, int sms,
                        cudaStream_t s);
 
+// Per-step values of a training run, computed on the device at the start of
+// each step (so that every step is the same captured graph): the batch's
+// first row, its epoch, the scheduled learning rate and Adam's bias
+// corrections.
+struct StepCtl {
+    long long k;       // steps taken in this run
+    long long r0;      // first row of this step's batch
+    int ep;            // epoch of this step
+    float lr, c1, c2;
+};
+
+// Fused training step on the tensor cores (kerr_train_tc.cu): three kernels
+// per step.  train_chain runs, for every 128-row tile of the batch in one
+// CTA, the five forward layers, the loss and its output gradient, and the
+// four backward layers through the hidden weights; train_grads contracts the
+// stored activations and gradients over the batch into the weight and bias
+// gradients; train_adam updates the parameters and refreshes every bf16
+// copy of the weights.  Batch-sized buffers of up to `cap` rows (a multiple
+// of 128): silu'(Z_l) for l = 0..3 ([4][cap][256] fp32), the layer inputs
+// and the output gradients transposed, in 64-row blocks of the tensor-core
+// operand layout (bf16).  The parts never written (input features 4-15,
+// output-gradient rows 8-63) must be zero: allocate with train_zero_bufs.
+struct TrainBufs {
+    int64_t cap;
+    float *sp;
+    __nv_bfloat16 *ht;
+    __nv_bfloat16 *dt;
+};
+size_t train_sp_elems(int64_t cap);
+size_t train_ht_elems(int64_t cap);
+size_t train_dt_elems(int64_t cap);
+cudaError_t train_zero_bufs(TrainBufs b, cudaStream_t s);
+// Packed weights of the training kernels: the forward operands (as the
+// inference forward's) followed by the transposed operands of the backward
+// layers.
+size_t train_packed_elems();
+cudaError_t train_pack(const __nv_bfloat16 *wbf, const size_t woff[kLayers],
+                       __nv_bfloat16 *wtp, cudaStream_t s);
+// Shared-memory limits of the training kernels (once per device, outside
+// stream capture).
+cudaError_t train_prepare();
+// rows: batch size (1 .. cap); ctl (may be null): the batch starts at row
+// ctl->r0 of in / tgt / msk and the loss mean adds to loss_sum[ctl->ep]
+// (else row 0 and loss_sum[0]).  *err becomes nonzero if a pipeline wait
+// gave up.
+cudaError_t train_chain(const float *in, const float *tgt, const float *msk, int64_t rows,
+                        const StepCtl *ctl, float *loss_sum, const float *const bias[kLayers],
+                        const __nv_bfloat16 *wtp, TrainBufs b, unsigned *err, int sms,
+                        cudaStream_t s);
+// Adds the batch's weight and bias gradients to g (parameter layout: W_l at
+// woff[l], b_l at boff[l]).
+cudaError_t train_grads(TrainBufs b, int64_t rows, float *g, const size_t woff[kLayers],
+                        const size_t boff[kLayers], unsigned *err, int sms, cudaStream_t s);
+// Adam on the n parameters with the step's learning rate and bias
+// corrections from ctl; writes the bf16 weights (wbf [out][in], wbfT
+// [in][out] per layer) and the packed training weights, and zeroes g.
+cudaError_t train_adam(float *w, float *g, float *m, float *v, __nv_bfloat16 *wbf,
+                       __nv_bfloat16 *wbfT, __nv_bfloat16 *wtp, const size_t woff[kLayers],
+                       size_t n, const StepCtl *ctl, float b1, float b2, float eps,
+                       cudaStream_t s);
+
 } // namespace mlp
 } // namespace kerr

@@ -103,22 +103,6 @@ struct Bias {
     const float *b[kLayers];
 };
 
-constexpr float kLog2e = 1.4426950408889634f;
-
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 // SiLU of two accumulator values with their biases, rounded to a bf16 pair:
 // z = acc + b, silu(z) = z / (1 + e^-z) with e^-z = 2^(-z log2 e) and the
 // reciprocal from the hardware's approximate exp2 and reciprocal (two MUFU
@@ -135,18 +119,6 @@ __device__ __forceinline__ uint32_t silu2_bf16(uint32_t a0, uint32_t a1, float b
                                 make_float2(1.0f, 1.0f));
     const float2 y = __fmul2_rn(z, make_float2(rcp_approx(d.x), rcp_approx(d.y)));
     return pack_bf16(y.x, y.y);
-}
-
-// A 16-byte shared store without a compiler memory barrier: the epilogue's
-// stores only write the A operand, which no load of this thread reads, so
-// the bias loads and arithmetic of neighbouring column groups may move across
-// them.  Every store still precedes the fence and mbarrier arrive that
-// publish the operand (volatile asm statements keep their order).
-__device__ __forceinline__ void st_act_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
-                                          uint32_t d)
-{
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
-                 "r"(d));
 }
 
 // Hidden-layer epilogue of one thread: accumulator row (TMEM lane) at
@@ -167,7 +139,7 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t tmem_row, const float *
         for (int q = 0; q < 4; ++q) {
             const float4 lo = b[2 * q], hi = b[2 * q + 1];
             const uint32_t *u = v + 8 * q;
-            st_act_v4(row + (4 * c + q) * 128, silu2_bf16(u[0], u[1], lo.x, lo.y),
+            st_shared_v4_relaxed(row + (4 * c + q) * 128, silu2_bf16(u[0], u[1], lo.x, lo.y),
                       silu2_bf16(u[2], u[3], lo.z, lo.w), silu2_bf16(u[4], u[5], hi.x, hi.y),
                       silu2_bf16(u[6], u[7], hi.z, hi.w));
         }
@@ -196,20 +168,6 @@ __device__ __forceinline__ void write_x(float4 x, uint32_t sx, int t)
     const uint32_t xrow = sx + (t >> 3) * (kInPad * 16) + (t & 7) * 16;
     st_shared_v4(xrow, pack_bf16(x.x, x.y), pack_bf16(x.z, x.w), 0u, 0u);
     st_shared_v4(xrow + 128, 0u, 0u, 0u, 0u);
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// Bounded wait that also gives up early once another role has aborted.
-__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
-                                              const volatile int *abort_flag)
-{
-    if (*abort_flag)
-        return false;
-    return mbar_wait(bar, parity);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)

@@ -79,17 +79,6 @@ __global__ void to_bf16_kernel(const float *__restrict__ src, bf16 *__restrict__
         dst[i] = __float2bfloat16(src[i]);
 }
 
-// Per-step values of a training run, computed on the device by
-// train_step_kernel at the start of each step (so that every step is the
-// same captured graph): the batch's first row, its epoch, the scheduled
-// learning rate and Adam's bias corrections.
-struct StepCtl {
-    long long k;       // steps taken in this run
-    long long r0;      // first row of this step's batch
-    int ep;            // epoch of this step
-    float lr, c1, c2;
-};
-
 // Step k's values; sched[k] = (learning rate, Adam bias corrections) from
 // the host (cosine schedule, 1 / (1 - beta^t)).
 __global__ void train_step_kernel(StepCtl *ctl, const float3 *__restrict__ sched,
@@ -333,7 +322,50 @@ struct kerr_surrogate {
     bf16 *wpk = nullptr;          // weights in the tensor-core operand layout
     unsigned *tc_err = nullptr;   // fused forward: a pipeline wait gave up
     int sms = 0;
+    // fused training (kerr_train_tc.cu): batch buffers of tb.cap rows and the
+    // packed training weights (valid unless the GEMM path's Adam ran last)
+    TrainBufs tb{};
+    bf16 *wtp = nullptr;
+    bool wtp_valid = false;
 };
+
+static void free_train(kerr_surrogate *s)
+{
+    cudaFree(s->tb.sp);
+    cudaFree(s->tb.ht);
+    cudaFree(s->tb.dt);
+    s->tb = TrainBufs{};
+}
+
+// Batch buffers of the fused training kernels for `rows` rows (capacity a
+// multiple of 128, grow-only); the never-written parts are zeroed once.
+static int ensure_train(kerr_surrogate *s, int64_t rows)
+{
+    const int64_t cap = (rows + 127) / 128 * 128;
+    if (cap <= s->tb.cap)
+        return KERR_OK;
+    free_train(s);
+    TrainBufs b{};
+    b.cap = cap;
+    cudaError_t e = dev_alloc(&b.sp, train_sp_elems(cap) * sizeof(float));
+    if (e == cudaSuccess)
+        e = dev_alloc(&b.ht, train_ht_elems(cap) * sizeof(bf16));
+    if (e == cudaSuccess)
+        e = dev_alloc(&b.dt, train_dt_elems(cap) * sizeof(bf16));
+    if (e == cudaSuccess)
+        e = train_zero_bufs(b, 0);
+    if (e == cudaSuccess)
+        e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(b.sp);
+        cudaFree(b.ht);
+        cudaFree(b.dt);
+        return fail(KERR_ENOMEM, "surrogate: training buffers");
+    }
+    s->tb = b;
+    return KERR_OK;
+}
 
 static void free_batch(kerr_surrogate *s)
 {
@@ -407,6 +439,8 @@ extern "C" int kerr_surrogate_destroy(kerr_surrogate *s)
         return KERR_OK;
     cudaDeviceSynchronize();
     free_batch(s);
+    free_train(s);
+    cudaFree(s->wtp);
     cudaFree(s->w);
     cudaFree(s->g);
     cudaFree(s->m);
@@ -456,6 +490,8 @@ extern "C" int kerr_surrogate_create(const float *init, kerr_surrogate **out)
     if (e == cudaSuccess)
         e = dev_alloc(&s->wpk, packed_weight_elems() * sizeof(bf16));
     if (e == cudaSuccess)
+        e = dev_alloc(&s->wtp, train_packed_elems() * sizeof(bf16));
+    if (e == cudaSuccess)
         e = dev_alloc(&s->tc_err, sizeof(unsigned));
     if (e == cudaSuccess)
         e = cudaMemset(s->tc_err, 0, sizeof(unsigned));
@@ -463,6 +499,8 @@ extern "C" int kerr_surrogate_create(const float *init, kerr_surrogate **out)
         e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
     if (e == cudaSuccess)
         e = gemm_tc_prepare();
+    if (e == cudaSuccess)
+        e = train_prepare();
     if (e == cudaSuccess)
         e = cudaMemcpy(s->w, init, n * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -476,6 +514,10 @@ extern "C" int kerr_surrogate_create(const float *init, kerr_surrogate **out)
         transpose_weights_kernel<<<grid_1d(n), 256>>>(s->wbf, s->wbfT, woffsets());
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess)
+        e = train_pack(s->wbf, kL.w, s->wtp, 0);
+    if (e == cudaSuccess)
+        s->wtp_valid = true;
     if (e == cudaSuccess)
         e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -699,26 +741,61 @@ extern "C" int kerr_surrogate_forward_impl(kerr_surrogate *s, const float *in, i
     return check_tc(s);
 }
 
-extern "C" int kerr_surrogate_grad(kerr_surrogate *s, const float *in, const float *targets,
-                                   const float *mask, int64_t n, float *loss, void *stream)
+// The packed training weights, refreshed from the bf16 copy when the GEMM
+// path's Adam was the last to change the weights.
+static cudaError_t ensure_packed(kerr_surrogate *s, cudaStream_t st)
+{
+    if (s->wtp_valid)
+        return cudaSuccess;
+    const cudaError_t e = train_pack(s->wbf, kL.w, s->wtp, st);
+    if (e == cudaSuccess)
+        s->wtp_valid = true;
+    return e;
+}
+
+static void train_biases(const kerr_surrogate *s, const float *bias[kLayers])
+{
+    for (int l = 0; l < kLayers; ++l)
+        bias[l] = s->w + kL.b[l];
+}
+
+extern "C" int kerr_surrogate_grad_impl(kerr_surrogate *s, const float *in,
+                                        const float *targets, const float *mask, int64_t n,
+                                        float *loss, int32_t impl, void *stream)
 {
     if (!s || !in || !targets || !mask || n < 1)
         return fail(KERR_EINVAL, "kerr_surrogate_grad: bad argument");
+    if (impl != KERR_SURR_TRAIN_FUSED && impl != KERR_SURR_TRAIN_GEMM)
+        return fail(KERR_EINVAL, "kerr_surrogate_grad: unknown implementation");
     int rc = check_rows(n);
     if (rc)
         return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    rc = ensure_batch(s, n, true);
-    if (rc)
-        return rc;
-    input_kernel<<<grid_1d(n * kInPad), 256, 0, st>>>(in, s->A[0], n, s->AT[0], s->ldT);
-    SURR_CUDA(cudaGetLastError());
-    SURR_CUDA(forward_rows(s, n, true, st));
-    SURR_CUDA(cudaMemsetAsync(s->loss, 0, sizeof(float), st));
-    loss_kernel<<<grid_1d(n, 64), 64, 0, st>>>(s->out, targets, mask, n, 1.0f / (float)n,
-                                               s->dOut, s->loss, s->OT, s->ldT);
-    SURR_CUDA(cudaGetLastError());
-    SURR_CUDA(backward_rows(s, n, st));
+    if (impl == KERR_SURR_TRAIN_FUSED) {
+        rc = ensure_train(s, n);
+        if (rc)
+            return rc;
+        const float *bias[kLayers];
+        train_biases(s, bias);
+        SURR_CUDA(ensure_packed(s, st));
+        SURR_CUDA(cudaMemsetAsync(s->g, 0, kL.total * sizeof(float), st));
+        SURR_CUDA(cudaMemsetAsync(s->loss, 0, sizeof(float), st));
+        SURR_CUDA(train_chain(in, targets, mask, n, nullptr, s->loss, bias, s->wtp, s->tb,
+                              s->tc_err, s->sms, st));
+        SURR_CUDA(train_grads(s->tb, n, s->g, kL.w, kL.b, s->tc_err, s->sms, st));
+    } else {
+        rc = ensure_batch(s, n, true);
+        if (rc)
+            return rc;
+        input_kernel<<<grid_1d(n * kInPad), 256, 0, st>>>(in, s->A[0], n, s->AT[0], s->ldT);
+        SURR_CUDA(cudaGetLastError());
+        SURR_CUDA(forward_rows(s, n, true, st));
+        SURR_CUDA(cudaMemsetAsync(s->loss, 0, sizeof(float), st));
+        loss_kernel<<<grid_1d(n, 64), 64, 0, st>>>(s->out, targets, mask, n, 1.0f / (float)n,
+                                                   s->dOut, s->loss, s->OT, s->ldT);
+        SURR_CUDA(cudaGetLastError());
+        SURR_CUDA(backward_rows(s, n, st));
+    }
     float h = 0.f;
     SURR_CUDA(cudaMemcpyAsync(&h, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st));
     SURR_CUDA(cudaStreamSynchronize(st));
@@ -730,20 +807,33 @@ extern "C" int kerr_surrogate_grad(kerr_surrogate *s, const float *in, const flo
     return KERR_OK;
 }
 
-extern "C" int kerr_surrogate_train(kerr_surrogate *s, const float *in, const float *targets,
-                                    const float *mask, int64_t n, int32_t epochs, int32_t batch,
-                                    float lr, float *loss_per_epoch, void *stream)
+extern "C" int kerr_surrogate_grad(kerr_surrogate *s, const float *in, const float *targets,
+                                   const float *mask, int64_t n, float *loss, void *stream)
+{
+    return kerr_surrogate_grad_impl(s, in, targets, mask, n, loss, KERR_SURR_TRAIN_FUSED,
+                                    stream);
+}
+
+extern "C" int kerr_surrogate_train_impl(kerr_surrogate *s, const float *in,
+                                         const float *targets, const float *mask, int64_t n,
+                                         int32_t epochs, int32_t batch, float lr,
+                                         float *loss_per_epoch, int32_t impl, void *stream)
 {
     if (!s || !in || !targets || !mask || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.f))
         return fail(KERR_EINVAL, "kerr_surrogate_train: bad argument");
+    if (impl != KERR_SURR_TRAIN_FUSED && impl != KERR_SURR_TRAIN_GEMM)
+        return fail(KERR_EINVAL, "kerr_surrogate_train: unknown implementation");
     int rc = check_rows(n);
     if (rc)
         return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t B = std::min<int64_t>(batch, n);
-    rc = ensure_batch(s, B, true);
+    const bool fused = impl == KERR_SURR_TRAIN_FUSED;
+    rc = fused ? ensure_train(s, B) : ensure_batch(s, B, true);
     if (rc)
         return rc;
+    const float *bias[kLayers];
+    train_biases(s, bias);
     const int64_t steps_per_epoch = n / B;
     const int64_t total = std::max<int64_t>(1, steps_per_epoch * epochs);
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
@@ -770,6 +860,17 @@ extern "C" int kerr_surrogate_train(kerr_surrogate *s, const float *in, const fl
     cudaGraphExec_t xU = nullptr, x1 = nullptr;
     auto enqueue_step = [&](cudaStream_t q) -> cudaError_t {
         train_step_kernel<<<1, 32, 0, q>>>(ctl, sched, steps_per_epoch, B);
+        if (fused) {
+            // chain, gradients, Adam (which also zeroes the gradient)
+            cudaError_t e = train_chain(in, targets, mask, B, ctl, d_epoch, bias, s->wtp, s->tb,
+                                        s->tc_err, s->sms, q);
+            if (e == cudaSuccess)
+                e = train_grads(s->tb, B, s->g, kL.w, kL.b, s->tc_err, s->sms, q);
+            if (e == cudaSuccess)
+                e = train_adam(s->w, s->g, s->m, s->v, s->wbf, s->wbfT, s->wtp, kL.w, kL.total,
+                               ctl, b1, b2, eps, q);
+            return e;
+        }
         input_kernel<<<grid_1d(B * kInPad), 256, 0, q>>>(in, s->A[0], B, s->AT[0], s->ldT, ctl);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess)
@@ -820,6 +921,10 @@ extern "C" int kerr_surrogate_train(kerr_surrogate *s, const float *in, const fl
         e = cudaMemsetAsync(d_epoch, 0, sizeof(float) * epochs, st);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(ctl, 0, sizeof(StepCtl), st);
+    if (e == cudaSuccess && fused)
+        e = cudaMemsetAsync(s->g, 0, kL.total * sizeof(float), st);
+    if (e == cudaSuccess && fused)
+        e = ensure_packed(s, st);
     if (e == cudaSuccess)
         e = cudaEventRecord(ev0, st);
     if (e == cudaSuccess)
@@ -843,6 +948,8 @@ extern "C" int kerr_surrogate_train(kerr_surrogate *s, const float *in, const fl
         e = cudaStreamSynchronize(st);
     if (e == cudaSuccess)
         s->step += total;
+    if (!fused)
+        s->wtp_valid = false;       // the GEMM path's Adam leaves the packed weights stale
     if (xU)
         cudaGraphExecDestroy(xU);
     if (x1)
@@ -873,6 +980,14 @@ extern "C" int kerr_surrogate_train(kerr_surrogate *s, const float *in, const fl
         for (int ep = 0; ep < epochs; ++ep)
             loss_per_epoch[ep] = h[ep] / (float)std::max<int64_t>(1, steps_per_epoch);
     return KERR_OK;
+}
+
+extern "C" int kerr_surrogate_train(kerr_surrogate *s, const float *in, const float *targets,
+                                    const float *mask, int64_t n, int32_t epochs, int32_t batch,
+                                    float lr, float *loss_per_epoch, void *stream)
+{
+    return kerr_surrogate_train_impl(s, in, targets, mask, n, epochs, batch, lr, loss_per_epoch,
+                                     KERR_SURR_TRAIN_FUSED, stream);
 }
 
 // ===========================================================================

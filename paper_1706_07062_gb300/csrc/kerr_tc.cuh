@@ -149,6 +149,50 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
                  : "memory");
 }
 
+// A 16-byte shared store without a compiler memory barrier, for epilogues
+// whose stores only write an MMA operand that no load of the thread reads:
+// neighbouring loads and arithmetic may move across it, while every such
+// store still precedes the (volatile, memory-clobbering) fence and mbarrier
+// arrive that publish the operand.
+__device__ __forceinline__ void st_shared_v4_relaxed(uint32_t addr, uint32_t a, uint32_t b,
+                                                     uint32_t c, uint32_t d)
+{
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+                 "r"(d));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Bounded wait that also gives up early once another role has aborted.
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity,
+                                              const volatile int *abort_flag)
+{
+    if (*abort_flag)
+        return false;
+    return mbar_wait(bar, parity);
+}
+
+// The hardware's approximate 2^x and 1/x (one MUFU operation each; inputs and
+// outputs below 2^-126 flush to zero).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);

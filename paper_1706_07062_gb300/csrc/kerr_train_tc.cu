@@ -1,0 +1,923 @@
+// kerr_train_tc.cu -- the surrogate's training step as three tensor-core
+// kernels (tcgen05, accumulators in tensor memory).
+//
+// train_chain_kernel: one CTA per 128-row tile of the batch runs the tile's
+// whole chain of nine dependent layers:
+//   forward   F0 .. F3: Z_l = A_l W_l^T + b_l, A_{l+1} = bf16(silu(Z_l))
+//             F4:       out = A_4 W_4^T + b_4, loss, D_4 = bf16(dL/dout)
+//   backward  B4 .. B1: D_{l-1} = bf16((D_l W_l) * silu'(Z_{l-1}))
+// Every layer's A operand stays in shared memory, its accumulator in tensor
+// memory; the weights stream through four 32 KB slots (K-slices of 64, the
+// backward layers' operands transposed at packing time).  The epilogues keep
+// what the weight gradients need, in global memory: silu'(Z_l) (fp32), and
+// the layer inputs A_l and output gradients D_l transposed.
+//
+// train_grads_kernel: dW_l = D_l^T A_l and db_l = D_l^T 1 contracted over the
+// batch: one CTA per (layer, 128 output features, batch split), the
+// transposed operands streamed in 64-row blocks, partial sums added to the
+// gradient with vector atomics.  The bias gradient is one more MMA per
+// K-step against a ones operand, i.e. the column sum of the bf16 gradient.
+//
+// train_adam_kernel: Adam on every parameter, then every bf16 copy of the
+// weights (row-major, transposed, and the packed operands of the chain).
+//
+// Arithmetic as the layer-by-layer GEMM path: bf16 operands, fp32
+// accumulation, bias and SiLU in fp32 (hardware exp2 and reciprocal
+// approximations), bf16 activations and gradients.
+//
+// Operand layout (K-major, no swizzle) as in kerr_mlp_tc.cu: a tile of R rows
+// and K columns is stored as 8 x 8 core matrices of 128 contiguous bytes,
+// byte(r, k) = (r / 8) * (K * 16) + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2.
+// The transposed batch operands of the weight gradients are kept in 64-row
+// blocks of that layout, [feature][row]: block b holds rows 64 b .. 64 b + 63
+// of every feature, so that any 128 features of one block are one
+// contiguous bulk copy.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kerr_mlp.cuh"
+#include "kerr_tc.cuh"
+
+namespace kerr {
+namespace mlp {
+
+namespace {
+
+using namespace kerr::tc;
+using bf16 = __nv_bfloat16;
+
+constexpr int TM = 128;            // rows per tile (MMA M)
+constexpr int KS = 64;             // K columns per weight slice
+constexpr int kSlices = kHidden / KS;
+
+// ---- packed training weights (bf16 elements)
+// forward: W0 [256][16], then layers 1-3 as four [256][64] K-slices and the
+// output layer as four [64][64] K-slices (the inference forward's layout);
+// backward: W_4^T [256][64], then W_3^T, W_2^T, W_1^T as four [256][64]
+// K-slices each (B[n][k] = W_l[k][n]).
+constexpr size_t kFwdElems = (size_t)kHidden * kInPad + 3 * kSlices * (size_t)kHidden * KS +
+                             kSlices * (size_t)kOutPad * KS;
+__host__ __device__ constexpr size_t fwd_off(int l, int s)
+{
+    return (size_t)kHidden * kInPad +
+           (l < kLayers - 1 ? (size_t)(l - 1) * kSlices * kHidden * KS + (size_t)s * kHidden * KS
+                            : 3 * (size_t)kSlices * kHidden * KS + (size_t)s * kOutPad * KS);
+}
+__host__ __device__ constexpr size_t bwd_off(int l, int s)
+{
+    return kFwdElems + (l == kLayers - 1 ? 0
+                                         : (size_t)kHidden * kOutPad +
+                                               (size_t)(3 - l) * kSlices * kHidden * KS +
+                                               (size_t)s * kHidden * KS);
+}
+constexpr size_t kPackedElems = bwd_off(1, kSlices);
+static_assert(kFwdElems == 217088 && fwd_off(4, 0) == 4096 + 3 * 65536, "forward packing");
+static_assert(kPackedElems == kFwdElems + 16384 + 3 * 65536, "backward packing");
+
+// Element (r, k) of an [R][K] operand tile in the core-matrix layout.
+__host__ __device__ constexpr size_t cm(int r, int k, int K)
+{
+    return (size_t)(r >> 3) * (K * 8) + (size_t)(k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+// ---- transposed batch operands: features F, 64-row blocks
+__host__ __device__ constexpr size_t blk(int f, int64_t r, int F)
+{
+    return (size_t)(r >> 6) * ((size_t)F * 64) + cm(f, (int)(r & 63), 64);
+}
+// layer inputs A_l^T (l = 0: the 16 padded input features; 1-4: 256)
+__host__ __device__ constexpr size_t ht_base(int l, int64_t cap)
+{
+    return l == 0 ? 0 : (size_t)cap * kInPad + (size_t)(l - 1) * cap * kHidden;
+}
+__host__ __device__ constexpr int ht_feat(int l) { return l == 0 ? kInPad : kHidden; }
+// output gradients D_l^T (l = 0-3: 256 features; 4: the 64 padded outputs)
+__host__ __device__ constexpr size_t dt_base(int l, int64_t cap) { return (size_t)l * cap * kHidden; }
+__host__ __device__ constexpr int dt_feat(int l) { return l == kLayers - 1 ? kOutPad : kHidden; }
+
+// Weights from the bf16 copy ([out][in] per layer) into the packed training
+// operands: one thread per source element, written to its forward and (for
+// layers 1-4) its backward position.
+struct WOff {
+    size_t w[kLayers];
+};
+
+__global__ void train_pack_kernel(const bf16 *__restrict__ wbf, const WOff woff,
+                                  bf16 *__restrict__ wtp)
+{
+    size_t total = 0;
+    for (int l = 0; l < kLayers; ++l)
+        total += (size_t)out_dim(l) * in_dim(l);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int l = 0;
+        size_t j = i;
+        while (l + 1 < kLayers && j >= (size_t)out_dim(l) * in_dim(l)) {
+            j -= (size_t)out_dim(l) * in_dim(l);
+            ++l;
+        }
+        const int K = in_dim(l);
+        const int o = (int)(j / K), k = (int)(j % K);      // W_l[o][k]
+        const bf16 v = wbf[woff.w[l] + j];
+        if (l == 0) {
+            wtp[cm(o, k, kInPad)] = v;
+        } else {
+            wtp[fwd_off(l, k / KS) + cm(o, k % KS, KS)] = v;
+            // backward operand B[n = k][kk = o] in K-slices over o
+            wtp[bwd_off(l, o / KS) + cm(k, o % KS, KS)] = v;
+        }
+    }
+}
+
+} // namespace
+
+size_t train_sp_elems(int64_t cap) { return (size_t)4 * cap * kHidden; }
+size_t train_ht_elems(int64_t cap) { return ht_base(kLayers, cap); }
+size_t train_dt_elems(int64_t cap) { return dt_base(kLayers - 1, cap) + (size_t)cap * kOutPad; }
+size_t train_packed_elems() { return kPackedElems; }
+
+cudaError_t train_zero_bufs(TrainBufs b, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(b.ht, 0, train_ht_elems(b.cap) * sizeof(bf16), s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b.dt, 0, train_dt_elems(b.cap) * sizeof(bf16), s);
+    return e;
+}
+
+cudaError_t train_pack(const bf16 *wbf, const size_t woff[kLayers], bf16 *wtp, cudaStream_t s)
+{
+    WOff o;
+    for (int l = 0; l < kLayers; ++l)
+        o.w[l] = woff[l];
+    train_pack_kernel<<<256, 256, 0, s>>>(wbf, o, wtp);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// train_chain_kernel
+// ===========================================================================
+namespace {
+
+constexpr int kCSlots = 4;                                    // weight-slice buffers
+constexpr uint32_t kSlotBytes = kHidden * KS * 2;             // 32 KB
+constexpr int kChainLayers = 9;                               // F0-F4, B4-B1
+constexpr int kChainSlices = 3 * kSlices + kSlices + 1 + 3 * kSlices;   // per tile
+
+// Shared memory (bytes) of the chain kernel.
+constexpr uint32_t C_ACT = 0;                                 // A operand [128][256]: 64 KB
+constexpr uint32_t C_SLOT = C_ACT + TM * kHidden * 2;         // 4 x 32 KB
+constexpr uint32_t C_W0 = C_SLOT + kCSlots * kSlotBytes;      // W0 [256][16]: 8 KB
+constexpr uint32_t C_BIAS = C_W0 + kHidden * kInPad * 2;      // 4 x 256 + 64 floats
+constexpr uint32_t C_BAR = C_BIAS + (4 * kHidden + kOutPad) * 4;
+// barriers: full[4], empty[4], accfull, actready, w0, final; TMEM slot; abort flag
+constexpr int kCBars = 2 * kCSlots + 4;
+constexpr uint32_t C_TOTAL = C_BAR + kCBars * 8 + 8 + 8;
+static_assert(C_TOTAL <= 227 * 1024, "shared memory of the chain kernel");
+static_assert(C_SLOT % 1024 == 0 && C_W0 % 16 == 0 && C_BIAS % 16 == 0 && C_BAR % 8 == 0,
+              "bulk-copy, vector-load and mbarrier alignment");
+constexpr int kCThreads = 64 + 512;       // producer warp, MMA warp, 16 epilogue warps
+constexpr int kCEpi = 512;
+
+struct Biases {
+    const float *b[kLayers];
+};
+
+// Weight slice i of a tile's schedule: F1-F3 (four [256][64] slices each),
+// F4 (four [64][64]), B4 (one [256][64]: K = 64), B3-B1 (four each).
+__device__ __forceinline__ void chain_slice(int i, size_t &off, uint32_t &bytes)
+{
+    if (i < 3 * kSlices) {
+        off = fwd_off(1 + i / kSlices, i % kSlices);
+        bytes = kSlotBytes;
+    } else if (i < 4 * kSlices) {
+        off = fwd_off(kLayers - 1, i - 3 * kSlices);
+        bytes = kOutPad * KS * 2;
+    } else if (i == 4 * kSlices) {
+        off = bwd_off(kLayers - 1, 0);
+        bytes = kSlotBytes;
+    } else {
+        const int j = i - 4 * kSlices - 1;
+        off = bwd_off(3 - j / kSlices, j % kSlices);
+        bytes = kSlotBytes;
+    }
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x)
+{
+    const bf16 h = __float2bfloat16(x);
+    return *reinterpret_cast<const uint16_t *>(&h);
+}
+
+// Input row `t` (< 128) of tile `tile` as the layer-0 A operand ([128][16],
+// columns 4-15 zero) at `act`, and its 4 live features into A_0^T.
+__device__ __forceinline__ void chain_stage_x(const float *__restrict__ in, int64_t rows,
+                                              int64_t r0, int64_t tile, int t, uint32_t act,
+                                              uint16_t *__restrict__ ht0)
+{
+    const int64_t r = tile * TM + t;
+    float x[4] = {0.f, 0.f, 0.f, 0.f};
+    if (r < rows) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            x[j] = in[(r0 + r) * kIn + j];
+    }
+    const uint32_t xrow = act + (t >> 3) * (kInPad * 16) + (t & 7) * 16;
+    st_shared_v4(xrow, pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), 0u, 0u);
+    st_shared_v4(xrow + 128, 0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        ht0[blk(j, r, kInPad)] = bf16_bits(x[j]);
+}
+
+} // namespace
+
+namespace {
+
+__global__ void __launch_bounds__(kCThreads, 1)
+    train_chain_kernel(const float *__restrict__ in, const float *__restrict__ tgt,
+                       const float *__restrict__ msk, int64_t rows,
+                       const StepCtl *__restrict__ ctl, float *__restrict__ loss_sum,
+                       const Biases bias, const bf16 *__restrict__ wtp, const TrainBufs bufs,
+                       unsigned *__restrict__ err)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int t = threadIdx.x;
+    const int warp = t >> 5;
+    const int lane = t & 31;
+    float *sb = reinterpret_cast<float *>(smem + C_BIAS);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C_BAR);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + C_BAR + kCBars * 8);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + C_BAR + kCBars * 8 + 8);
+    auto bar = [&](int i) { return smem_u32(&bars[i]); };
+    const int B_FULL = 0, B_EMPTY = kCSlots, B_ACC = 2 * kCSlots, B_ACT = 2 * kCSlots + 1,
+              B_W0 = 2 * kCSlots + 2, B_FIN = 2 * kCSlots + 3;
+    const uint32_t s_act = smem_u32(smem + C_ACT);
+    const uint32_t s_slot = smem_u32(smem + C_SLOT);
+    const uint32_t s_w0 = smem_u32(smem + C_W0);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        for (int i = 0; i < kCSlots; ++i) {
+            mbar_init(bar(B_FULL + i), 1);
+            mbar_init(bar(B_EMPTY + i), 1);
+        }
+        mbar_init(bar(B_ACC), 1);
+        mbar_init(bar(B_ACT), kCEpi);
+        mbar_init(bar(B_W0), 1);
+        mbar_init(bar(B_FIN), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = t; i < 4 * kHidden + kOutPad; i += blockDim.x)
+        sb[i] = i < 4 * kHidden ? bias.b[i / kHidden][i % kHidden]
+                                : bias.b[kLayers - 1][i - 4 * kHidden];
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int64_t ntiles = (rows + TM - 1) / TM;
+    const int64_t r0 = ctl ? ctl->r0 : 0;
+    bool ok = true;
+
+    if (warp == 0) {
+        // ---- producer: lane p streams the slices that go through slot p
+        // (bulk copies of one thread complete one after another, those of
+        // different threads overlap); W0 once, from lane 0
+        if (lane < kCSlots) {
+            const int p = lane;
+            if (p == 0) {
+                mbar_expect_tx(bar(B_W0), kHidden * kInPad * 2);
+                bulk_load(s_w0, wtp, kHidden * kInPad * 2, bar(B_W0));
+            }
+            uint32_t k = 0, issued = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                for (int i = 0; i < kChainSlices; ++i, ++k) {
+                    if (k % kCSlots != (uint32_t)p)
+                        continue;
+                    const uint32_t use = k / kCSlots;
+                    if (use >= 1 &&
+                        !wait_or_abort(bar(B_EMPTY + p), (use - 1) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    size_t off;
+                    uint32_t bytes;
+                    chain_slice(i, off, bytes);
+                    mbar_expect_tx(bar(B_FULL + p), bytes);
+                    bulk_load(s_slot + p * kSlotBytes, wtp + off, bytes, bar(B_FULL + p));
+                    issued = use + 1;
+                }
+            }
+            if (!ok)
+                *abort_flag = 1;
+            // the copies issued have landed before the CTA can exit (already
+            // true unless a wait gave up)
+            if (issued > 0)
+                mbar_wait(bar(B_FULL + p), (issued - 1) & 1);
+            if (p == 0)
+                mbar_wait(bar(B_W0), 0);
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer: per tile F0 (one MMA against the resident W0), then
+        // F1-F3, F4, B4, B3-B1 on the streamed slices
+        if (lane == 0) {
+            uint32_t k = 0, ph_act = 0;
+            ok = wait_or_abort(bar(B_W0), 0, abort_flag);
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                for (int L = 0; L < kChainLayers && ok; ++L) {
+                    if (!wait_or_abort(bar(B_ACT), ph_act, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    ph_act ^= 1;
+                    fence_after();
+                    if (L == 0) {
+                        mma_bf16(tmem, make_desc(s_act, 128, kInPad * 16),
+                                 make_desc(s_w0, 128, kInPad * 16), make_idesc(TM, kHidden), 0u);
+                    } else {
+                        const bool b4 = L == 5;                 // A: D_4 [128][64], K = 64
+                        const int ns = b4 ? 1 : kSlices;
+                        const uint32_t idesc =
+                            L == 4 ? make_idesc(TM, kOutPad) : make_idesc(TM, kHidden);
+                        const uint32_t asbo = b4 ? KS * 16 : kHidden * 16;
+                        for (int s = 0; s < ns; ++s, ++k) {
+                            const uint32_t slot = k % kCSlots;
+                            if (!wait_or_abort(bar(B_FULL + slot), (k / kCSlots) & 1,
+                                               abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            fence_after();
+                            const uint32_t w = s_slot + slot * kSlotBytes;
+#pragma unroll
+                            for (int j = 0; j < KS / 16; ++j)
+                                mma_bf16(tmem, make_desc(s_act + s * (KS / 8) * 128 + j * 256, 128, asbo),
+                                         make_desc(w + j * 256, 128, KS * 16), idesc,
+                                         (s > 0 || j > 0) ? 1u : 0u);
+                            mma_commit(bar(B_EMPTY + slot));
+                        }
+                    }
+                    if (ok)
+                        mma_commit(bar(B_ACC));
+                }
+            }
+            if (!ok)
+                *abort_flag = 1;
+            // every MMA issued has completed before the tensor memory is freed
+            mma_commit(bar(B_FIN));
+            mbar_wait(bar(B_FIN), 0);
+        }
+    } else {
+        // ---- epilogue: sixteen warps; the four warps of a TMEM lane quarter
+        // take 64 of the 256 columns each (two 32-column chunks)
+        const int ew = warp - 2;
+        const int et = t - 64;                          // 0 .. 511
+        const int quarter = warp & 3;
+        const int colq = ew >> 2;
+        const int row = 32 * quarter + lane;            // accumulator row of this thread
+        const uint32_t acc_row = tmem + ((uint32_t)(32 * quarter) << 16);
+        const uint32_t arow = s_act + (row >> 3) * (kHidden * 16) + (row & 7) * 16;
+        const int64_t cap = bufs.cap;
+        uint16_t *ht = reinterpret_cast<uint16_t *>(bufs.ht);
+        uint16_t *dt = reinterpret_cast<uint16_t *>(bufs.dt);
+        const float inv_n = 1.0f / (float)rows;
+        float *lsum = loss_sum + (ctl ? ctl->ep : 0);
+        uint32_t ph = 0;
+        auto wait_acc = [&]() -> bool {
+            if (!wait_or_abort(bar(B_ACC), ph, abort_flag))
+                return false;
+            ph ^= 1;
+            fence_after();
+            return true;
+        };
+        auto publish = [&]() {
+            fence_proxy_async();
+            fence_before();
+            mbar_arrive(bar(B_ACT));
+        };
+        if ((int64_t)blockIdx.x < ntiles) {
+            if (et < TM)
+                chain_stage_x(in, rows, r0, blockIdx.x, et, s_act, ht + ht_base(0, cap));
+            publish();
+        }
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int64_t r = tile * TM + row;          // batch row of this thread
+            // F0-F3: bias and SiLU; A_{l+1} into shared memory (the next A
+            // operand) and transposed into global memory, silu'(Z_l) too
+            for (int l = 0; l < kLayers - 1 && ok; ++l) {
+                if (!wait_acc()) {
+                    ok = false;
+                    break;
+                }
+                const float *bl = sb + l * kHidden;
+                float *spr = bufs.sp + ((size_t)l * cap + r) * kHidden;
+                uint16_t *htl = ht + ht_base(l + 1, cap);
+#pragma unroll 1
+                for (int c = 2 * colq; c < 2 * colq + 2; ++c) {
+                    uint32_t v[32];
+                    tmem_ld32(acc_row + 32 * c, v);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int f0 = 32 * c + 8 * q;
+                        const float4 b0 = *reinterpret_cast<const float4 *>(bl + f0);
+                        const float4 b1 = *reinterpret_cast<const float4 *>(bl + f0 + 4);
+                        const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                        float h[8], sp[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float z = __uint_as_float(v[8 * q + j]) + bb[j];
+                            const float sg = rcp_approx(1.0f + ex2_approx(-z * kLog2e));
+                            h[j] = z * sg;
+                            sp[j] = sg * (1.0f + z * (1.0f - sg));
+                        }
+                        const uint32_t pp[4] = {pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]),
+                                                pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7])};
+                        st_shared_v4_relaxed(arow + (4 * c + q) * 128, pp[0], pp[1], pp[2], pp[3]);
+                        float4 *s4 = reinterpret_cast<float4 *>(spr + f0);
+                        s4[0] = make_float4(sp[0], sp[1], sp[2], sp[3]);
+                        s4[1] = make_float4(sp[4], sp[5], sp[6], sp[7]);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            htl[blk(f0 + j, r, kHidden)] = (uint16_t)(pp[j >> 1] >> (16 * (j & 1)));
+                    }
+                }
+                publish();
+            }
+            if (!ok)
+                break;
+            // F4: outputs, the row's loss and its gradient D_4 (bf16): the A
+            // operand of B4 ([128][64]) and transposed into global memory
+            if (!wait_acc()) {
+                ok = false;
+                break;
+            }
+            if (colq == 0) {
+                uint32_t v[8];
+                tmem_ld8(acc_row, v);
+                float dv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float lrow = 0.0f;
+                if (r < rows) {
+                    const float *b4 = sb + 4 * kHidden;
+                    const float *y = tgt + (r0 + r) * kOut;
+                    const float *m = msk + (r0 + r) * kOut;
+                    float o[kOut];
+#pragma unroll
+                    for (int j = 0; j < kOut; ++j)
+                        o[j] = __uint_as_float(v[j]) + b4[j];
+                    const float z = o[0];
+                    const float spl = z > 0.f ? z + log1pf(__expf(-z)) : log1pf(__expf(z));
+                    lrow = spl - y[0] * z;
+                    const float sig = 1.0f / (1.0f + __expf(-z));
+                    dv[0] = (sig - y[0]) * inv_n;
+#pragma unroll
+                    for (int j = 1; j < kOut; ++j) {
+                        const float e = m[j] * (o[j] - y[j]);
+                        lrow += e * (o[j] - y[j]);
+                        dv[j] = 2.0f * e * inv_n;
+                    }
+                }
+                const uint32_t pp[4] = {pack_bf16(dv[0], dv[1]), pack_bf16(dv[2], dv[3]),
+                                        pack_bf16(dv[4], dv[5]), pack_bf16(dv[6], dv[7])};
+                const uint32_t drow = s_act + (row >> 3) * (KS * 16) + (row & 7) * 16;
+                st_shared_v4_relaxed(drow, pp[0], pp[1], pp[2], pp[3]);
+#pragma unroll
+                for (int kc = 1; kc < KS / 8; ++kc)
+                    st_shared_v4_relaxed(drow + kc * 128, 0u, 0u, 0u, 0u);
+                uint16_t *d4 = dt + dt_base(kLayers - 1, cap);
+#pragma unroll
+                for (int j = 0; j < kOut; ++j)
+                    d4[blk(j, r, kOutPad)] = (uint16_t)(pp[j >> 1] >> (16 * (j & 1)));
+                // the batch mean: a warp sum, one atomic per warp
+#pragma unroll
+                for (int o2 = 16; o2 > 0; o2 >>= 1)
+                    lrow += __shfl_xor_sync(0xffffffffu, lrow, o2);
+                if (lane == 0)
+                    atomicAdd(lsum, lrow * inv_n);
+            }
+            publish();
+            // B4 .. B1: D_lz = bf16(acc * silu'(Z_lz)) for lz = 3 .. 0, the A
+            // operand of the next backward layer (lz > 0) and transposed
+            for (int lz = kLayers - 2; lz >= 0 && ok; --lz) {
+                const float *spr = bufs.sp + ((size_t)lz * cap + r) * kHidden;
+                uint16_t *dtl = dt + dt_base(lz, cap);
+                float4 s4[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)             // in flight during the wait
+                    s4[i] = reinterpret_cast<const float4 *>(spr + 64 * colq)[i];
+                if (!wait_acc()) {
+                    ok = false;
+                    break;
+                }
+#pragma unroll 1
+                for (int c = 2 * colq; c < 2 * colq + 2; ++c) {
+                    if (c != 2 * colq) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            s4[i] = reinterpret_cast<const float4 *>(spr + 32 * c)[i];
+                    }
+                    uint32_t v[32];
+                    tmem_ld32(acc_row + 32 * c, v);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int f0 = 32 * c + 8 * q;
+                        const float sp[8] = {s4[2 * q].x,     s4[2 * q].y,     s4[2 * q].z,
+                                             s4[2 * q].w,     s4[2 * q + 1].x, s4[2 * q + 1].y,
+                                             s4[2 * q + 1].z, s4[2 * q + 1].w};
+                        float d[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            d[j] = __uint_as_float(v[8 * q + j]) * sp[j];
+                        const uint32_t pp[4] = {pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]),
+                                                pack_bf16(d[4], d[5]), pack_bf16(d[6], d[7])};
+                        if (lz > 0)
+                            st_shared_v4_relaxed(arow + (4 * c + q) * 128, pp[0], pp[1], pp[2],
+                                                 pp[3]);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            dtl[blk(f0 + j, r, kHidden)] = (uint16_t)(pp[j >> 1] >> (16 * (j & 1)));
+                    }
+                }
+                if (lz > 0)
+                    publish();
+            }
+            if (!ok)
+                break;
+            // the next tile's input rows (B1's MMA, the last reader of the A
+            // operand, has completed)
+            const int64_t nt = tile + gridDim.x;
+            if (nt < ntiles) {
+                if (et < TM)
+                    chain_stage_x(in, rows, r0, nt, et, s_act, ht + ht_base(0, cap));
+                publish();
+            }
+        }
+        if (!ok)
+            *abort_flag = 1;
+    }
+
+    if (!ok && err)
+        atomicExch(err, 1u);
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256)
+                     : "memory");
+    }
+}
+
+} // namespace
+
+// ===========================================================================
+// train_grads_kernel
+// ===========================================================================
+namespace {
+
+constexpr int kGStages = 4;
+constexpr uint32_t G_ABYTES = TM * KS * 2;               // 128 features x 64 rows: 16 KB
+constexpr uint32_t G_BBYTES = kHidden * KS * 2;          // 256 features x 64 rows: 32 KB
+constexpr uint32_t G_STAGE = G_ABYTES + G_BBYTES;
+constexpr uint32_t G_ONES = kGStages * G_STAGE;          // ones operand [16][64]: 2 KB
+constexpr uint32_t G_BAR = G_ONES + 16 * KS * 2;
+// barriers: full[4], empty[4], accfull, final; TMEM slot; abort flag
+constexpr int kGBars = 2 * kGStages + 2;
+constexpr uint32_t G_TOTAL = G_BAR + kGBars * 8 + 8 + 8;
+static_assert(G_TOTAL <= 227 * 1024, "shared memory of the gradient kernel");
+constexpr int kGThreads = 64 + 128;       // producer warp, MMA warp, 4 epilogue warps
+constexpr int kGTiles = 9;                // (layer, 128 output features) tiles
+constexpr int kGMaxSplits = 16;
+
+struct GOff {
+    size_t w[kLayers], b[kLayers];
+};
+
+// Gradient tile i: layers 1-3 two each (output features 0-127, 128-255),
+// layer 0 two (16 input features), the output layer one (64 features).
+__device__ __forceinline__ void grad_tile(int i, int &l, int &m0)
+{
+    if (i < 6) {
+        l = 1 + i / 2;
+        m0 = TM * (i % 2);
+    } else if (i < 8) {
+        l = 0;
+        m0 = TM * (i - 6);
+    } else {
+        l = kLayers - 1;
+        m0 = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kGThreads, 1)
+    train_grads_kernel(const TrainBufs bufs, int64_t nblk, int splits, float *__restrict__ g,
+                       const GOff off, unsigned *__restrict__ err)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int t = threadIdx.x;
+    const int warp = t >> 5;
+    const int lane = t & 31;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + G_BAR);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + G_BAR + kGBars * 8);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + G_BAR + kGBars * 8 + 8);
+    auto bar = [&](int i) { return smem_u32(&bars[i]); };
+    const int B_FULL = 0, B_EMPTY = kGStages, B_ACC = 2 * kGStages, B_FIN = 2 * kGStages + 1;
+    const uint32_t s_stage = smem_u32(smem);
+    const uint32_t s_ones = smem_u32(smem + G_ONES);
+
+    int l, m0;
+    grad_tile(blockIdx.x / splits, l, m0);
+    const int split = blockIdx.x % splits;
+    const int64_t kb0 = nblk * split / splits, kb1 = nblk * (split + 1) / splits;
+    const int nk = (int)(kb1 - kb0);
+    const int Fo = dt_feat(l), Fi = ht_feat(l);
+    const uint32_t abytes = (uint32_t)min(TM, Fo - m0) * KS * 2;
+    const uint32_t bbytes = (uint32_t)Fi * KS * 2;
+    const bf16 *A = bufs.dt + dt_base(l, bufs.cap) + cm(m0, 0, KS);
+    const bf16 *B = bufs.ht + ht_base(l, bufs.cap);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        for (int i = 0; i < kGStages; ++i) {
+            mbar_init(bar(B_FULL + i), 1);
+            mbar_init(bar(B_EMPTY + i), 1);
+        }
+        mbar_init(bar(B_ACC), 1);
+        mbar_init(bar(B_FIN), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // the ones operand, and zero A rows beyond a narrow layer's features (they
+    // only feed accumulator rows that are not stored)
+    uint32_t *ones = reinterpret_cast<uint32_t *>(smem + G_ONES);
+    for (int i = t; i < 16 * KS / 2; i += blockDim.x)
+        ones[i] = 0x3F803F80u;                          // two bf16 1.0
+    if (abytes < G_ABYTES) {
+        for (int s = 0; s < kGStages; ++s) {
+            uint32_t *z = reinterpret_cast<uint32_t *>(smem + s * G_STAGE + abytes);
+            for (int i = t; i < (int)(G_ABYTES - abytes) / 4; i += blockDim.x)
+                z[i] = 0u;
+        }
+    }
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0) {
+        // ---- producer: lane 2 s copies stage s's A block, lane 2 s + 1 its
+        // B block (separate threads, so that the copies overlap)
+        if (lane < 2 * kGStages) {
+            const int s = lane >> 1;
+            const bool is_a = (lane & 1) == 0;
+            uint32_t issued = 0;
+            for (int i = s; i < nk && ok; i += kGStages) {
+                const uint32_t use = (uint32_t)(i / kGStages);
+                if (use >= 1 && !wait_or_abort(bar(B_EMPTY + s), (use - 1) & 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                const int64_t kb = kb0 + i;
+                const uint32_t dst = s_stage + s * G_STAGE;
+                if (is_a) {
+                    mbar_expect_tx(bar(B_FULL + s), abytes + bbytes);
+                    bulk_load(dst, A + (size_t)kb * Fo * KS, abytes, bar(B_FULL + s));
+                } else {
+                    bulk_load(dst + G_ABYTES, B + (size_t)kb * Fi * KS, bbytes, bar(B_FULL + s));
+                }
+                issued = use + 1;
+            }
+            if (!ok)
+                *abort_flag = 1;
+            if (issued > 0)
+                mbar_wait(bar(B_FULL + s), (issued - 1) & 1);
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer: per 64-row block four K-steps of the weight
+        // gradient (N = the layer's input width) and of the bias gradient
+        // against the ones operand (N = 16, column 0 read back)
+        if (lane == 0) {
+            const uint32_t idesc = make_idesc(TM, Fi), idesc1 = make_idesc(TM, 16);
+            for (int i = 0; i < nk && ok; ++i) {
+                const int s = i % kGStages;
+                if (!wait_or_abort(bar(B_FULL + s), (i / kGStages) & 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t sa = s_stage + s * G_STAGE, sbb = sa + G_ABYTES;
+#pragma unroll
+                for (int j = 0; j < KS / 16; ++j) {
+                    const uint32_t acc = (i > 0 || j > 0) ? 1u : 0u;
+                    const uint64_t da = make_desc(sa + j * 256, 128, KS * 16);
+                    mma_bf16(tmem, da, make_desc(sbb + j * 256, 128, KS * 16), idesc, acc);
+                    mma_bf16(tmem + 256, da, make_desc(s_ones + j * 256, 128, KS * 16), idesc1,
+                             acc);
+                }
+                mma_commit(bar(B_EMPTY + s));
+            }
+            if (ok && nk > 0)
+                mma_commit(bar(B_ACC));
+            if (!ok)
+                *abort_flag = 1;
+            mma_commit(bar(B_FIN));
+            mbar_wait(bar(B_FIN), 0);
+        }
+    } else {
+        // ---- epilogue: warp w reads accumulator rows 32 (w % 4) .. + 31 (one
+        // output feature each) and adds them to the gradient
+        const int quarter = warp & 3;
+        const int m = m0 + 32 * quarter + lane;
+        const bool live = m < Fo;
+        const uint32_t acc_row = tmem + ((uint32_t)(32 * quarter) << 16);
+        if (nk > 0) {
+            if (!wait_or_abort(bar(B_ACC), 0, abort_flag)) {
+                ok = false;
+            } else {
+                fence_after();
+                float *gw = g + off.w[l] + (size_t)m * Fi;
+                if (Fi == kHidden) {
+#pragma unroll 1
+                    for (int c = 0; c < kHidden / 32; ++c) {
+                        uint32_t v[32];
+                        tmem_ld32(acc_row + 32 * c, v);
+                        if (live) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i)
+                                atomicAdd(reinterpret_cast<float4 *>(gw + 32 * c + 4 * i),
+                                          make_float4(__uint_as_float(v[4 * i]),
+                                                      __uint_as_float(v[4 * i + 1]),
+                                                      __uint_as_float(v[4 * i + 2]),
+                                                      __uint_as_float(v[4 * i + 3])));
+                        }
+                    }
+                } else {
+#pragma unroll 1
+                    for (int c = 0; c < kInPad / 8; ++c) {
+                        uint32_t v[8];
+                        tmem_ld8(acc_row + 8 * c, v);
+                        if (live) {
+#pragma unroll
+                            for (int i = 0; i < 2; ++i)
+                                atomicAdd(reinterpret_cast<float4 *>(gw + 8 * c + 4 * i),
+                                          make_float4(__uint_as_float(v[4 * i]),
+                                                      __uint_as_float(v[4 * i + 1]),
+                                                      __uint_as_float(v[4 * i + 2]),
+                                                      __uint_as_float(v[4 * i + 3])));
+                        }
+                    }
+                }
+                uint32_t vb[8];
+                tmem_ld8(acc_row + 256, vb);
+                if (live)
+                    atomicAdd(g + off.b[l] + m, __uint_as_float(vb[0]));
+            }
+        }
+        if (!ok)
+            *abort_flag = 1;
+    }
+
+    if (!ok && err)
+        atomicExch(err, 1u);
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                     : "memory");
+    }
+}
+
+} // namespace
+
+// ===========================================================================
+// train_adam_kernel
+// ===========================================================================
+namespace {
+
+// Adam on the whole parameter vector with the step's learning rate and bias
+// corrections; writes every bf16 copy of the weights (row-major [out][in],
+// transposed [in][out] at the same offset, packed training operands) and
+// zeroes the gradient for the next step.
+__global__ void train_adam_kernel(float *__restrict__ w, float *__restrict__ g,
+                                  float *__restrict__ m, float *__restrict__ v,
+                                  bf16 *__restrict__ wbf, bf16 *__restrict__ wbfT,
+                                  bf16 *__restrict__ wtp, const WOff o, int64_t n,
+                                  const StepCtl *__restrict__ ctl, float b1, float b2, float eps)
+{
+    const float lr = ctl->lr, c1 = ctl->c1, c2 = ctl->c2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        g[i] = 0.0f;
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+        w[i] = wi;
+        const bf16 wb = __float2bfloat16(wi);
+        wbf[i] = wb;
+        int l = 0;
+        while (l + 1 < kLayers && (size_t)i >= o.w[l + 1])
+            ++l;
+        const int64_t j = i - (int64_t)o.w[l];
+        const int K = in_dim(l), N = out_dim(l);
+        if (j < (int64_t)N * K) {                               // weights, not biases
+            const int oo = (int)(j / K), k = (int)(j % K);
+            wbfT[o.w[l] + (size_t)k * N + oo] = wb;
+            if (l == 0) {
+                wtp[cm(oo, k, kInPad)] = wb;
+            } else {
+                wtp[fwd_off(l, k / KS) + cm(oo, k % KS, KS)] = wb;
+                wtp[bwd_off(l, oo / KS) + cm(k, oo % KS, KS)] = wb;
+            }
+        }
+    }
+}
+
+} // namespace
+
+cudaError_t train_prepare()
+{
+    cudaError_t e = cudaFuncSetAttribute(train_chain_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C_TOTAL);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(train_grads_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)G_TOTAL);
+    return e;
+}
+
+cudaError_t train_chain(const float *in, const float *tgt, const float *msk, int64_t rows,
+                        const StepCtl *ctl, float *loss_sum, const float *const bias[kLayers],
+                        const bf16 *wtp, TrainBufs b, unsigned *err, int sms, cudaStream_t s)
+{
+    if (rows <= 0)
+        return cudaSuccess;
+    if (rows > b.cap || (b.cap % TM) != 0)
+        return cudaErrorInvalidValue;
+    Biases bb;
+    for (int l = 0; l < kLayers; ++l)
+        bb.b[l] = bias[l];
+    const int64_t ntiles = (rows + TM - 1) / TM;
+    const int grid = (int)(ntiles < sms ? ntiles : sms);
+    train_chain_kernel<<<grid, kCThreads, C_TOTAL, s>>>(in, tgt, msk, rows, ctl, loss_sum, bb, wtp,
+                                                        b, err);
+    return cudaGetLastError();
+}
+
+cudaError_t train_grads(TrainBufs b, int64_t rows, float *g, const size_t woff[kLayers],
+                        const size_t boff[kLayers], unsigned *err, int sms, cudaStream_t s)
+{
+    if (rows <= 0)
+        return cudaSuccess;
+    if (rows > b.cap || (b.cap % TM) != 0)
+        return cudaErrorInvalidValue;
+    const int64_t nblk = 2 * ((rows + TM - 1) / TM);       // 64-row blocks of the batch
+    int64_t splits = sms / kGTiles;
+    if (splits > kGMaxSplits)
+        splits = kGMaxSplits;
+    if (splits > nblk)
+        splits = nblk;
+    if (splits < 1)
+        splits = 1;
+    GOff o;
+    for (int l = 0; l < kLayers; ++l) {
+        o.w[l] = woff[l];
+        o.b[l] = boff[l];
+    }
+    train_grads_kernel<<<kGTiles * (int)splits, kGThreads, G_TOTAL, s>>>(b, nblk, (int)splits, g,
+                                                                         o, err);
+    return cudaGetLastError();
+}
+
+cudaError_t train_adam(float *w, float *g, float *m, float *v, bf16 *wbf, bf16 *wbfT, bf16 *wtp,
+                       const size_t woff[kLayers], size_t n, const StepCtl *ctl, float b1,
+                       float b2, float eps, cudaStream_t s)
+{
+    WOff o;
+    for (int l = 0; l < kLayers; ++l)
+        o.w[l] = woff[l];
+    const int64_t blocks = ((int64_t)n + 255) / 256;
+    train_adam_kernel<<<(int)(blocks < 2432 ? blocks : 2432), 256, 0, s>>>(
+        w, g, m, v, wbf, wbfT, wtp, o, (int64_t)n, ctl, b1, b2, eps);
+    return cudaGetLastError();
+}
+
+} // namespace mlp
+} // namespace kerr

@@ -121,6 +121,10 @@ def lib():
         L.kerr_surrogate_forward_impl.argtypes = [vp, vp, i64, vp, i32, vp]
         L.kerr_surrogate_grad.argtypes = [vp, vp, vp, vp, i64, c.POINTER(c.c_float), vp]
         L.kerr_surrogate_train.argtypes = [vp, vp, vp, vp, i64, i32, i32, c.c_float, vp, vp]
+        L.kerr_surrogate_grad_impl.argtypes = [vp, vp, vp, vp, i64, c.POINTER(c.c_float), i32,
+                                               vp]
+        L.kerr_surrogate_train_impl.argtypes = [vp, vp, vp, vp, i64, i32, i32, c.c_float, vp,
+                                                i32, vp]
         L.kerr_surrogate_render.argtypes = [vp, vp, c.POINTER(Camera), c.POINTER(Opts), c.c_float,
                                             c.c_float, c.c_float, vp, vp, c.POINTER(i64), vp]
         L.kerr_num_variants.argtypes = []
@@ -177,7 +181,8 @@ def lib():
                      "kerr_surrogate_save", "kerr_surrogate_load", "kerr_autotune_cameras",
                      "kerr_autotune_particles", "kerr_tune_key_cameras",
                      "kerr_tune_key_particles", "kerr_tune_cache_lookup",
-                     "kerr_tune_cache_store", "kerr_trace_camera_pixels"):
+                     "kerr_tune_cache_store", "kerr_trace_camera_pixels",
+                     "kerr_surrogate_grad_impl", "kerr_surrogate_train_impl"):
             getattr(L, name).restype = c.c_int
         _lib = L
     return _lib
@@ -531,21 +536,40 @@ def kerr_surrogate_forward(s: Surrogate, inp, out=None, stream=None, impl=None):
     return out
 
 
-def kerr_surrogate_grad(s: Surrogate, inp, tgt, msk, stream=None) -> float:
+SURR_TRAIN_FUSED, SURR_TRAIN_GEMM = 0, 1
+
+
+def kerr_surrogate_grad(s: Surrogate, inp, tgt, msk, stream=None, impl=None) -> float:
+    """Batch loss; the gradient stays in the surrogate (Surrogate.grad()).
+    impl None = the fused training kernels."""
     loss = ctypes.c_float()
-    _check(lib().kerr_surrogate_grad(s.handle, _ptr(inp), _ptr(tgt), _ptr(msk),
-                                     int(inp.shape[0]), ctypes.byref(loss),
-                                     _stream_ptr(stream, inp)), "kerr_surrogate_grad")
+    if impl is None:
+        _check(lib().kerr_surrogate_grad(s.handle, _ptr(inp), _ptr(tgt), _ptr(msk),
+                                         int(inp.shape[0]), ctypes.byref(loss),
+                                         _stream_ptr(stream, inp)), "kerr_surrogate_grad")
+    else:
+        _check(lib().kerr_surrogate_grad_impl(s.handle, _ptr(inp), _ptr(tgt), _ptr(msk),
+                                              int(inp.shape[0]), ctypes.byref(loss), int(impl),
+                                              _stream_ptr(stream, inp)),
+               "kerr_surrogate_grad_impl")
     return loss.value
 
 
 def kerr_surrogate_train(s: Surrogate, inp, tgt, msk, epochs: int, batch: int, lr: float,
-                         stream=None) -> np.ndarray:
+                         stream=None, impl=None) -> np.ndarray:
+    """Mean batch loss per epoch; impl None = the fused training kernels."""
     losses = np.zeros(epochs, np.float32)
-    _check(lib().kerr_surrogate_train(s.handle, _ptr(inp), _ptr(tgt), _ptr(msk),
-                                      int(inp.shape[0]), int(epochs), int(batch), float(lr),
-                                      losses.ctypes.data, _stream_ptr(stream, inp)),
-           "kerr_surrogate_train")
+    if impl is None:
+        _check(lib().kerr_surrogate_train(s.handle, _ptr(inp), _ptr(tgt), _ptr(msk),
+                                          int(inp.shape[0]), int(epochs), int(batch), float(lr),
+                                          losses.ctypes.data, _stream_ptr(stream, inp)),
+               "kerr_surrogate_train")
+    else:
+        _check(lib().kerr_surrogate_train_impl(s.handle, _ptr(inp), _ptr(tgt), _ptr(msk),
+                                               int(inp.shape[0]), int(epochs), int(batch),
+                                               float(lr), losses.ctypes.data, int(impl),
+                                               _stream_ptr(stream, inp)),
+               "kerr_surrogate_train_impl")
     return losses
 
 

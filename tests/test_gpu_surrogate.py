@@ -78,16 +78,18 @@ def test_fused_forward_many_tiles_per_cta():
     s.close()
 
 
-@pytest.mark.parametrize("n", [4096, 1000, 37])
-def test_gradient_matches_reference_network(n):
-    """Weight, bias and loss gradients of the tensor-core training GEMMs
-    against the FP64 reference network, on batches that fill whole tiles and
-    on ragged ones (partial row tiles, a partial last K slice of the
-    batch-contracted weight gradients, split-K)."""
+@pytest.mark.parametrize("impl", [K.SURR_TRAIN_FUSED, K.SURR_TRAIN_GEMM])
+@pytest.mark.parametrize("n", [4096, 1000, 129, 37])
+def test_gradient_matches_reference_network(impl, n):
+    """Weight, bias and loss gradients of both training implementations (the
+    fused chain / gradient kernels; the layer-by-layer GEMMs) against the FP64
+    reference network, on batches that fill whole tiles and on ragged ones
+    (partial row tiles, a partial last 64-row block of the batch-contracted
+    weight gradients, split batches)."""
     p = M.init_params(12)
     s = K.Surrogate(p)
     x, y, m = random_batch(n, 6)
-    loss = K.kerr_surrogate_grad(s, dev(x), dev(y), dev(m))
+    loss = K.kerr_surrogate_grad(s, dev(x), dev(y), dev(m), impl=impl)
     g = s.grad().astype(np.float64)
     Lq, gq = M.grad(p.astype(np.float64), x, y, m, quantize=True)
     L, gref = M.grad(p.astype(np.float64), x, y, m, quantize=False)
@@ -106,7 +108,50 @@ def test_gradient_matches_reference_network(n):
     s.close()
 
 
-def test_training_fits_a_teacher_network():
+@pytest.mark.parametrize("n", [20000, 8192 + 77])
+def test_fused_and_gemm_gradients_agree(n):
+    """The two training implementations on batches of more 128-row tiles than
+    the GPU has SMs (several tiles per CTA of the chain kernel) and with a
+    ragged tail: gradients equal to accumulation order (the GEMM path sums the
+    bias gradient in fp32 before rounding, the fused path sums the bf16
+    gradient as the reference network does)."""
+    p = M.init_params(14)
+    s = K.Surrogate(p)
+    x, y, m = random_batch(n, 7)
+    xd, yd, md = dev(x), dev(y), dev(m)
+    lf = K.kerr_surrogate_grad(s, xd, yd, md, impl=K.SURR_TRAIN_FUSED)
+    gf = s.grad().astype(np.float64)
+    lg = K.kerr_surrogate_grad(s, xd, yd, md, impl=K.SURR_TRAIN_GEMM)
+    gg = s.grad().astype(np.float64)
+    assert abs(lf - lg) < 1e-5 * (1 + abs(lg))
+    Wf, bf = M.unpack(gf)
+    Wg, bg = M.unpack(gg)
+    for l in range(M.LAYERS):
+        assert np.linalg.norm(Wf[l] - Wg[l]) < 5e-3 * np.linalg.norm(Wg[l]), l
+        assert np.linalg.norm(bf[l] - bg[l]) < 1e-2 * np.linalg.norm(bg[l]) + 1e-7, l
+    s.close()
+
+
+def test_training_implementations_share_the_weights():
+    """After steps on the GEMM path the fused kernels see the updated weights
+    (their packed copy is refreshed), and the reverse."""
+    x, y, m = random_batch(4096, 8)
+    xd, yd, md = dev(x), dev(y), dev(m)
+    s = K.Surrogate(M.init_params(15))
+    for first, second in ((K.SURR_TRAIN_GEMM, K.SURR_TRAIN_FUSED),
+                          (K.SURR_TRAIN_FUSED, K.SURR_TRAIN_GEMM)):
+        K.kerr_surrogate_train(s, xd, yd, md, epochs=1, batch=1024, lr=1e-3, impl=first)
+        lf = K.kerr_surrogate_grad(s, xd, yd, md, impl=second)
+        g2 = s.grad().astype(np.float64)
+        lg = K.kerr_surrogate_grad(s, xd, yd, md, impl=first)
+        g1 = s.grad().astype(np.float64)
+        assert abs(lf - lg) < 1e-5 * (1 + abs(lg))
+        assert np.linalg.norm(g2 - g1) < 1e-2 * np.linalg.norm(g1)
+    s.close()
+
+
+@pytest.mark.parametrize("impl", [K.SURR_TRAIN_FUSED, K.SURR_TRAIN_GEMM])
+def test_training_fits_a_teacher_network(impl):
     """Adam on the tensor-core gradients fits targets made by another network."""
     teacher = M.init_params(21)
     rng = np.random.default_rng(4)
@@ -119,7 +164,8 @@ def test_training_fits_a_teacher_network():
     y[:, 1:] = yt[:, 1:]
     m = np.ones((n, 8))
     s = K.Surrogate(M.init_params(22))
-    losses = K.kerr_surrogate_train(s, dev(x), dev(y), dev(m), epochs=8, batch=4096, lr=2e-3)
+    losses = K.kerr_surrogate_train(s, dev(x), dev(y), dev(m), epochs=8, batch=4096, lr=2e-3,
+                                    impl=impl)
     assert np.all(np.isfinite(losses))
     assert losses[-1] < 0.2 * losses[0], losses
     s.close()
