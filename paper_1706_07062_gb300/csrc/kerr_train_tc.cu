@@ -203,6 +203,64 @@ __device__ __forceinline__ void chain_slice(int i, size_t &off, uint32_t &bytes)
     }
 }
 
+// Named barrier 1 over the sixteen epilogue warps (the producer and MMA
+// warps never take part).
+__device__ __forceinline__ void epi_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(kCEpi) : "memory");
+}
+
+// The same barrier with a vote: true for every epilogue thread iff p holds
+// for all of them.  Every wait outcome goes through it, so that the warps
+// leave their loops together and never strand one another at a barrier.
+__device__ __forceinline__ bool epi_all(bool p)
+{
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred q, rp;\n\t"
+                 "setp.ne.u32 q, %1, 0;\n\t"
+                 "bar.red.and.pred rp, 1, %2, q;\n\t"
+                 "selp.u32 %0, 1, 0, rp;\n\t}\n"
+                 : "=r"(r)
+                 : "r"((uint32_t)p), "n"(kCEpi)
+                 : "memory");
+    return r != 0;
+}
+
+// silu'(Z_l) of (row r, features f .. f + 3) in [l][feature / 4][row][4]
+// floats: the 32 rows of a warp read or write 512 contiguous bytes.
+__device__ __forceinline__ size_t sp_at(int l, int f, int64_t r, int64_t cap)
+{
+    return (((size_t)l * (kHidden / 4) + (f >> 2)) * cap + r) * 4;
+}
+
+// The tile's A operand ([128][256] bf16 in shared memory) transposed into the
+// 64-row blocks of a batch operand (256 features): 512 8 x 8 matrices, four
+// per ldmatrix.trans, which leaves each lane two rows of one feature, stored
+// as one 4-byte word (a warp's store covers 128 contiguous bytes).  ew: the
+// epilogue warp (0-15); dst: the operand's base; tile: the tile index.
+__device__ __forceinline__ void export_transposed(uint32_t act, uint32_t *__restrict__ dst,
+                                                  int64_t tile, int ew, int lane)
+{
+#pragma unroll 2
+    for (int it = 0; it < 8; ++it) {
+        const int mi = (ew * 8 + it) * 4;               // four matrices of one row group
+        const int ma = mi + (lane >> 3);                // the matrix this lane addresses
+        const uint32_t addr = act + (ma >> 5) * (kHidden * 16) + (ma & 31) * 128 + (lane & 7) * 16;
+        uint32_t v[4];
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                     : "r"(addr)
+                     : "memory");
+        const int rr = 8 * (mi >> 5) + 2 * (lane & 3);  // tile row of the pair's first element
+        const int64_t r = tile * TM + rr;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int f = 8 * ((mi + k) & 31) + (lane >> 2);
+            dst[blk(f, r, kHidden) >> 1] = v[k];
+        }
+    }
+}
+
 __device__ __forceinline__ uint16_t bf16_bits(float x)
 {
     const bf16 h = __float2bfloat16(x);
@@ -408,18 +466,20 @@ __global__ void __launch_bounds__(kCThreads, 1)
                 chain_stage_x(in, rows, r0, blockIdx.x, et, s_act, ht + ht_base(0, cap));
             publish();
         }
+        // Per layer: wait for the accumulator, write the next A operand into
+        // shared memory (and silu'(Z) to global memory), synchronise the
+        // epilogue warps, publish the operand to the MMA warp, then export it
+        // transposed into global memory and synchronise again before the
+        // next layer overwrites it.
         for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const int64_t r = tile * TM + row;          // batch row of this thread
-            // F0-F3: bias and SiLU; A_{l+1} into shared memory (the next A
-            // operand) and transposed into global memory, silu'(Z_l) too
+            // F0-F3: bias and SiLU
             for (int l = 0; l < kLayers - 1 && ok; ++l) {
-                if (!wait_acc()) {
+                if (!epi_all(wait_acc())) {
                     ok = false;
                     break;
                 }
                 const float *bl = sb + l * kHidden;
-                float *spr = bufs.sp + ((size_t)l * cap + r) * kHidden;
-                uint16_t *htl = ht + ht_base(l + 1, cap);
 #pragma unroll 1
                 for (int c = 2 * colq; c < 2 * colq + 2; ++c) {
                     uint32_t v[32];
@@ -438,24 +498,27 @@ __global__ void __launch_bounds__(kCThreads, 1)
                             h[j] = z * sg;
                             sp[j] = sg * (1.0f + z * (1.0f - sg));
                         }
-                        const uint32_t pp[4] = {pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]),
-                                                pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7])};
-                        st_shared_v4_relaxed(arow + (4 * c + q) * 128, pp[0], pp[1], pp[2], pp[3]);
-                        float4 *s4 = reinterpret_cast<float4 *>(spr + f0);
-                        s4[0] = make_float4(sp[0], sp[1], sp[2], sp[3]);
-                        s4[1] = make_float4(sp[4], sp[5], sp[6], sp[7]);
-#pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            htl[blk(f0 + j, r, kHidden)] = (uint16_t)(pp[j >> 1] >> (16 * (j & 1)));
+                        st_shared_v4_relaxed(arow + (4 * c + q) * 128, pack_bf16(h[0], h[1]),
+                                             pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]),
+                                             pack_bf16(h[6], h[7]));
+                        *reinterpret_cast<float4 *>(bufs.sp + sp_at(l, f0, r, cap)) =
+                            make_float4(sp[0], sp[1], sp[2], sp[3]);
+                        *reinterpret_cast<float4 *>(bufs.sp + sp_at(l, f0 + 4, r, cap)) =
+                            make_float4(sp[4], sp[5], sp[6], sp[7]);
                     }
                 }
+                fence_proxy_async();
+                epi_sync();
                 publish();
+                export_transposed(s_act, reinterpret_cast<uint32_t *>(ht + ht_base(l + 1, cap)),
+                                  tile, ew, lane);
+                epi_sync();
             }
             if (!ok)
                 break;
             // F4: outputs, the row's loss and its gradient D_4 (bf16): the A
             // operand of B4 ([128][64]) and transposed into global memory
-            if (!wait_acc()) {
+            if (!epi_all(wait_acc())) {
                 ok = false;
                 break;
             }
@@ -504,15 +567,14 @@ __global__ void __launch_bounds__(kCThreads, 1)
             }
             publish();
             // B4 .. B1: D_lz = bf16(acc * silu'(Z_lz)) for lz = 3 .. 0, the A
-            // operand of the next backward layer (lz > 0) and transposed
+            // operand of the next backward layer (lz > 0), exported transposed
             for (int lz = kLayers - 2; lz >= 0 && ok; --lz) {
-                const float *spr = bufs.sp + ((size_t)lz * cap + r) * kHidden;
-                uint16_t *dtl = dt + dt_base(lz, cap);
                 float4 s4[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i)             // in flight during the wait
-                    s4[i] = reinterpret_cast<const float4 *>(spr + 64 * colq)[i];
-                if (!wait_acc()) {
+                    s4[i] = *reinterpret_cast<const float4 *>(
+                        bufs.sp + sp_at(lz, 64 * colq + 4 * i, r, cap));
+                if (!epi_all(wait_acc())) {
                     ok = false;
                     break;
                 }
@@ -521,13 +583,13 @@ __global__ void __launch_bounds__(kCThreads, 1)
                     if (c != 2 * colq) {
 #pragma unroll
                         for (int i = 0; i < 8; ++i)
-                            s4[i] = reinterpret_cast<const float4 *>(spr + 32 * c)[i];
+                            s4[i] = *reinterpret_cast<const float4 *>(
+                                bufs.sp + sp_at(lz, 32 * c + 4 * i, r, cap));
                     }
                     uint32_t v[32];
                     tmem_ld32(acc_row + 32 * c, v);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int f0 = 32 * c + 8 * q;
                         const float sp[8] = {s4[2 * q].x,     s4[2 * q].y,     s4[2 * q].z,
                                              s4[2 * q].w,     s4[2 * q + 1].x, s4[2 * q + 1].y,
                                              s4[2 * q + 1].z, s4[2 * q + 1].w};
@@ -535,23 +597,23 @@ __global__ void __launch_bounds__(kCThreads, 1)
 #pragma unroll
                         for (int j = 0; j < 8; ++j)
                             d[j] = __uint_as_float(v[8 * q + j]) * sp[j];
-                        const uint32_t pp[4] = {pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]),
-                                                pack_bf16(d[4], d[5]), pack_bf16(d[6], d[7])};
-                        if (lz > 0)
-                            st_shared_v4_relaxed(arow + (4 * c + q) * 128, pp[0], pp[1], pp[2],
-                                                 pp[3]);
-#pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            dtl[blk(f0 + j, r, kHidden)] = (uint16_t)(pp[j >> 1] >> (16 * (j & 1)));
+                        st_shared_v4_relaxed(arow + (4 * c + q) * 128, pack_bf16(d[0], d[1]),
+                                             pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]),
+                                             pack_bf16(d[6], d[7]));
                     }
                 }
+                fence_proxy_async();
+                epi_sync();
                 if (lz > 0)
                     publish();
+                export_transposed(s_act, reinterpret_cast<uint32_t *>(dt + dt_base(lz, cap)),
+                                  tile, ew, lane);
+                epi_sync();
             }
             if (!ok)
                 break;
             // the next tile's input rows (B1's MMA, the last reader of the A
-            // operand, has completed)
+            // operand, has completed; the last export is done)
             const int64_t nt = tile + gridDim.x;
             if (nt < ntiles) {
                 if (et < TM)
