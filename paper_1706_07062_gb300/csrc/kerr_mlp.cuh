@@ -92,9 +92,9 @@ struct StepCtl {
 // per step.  train_chain runs, for every 128-row tile of the batch in one
 // CTA, the five forward layers, the loss and its output gradient, and the
 // four backward layers through the hidden weights; train_grads contracts the
-// stored activations and gradients over the batch into the weight and bias
-// gradients; train_adam updates the parameters and refreshes every bf16
-// copy of the weights.  Batch-sized buffers of up to `cap` rows (a multiple
+// stored activations and gradients over the batch into partial weight and
+// bias gradients; train_adam sums them, updates the parameters and refreshes
+// the bf16 weights of the forward and training kernels.  Batch-sized buffers of up to `cap` rows (a multiple
 // of 128): silu'(Z_l) for l = 0..3 ([4][cap][256] fp32), the layer inputs
 // and the output gradients transposed, in 64-row blocks of the tensor-core
 // operand layout (bf16).  The parts never written (input features 4-15,
@@ -126,16 +126,25 @@ cudaError_t train_chain(const float *in, const float *tgt, const float *msk, int
                         const StepCtl *ctl, float *loss_sum, const float *const bias[kLayers],
                         const __nv_bfloat16 *wtp, TrainBufs b, unsigned *err, int sms,
                         cudaStream_t s);
-// Adds the batch's weight and bias gradients to g (parameter layout: W_l at
-// woff[l], b_l at boff[l]).
-cudaError_t train_grads(TrainBufs b, int64_t rows, float *g, const size_t woff[kLayers],
-                        const size_t boff[kLayers], unsigned *err, int sms, cudaStream_t s);
-// Adam on the n parameters with the step's learning rate and bias
-// corrections from ctl; writes the bf16 weights (wbf [out][in], wbfT
-// [in][out] per layer) and the packed training weights, and zeroes g.
-cudaError_t train_adam(float *w, float *g, float *m, float *v, __nv_bfloat16 *wbf,
-                       __nv_bfloat16 *wbfT, __nv_bfloat16 *wtp, const size_t woff[kLayers],
-                       size_t n, const StepCtl *ctl, float b1, float b2, float eps,
+// The batch's weight and bias gradients as train_splits(rows, sms) partial
+// sums over batch splits, each a full copy in the parameter layout (W_l at
+// woff[l], b_l at boff[l]; np parameters, a multiple of 8): part[s * np + i].
+// Every parameter of every split is written (no zeroing needed); summed in
+// split order by train_reduce (into g) or by train_adam.  part holds
+// train_part_elems(np) floats.
+int train_splits(int64_t rows, int sms);
+size_t train_part_elems(size_t np);
+cudaError_t train_grads(TrainBufs b, int64_t rows, float *part, size_t np,
+                        const size_t woff[kLayers], const size_t boff[kLayers], unsigned *err,
+                        int sms, cudaStream_t s);
+cudaError_t train_reduce(const float *part, int splits, size_t np, float *g, cudaStream_t s);
+// Adam on the np parameters with the gradient summed from the partials and
+// the step's learning rate and bias corrections from ctl; writes the bf16
+// weights (wbf [out][in] per layer) and the packed training weights.  The
+// transposed bf16 copy of the GEMM path is not written.
+cudaError_t train_adam(float *w, const float *part, int splits, float *m, float *v,
+                       __nv_bfloat16 *wbf, __nv_bfloat16 *wtp, const size_t woff[kLayers],
+                       size_t np, const StepCtl *ctl, float b1, float b2, float eps,
                        cudaStream_t s);
 
 } // namespace mlp

@@ -327,6 +327,8 @@ struct kerr_surrogate {
     TrainBufs tb{};
     bf16 *wtp = nullptr;
     bool wtp_valid = false;
+    float *part = nullptr;        // the gradient's partial sums over batch splits
+    bool wbfT_valid = true;       // the transposed bf16 copy (the fused Adam skips it)
 };
 
 static void free_train(kerr_surrogate *s)
@@ -441,6 +443,7 @@ extern "C" int kerr_surrogate_destroy(kerr_surrogate *s)
     free_batch(s);
     free_train(s);
     cudaFree(s->wtp);
+    cudaFree(s->part);
     cudaFree(s->w);
     cudaFree(s->g);
     cudaFree(s->m);
@@ -491,6 +494,8 @@ extern "C" int kerr_surrogate_create(const float *init, kerr_surrogate **out)
         e = dev_alloc(&s->wpk, packed_weight_elems() * sizeof(bf16));
     if (e == cudaSuccess)
         e = dev_alloc(&s->wtp, train_packed_elems() * sizeof(bf16));
+    if (e == cudaSuccess)
+        e = dev_alloc(&s->part, train_part_elems(n) * sizeof(float));
     if (e == cudaSuccess)
         e = dev_alloc(&s->tc_err, sizeof(unsigned));
     if (e == cudaSuccess)
@@ -753,6 +758,19 @@ static cudaError_t ensure_packed(kerr_surrogate *s, cudaStream_t st)
     return e;
 }
 
+// The transposed bf16 weights of the GEMM path's input gradients, refreshed
+// from the bf16 copy after fused Adam steps.
+static cudaError_t ensure_wbfT(kerr_surrogate *s, cudaStream_t st)
+{
+    if (s->wbfT_valid)
+        return cudaSuccess;
+    transpose_weights_kernel<<<grid_1d(kL.total), 256, 0, st>>>(s->wbf, s->wbfT, woffsets());
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        s->wbfT_valid = true;
+    return e;
+}
+
 static void train_biases(const kerr_surrogate *s, const float *bias[kLayers])
 {
     for (int l = 0; l < kLayers; ++l)
@@ -778,15 +796,16 @@ extern "C" int kerr_surrogate_grad_impl(kerr_surrogate *s, const float *in,
         const float *bias[kLayers];
         train_biases(s, bias);
         SURR_CUDA(ensure_packed(s, st));
-        SURR_CUDA(cudaMemsetAsync(s->g, 0, kL.total * sizeof(float), st));
         SURR_CUDA(cudaMemsetAsync(s->loss, 0, sizeof(float), st));
         SURR_CUDA(train_chain(in, targets, mask, n, nullptr, s->loss, bias, s->wtp, s->tb,
                               s->tc_err, s->sms, st));
-        SURR_CUDA(train_grads(s->tb, n, s->g, kL.w, kL.b, s->tc_err, s->sms, st));
+        SURR_CUDA(train_grads(s->tb, n, s->part, kL.total, kL.w, kL.b, s->tc_err, s->sms, st));
+        SURR_CUDA(train_reduce(s->part, train_splits(n, s->sms), kL.total, s->g, st));
     } else {
         rc = ensure_batch(s, n, true);
         if (rc)
             return rc;
+        SURR_CUDA(ensure_wbfT(s, st));
         input_kernel<<<grid_1d(n * kInPad), 256, 0, st>>>(in, s->A[0], n, s->AT[0], s->ldT);
         SURR_CUDA(cudaGetLastError());
         SURR_CUDA(forward_rows(s, n, true, st));
@@ -861,14 +880,14 @@ extern "C" int kerr_surrogate_train_impl(kerr_surrogate *s, const float *in,
     auto enqueue_step = [&](cudaStream_t q) -> cudaError_t {
         train_step_kernel<<<1, 32, 0, q>>>(ctl, sched, steps_per_epoch, B);
         if (fused) {
-            // chain, gradients, Adam (which also zeroes the gradient)
+            // chain, partial gradients, Adam on their sum
             cudaError_t e = train_chain(in, targets, mask, B, ctl, d_epoch, bias, s->wtp, s->tb,
                                         s->tc_err, s->sms, q);
             if (e == cudaSuccess)
-                e = train_grads(s->tb, B, s->g, kL.w, kL.b, s->tc_err, s->sms, q);
+                e = train_grads(s->tb, B, s->part, kL.total, kL.w, kL.b, s->tc_err, s->sms, q);
             if (e == cudaSuccess)
-                e = train_adam(s->w, s->g, s->m, s->v, s->wbf, s->wbfT, s->wtp, kL.w, kL.total,
-                               ctl, b1, b2, eps, q);
+                e = train_adam(s->w, s->part, train_splits(B, s->sms), s->m, s->v, s->wbf,
+                               s->wtp, kL.w, kL.total, ctl, b1, b2, eps, q);
             return e;
         }
         input_kernel<<<grid_1d(B * kInPad), 256, 0, q>>>(in, s->A[0], B, s->AT[0], s->ldT, ctl);
@@ -921,10 +940,8 @@ extern "C" int kerr_surrogate_train_impl(kerr_surrogate *s, const float *in,
         e = cudaMemsetAsync(d_epoch, 0, sizeof(float) * epochs, st);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(ctl, 0, sizeof(StepCtl), st);
-    if (e == cudaSuccess && fused)
-        e = cudaMemsetAsync(s->g, 0, kL.total * sizeof(float), st);
-    if (e == cudaSuccess && fused)
-        e = ensure_packed(s, st);
+    if (e == cudaSuccess)
+        e = fused ? ensure_packed(s, st) : ensure_wbfT(s, st);
     if (e == cudaSuccess)
         e = cudaEventRecord(ev0, st);
     if (e == cudaSuccess)
@@ -950,6 +967,8 @@ extern "C" int kerr_surrogate_train_impl(kerr_surrogate *s, const float *in,
         s->step += total;
     if (!fused)
         s->wtp_valid = false;       // the GEMM path's Adam leaves the packed weights stale
+    else
+        s->wbfT_valid = false;      // the fused Adam leaves the transposed copy stale
     if (xU)
         cudaGraphExecDestroy(xU);
     if (x1)

@@ -678,8 +678,8 @@ __device__ __forceinline__ void grad_tile(int i, int &l, int &m0)
 }
 
 __global__ void __launch_bounds__(kGThreads, 1)
-    train_grads_kernel(const TrainBufs bufs, int64_t nblk, int splits, float *__restrict__ g,
-                       const GOff off, unsigned *__restrict__ err)
+    train_grads_kernel(const TrainBufs bufs, int64_t nblk, int splits, float *__restrict__ part,
+                       size_t np, const GOff off, unsigned *__restrict__ err)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int t = threadIdx.x;
@@ -801,7 +801,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
         }
     } else {
         // ---- epilogue: warp w reads accumulator rows 32 (w % 4) .. + 31 (one
-        // output feature each) and adds them to the gradient
+        // output feature each) and stores them as this split's partial
+        // gradient (the parameter layout, one copy per split)
         const int quarter = warp & 3;
         const int m = m0 + 32 * quarter + lane;
         const bool live = m < Fo;
@@ -811,7 +812,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
                 ok = false;
             } else {
                 fence_after();
-                float *gw = g + off.w[l] + (size_t)m * Fi;
+                float *pg = part + (size_t)split * np;
+                float *gw = pg + off.w[l] + (size_t)m * Fi;
                 if (Fi == kHidden) {
 #pragma unroll 1
                     for (int c = 0; c < kHidden / 32; ++c) {
@@ -820,11 +822,11 @@ __global__ void __launch_bounds__(kGThreads, 1)
                         if (live) {
 #pragma unroll
                             for (int i = 0; i < 8; ++i)
-                                atomicAdd(reinterpret_cast<float4 *>(gw + 32 * c + 4 * i),
-                                          make_float4(__uint_as_float(v[4 * i]),
-                                                      __uint_as_float(v[4 * i + 1]),
-                                                      __uint_as_float(v[4 * i + 2]),
-                                                      __uint_as_float(v[4 * i + 3])));
+                                *reinterpret_cast<float4 *>(gw + 32 * c + 4 * i) =
+                                    make_float4(__uint_as_float(v[4 * i]),
+                                                __uint_as_float(v[4 * i + 1]),
+                                                __uint_as_float(v[4 * i + 2]),
+                                                __uint_as_float(v[4 * i + 3]));
                         }
                     }
                 } else {
@@ -835,18 +837,18 @@ __global__ void __launch_bounds__(kGThreads, 1)
                         if (live) {
 #pragma unroll
                             for (int i = 0; i < 2; ++i)
-                                atomicAdd(reinterpret_cast<float4 *>(gw + 8 * c + 4 * i),
-                                          make_float4(__uint_as_float(v[4 * i]),
-                                                      __uint_as_float(v[4 * i + 1]),
-                                                      __uint_as_float(v[4 * i + 2]),
-                                                      __uint_as_float(v[4 * i + 3])));
+                                *reinterpret_cast<float4 *>(gw + 8 * c + 4 * i) =
+                                    make_float4(__uint_as_float(v[4 * i]),
+                                                __uint_as_float(v[4 * i + 1]),
+                                                __uint_as_float(v[4 * i + 2]),
+                                                __uint_as_float(v[4 * i + 3]));
                         }
                     }
                 }
                 uint32_t vb[8];
                 tmem_ld8(acc_row + 256, vb);
                 if (live)
-                    atomicAdd(g + off.b[l] + m, __uint_as_float(vb[0]));
+                    pg[off.b[l] + m] = __uint_as_float(vb[0]);
             }
         }
         if (!ok)
@@ -871,42 +873,91 @@ __global__ void __launch_bounds__(kGThreads, 1)
 // ===========================================================================
 namespace {
 
-// Adam on the whole parameter vector with the step's learning rate and bias
-// corrections; writes every bf16 copy of the weights (row-major [out][in],
-// transposed [in][out] at the same offset, packed training operands) and
-// zeroes the gradient for the next step.
-__global__ void train_adam_kernel(float *__restrict__ w, float *__restrict__ g,
-                                  float *__restrict__ m, float *__restrict__ v,
-                                  bf16 *__restrict__ wbf, bf16 *__restrict__ wbfT,
-                                  bf16 *__restrict__ wtp, const WOff o, int64_t n,
-                                  const StepCtl *__restrict__ ctl, float b1, float b2, float eps)
+// Sum of the splits' partial gradients of eight consecutive parameters.
+__device__ __forceinline__ void sum_parts(const float *__restrict__ part, int splits, size_t np,
+                                          size_t i, float gs[8])
+{
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        gs[j] = 0.0f;
+    for (int s = 0; s < splits; ++s) {
+        const float4 a = *reinterpret_cast<const float4 *>(part + (size_t)s * np + i);
+        const float4 b = *reinterpret_cast<const float4 *>(part + (size_t)s * np + i + 4);
+        gs[0] += a.x, gs[1] += a.y, gs[2] += a.z, gs[3] += a.w;
+        gs[4] += b.x, gs[5] += b.y, gs[6] += b.z, gs[7] += b.w;
+    }
+}
+
+// g = the sum of the partial gradients (eight parameters per thread).
+__global__ void train_reduce_kernel(const float *__restrict__ part, int splits, size_t np,
+                                    float *__restrict__ g)
+{
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < np / 8;
+         c += (size_t)gridDim.x * blockDim.x) {
+        float gs[8];
+        sum_parts(part, splits, np, 8 * c, gs);
+        reinterpret_cast<float4 *>(g + 8 * c)[0] = make_float4(gs[0], gs[1], gs[2], gs[3]);
+        reinterpret_cast<float4 *>(g + 8 * c)[1] = make_float4(gs[4], gs[5], gs[6], gs[7]);
+    }
+}
+
+// Adam with the step's learning rate and bias corrections, eight
+// consecutive parameters per thread (a weight row segment or biases: every
+// layer's offsets and widths are multiples of 8): the gradient is the sum of
+// the partials, then w, m, v, the bf16 copy [out][in] and the packed forward
+// operand (one 16-byte store each) and the packed backward operand (eight
+// 2-byte stores) are written.
+__global__ void train_adam_kernel(float *__restrict__ w, const float *__restrict__ part,
+                                  int splits, float *__restrict__ m, float *__restrict__ v,
+                                  bf16 *__restrict__ wbf, bf16 *__restrict__ wtp, const WOff o,
+                                  size_t np, const StepCtl *__restrict__ ctl, float b1, float b2,
+                                  float eps)
 {
     const float lr = ctl->lr, c1 = ctl->c1, c2 = ctl->c2;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        g[i] = 0.0f;
-        const float mi = b1 * m[i] + (1.0f - b1) * gi;
-        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        const float wi = w[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
-        w[i] = wi;
-        const bf16 wb = __float2bfloat16(wi);
-        wbf[i] = wb;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < np / 8;
+         c += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = 8 * c;
+        float gs[8], wv[8], mv[8], vv[8];
+        sum_parts(part, splits, np, i, gs);
+        *reinterpret_cast<float4 *>(wv) = reinterpret_cast<const float4 *>(w + i)[0];
+        *reinterpret_cast<float4 *>(wv + 4) = reinterpret_cast<const float4 *>(w + i)[1];
+        *reinterpret_cast<float4 *>(mv) = reinterpret_cast<const float4 *>(m + i)[0];
+        *reinterpret_cast<float4 *>(mv + 4) = reinterpret_cast<const float4 *>(m + i)[1];
+        *reinterpret_cast<float4 *>(vv) = reinterpret_cast<const float4 *>(v + i)[0];
+        *reinterpret_cast<float4 *>(vv + 4) = reinterpret_cast<const float4 *>(v + i)[1];
+        uint32_t wb[4];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            mv[j] = b1 * mv[j] + (1.0f - b1) * gs[j];
+            vv[j] = b2 * vv[j] + (1.0f - b2) * gs[j] * gs[j];
+            wv[j] = wv[j] - lr * (mv[j] * c1) / (sqrtf(vv[j] * c2) + eps);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            wb[j] = pack_bf16(wv[2 * j], wv[2 * j + 1]);
+        reinterpret_cast<float4 *>(w + i)[0] = *reinterpret_cast<const float4 *>(wv);
+        reinterpret_cast<float4 *>(w + i)[1] = *reinterpret_cast<const float4 *>(wv + 4);
+        reinterpret_cast<float4 *>(m + i)[0] = *reinterpret_cast<const float4 *>(mv);
+        reinterpret_cast<float4 *>(m + i)[1] = *reinterpret_cast<const float4 *>(mv + 4);
+        reinterpret_cast<float4 *>(v + i)[0] = *reinterpret_cast<const float4 *>(vv);
+        reinterpret_cast<float4 *>(v + i)[1] = *reinterpret_cast<const float4 *>(vv + 4);
+        const uint4 wq = make_uint4(wb[0], wb[1], wb[2], wb[3]);
+        *reinterpret_cast<uint4 *>(wbf + i) = wq;
         int l = 0;
-        while (l + 1 < kLayers && (size_t)i >= o.w[l + 1])
+        while (l + 1 < kLayers && i >= o.w[l + 1])
             ++l;
-        const int64_t j = i - (int64_t)o.w[l];
+        const size_t j = i - o.w[l];
         const int K = in_dim(l), N = out_dim(l);
-        if (j < (int64_t)N * K) {                               // weights, not biases
-            const int oo = (int)(j / K), k = (int)(j % K);
-            wbfT[o.w[l] + (size_t)k * N + oo] = wb;
+        if (j < (size_t)N * K) {                                // weights, not biases
+            const int oo = (int)(j / K), k = (int)(j % K);      // k .. k + 7 in row oo
             if (l == 0) {
-                wtp[cm(oo, k, kInPad)] = wb;
+                *reinterpret_cast<uint4 *>(wtp + cm(oo, k, kInPad)) = wq;
             } else {
-                wtp[fwd_off(l, k / KS) + cm(oo, k % KS, KS)] = wb;
-                wtp[bwd_off(l, oo / KS) + cm(k, oo % KS, KS)] = wb;
+                *reinterpret_cast<uint4 *>(wtp + fwd_off(l, k / KS) + cm(oo, k % KS, KS)) = wq;
+                uint16_t *bw = reinterpret_cast<uint16_t *>(wtp + bwd_off(l, oo / KS));
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj)
+                    bw[cm(k + jj, oo % KS, KS)] = (uint16_t)(wb[jj >> 1] >> (16 * (jj & 1)));
             }
         }
     }
@@ -943,41 +994,58 @@ cudaError_t train_chain(const float *in, const float *tgt, const float *msk, int
     return cudaGetLastError();
 }
 
-cudaError_t train_grads(TrainBufs b, int64_t rows, float *g, const size_t woff[kLayers],
-                        const size_t boff[kLayers], unsigned *err, int sms, cudaStream_t s)
+int train_splits(int64_t rows, int sms)
 {
-    if (rows <= 0)
-        return cudaSuccess;
-    if (rows > b.cap || (b.cap % TM) != 0)
-        return cudaErrorInvalidValue;
     const int64_t nblk = 2 * ((rows + TM - 1) / TM);       // 64-row blocks of the batch
     int64_t splits = sms / kGTiles;
     if (splits > kGMaxSplits)
         splits = kGMaxSplits;
     if (splits > nblk)
         splits = nblk;
-    if (splits < 1)
-        splits = 1;
+    return (int)(splits < 1 ? 1 : splits);
+}
+
+size_t train_part_elems(size_t np) { return (size_t)kGMaxSplits * np; }
+
+cudaError_t train_grads(TrainBufs b, int64_t rows, float *part, size_t np,
+                        const size_t woff[kLayers], const size_t boff[kLayers], unsigned *err,
+                        int sms, cudaStream_t s)
+{
+    if (rows <= 0)
+        return cudaSuccess;
+    if (rows > b.cap || (b.cap % TM) != 0 || (np % 8) != 0)
+        return cudaErrorInvalidValue;
+    const int64_t nblk = 2 * ((rows + TM - 1) / TM);
+    const int splits = train_splits(rows, sms);
     GOff o;
     for (int l = 0; l < kLayers; ++l) {
         o.w[l] = woff[l];
         o.b[l] = boff[l];
     }
-    train_grads_kernel<<<kGTiles * (int)splits, kGThreads, G_TOTAL, s>>>(b, nblk, (int)splits, g,
-                                                                         o, err);
+    train_grads_kernel<<<kGTiles * splits, kGThreads, G_TOTAL, s>>>(b, nblk, splits, part, np, o,
+                                                                    err);
     return cudaGetLastError();
 }
 
-cudaError_t train_adam(float *w, float *g, float *m, float *v, bf16 *wbf, bf16 *wbfT, bf16 *wtp,
-                       const size_t woff[kLayers], size_t n, const StepCtl *ctl, float b1,
-                       float b2, float eps, cudaStream_t s)
+cudaError_t train_reduce(const float *part, int splits, size_t np, float *g, cudaStream_t s)
 {
+    const int64_t blocks = ((int64_t)np / 8 + 255) / 256;
+    train_reduce_kernel<<<(int)blocks, 256, 0, s>>>(part, splits, np, g);
+    return cudaGetLastError();
+}
+
+cudaError_t train_adam(float *w, const float *part, int splits, float *m, float *v, bf16 *wbf,
+                       bf16 *wtp, const size_t woff[kLayers], size_t np, const StepCtl *ctl,
+                       float b1, float b2, float eps, cudaStream_t s)
+{
+    if ((np % 8) != 0)
+        return cudaErrorInvalidValue;
     WOff o;
     for (int l = 0; l < kLayers; ++l)
         o.w[l] = woff[l];
-    const int64_t blocks = ((int64_t)n + 255) / 256;
-    train_adam_kernel<<<(int)(blocks < 2432 ? blocks : 2432), 256, 0, s>>>(
-        w, g, m, v, wbf, wbfT, wtp, o, (int64_t)n, ctl, b1, b2, eps);
+    const int64_t blocks = ((int64_t)np / 8 + 255) / 256;
+    train_adam_kernel<<<(int)blocks, 256, 0, s>>>(w, part, splits, m, v, wbf, wtp, o, np, ctl, b1,
+                                                  b2, eps);
     return cudaGetLastError();
 }
 
