@@ -14,12 +14,14 @@
 //
 // train_grads_kernel: dW_l = D_l^T A_l and db_l = D_l^T 1 contracted over the
 // batch: one CTA per (layer, 128 output features, batch split), the
-// transposed operands streamed in 64-row blocks, partial sums added to the
-// gradient with vector atomics.  The bias gradient is one more MMA per
-// K-step against a ones operand, i.e. the column sum of the bf16 gradient.
+// transposed operands streamed in 64-row blocks, each split's partial sums
+// stored as a full copy of the gradient (no atomics).  The bias gradient is
+// one more MMA per K-step against a ones operand, i.e. the column sum of the
+// bf16 gradient.
 //
-// train_adam_kernel: Adam on every parameter, then every bf16 copy of the
-// weights (row-major, transposed, and the packed operands of the chain).
+// train_adam_kernel: sums the splits' partials in split order (so the
+// gradient is deterministic), applies Adam to every parameter and writes the
+// row-major bf16 weights and the packed operands of the chain.
 //
 // Arithmetic as the layer-by-layer GEMM path: bf16 operands, fp32
 // accumulation, bias and SiLU in fp32 (hardware exp2 and reciprocal
@@ -653,7 +655,7 @@ constexpr uint32_t G_BAR = G_ONES + 16 * KS * 2;
 constexpr int kGBars = 2 * kGStages + 2;
 constexpr uint32_t G_TOTAL = G_BAR + kGBars * 8 + 8 + 8;
 static_assert(G_TOTAL <= 227 * 1024, "shared memory of the gradient kernel");
-constexpr int kGThreads = 64 + 128;       // producer warp, MMA warp, 4 epilogue warps
+constexpr int kGThreads = 64 + 256;       // producer warp, MMA warp, 8 epilogue warps
 constexpr int kGTiles = 9;                // (layer, 128 output features) tiles
 constexpr int kGMaxSplits = 16;
 
@@ -741,11 +743,12 @@ __global__ void __launch_bounds__(kGThreads, 1)
     bool ok = true;
 
     if (warp == 0) {
-        // ---- producer: lane 2 s copies stage s's A block, lane 2 s + 1 its
-        // B block (separate threads, so that the copies overlap)
-        if (lane < 2 * kGStages) {
-            const int s = lane >> 1;
-            const bool is_a = (lane & 1) == 0;
+        // ---- producer: lane 3 s copies stage s's A block, lanes 3 s + 1 and
+        // 3 s + 2 the two halves of its B block (separate threads, so that the
+        // copies overlap)
+        if (lane < 3 * kGStages) {
+            const int s = lane / 3, part_i = lane % 3;
+            const uint32_t bhalf = bbytes >= 2 * 16384 ? bbytes / 2 : bbytes;
             uint32_t issued = 0;
             for (int i = s; i < nk && ok; i += kGStages) {
                 const uint32_t use = (uint32_t)(i / kGStages);
@@ -755,13 +758,17 @@ __global__ void __launch_bounds__(kGThreads, 1)
                 }
                 const int64_t kb = kb0 + i;
                 const uint32_t dst = s_stage + s * G_STAGE;
-                if (is_a) {
+                if (part_i == 0) {
                     mbar_expect_tx(bar(B_FULL + s), abytes + bbytes);
                     bulk_load(dst, A + (size_t)kb * Fo * KS, abytes, bar(B_FULL + s));
-                } else {
-                    bulk_load(dst + G_ABYTES, B + (size_t)kb * Fi * KS, bbytes, bar(B_FULL + s));
+                    issued = use + 1;
+                } else if (part_i == 1 || bhalf < bbytes) {
+                    const uint32_t o = (uint32_t)(part_i - 1) * bhalf;
+                    bulk_load(dst + G_ABYTES + o,
+                              reinterpret_cast<const uint8_t *>(B + (size_t)kb * Fi * KS) + o,
+                              bhalf, bar(B_FULL + s));
+                    issued = use + 1;
                 }
-                issued = use + 1;
             }
             if (!ok)
                 *abort_flag = 1;
@@ -800,55 +807,56 @@ __global__ void __launch_bounds__(kGThreads, 1)
             mbar_wait(bar(B_FIN), 0);
         }
     } else {
-        // ---- epilogue: warp w reads accumulator rows 32 (w % 4) .. + 31 (one
-        // output feature each) and stores them as this split's partial
-        // gradient (the parameter layout, one copy per split)
+        // ---- epilogue: eight warps; warp w reads accumulator rows
+        // 32 (w % 4) .. + 31 (one output feature each) in one column half and
+        // stores them as this split's partial gradient (the parameter layout,
+        // one copy per split).  Each 32 x 32 block goes through a per-warp
+        // tile in the idle stage buffers, so that every store instruction
+        // writes 32 consecutive floats of one row.
         const int quarter = warp & 3;
-        const int m = m0 + 32 * quarter + lane;
-        const bool live = m < Fo;
+        const int half = (warp - 2) >> 2;
+        const int mrow0 = m0 + 32 * quarter;            // first output feature of the warp
         const uint32_t acc_row = tmem + ((uint32_t)(32 * quarter) << 16);
+        float *tile = reinterpret_cast<float *>(smem) + (warp - 2) * (32 * 33);
         if (nk > 0) {
             if (!wait_or_abort(bar(B_ACC), 0, abort_flag)) {
                 ok = false;
             } else {
                 fence_after();
                 float *pg = part + (size_t)split * np;
-                float *gw = pg + off.w[l] + (size_t)m * Fi;
-                if (Fi == kHidden) {
+                const int ncol = Fi == kHidden ? kHidden / 2 : kInPad;   // this warp's columns
+                const int c0 = Fi == kHidden ? half * (kHidden / 2) : 0;
+                if (Fi == kHidden || half == 0) {
 #pragma unroll 1
-                    for (int c = 0; c < kHidden / 32; ++c) {
+                    for (int c = c0; c < c0 + ncol; c += 32) {
+                        const int w = min(32, ncol);
                         uint32_t v[32];
-                        tmem_ld32(acc_row + 32 * c, v);
-                        if (live) {
-#pragma unroll
-                            for (int i = 0; i < 8; ++i)
-                                *reinterpret_cast<float4 *>(gw + 32 * c + 4 * i) =
-                                    make_float4(__uint_as_float(v[4 * i]),
-                                                __uint_as_float(v[4 * i + 1]),
-                                                __uint_as_float(v[4 * i + 2]),
-                                                __uint_as_float(v[4 * i + 3]));
+                        if (w == 32) {
+                            tmem_ld32(acc_row + c, v);
+                        } else {
+                            tmem_ld8(acc_row + c, v);
+                            tmem_ld8(acc_row + c + 8, v + 8);
                         }
-                    }
-                } else {
-#pragma unroll 1
-                    for (int c = 0; c < kInPad / 8; ++c) {
-                        uint32_t v[8];
-                        tmem_ld8(acc_row + 8 * c, v);
-                        if (live) {
 #pragma unroll
-                            for (int i = 0; i < 2; ++i)
-                                *reinterpret_cast<float4 *>(gw + 8 * c + 4 * i) =
-                                    make_float4(__uint_as_float(v[4 * i]),
-                                                __uint_as_float(v[4 * i + 1]),
-                                                __uint_as_float(v[4 * i + 2]),
-                                                __uint_as_float(v[4 * i + 3]));
+                        for (int j = 0; j < 32; ++j)
+                            if (j < w)
+                                tile[lane * 33 + j] = __uint_as_float(v[j]);
+                        __syncwarp();
+#pragma unroll 4
+                        for (int rr = 0; rr < 32; ++rr) {
+                            const int m = mrow0 + rr;
+                            if (m < Fo && lane < w)
+                                pg[off.w[l] + (size_t)m * Fi + c + lane] = tile[rr * 33 + lane];
                         }
+                        __syncwarp();
                     }
                 }
-                uint32_t vb[8];
-                tmem_ld8(acc_row + 256, vb);
-                if (live)
-                    pg[off.b[l] + m] = __uint_as_float(vb[0]);
+                if (half == 0) {
+                    uint32_t vb[8];
+                    tmem_ld8(acc_row + 256, vb);
+                    if (mrow0 + lane < Fo)
+                        pg[off.b[l] + mrow0 + lane] = __uint_as_float(vb[0]);
+                }
             }
         }
         if (!ok)
@@ -880,6 +888,7 @@ __device__ __forceinline__ void sum_parts(const float *__restrict__ part, int sp
 #pragma unroll
     for (int j = 0; j < 8; ++j)
         gs[j] = 0.0f;
+#pragma unroll 4
     for (int s = 0; s < splits; ++s) {
         const float4 a = *reinterpret_cast<const float4 *>(part + (size_t)s * np + i);
         const float4 b = *reinterpret_cast<const float4 *>(part + (size_t)s * np + i + 4);
