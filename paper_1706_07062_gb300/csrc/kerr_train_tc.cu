@@ -178,7 +178,9 @@ constexpr uint32_t C_TOTAL = C_BAR + kCBars * 8 + 8 + 8;
 static_assert(C_TOTAL <= 227 * 1024, "shared memory of the chain kernel");
 static_assert(C_SLOT % 1024 == 0 && C_W0 % 16 == 0 && C_BIAS % 16 == 0 && C_BAR % 8 == 0,
               "bulk-copy, vector-load and mbarrier alignment");
-constexpr int kCThreads = 64 + 512;       // producer warp, MMA warp, 16 epilogue warps
+constexpr int kCMmaWarp = 1;              // warp 0: producer lanes 0-3 (one per slot)
+constexpr int kCEpiWarp0 = 2;             // warps 2-17: epilogue
+constexpr int kCThreads = 32 * kCEpiWarp0 + 512;
 constexpr int kCEpi = 512;
 
 struct Biases {
@@ -348,44 +350,47 @@ __global__ void __launch_bounds__(kCThreads, 1)
     bool ok = true;
 
     if (warp == 0) {
-        // ---- producer: lane p streams the slices that go through slot p
-        // (bulk copies of one thread complete one after another, those of
-        // different threads overlap); W0 once, from lane 0
-        if (lane < kCSlots) {
-            const int p = lane;
-            if (p == 0) {
-                mbar_expect_tx(bar(B_W0), kHidden * kInPad * 2);
-                bulk_load(s_w0, wtp, kHidden * kInPad * 2, bar(B_W0));
-            }
-            uint32_t k = 0, issued = 0;
-            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-                for (int i = 0; i < kChainSlices; ++i, ++k) {
-                    if (k % kCSlots != (uint32_t)p)
-                        continue;
-                    const uint32_t use = k / kCSlots;
-                    if (use >= 1 &&
-                        !wait_or_abort(bar(B_EMPTY + p), (use - 1) & 1, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    size_t off;
-                    uint32_t bytes;
-                    chain_slice(i, off, bytes);
-                    mbar_expect_tx(bar(B_FULL + p), bytes);
-                    bulk_load(s_slot + p * kSlotBytes, wtp + off, bytes, bar(B_FULL + p));
-                    issued = use + 1;
-                }
-            }
-            if (!ok)
-                *abort_flag = 1;
-            // the copies issued have landed before the CTA can exit (already
-            // true unless a wait gave up)
-            if (issued > 0)
-                mbar_wait(bar(B_FULL + p), (issued - 1) & 1);
-            if (p == 0)
-                mbar_wait(bar(B_W0), 0);
+        // ---- producer: lane p issues the copies of the slices that go
+        // through slot p (bulk copies of one thread complete one after
+        // another, those of different threads overlap).  The lanes walk the
+        // slices together in the MMA's order: at slice k only lane k % 4 waits
+        // (for the slot's previous slice, which the MMAs free in order) and
+        // issues, so no lane ever waits on a later slice while an earlier
+        // one is still to be issued.  W0 once, from lane 0.
+        const int p = lane;
+        if (p == 0) {
+            mbar_expect_tx(bar(B_W0), kHidden * kInPad * 2);
+            bulk_load(s_w0, wtp, kHidden * kInPad * 2, bar(B_W0));
         }
-    } else if (warp == 1) {
+        uint32_t k = 0, issued = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            for (int i = 0; i < kChainSlices && ok; ++i, ++k) {
+                const int owner = (int)(k % kCSlots);
+                if (p == owner) {
+                    const uint32_t use = k / kCSlots;
+                    if (use >= 1 && !wait_or_abort(bar(B_EMPTY + p), (use - 1) & 1, abort_flag)) {
+                        ok = false;
+                    } else {
+                        size_t off;
+                        uint32_t bytes;
+                        chain_slice(i, off, bytes);
+                        mbar_expect_tx(bar(B_FULL + p), bytes);
+                        bulk_load(s_slot + p * kSlotBytes, wtp + off, bytes, bar(B_FULL + p));
+                        issued = use + 1;
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, owner) != 0;
+            }
+        }
+        if (!ok && lane == 0)
+            *abort_flag = 1;
+        // the copies issued have landed before the CTA can exit (already
+        // true unless a wait gave up)
+        if (p < kCSlots && issued > 0)
+            mbar_wait(bar(B_FULL + p), (issued - 1) & 1);
+        if (p == 0)
+            mbar_wait(bar(B_W0), 0);
+    } else if (warp == kCMmaWarp) {
         // ---- MMA issuer: per tile F0 (one MMA against the resident W0), then
         // F1-F3, F4, B4, B3-B1 on the streamed slices
         if (lane == 0) {
@@ -438,8 +443,8 @@ __global__ void __launch_bounds__(kCThreads, 1)
     } else {
         // ---- epilogue: sixteen warps; the four warps of a TMEM lane quarter
         // take 64 of the 256 columns each (two 32-column chunks)
-        const int ew = warp - 2;
-        const int et = t - 64;                          // 0 .. 511
+        const int ew = warp - kCEpiWarp0;
+        const int et = t - 32 * kCEpiWarp0;             // 0 .. 511
         const int quarter = warp & 3;
         const int colq = ew >> 2;
         const int row = 32 * quarter + lane;            // accumulator row of this thread
@@ -492,6 +497,9 @@ __global__ void __launch_bounds__(kCThreads, 1)
                         const float4 b0 = *reinterpret_cast<const float4 *>(bl + f0);
                         const float4 b1 = *reinterpret_cast<const float4 *>(bl + f0 + 4);
                         const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                        // z = acc + b, sigma = 1 / (1 + 2^(-z log2 e)), h = z sigma,
+                        // silu'(z) = sigma (1 + z (1 - sigma)); scalar (the f32x2 pair
+                        // form was slower here)
                         float h[8], sp[8];
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
@@ -881,41 +889,44 @@ __global__ void __launch_bounds__(kGThreads, 1)
 // ===========================================================================
 namespace {
 
-// Sum of the splits' partial gradients of eight consecutive parameters.
-__device__ __forceinline__ void sum_parts(const float *__restrict__ part, int splits, size_t np,
-                                          size_t i, float gs[8])
+// Sum of the splits' partial gradients of four consecutive parameters: every
+// split's load is issued before the additions (splits <= kGMaxSplits), so a
+// thread keeps up to sixteen 16-byte loads in flight.
+__device__ __forceinline__ float4 sum_parts(const float *__restrict__ part, int splits,
+                                            size_t np, size_t i)
 {
+    float4 a[kGMaxSplits];
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-        gs[j] = 0.0f;
-#pragma unroll 4
-    for (int s = 0; s < splits; ++s) {
-        const float4 a = *reinterpret_cast<const float4 *>(part + (size_t)s * np + i);
-        const float4 b = *reinterpret_cast<const float4 *>(part + (size_t)s * np + i + 4);
-        gs[0] += a.x, gs[1] += a.y, gs[2] += a.z, gs[3] += a.w;
-        gs[4] += b.x, gs[5] += b.y, gs[6] += b.z, gs[7] += b.w;
-    }
+    for (int s = 0; s < kGMaxSplits; ++s)
+        if (s < splits)
+            a[s] = *reinterpret_cast<const float4 *>(part + (size_t)s * np + i);
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int s = 0; s < kGMaxSplits; ++s)
+        if (s < splits) {
+            g.x += a[s].x;
+            g.y += a[s].y;
+            g.z += a[s].z;
+            g.w += a[s].w;
+        }
+    return g;
 }
 
-// g = the sum of the partial gradients (eight parameters per thread).
+// g = the sum of the partial gradients (four parameters per thread).
 __global__ void train_reduce_kernel(const float *__restrict__ part, int splits, size_t np,
                                     float *__restrict__ g)
 {
-    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < np / 8;
-         c += (size_t)gridDim.x * blockDim.x) {
-        float gs[8];
-        sum_parts(part, splits, np, 8 * c, gs);
-        reinterpret_cast<float4 *>(g + 8 * c)[0] = make_float4(gs[0], gs[1], gs[2], gs[3]);
-        reinterpret_cast<float4 *>(g + 8 * c)[1] = make_float4(gs[4], gs[5], gs[6], gs[7]);
-    }
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < np / 4;
+         c += (size_t)gridDim.x * blockDim.x)
+        *reinterpret_cast<float4 *>(g + 4 * c) = sum_parts(part, splits, np, 4 * c);
 }
 
-// Adam with the step's learning rate and bias corrections, eight
-// consecutive parameters per thread (a weight row segment or biases: every
-// layer's offsets and widths are multiples of 8): the gradient is the sum of
-// the partials, then w, m, v, the bf16 copy [out][in] and the packed forward
-// operand (one 16-byte store each) and the packed backward operand (eight
-// 2-byte stores) are written.
+// Adam with the step's learning rate and bias corrections, four consecutive
+// parameters per thread (a weight row segment or biases: every layer's
+// offsets and widths are multiples of 8): the gradient is the sum of the
+// partials, then w, m, v, the bf16 copy [out][in] and the packed forward
+// operand (one 16- or 8-byte store each) and the packed backward operand
+// (four 2-byte stores) are written.
 __global__ void train_adam_kernel(float *__restrict__ w, const float *__restrict__ part,
                                   int splits, float *__restrict__ m, float *__restrict__ v,
                                   bf16 *__restrict__ wbf, bf16 *__restrict__ wtp, const WOff o,
@@ -923,49 +934,41 @@ __global__ void train_adam_kernel(float *__restrict__ w, const float *__restrict
                                   float eps)
 {
     const float lr = ctl->lr, c1 = ctl->c1, c2 = ctl->c2;
-    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < np / 8;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < np / 4;
          c += (size_t)gridDim.x * blockDim.x) {
-        const size_t i = 8 * c;
-        float gs[8], wv[8], mv[8], vv[8];
-        sum_parts(part, splits, np, i, gs);
-        *reinterpret_cast<float4 *>(wv) = reinterpret_cast<const float4 *>(w + i)[0];
-        *reinterpret_cast<float4 *>(wv + 4) = reinterpret_cast<const float4 *>(w + i)[1];
-        *reinterpret_cast<float4 *>(mv) = reinterpret_cast<const float4 *>(m + i)[0];
-        *reinterpret_cast<float4 *>(mv + 4) = reinterpret_cast<const float4 *>(m + i)[1];
-        *reinterpret_cast<float4 *>(vv) = reinterpret_cast<const float4 *>(v + i)[0];
-        *reinterpret_cast<float4 *>(vv + 4) = reinterpret_cast<const float4 *>(v + i)[1];
-        uint32_t wb[4];
+        const size_t i = 4 * c;
+        const float4 w4 = *reinterpret_cast<const float4 *>(w + i);
+        const float4 m4 = *reinterpret_cast<const float4 *>(m + i);
+        const float4 v4 = *reinterpret_cast<const float4 *>(v + i);
+        const float4 g4 = sum_parts(part, splits, np, i);
+        float gs[4] = {g4.x, g4.y, g4.z, g4.w}, wv[4] = {w4.x, w4.y, w4.z, w4.w},
+              mv[4] = {m4.x, m4.y, m4.z, m4.w}, vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 4; ++j) {
             mv[j] = b1 * mv[j] + (1.0f - b1) * gs[j];
             vv[j] = b2 * vv[j] + (1.0f - b2) * gs[j] * gs[j];
             wv[j] = wv[j] - lr * (mv[j] * c1) / (sqrtf(vv[j] * c2) + eps);
         }
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            wb[j] = pack_bf16(wv[2 * j], wv[2 * j + 1]);
-        reinterpret_cast<float4 *>(w + i)[0] = *reinterpret_cast<const float4 *>(wv);
-        reinterpret_cast<float4 *>(w + i)[1] = *reinterpret_cast<const float4 *>(wv + 4);
-        reinterpret_cast<float4 *>(m + i)[0] = *reinterpret_cast<const float4 *>(mv);
-        reinterpret_cast<float4 *>(m + i)[1] = *reinterpret_cast<const float4 *>(mv + 4);
-        reinterpret_cast<float4 *>(v + i)[0] = *reinterpret_cast<const float4 *>(vv);
-        reinterpret_cast<float4 *>(v + i)[1] = *reinterpret_cast<const float4 *>(vv + 4);
-        const uint4 wq = make_uint4(wb[0], wb[1], wb[2], wb[3]);
-        *reinterpret_cast<uint4 *>(wbf + i) = wq;
+        *reinterpret_cast<float4 *>(w + i) = make_float4(wv[0], wv[1], wv[2], wv[3]);
+        *reinterpret_cast<float4 *>(m + i) = make_float4(mv[0], mv[1], mv[2], mv[3]);
+        *reinterpret_cast<float4 *>(v + i) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+        const uint32_t wb[2] = {pack_bf16(wv[0], wv[1]), pack_bf16(wv[2], wv[3])};
+        const uint2 wq = make_uint2(wb[0], wb[1]);
+        *reinterpret_cast<uint2 *>(wbf + i) = wq;
         int l = 0;
         while (l + 1 < kLayers && i >= o.w[l + 1])
             ++l;
         const size_t j = i - o.w[l];
         const int K = in_dim(l), N = out_dim(l);
         if (j < (size_t)N * K) {                                // weights, not biases
-            const int oo = (int)(j / K), k = (int)(j % K);      // k .. k + 7 in row oo
+            const int oo = (int)(j / K), k = (int)(j % K);      // k .. k + 3 in row oo
             if (l == 0) {
-                *reinterpret_cast<uint4 *>(wtp + cm(oo, k, kInPad)) = wq;
+                *reinterpret_cast<uint2 *>(wtp + cm(oo, k, kInPad)) = wq;
             } else {
-                *reinterpret_cast<uint4 *>(wtp + fwd_off(l, k / KS) + cm(oo, k % KS, KS)) = wq;
+                *reinterpret_cast<uint2 *>(wtp + fwd_off(l, k / KS) + cm(oo, k % KS, KS)) = wq;
                 uint16_t *bw = reinterpret_cast<uint16_t *>(wtp + bwd_off(l, oo / KS));
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj)
+                for (int jj = 0; jj < 4; ++jj)
                     bw[cm(k + jj, oo % KS, KS)] = (uint16_t)(wb[jj >> 1] >> (16 * (jj & 1)));
             }
         }
@@ -1038,7 +1041,9 @@ cudaError_t train_grads(TrainBufs b, int64_t rows, float *part, size_t np,
 
 cudaError_t train_reduce(const float *part, int splits, size_t np, float *g, cudaStream_t s)
 {
-    const int64_t blocks = ((int64_t)np / 8 + 255) / 256;
+    if ((np % 8) != 0 || splits < 1 || splits > kGMaxSplits)
+        return cudaErrorInvalidValue;
+    const int64_t blocks = ((int64_t)np / 4 + 255) / 256;
     train_reduce_kernel<<<(int)blocks, 256, 0, s>>>(part, splits, np, g);
     return cudaGetLastError();
 }
@@ -1047,12 +1052,12 @@ cudaError_t train_adam(float *w, const float *part, int splits, float *m, float 
                        bf16 *wtp, const size_t woff[kLayers], size_t np, const StepCtl *ctl,
                        float b1, float b2, float eps, cudaStream_t s)
 {
-    if ((np % 8) != 0)
+    if ((np % 8) != 0 || splits < 1 || splits > kGMaxSplits)
         return cudaErrorInvalidValue;
     WOff o;
     for (int l = 0; l < kLayers; ++l)
         o.w[l] = woff[l];
-    const int64_t blocks = ((int64_t)np / 8 + 255) / 256;
+    const int64_t blocks = ((int64_t)np / 4 + 255) / 256;
     train_adam_kernel<<<(int)blocks, 256, 0, s>>>(w, part, splits, m, v, wbf, wtp, o, np, ctl, b1,
                                                   b2, eps);
     return cudaGetLastError();
