@@ -118,9 +118,11 @@ typedef struct {
                            /* zone: KERR_ZONE_FP64 or KERR_ZONE_F32X2            */
     int32_t zone_variant;  /* launch shape of the zone phase: -1 = default, else */
                            /* an index < kerr_num_zone_variants()                */
-    int32_t zone_quantum;  /* FP32 path, zone phase: after this many attempts a  */
-                           /* geodesic gives its lane to one that waits for a    */
-                           /* lane and goes to the back of the queue (processor  */
+    int32_t zone_quantum;  /* FP32 path, zone phase: every this many iterations */
+                           /* of a warp (staggered over the warps), geodesics    */
+                           /* that took at least half as many attempts since     */
+                           /* they got their lane give it to ones that wait for  */
+                           /* a lane and go to the back of the queue (processor  */
                            /* sharing; results do not depend on it); 0 = each    */
                            /* geodesic keeps its lane to the end; >= 0           */
 } kerr_opts;
@@ -172,8 +174,7 @@ typedef struct {
 /* Fills *opts with: prec FP32_KAHAN, tol 1e-6, h0 1, max_steps 1e6,
  * r_escape 0, t_end +inf, fp64_zone 1.5, renorm_every 0, clip_maxit 40,
  * variant -1, budget_ns 0, zone_prec KERR_ZONE_FP64, zone_variant -1,
- * zone_quantum 48 (measured best of 24..96 on the 1024x1024 image and the
- * 64-image batch). */
+ * zone_quantum 32 (measured best of 8..64 on the 1024x1024 image). */
 void kerr_opts_default(kerr_opts *opts);
 
 /* Creates a context for black-hole spin a (|a| <= 1, else KERR_EINVAL) on the

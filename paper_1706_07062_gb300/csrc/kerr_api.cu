@@ -116,7 +116,7 @@ extern "C" void kerr_opts_default(kerr_opts *o)
     o->budget_ns = 0;
     o->zone_prec = KERR_ZONE_FP64;
     o->zone_variant = -1;
-    o->zone_quantum = 48;
+    o->zone_quantum = 32;
 }
 
 extern "C" const char *kerr_last_error(void) { return g_err.c_str(); }

@@ -127,8 +127,10 @@ __device__ __forceinline__ bool operator!=(dfloat x, dfloat y) { return !(x == y
 
 __device__ __forceinline__ dfloat fabs(dfloat x) { return x.hi < 0.f ? -x : x; }
 __device__ __forceinline__ dfloat fmax(dfloat x, dfloat y) { return (x < y) ? y : x; }
+__device__ __forceinline__ dfloat k_absmax(dfloat u, dfloat v) { return fmax(fabs(u), fabs(v)); }
 __device__ __forceinline__ dfloat fmin(dfloat x, dfloat y) { return (y < x) ? y : x; }
 __device__ __forceinline__ bool isfinite(dfloat x) { return ::isfinite(x.hi) && ::isfinite(x.lo); }
+__device__ __forceinline__ bool k_isfinite(dfloat x) { return isfinite(x); }
 
 __device__ __forceinline__ dfloat &operator+=(dfloat &x, dfloat y) { return x = x + y; }
 __device__ __forceinline__ dfloat &operator*=(dfloat &x, dfloat y) { return x = x * y; }

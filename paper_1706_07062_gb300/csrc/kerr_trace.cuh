@@ -69,8 +69,10 @@ struct ZoneEntry {
     uint32_t nsteps;
     int32_t since_renorm;
     uint32_t seq;      // zone queue: (index + 1) mod 2^32 once written, 0 once read
-    int32_t pad;
+    int32_t fmt;       // ZE_PAIR: (y, c) is the compensated FP32 pair; ZE_FP64:
+                       // the FP64 state, low words in y, high words in c
 };
+enum : int32_t { ZE_PAIR = 0, ZE_FP64 = 1 };
 static_assert(sizeof(ZoneEntry) == 96, "zone entry layout");
 
 // Per-geodesic constants of the FP32 path, one float plane each.
@@ -109,8 +111,8 @@ struct TraceParams {
     double r_escape, t_end, fp64_zone;
     int32_t renorm_every, clip_maxit;
     int32_t zone_df;            // FP32 path: zone steps in float-float (1) or FP64 (0)
-    int32_t zone_quantum;       // zone phase: attempts before a geodesic yields its
-                                // lane to a waiting one (0: run to the end)
+    int32_t zone_quantum;       // zone phase: warp iterations between re-queue
+                                // points (0: each geodesic runs to its end)
     uint64_t budget_ns;
     const int32_t *abort;       // host-writable stop flag (mapped pinned memory), or null
     unsigned long long *head;   // work-queue counter, zero at launch
@@ -489,7 +491,7 @@ __device__ __forceinline__ T attempt(const T a, const T a2, const T y[8], const 
 #pragma unroll
         for (int i = 1; i < 8; ++i) {
             const T delta = (d[i] - df[i]) * T(1.0 / 15.0);
-            const T sc = tol * (T(1) + fmax(fabs(y[i]), fabs(y[i] + d[i])));
+            const T sc = tol * (T(1) + k_absmax(y[i], y[i] + d[i]));
             const T e = fabs(delta);
             const bool take = !(e * den <= num * sc);
             num = take ? e : num;
@@ -696,7 +698,7 @@ __device__ __forceinline__ int step_post(const RayConst &rc, const TraceParams &
         yn[i] = y[i];
         cn[i] = c[i];
         add_incr<KAHAN>(yn[i], cn[i], d[i]);
-        finite = finite && isfinite(yn[i]);
+        finite = finite && k_isfinite(yn[i]);
     }
     if (!finite) {
 #pragma unroll
@@ -1077,6 +1079,57 @@ static __device__ __noinline__ ZoneResult zone_step(const RayConst rc, const Tra
     return R;
 }
 
+// FP64 state held in the (y, c) registers of a lane as bit patterns (low
+// word in y, high word in c): consecutive zone steps of one geodesic keep
+// its FP64 state instead of rounding it to an FP32 pair after every attempt
+// (on GB300 each conversion costs the FP64 pipe as much as an FMA).
+__device__ __forceinline__ double d_from_bits(float lo, float hi)
+{
+    return __hiloint2double(__float_as_int(hi), __float_as_int(lo));
+}
+__device__ __forceinline__ void d_to_bits(double v, float &lo, float &hi)
+{
+    lo = __int_as_float(__double2loint(v));
+    hi = __int_as_float(__double2hiint(v));
+}
+
+struct Y8d {
+    double v[8];
+};
+struct ZoneResultD {
+    Y8d y;
+    float h, rnow;
+    int st;
+    uint32_t nrhs, nacc;
+    int since_renorm;
+    ClipRec clip;               // the step's clipping was deferred (state before it)
+};
+
+// One FP64 zone attempt on an FP64 state (zone phase): the arithmetic of
+// zone_step without the conversions from and to the FP32 pair.
+template <int RM>
+static __device__ __noinline__ ZoneResultD zone_step_d(const RayConst rc, const TraceParams &P,
+                                                      int64_t id, Y8d s, float h, float rnow,
+                                                      int since_renorm)
+{
+    double cd[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        cd[i] = 0.0;
+    double hd = (double)h, rd = (double)rnow;
+    ZoneResultD R;
+    R.nrhs = 0;
+    R.nacc = 0;
+    R.st = step_once<false, double, true, RM>(rc, P, id, P.tol, s.v, cd, hd, rd, R.nrhs,
+                                              R.nacc, since_renorm, nullptr,
+                                              P.clipq ? &R.clip : nullptr);
+    R.y = s;
+    R.h = (float)hd;
+    R.rnow = (float)rd;
+    R.since_renorm = since_renorm;
+    return R;
+}
+
 // The same step in float-float arithmetic: the compensated pair (y, c) is
 // already a float-float number, so no FP64 instruction is needed.
 template <int RM>
@@ -1392,8 +1445,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f64_kernel(const TraceParam
 // queue (warp-aggregated; every lane of the warp calls this): FP32 clips from
 // the front, zone-arithmetic clips from the back.  Each geodesic ends once,
 // so the two ends never meet.
+// Clip-queue entries of zone clips whose stored state is FP64 bit patterns
+// (zone phase) rather than an FP32 pair carry this bit.
+constexpr int64_t kClipFP64State = 1ll << 62;
+
 __device__ __forceinline__ void enqueue_clips(const TraceParams &P, bool pend32, bool pend64,
-                                              int64_t id)
+                                              int64_t id, bool fp64_state = false)
 {
     const unsigned FULL = 0xffffffffu;
     const unsigned lt_mask = (1u << (threadIdx.x & 31)) - 1u;
@@ -1407,7 +1464,8 @@ __device__ __forceinline__ void enqueue_clips(const TraceParams &P, bool pend32,
     if (m64) {
         const unsigned long long b = warp_claim(P.cq64, m64);
         if (pend64)
-            P.clipq[P.n - 1 - (int64_t)(b + __popc(m64 & lt_mask))] = id;
+            P.clipq[P.n - 1 - (int64_t)(b + __popc(m64 & lt_mask))] =
+                fp64_state ? (id | kClipFP64State) : id;
     }
 }
 
@@ -1560,14 +1618,17 @@ __device__ __forceinline__ void zsplit(dfloat v, float &y, float &c)
 // float-float): the zone step's arithmetic and its 1e-10 tolerance.
 template <typename T>
 __device__ void clip_end_zone(const TraceParams &P, int64_t id, int st, float y[8], float c[8],
-                              uint32_t &nrhs)
+                              bool fp64_state, uint32_t &nrhs)
 {
     RayConst rc;
     load_const_full(P, id, rc);
     T yd[8], cd[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        yd[i] = zfold(y[i], c[i], T(0));
+        if constexpr (std::is_same<T, double>::value)
+            yd[i] = fp64_state ? d_from_bits(y[i], c[i]) : zfold(y[i], c[i], T(0));
+        else
+            yd[i] = zfold(y[i], c[i], T(0));
         cd[i] = T(0);
     }
     const T a = RC<T>::a(rc), a2 = a * a;
@@ -1601,7 +1662,9 @@ static __global__ void __launch_bounds__(128) f32_clip_kernel(const TraceParams 
     for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
          k < total; k += (unsigned long long)gridDim.x * blockDim.x) {
         const bool fp32 = k < n32;
-        const int64_t id = fp32 ? P.clipq[k] : P.clipq[n - 1 - (int64_t)(k - n32)];
+        const int64_t q = fp32 ? P.clipq[k] : P.clipq[n - 1 - (int64_t)(k - n32)];
+        const bool fp64_state = (q & kClipFP64State) != 0;
+        const int64_t id = q & ~kClipFP64State;
         const int st = P.status[id];
         float y[8], c[8];
 #pragma unroll
@@ -1613,9 +1676,9 @@ static __global__ void __launch_bounds__(128) f32_clip_kernel(const TraceParams 
         if (fp32)
             clip_end_f32(P, id, st, y, c, nrhs);
         else if (P.zone_df)
-            clip_end_zone<dfloat>(P, id, st, y, c, nrhs);
+            clip_end_zone<dfloat>(P, id, st, y, c, false, nrhs);
         else
-            clip_end_zone<double>(P, id, st, y, c, nrhs);
+            clip_end_zone<double>(P, id, st, y, c, fp64_state, nrhs);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             P.s_state[i * n + id] = y[i];
@@ -1683,6 +1746,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
     const bool can_defer = PHASE == 0 && P.zbuf != nullptr && P.fp64_zone > 0.0;
     const float tol = (float)P.tol;
     const float h0 = (float)P.h0;
+    // zone phase: re-queueing is tested every zone_quantum iterations of a
+    // warp, staggered over the warps of the grid, so that the warps do not
+    // all reach the queue's counters at once
+    const uint32_t zq = P.zone_quantum > 0 ? (uint32_t)P.zone_quantum : 1u;
+    const uint32_t zq_min = zq > 1 ? zq / 2 : 1u;
+    uint32_t wit = (uint32_t)((blockIdx.x * (unsigned)(BLOCK / 32) + (threadIdx.x >> 5)) % zq);
 
     bool has = false, drained = false, timed_out = false;
     int64_t id = 0;
@@ -1691,6 +1760,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
     float h = 0.f, rnow = 0.f;
     uint32_t nsteps = 0, quantum = 0;
     int since_renorm = 0;
+    // FP64 zone phase: (y, c) hold the FP64 state's bit patterns (see
+    // d_from_bits) instead of an FP32 pair
+    bool zd = false;
+    auto to_pair = [&]() {
+        if (PHASE == 1 && zd) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                zsplit(d_from_bits(y[i], c[i]), y[i], c[i]);
+            zd = false;
+        }
+    };
     Counters C;
     const unsigned long long t_start = global_ns();
     uint32_t iter = 0;
@@ -1741,6 +1821,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                         rnow = __ldcg(&e.rnow);
                         nsteps = __ldcg(&e.nsteps);
                         since_renorm = __ldcg(&e.since_renorm);
+                        zd = PHASE == 1 && __ldcg(&e.fmt) == ZE_FP64;
                         st_release(&e.seq, 0u);
                         load_const_full(P, id, rc);
                         quantum = 0;
@@ -1772,6 +1853,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                         P.steps[id] = nsteps;
                         C.status(ST_TIMEOUT);
                         if (PHASE != 0) {
+                            to_pair();
 #pragma unroll
                             for (int i = 0; i < 8; ++i) {
                                 P.s_state[i * n + id] = y[i];
@@ -1810,6 +1892,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                         e.rnow = rnow;
                         e.nsteps = nsteps;
                         e.since_renorm = since_renorm;
+                        e.fmt = ZE_PAIR;
                         e.seq = (uint32_t)(slot + 1ull);   // visible to the next launch
                         ++C.def;
                         has = false;
@@ -1820,7 +1903,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
         }
         // clipping deferred to the clip pass: the last step ran in FP32 (front
         // of the clip queue) or in the zone's arithmetic (back)
-        bool pend32 = false, pend64 = false;
+        bool pend32 = false, pend64 = false, clip_bits = false;
         if (has) {
             int st = ST_NONE;
             ClipRec cr;
@@ -1833,7 +1916,33 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                 ++nsteps;
                 ++quantum;
                 ++C.att;
-                if (in_zone) {
+                if (PHASE == 1 && in_zone) {
+                    // FP64 zone phase: the state stays FP64 from one attempt
+                    // to the next
+                    if (!zd) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            d_to_bits((double)y[i] + (double)c[i], y[i], c[i]);
+                        zd = true;
+                    }
+                    Y8d ys;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        ys.v[i] = d_from_bits(y[i], c[i]);
+                    const ZoneResultD R = zone_step_d<RM>(rc, P, id, ys, h, rnow, since_renorm);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        d_to_bits(R.y.v[i], y[i], c[i]);
+                    h = R.h;
+                    rnow = R.rnow;
+                    since_renorm = R.since_renorm;
+                    st = R.st;
+                    cr = R.clip;
+                    zone_step_taken = true;
+                    C.rhs64 += R.nrhs;
+                    C.acc += R.nacc;
+                    ++C.att64;
+                } else if (in_zone) {
                     if (PHASE == 0)
                         load_const_full(P, id, rc);   // in-place zone step: FP64 constants
                     LaneF ls;
@@ -1864,6 +1973,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     C.acc += R.nacc;
                     ++C.att64;
                 } else {
+                    to_pair();     // FP64 zone phase: a geodesic that left the zone
                     uint32_t r = 0;
                     // FP32 steps: the variant's right-hand-side mode in the
                     // stepping phase; out of line in the zone phase (as in the
@@ -1879,7 +1989,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     }
                 }
             }
+            // a deferred clip of an FP64 zone-phase step keeps the FP64 state
+            // before the step, exactly (flagged in the clip queue)
+            clip_bits = st != ST_NONE && zd && cr.pending && zone_step_taken;
             if (st != ST_NONE) {
+                if (!clip_bits)
+                    to_pair();
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     P.s_state[i * n + id] = y[i];
@@ -1898,12 +2013,18 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
             }
         }
         if (P.clipq)
-            enqueue_clips(P, pend32, pend64, id);
-        // ---- zone phase: after zone_quantum attempts a geodesic yields its
+            enqueue_clips(P, pend32, pend64, id, clip_bits);
+        // ---- zone phase: every zone_quantum iterations of the warp, a
+        // geodesic that took at least half a quantum of attempts yields its
         // lane to one that waits in the queue (processor sharing), so that
-        // the phase is not left with a second, partly filled wave of lanes
-        if (PHASE != 0 && requeue) {
-            const bool want = has && !timed_out && quantum >= (uint32_t)P.zone_quantum;
+        // the phase is not left with a second, partly filled wave of lanes.
+        // The re-queue points of the warps are staggered: when all warps
+        // reached the queue counters' compare-and-swap together, each
+        // re-queue point cost a warp ~150 us of retries (measured on the
+        // 1024 x 1024 image), several attempts' worth.
+        if (PHASE != 0 && requeue && ++wit >= zq) {
+            wit = 0;
+            const bool want = has && !timed_out && quantum >= zq_min;
             const unsigned pm = __ballot_sync(FULL, want);
             if (pm) {
                 const int leader = __ffs(pm) - 1;
@@ -1927,6 +2048,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                             e.rnow = rnow;
                             e.nsteps = nsteps;
                             e.since_renorm = since_renorm;
+                            e.fmt = zd ? ZE_FP64 : ZE_PAIR;
                             st_release(&e.seq, (uint32_t)(idx + 1ull));
                             ++C.req;
                             has = false;
@@ -1935,8 +2057,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                             quantum = 0;
                         }
                     }
-                } else if (want) {
-                    quantum = 0;     // nobody waits: another quantum here
                 }
             }
         }

@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32x2_kernel(const TracePar
                             e.rnow = rnow[s];
                             e.nsteps = nsteps[s];
                             e.since_renorm = since_renorm[s];
+                            e.fmt = ZE_PAIR;
                             e.seq = (uint32_t)(slot + 1ull);   // visible to the next launch
                             ++C.def;
                             has[s] = false;

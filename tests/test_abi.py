@@ -69,7 +69,7 @@ def test_defaults_and_variants_without_gpu(libpath):
     assert o.prec == K.FP32_KAHAN and o.tol == 1e-6 and o.h0 == 1.0
     assert o.max_steps == 1_000_000 and o.r_escape == 0.0 and np.isinf(o.t_end)
     assert o.fp64_zone == 1.5 and o.clip_maxit == 40 and o.variant == -1
-    assert o.zone_quantum == 48 and o.zone_variant == -1
+    assert o.zone_quantum == 32 and o.zone_variant == -1
     n = K.kerr_num_variants()
     assert n >= 1
     rays = []
