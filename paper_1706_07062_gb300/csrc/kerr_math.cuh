@@ -172,16 +172,18 @@ __device__ __forceinline__ void accel(const T a, const T a2, const T x, const T 
     const T lz = z * ir;
     const T L = k_fma(lx, kx, k_fma(ly, ky, k_fma(lz, kz, kt)));
     // d_i r = (f/2) (x, y, zt)_i and k . grad r
-    const T zt = z * k_fma(a2, ir * ir, T(1));
+    const T ir2 = ir * ir;
+    const T a2z = a2 * z;
+    const T zt = k_fma(a2z, ir2, z);
     const T kr = hf * k_fma(x, kx, k_fma(y, ky, zt * kz));
     // d_i f = c1 d_i r + g delta_iz
     const T c1 = f * k_fma(T(3), ir, -(f + f));
-    const T g = -(f + f) * (a2 * z) * iq;
+    const T g = -(f + f) * a2z * iq;
     // e of d_al l_i = r_al e_i + M_{al i}
     const T m2r = -(r + r);
     const T ex = is * k_fma(m2r, lx, x);
     const T ey = is * k_fma(m2r, ly, y);
-    const T ez = -lz * ir;
+    const T ez = -z * ir2;
     const T ek = k_fma(ex, kx, k_fma(ey, ky, ez * kz));     // e . k
     // A_al k^al and l . grad f
     const T gk = k_fma(c1, kr, g * kz);
@@ -190,13 +192,15 @@ __device__ __forceinline__ void accel(const T a, const T a2, const T x, const T 
     const T lf = k_fma(g, lz, c1);
     const T L2 = L * L;
     const T hLL = T(0.5) * L2;
-    const T F = -(hf * L2) * lf;
-    at = Ak - F;
+    // at = A.k - F with F = -(f/2) L^2 (l.grad f), as one explicit fused
+    // multiply-add (so that no compiler contraction can make the scalar and
+    // the packed two-per-thread forms round differently)
+    at = k_fma(hf * L2, lf, Ak);
     // x_i'' with d_i f and d_i r expanded: (f/2)(L^2 c1/2 + f L e.k)(x, y, zt)_i
     // - f L (k.grad r) e_i - 2 f L Q (k_y, -k_x, 0)_i + (L^2/2) g delta_iz
     // + l_i (F - A.k)
     const T fL = f * L;
-    const T FmA = F - Ak;
+    const T FmA = -at;                          // F - A.k, exactly
     const T hw = hf * k_fma(hLL, c1, fL * ek);
     const T fLkr = fL * kr;
     const T fLQ2 = fL * (Q + Q);

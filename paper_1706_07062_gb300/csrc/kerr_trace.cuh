@@ -1106,7 +1106,8 @@ struct ZoneResultD {
 };
 
 // One FP64 zone attempt on an FP64 state (zone phase): the arithmetic of
-// zone_step without the conversions from and to the FP32 pair.
+// zone_step without the conversions from and to the FP32 pair; the lane
+// keeps the state in FP64 between attempts.
 template <int RM>
 static __device__ __noinline__ ZoneResultD zone_step_d(const RayConst rc, const TraceParams &P,
                                                       int64_t id, Y8d s, float h, float rnow,
@@ -1761,7 +1762,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
     uint32_t nsteps = 0, quantum = 0;
     int since_renorm = 0;
     // FP64 zone phase: (y, c) hold the FP64 state's bit patterns (see
-    // d_from_bits) instead of an FP32 pair
+    // d_from_bits) instead of an FP32 pair while a geodesic is in the zone
     bool zd = false;
     auto to_pair = [&]() {
         if (PHASE == 1 && zd) {
@@ -1930,9 +1931,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     for (int i = 0; i < 8; ++i)
                         ys.v[i] = d_from_bits(y[i], c[i]);
                     const ZoneResultD R = zone_step_d<RM>(rc, P, id, ys, h, rnow, since_renorm);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        d_to_bits(R.y.v[i], y[i], c[i]);
                     h = R.h;
                     rnow = R.rnow;
                     since_renorm = R.since_renorm;
@@ -1942,6 +1940,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     C.rhs64 += R.nrhs;
                     C.acc += R.nacc;
                     ++C.att64;
+                    if (st == ST_NONE && !(rnow < rc.zonef)) {
+                        // leaving the zone: its FP32 steps take the pair
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            zsplit(R.y.v[i], y[i], c[i]);
+                        zd = false;
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            d_to_bits(R.y.v[i], y[i], c[i]);
+                    }
                 } else if (in_zone) {
                     if (PHASE == 0)
                         load_const_full(P, id, rc);   // in-place zone step: FP64 constants
@@ -1953,6 +1962,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     }
                     ls.h = h;
                     ls.rnow = rnow;
+                    // float-float zone phase, or in-place zone steps of the
+                    // stepping phase (one attempt from the FP32 pair and back)
                     ZoneResult R;
                     if (PHASE == 2 || (PHASE == 0 && P.zone_df))
                         R = zone_step_df<PHASE == 2 ? RM : RHS_INLINE>(rc, P, id, ls, since_renorm);
@@ -1973,7 +1984,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     C.acc += R.nacc;
                     ++C.att64;
                 } else {
-                    to_pair();     // FP64 zone phase: a geodesic that left the zone
                     uint32_t r = 0;
                     // FP32 steps: the variant's right-hand-side mode in the
                     // stepping phase; out of line in the zone phase (as in the

@@ -477,7 +477,12 @@ def test_zone_buffer_overflow_falls_back_in_place(ctx):
     """A 512 x 512 image of the shadow itself: most rays enter the zone, more
     than a fresh context's deferred buffer holds (a quarter of the rays), so
     the rest take their FP64 zone steps in place.  The result must match a run
-    whose buffer holds every deferred ray (same arithmetic, other launch)."""
+    whose buffer holds every deferred ray: the same FP64 zone arithmetic and
+    the same step sequence, except that an in-place zone step rounds the FP64
+    state to the compensated FP32 pair after every attempt (~2^-48 relative)
+    while the zone phase keeps it in FP64 from one attempt to the next; the
+    plunge into the horizon amplifies that to ~1e-7 at the end points, so
+    they are compared at 1e-6."""
     spec = W.CameraSpec(0.9, 1.0, 1000.0, 3.0, 512, 512)
     opts = K.default_opts(tol=1e-6)
     fresh = K.kerr_init(spec.a)
@@ -499,7 +504,7 @@ def test_zone_buffer_overflow_falls_back_in_place(ctx):
     assert np.array_equal(to_np(out1.status), to_np(out2.status))
     ex, ek, _ = rel_errors(to_np(out1.x), to_np(out1.k),
                            np.concatenate([to_np(out2.x).T, to_np(out2.k).T], 1))
-    assert max(ex.max(), ek.max()) < 1e-9
+    assert max(ex.max(), ek.max()) < 1e-6
 
 
 # ---------------------------------------------------------------------------

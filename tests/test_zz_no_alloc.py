@@ -94,7 +94,10 @@ def test_static_zone_buffer_overflow_runs_in_place():
     """A 256 x 256 image of the shadow itself: most of its 65536 rays enter the
     FP64 zone, more than the array's zone buffer (32768 entries) holds, so the
     rest take their zone steps in place; the allocating entry point's buffer
-    holds them all.  Same statuses, end points equal to rounding."""
+    holds them all.  Same statuses; end points equal to the rounding of the
+    in-place steps, which round the FP64 state to the compensated FP32 pair
+    after every attempt (the zone phase keeps it in FP64; the plunge into the
+    horizon amplifies the difference to ~1e-7), so they are compared at 1e-6."""
     K.lib()
     cams = [K.camera(0.9, 1.0, 1000.0, 3.0, 256, 256)]
     opts = K.default_opts(tol=1e-6)
@@ -108,8 +111,8 @@ def test_static_zone_buffer_overflow_runs_in_place():
         out = K.kerr_trace_camera_static(cams, opts, device=DEV)
         torch.cuda.synchronize()
         assert torch.equal(out.status, ref.status)
-        assert _rel(out.x[1:4], ref.x[1:4]) <= 1e-9
-        assert _rel(out.k, ref.k) <= 1e-9
+        assert _rel(out.x[1:4], ref.x[1:4]) <= 1e-6
+        assert _rel(out.k, ref.k) <= 1e-6
 
 
 @pytest.mark.parametrize("prec", [K.FP32_KAHAN, K.FP64])
