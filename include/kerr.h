@@ -357,7 +357,7 @@ int kerr_autotune(kerr_ctx *ctx, const kerr_camera *cam, const kerr_opts *opts,
  * (kerr_get_stats needs a context). */
 #define KERR_STATIC_MAX_GEODESICS 131072
 #define KERR_STATIC_MAX_CAMERAS 64
-#define KERR_STATIC_SCRATCH_BYTES 18877696
+#define KERR_STATIC_SCRATCH_BYTES 18878208
 int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam, const kerr_opts *opts,
                              double *x_out, double *k_out, int32_t *status, int32_t *steps,
                              float *diag, float *cross, void *stream);

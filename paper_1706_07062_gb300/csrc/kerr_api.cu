@@ -789,7 +789,8 @@ int kerr::build_cams(const kerr_camera *cams, int32_t ncam, CamDev *out, int64_t
         const double rh = 1.0 + std::sqrt(std::max(0.0, 1.0 - k.a * k.a));
         if (!(k.r_obs > 1.01 * rh) || !std::isfinite(k.r_obs) || !std::isfinite(k.incl))
             return fail(KERR_EINVAL, "camera %d: r_obs %g / incl %g invalid", i, k.r_obs, k.incl);
-        out[i] = CamDev{k.a, k.incl, k.r_obs, k.half_width, k.nx, k.ny, n};
+        out[i] = CamDev{k.a, std::sin(k.incl), std::cos(k.incl), k.r_obs, k.half_width, k.nx, k.ny,
+                        n};
         n += (int64_t)k.nx * k.ny;
     }
     *n_out = n;

@@ -257,16 +257,23 @@ struct KSPoint {
     double r, f, lx, ly, lz;
 };
 
+// r, f and l at a point (eqs. def:CKS, CKSr), with the refined FP64
+// reciprocal square root and the shared reciprocal of the right-hand side
+// (within a few ulp; IEEE division and square root cost several times as
+// many FP64 instructions on GB300).
 __device__ __forceinline__ KSPoint ks_point(double a, double x, double y, double z)
 {
     KSPoint p;
     const double a2 = a * a;
     const double r2 = ks_r2(a2, x, y, z);
-    p.r = sqrt(r2);
-    p.f = 2.0 * p.r * r2 / (r2 * r2 + a2 * z * z);
-    p.lx = (p.r * x + a * y) / (r2 + a2);
-    p.ly = (p.r * y - a * x) / (r2 + a2);
-    p.lz = z / p.r;
+    const double ir = k_rsqrt(r2);
+    p.r = r2 * ir;
+    double iq, is;
+    recip2(k_fma(r2, r2, a2 * (z * z)), r2 + a2, iq, is);
+    p.f = 2.0 * p.r * r2 * iq;
+    p.lx = (p.r * x + a * y) * is;
+    p.ly = (p.r * y - a * x) * is;
+    p.lz = z * ir;
     return p;
 }
 
@@ -316,11 +323,12 @@ __device__ __forceinline__ void constants(double a, const double y[8], float out
     const double u2 = pt * y[4] + px * y[5] + py * y[6] + pz * y[7];
     const double E = -pt;
     const double Lz = y[1] * py - y[2] * px;
-    const double c = y[3] / p.r;
+    const double c = p.lz;                      // cos(theta) = z / r
     const double s2 = 1.0 - c * c;
-    const double s = sqrt(s2);
-    const double pth = (c / s) * (y[1] * px + y[2] * py) - p.r * s * pz;
-    const double Q = pth * pth + c * c * (a * a * (-u2 - E * E) + Lz * Lz / s2);
+    const double is = k_rsqrt(s2);              // 1 / sin(theta)
+    const double s = s2 * is;
+    const double pth = (c * is) * (y[1] * px + y[2] * py) - p.r * s * pz;
+    const double Q = pth * pth + c * c * (a * a * (-u2 - E * E) + Lz * Lz * (is * is));
     out[0] = (float)E;
     out[1] = (float)Lz;
     out[2] = (float)Q;

@@ -32,10 +32,11 @@ enum : int {
 
 enum : int { MODE_RAYS = 0, MODE_CAMERA = 1, MODE_PARTICLES = 2, MODE_POINTS = 3 };
 
-// Camera as the kernel sees it: the public kerr_camera plus the index of its
+// Camera as the kernel sees it: the public kerr_camera (the inclination as
+// its sine and cosine, evaluated once on the host) plus the index of its
 // first ray.
 struct CamDev {
-    double a, incl, r_obs, w;
+    double a, sin_incl, cos_incl, r_obs, w;
     int32_t nx, ny;
     int64_t offset;
 };
@@ -856,8 +857,10 @@ __device__ __forceinline__ int init_geodesic(const TraceParams &P, int64_t id, d
     const int64_t n = P.n;
     double a = P.a;
     int st = ST_NONE;
+    KSPoint kp;                 // the metric's pieces at the start point
+    bool have_kp = false;
     if (P.mode == MODE_CAMERA || P.mode == MODE_POINTS) {
-        double al, be, incl, r_obs;
+        double al, be, r_obs, si, ci;
         if (P.mode == MODE_CAMERA) {
             const int64_t pix = P.index ? P.index[id] : id;
             int lo = 0, hi = P.ncam - 1;
@@ -874,17 +877,16 @@ __device__ __forceinline__ int init_geodesic(const TraceParams &P, int64_t id, d
             const int64_t p = local % cam.nx, q = local / cam.nx;
             al = -cam.w + (p + 0.5) * 2.0 * cam.w / cam.nx;
             be = -cam.w + (q + 0.5) * 2.0 * cam.w / cam.ny;
-            incl = cam.incl;
+            si = cam.sin_incl;
+            ci = cam.cos_incl;
             r_obs = cam.r_obs;
         } else {
             al = P.points[4 * id];
             be = P.points[4 * id + 1];
             a = P.points[4 * id + 2];
-            incl = P.points[4 * id + 3];
+            sincos(P.points[4 * id + 3], &si, &ci);
             r_obs = P.r_obs;
         }
-        double si, ci;
-        sincos(incl, &si, &ci);
         y[0] = 0.0;
         y[1] = r_obs * si - be * ci;
         y[2] = al;
@@ -893,7 +895,8 @@ __device__ __forceinline__ int init_geodesic(const TraceParams &P, int64_t id, d
         y[6] = 0.0;
         y[7] = -ci;
         y[4] = 0.0;
-        const KSPoint kp = ks_point(a, y[1], y[2], y[3]);
+        kp = ks_point(a, y[1], y[2], y[3]);
+        have_kp = true;
         if (!solve_kt(kp, y + 4, 0.0, -1))
             st = ST_INVALID_IC;
     } else {
@@ -906,7 +909,8 @@ __device__ __forceinline__ int init_geodesic(const TraceParams &P, int64_t id, d
                 y[4 + j] = P.k0[j * n + id];
         } else {
             const double v1 = P.k0[id], v2 = P.k0[n + id], v3 = P.k0[2 * n + id];
-            const KSPoint kp = ks_point(a, y[1], y[2], y[3]);
+            kp = ks_point(a, y[1], y[2], y[3]);
+            have_kp = true;
             const double lv = 1.0 + kp.lx * v1 + kp.ly * v2 + kp.lz * v3;
             const double s = -1.0 + v1 * v1 + v2 * v2 + v3 * v3 + kp.f * lv * lv;
             if (s < 0.0) {
@@ -933,14 +937,15 @@ __device__ __forceinline__ int init_geodesic(const TraceParams &P, int64_t id, d
     bool finite = true;
 #pragma unroll
     for (int i = 0; i < 8; ++i)
-        finite = finite && isfinite(y[i]);
+        finite = finite && k_isfinite(y[i]);
     if (st == ST_NONE && !finite)
         st = ST_NONFINITE;
     const double r0 = finite ? ks_r(a * a, y[1], y[2], y[3]) : 0.0;
     rc.resc = P.r_escape > 0.0 ? P.r_escape : (P.r_escape == 0.0 ? r0 : INFINITY);
     rc.xi = 0.0;
     if (st == ST_NONE) {
-        const KSPoint kp = ks_point(a, y[1], y[2], y[3]);
+        if (!have_kp)
+            kp = ks_point(a, y[1], y[2], y[3]);
         rc.u2_0 = norm2(kp, y + 4);
         // E = -p_t and L_z = x p_y - y p_x with p = eta k + f l (l.k)
         const double L = y[4] + kp.lx * y[5] + kp.ly * y[6] + kp.lz * y[7];
@@ -1493,7 +1498,7 @@ static __global__ void __launch_bounds__(256) f32_setup_kernel(const TraceParams
         for (int i = 0; i < 8; ++i) {
             const float hi = (float)yd[i];
             P.s_state[i * n + id] = hi;
-            P.s_state[(8 + i) * n + id] = isfinite(yd[i]) ? (float)(yd[i] - (double)hi) : 0.0f;
+            P.s_state[(8 + i) * n + id] = k_isfinite(yd[i]) ? (float)(yd[i] - (double)hi) : 0.0f;
         }
         P.s_const[KC_A * n + id] = rc.af;
         P.s_const[KC_RCAP * n + id] = rc.rcapf;
