@@ -339,9 +339,9 @@ int kerr_autotune(kerr_ctx *ctx, const kerr_camera *cam, const kerr_opts *opts,
  * that every GPU that loads the library holds until the process exits.
  * Limits: at most KERR_STATIC_MAX_GEODESICS rays and KERR_STATIC_MAX_CAMERAS
  * cameras per call (KERR_EINVAL beyond); outputs must be device memory
- * (KERR_EINVAL otherwise, since host buffers would need staging).  Geodesics
- * entering the FP64 zone beyond the array's zone buffer (a quarter of the
- * maximum) take their zone steps in place.
+ * (KERR_EINVAL otherwise, since host buffers would need staging).  The
+ * array's zone buffer holds one entry per geodesic, as the allocating entry
+ * point's does.
  *
  * The first call on a device is the set-up: it looks up the array's device
  * address (cudaGetSymbolAddress) with that device current and caches it, and
@@ -357,7 +357,7 @@ int kerr_autotune(kerr_ctx *ctx, const kerr_camera *cam, const kerr_opts *opts,
  * (kerr_get_stats needs a context). */
 #define KERR_STATIC_MAX_GEODESICS 131072
 #define KERR_STATIC_MAX_CAMERAS 64
-#define KERR_STATIC_SCRATCH_BYTES 18878208
+#define KERR_STATIC_SCRATCH_BYTES 28315392
 int kerr_trace_camera_static(const kerr_camera *cams, int32_t ncam, const kerr_opts *opts,
                              double *x_out, double *k_out, int32_t *status, int32_t *steps,
                              float *diag, float *cross, void *stream);

@@ -506,9 +506,10 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
         bind_f32_scratch(P, c->d_work, c->d_scratch, n);
     }
     if (o->prec == KERR_FP32_KAHAN && o->fp64_zone > 0.0) {
-        // Deferred-zone buffer: a quarter of the geodesics (at least 64 Ki);
-        // geodesics beyond it take their zone steps in place.
-        const int64_t want = std::min<int64_t>(n, std::max<int64_t>(1 << 16, n / 4));
+        // Deferred-zone buffer: one entry per geodesic (each is deferred at
+        // most once), so the stepping phase never steps in the zone itself --
+        // an in-place FP64 step in that kernel cost it registers and spills.
+        const int64_t want = n;
         if (want > c->zone_cap) {
             cudaStreamSynchronize(c->stream);
             cudaFree(c->d_zone);

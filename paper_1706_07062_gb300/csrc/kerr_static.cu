@@ -34,7 +34,7 @@ namespace {
 
 constexpr int64_t kMaxGeo = KERR_STATIC_MAX_GEODESICS;
 constexpr int kMaxCams = KERR_STATIC_MAX_CAMERAS;
-constexpr int64_t kZoneCap = kMaxGeo / 4;
+constexpr int64_t kZoneCap = kMaxGeo;      // one zone entry per geodesic
 constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 

@@ -1056,34 +1056,6 @@ struct ZoneResult {
     ClipRec clip;               // the step's clipping was deferred (state before it)
 };
 
-template <int RM>
-static __device__ __noinline__ ZoneResult zone_step(const RayConst rc, const TraceParams &P,
-                                                    int64_t id, LaneF s, int since_renorm)
-{
-    double yd[8], cd[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        yd[i] = (double)s.y[i] + (double)s.c[i];
-        cd[i] = 0.0;
-    }
-    double hd = (double)s.h, rd = (double)s.rnow;
-    ZoneResult R;
-    R.nrhs = 0;
-    R.nacc = 0;
-    R.st = step_once<false, double, true, RM>(rc, P, id, P.tol, yd, cd, hd, rd, R.nrhs,
-                                              R.nacc, since_renorm, nullptr,
-                                              P.clipq ? &R.clip : nullptr);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        R.s.y[i] = (float)yd[i];
-        R.s.c[i] = (float)(yd[i] - (double)R.s.y[i]);
-    }
-    R.s.h = (float)hd;
-    R.s.rnow = (float)rd;
-    R.since_renorm = since_renorm;
-    return R;
-}
-
 // FP64 state held in the (y, c) registers of a lane as bit patterns (low
 // word in y, high word in c): consecutive zone steps of one geodesic keep
 // its FP64 state instead of rounding it to an FP32 pair after every attempt
@@ -1110,9 +1082,8 @@ struct ZoneResultD {
     ClipRec clip;               // the step's clipping was deferred (state before it)
 };
 
-// One FP64 zone attempt on an FP64 state (zone phase): the arithmetic of
-// zone_step without the conversions from and to the FP32 pair; the lane
-// keeps the state in FP64 between attempts.
+// One FP64 zone attempt on an FP64 state (zone phase); the lane keeps the
+// state in FP64 between attempts.
 template <int RM>
 static __device__ __noinline__ ZoneResultD zone_step_d(const RayConst rc, const TraceParams &P,
                                                       int64_t id, Y8d s, float h, float rnow,
@@ -1442,7 +1413,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f64_kernel(const TraceParam
 //                      into FP32 pairs + per-geodesic constants in scratch;
 //                      geodesics that end at once get their status here.
 //   trace_f32_kernel   PHASE 0: persistent FP32 stepping, no FP64 arithmetic
-//                      except zone steps that do not fit the zone buffer;
+//                      (geodesics entering the zone are deferred; the zone
+//                      buffer holds one entry per geodesic);
 //                      PHASE 1: continues the deferred zone geodesics.
 //   f32_finish_kernel  folds the compensated pairs into FP64 outputs and
 //                      computes the FP64 diagnostics (whole warps).
@@ -1712,7 +1684,7 @@ __device__ __forceinline__ void load_const_f32(const TraceParams &P, int64_t id,
     rc.tpos = (fl >> 1) & 1;
 }
 
-// Full constants (FP64 fields too) for the zone phase and in-place zone steps.
+// Full constants (FP64 fields too) for the zone phase and the clip pass.
 __device__ __forceinline__ void load_const_full(const TraceParams &P, int64_t id, RayConst &rc)
 {
     const int64_t n = P.n;
@@ -1739,7 +1711,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
     if (P.n_dev && *P.n_dev < n_items)
         n_items = *P.n_dev;
     // zone phase: n0 entries from the FP32 phase; re-queueing needs them all
-    // in the ring (no overflow)
+    // in the ring (with one entry per geodesic the ring cannot overflow; the
+    // check stays as a guard)
     unsigned long long n0 = 0;
     bool requeue = false;
     if (PHASE != 0) {
@@ -1956,9 +1929,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                         for (int i = 0; i < 8; ++i)
                             d_to_bits(R.y.v[i], y[i], c[i]);
                     }
-                } else if (in_zone) {
-                    if (PHASE == 0)
-                        load_const_full(P, id, rc);   // in-place zone step: FP64 constants
+                } else if (PHASE == 2 && in_zone) {
                     LaneF ls;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -1967,13 +1938,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     }
                     ls.h = h;
                     ls.rnow = rnow;
-                    // float-float zone phase, or in-place zone steps of the
-                    // stepping phase (one attempt from the FP32 pair and back)
-                    ZoneResult R;
-                    if (PHASE == 2 || (PHASE == 0 && P.zone_df))
-                        R = zone_step_df<PHASE == 2 ? RM : RHS_INLINE>(rc, P, id, ls, since_renorm);
-                    else
-                        R = zone_step<RM>(rc, P, id, ls, since_renorm);
+                    // float-float zone phase
+                    const ZoneResult R = zone_step_df<RM>(rc, P, id, ls, since_renorm);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         y[i] = R.s.y[i];
@@ -1989,6 +1955,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     C.acc += R.nacc;
                     ++C.att64;
                 } else {
+                    // (stepping phase: a geodesic inside the zone is always
+                    // deferred -- the zone buffer holds one entry per geodesic;
+                    // one that could not be would be counted and step in FP32)
+                    if (PHASE == 0 && in_zone)
+                        C.status(ST_NONE);
                     uint32_t r = 0;
                     // FP32 steps: the variant's right-hand-side mode in the
                     // stepping phase; out of line in the zone phase (as in the

@@ -5,8 +5,8 @@
 // on packed f32x2 instructions (kerr_f2.cuh), so a warp issues about half the
 // FP32 arithmetic instructions per geodesic of the one-per-thread kernel.
 // Everything that branches per geodesic -- the error measure, step control,
-// compensated update, termination events, crossings, renormalisation, the
-// in-place FP64 zone steps -- runs per slot in scalar FP32 (or FP64) code,
+// compensated update, termination events, crossings, renormalisation -- runs
+// per slot in scalar FP32 (or FP64) code,
 // the same functions the one-per-thread kernel calls, so a geodesic's
 // arithmetic is that of the one-per-thread kernel with out-of-line
 // right-hand sides.  Work distribution as in trace_f32_kernel (phase 0): idle
@@ -169,11 +169,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32x2_kernel(const TracePar
                 }
             }
         }
-        // ---- per-slot checks; in-place zone steps (zone buffer full or absent)
+        // ---- per-slot checks
         int st[2] = {ST_NONE, ST_NONE};
         bool fp32_step[2] = {false, false};
         ClipRec cr[2];
-        bool zstep[2] = {false, false};
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             if (!has[s])
@@ -185,39 +184,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32x2_kernel(const TracePar
             } else {
                 ++nsteps[s];
                 ++C.att;
-                if (in_zone[s]) {
-                    RayConst rz;
-                    load_const_full(P, id[s], rz);
-                    LaneF ls;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        ls.y[i] = slot_get(y[i], s);
-                        ls.c[i] = slot_get(c[i], s);
-                    }
-                    ls.h = h[s];
-                    ls.rnow = rnow[s];
-                    ZoneResult R;
-                    if (P.zone_df)
-                        R = zone_step_df<RHS_INLINE>(rz, P, id[s], ls, since_renorm[s]);
-                    else
-                        R = zone_step<RM>(rz, P, id[s], ls, since_renorm[s]);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        slot_put(y[i], s, R.s.y[i]);
-                        slot_put(c[i], s, R.s.c[i]);
-                    }
-                    h[s] = R.s.h;
-                    rnow[s] = R.s.rnow;
-                    since_renorm[s] = R.since_renorm;
-                    st[s] = R.st;
-                    cr[s] = R.clip;
-                    zstep[s] = true;
-                    C.rhs64 += R.nrhs;
-                    C.acc += R.nacc;
-                    ++C.att64;
-                } else {
-                    fp32_step[s] = true;
-                }
+                // a geodesic inside the zone is always deferred (the zone
+                // buffer holds one entry per geodesic); one that could not be
+                // would be counted and step in FP32
+                if (in_zone[s])
+                    C.status(ST_NONE);
+                fp32_step[s] = true;
             }
         }
         // ---- one packed attempt for the slots stepping in FP32 (an idle
@@ -262,7 +234,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32x2_kernel(const TracePar
         }
         // ---- geodesics that ended (a deferred clip keeps the state before
         // the step and goes to the clip queue)
-        bool p32[2] = {false, false}, p64[2] = {false, false};
+        bool p32[2] = {false, false};
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             if (st[s] == ST_NONE)
@@ -278,8 +250,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32x2_kernel(const TracePar
             if (cr[s].pending) {
                 P.clip_h[g] = h[s];
                 P.clip_shi[g] = cr[s].s_hi;
-                p64[s] = zstep[s];
-                p32[s] = !zstep[s];
+                p32[s] = true;      // all steps of this kernel are FP32 steps
             }
             C.status(st[s]);
             has[s] = false;
@@ -287,7 +258,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32x2_kernel(const TracePar
         if (P.clipq) {
 #pragma unroll
             for (int s = 0; s < 2; ++s)
-                enqueue_clips(P, p32[s], p64[s], id[s]);
+                enqueue_clips(P, p32[s], false, id[s]);
         }
         // ---- wall-time budget (warp-uniform decision)
         if ((P.budget_ns || P.abort) && ((++iter & 31u) == 0) && !timed_out) {

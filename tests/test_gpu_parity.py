@@ -473,16 +473,12 @@ def test_zone_requeue_is_exact(ctx, zone_prec):
         assert s.attempts_fp64 == s0.attempts_fp64 and s.rhs_fp64 == s0.rhs_fp64
 
 
-def test_zone_buffer_overflow_falls_back_in_place(ctx):
-    """A 512 x 512 image of the shadow itself: most rays enter the zone, more
-    than a fresh context's deferred buffer holds (a quarter of the rays), so
-    the rest take their FP64 zone steps in place.  The result must match a run
-    whose buffer holds every deferred ray: the same FP64 zone arithmetic and
-    the same step sequence, except that an in-place zone step rounds the FP64
-    state to the compensated FP32 pair after every attempt (~2^-48 relative)
-    while the zone phase keeps it in FP64 from one attempt to the next; the
-    plunge into the horizon amplifies that to ~1e-7 at the end points, so
-    they are compared at 1e-6."""
+def test_zone_buffer_holds_every_deferred_geodesic(ctx):
+    """A 512 x 512 image of the shadow itself: most rays enter the zone.  The
+    zone buffer holds one entry per geodesic (each is deferred at most once),
+    so every one of them is deferred, none is lost and re-queueing stays on;
+    a fresh context and one whose buffers were grown by a larger image give
+    the same result bit for bit."""
     spec = W.CameraSpec(0.9, 1.0, 1000.0, 3.0, 512, 512)
     opts = K.default_opts(tol=1e-6)
     fresh = K.kerr_init(spec.a)
@@ -490,21 +486,19 @@ def test_zone_buffer_overflow_falls_back_in_place(ctx):
     torch.cuda.synchronize()
     s1 = K.kerr_get_stats(fresh)
     fresh.close()
-    assert s1.deferred == spec.n // 4            # buffer full: the rest ran in place
-    assert s1.requeued == 0 and s1.queue_errors == 0   # no re-queueing after an overflow
+    assert s1.deferred > spec.n // 2             # most rays enter the zone
+    assert s1.queue_errors == 0 and s1.requeued > 0
+    assert sum(s1.status_count[1:]) == spec.n
     big = K.kerr_init(spec.a)
     K.kerr_trace_camera(big, cam(W.CameraSpec(0.9, 1.0, 1000.0, 3.0, 1024, 1024)), opts,
-                        device=DEV)                # grows the buffer to 2^18 entries
+                        device=DEV)                # grows the buffers to 2^20 geodesics
     out2 = K.kerr_trace_camera(big, cam(spec), opts, device=DEV)
     torch.cuda.synchronize()
     s2 = K.kerr_get_stats(big)
     big.close()
-    assert s2.deferred > s1.deferred
-    assert s1.attempts_fp64 == s2.attempts_fp64
-    assert np.array_equal(to_np(out1.status), to_np(out2.status))
-    ex, ek, _ = rel_errors(to_np(out1.x), to_np(out1.k),
-                           np.concatenate([to_np(out2.x).T, to_np(out2.k).T], 1))
-    assert max(ex.max(), ek.max()) < 1e-6
+    assert s2.deferred == s1.deferred and s2.attempts_fp64 == s1.attempts_fp64
+    for name in ("x", "k", "status", "steps"):
+        assert torch.equal(getattr(out1, name), getattr(out2, name)), name
 
 
 # ---------------------------------------------------------------------------
