@@ -1038,12 +1038,10 @@ __device__ __forceinline__ bool stop_requested(const TraceParams &P, unsigned lo
     return false;
 }
 
-// One attempted step of an FP32+Kahan geodesic taken in FP64 (inside the
-// zone r < fp64_zone r_h, where f l l is large): the compensated pair is
-// folded into one FP64 state, stepped, and split back.  Kept out of line so
-// that its FP64 registers do not raise the register count of the FP32 loop.
-// The lane state travels by value so that the caller's arrays stay in
-// registers.
+// Zone steps of an FP32+Kahan geodesic (inside the zone r < fp64_zone r_h,
+// where f l l is large) run out of line, so that their registers do not raise
+// the register count of the loop around them; the lane state travels by
+// value so that the caller's arrays stay in registers.
 struct LaneF {
     float y[8], c[8];
     float h, rnow;
@@ -1107,8 +1105,9 @@ static __device__ __noinline__ ZoneResultD zone_step_d(const RayConst rc, const 
     return R;
 }
 
-// The same step in float-float arithmetic: the compensated pair (y, c) is
-// already a float-float number, so no FP64 instruction is needed.
+// One zone attempt in float-float arithmetic (zone_prec KERR_ZONE_F32X2):
+// the compensated pair (y, c) is already a float-float number, so no FP64
+// instruction is needed.
 template <int RM>
 static __device__ __noinline__ ZoneResult zone_step_df(const RayConst rc, const TraceParams &P,
                                                        int64_t id, LaneF s, int since_renorm)
