@@ -31,7 +31,7 @@ constexpr int kNumVariants = 14;
 constexpr int kFirstX2Variant = 10;
 // Defaults before autotuning, per precision (KERR_FP64, KERR_FP32_KAHAN):
 // the fastest on the 1024 x 1024, a = 0.99 camera.
-constexpr int kDefaultVariant[2] = {1, 3};
+constexpr int kDefaultVariant[2] = {1, 8};
 constexpr Variant kVariants[kNumVariants] = {{128, 4}, {128, 3}, {256, 2}, {128, 4}, {128, 3},
                                              {128, 2}, {64, 8},  {128, 5}, {256, 2}, {128, 5},
                                              {128, 2}, {128, 3}, {64, 4},  {64, 6}};
