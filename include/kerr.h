@@ -257,7 +257,12 @@ int kerr_variant_shape(int v, int32_t *block, int32_t *min_blocks, int32_t *rays
                        int32_t *rhs_mode);
 
 /* Launch shapes of the FP32 path's zone phase (threads per block, blocks per
- * SM); fewer threads than deferred geodesics lets lanes refill. */
+ * SM); fewer threads than deferred geodesics lets lanes refill.  Variant 7
+ * (the default) is variant 3 whose tail -- once at most half as many zone
+ * geodesics remain as the launch has lanes -- keeps at most 16 geodesics per
+ * warp and pairs each with an idle lane: the helper computes the full RK4
+ * step while the owner computes the half steps (the same arithmetic: results
+ * bit-identical to variant 3). */
 int kerr_num_zone_variants(void);
 int kerr_zone_variant_info(int v, int32_t *block, int32_t *blocks_per_sm);
 

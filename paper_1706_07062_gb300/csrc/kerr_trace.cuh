@@ -125,6 +125,7 @@ struct TraceParams {
     unsigned long long *zcount; // entries appended, zero at launch
     unsigned long long *zhead;  // zone-phase work-queue counter, zero at launch
     unsigned long long *zpush;  // zone phase: re-queued geodesics, zero at launch
+    unsigned long long *zdone;  // zone phase: geodesics finished, zero at launch
     double *traj;               // FP64 path: stored solution [n][traj_cap][9] (lambda, y)
     int32_t traj_cap;           // records per geodesic (the start state is the first)
     int32_t *traj_count;        // [n] records stored
@@ -267,6 +268,14 @@ __device__ __forceinline__ void rhs2(const T a, const T a2, const T p[7], const 
     }
 }
 
+// The final product of an RK4 increment.  FP64: an explicit IEEE multiply,
+// which the compiler never fuses into a later addition or subtraction (the
+// error measure's d - df, the update y + d), so an increment has the same
+// value wherever it is consumed -- in the lane that computed it or, in the
+// zone phase's two-lane attempts, in another lane.  Other types: a * b.
+template <typename T> __device__ __forceinline__ T k_mul_x(T a, T b) { return a * b; }
+__device__ __forceinline__ double k_mul_x(double a, double b) { return __dmul_rn(a, b); }
+
 // Increments d = y(lambda + h) - y(lambda) of one classic RK4 step (Sec. 3)
 // from y, with A0 = accel(y) already known: 3 right-hand sides.
 template <int RM, typename T>
@@ -304,8 +313,8 @@ __device__ __forceinline__ void rk4_incr_body(const T a, const T a2, const T y[8
     const T h6 = h * T(1.0 / 6.0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        d[j] = h6 * (Sk[j] + m[j]);
-        d[4 + j] = h6 * (SA[j] + A[j]);
+        d[j] = k_mul_x(h6, Sk[j] + m[j]);
+        d[4 + j] = k_mul_x(h6, SA[j] + A[j]);
     }
 }
 
@@ -407,10 +416,10 @@ __device__ __forceinline__ void rk4_incr2(const T a, const T a2, const T y[8], c
     const T h61 = h1 * T(1.0 / 6.0), h62 = h2 * T(1.0 / 6.0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        d1[j] = h61 * (Sk1[j] + m1[j]);
-        d1[4 + j] = h61 * (SA1[j] + A1[j]);
-        d2[j] = h62 * (Sk2[j] + m2[j]);
-        d2[4 + j] = h62 * (SA2[j] + A2[j]);
+        d1[j] = k_mul_x(h61, Sk1[j] + m1[j]);
+        d1[4 + j] = k_mul_x(h61, SA1[j] + A1[j]);
+        d2[j] = k_mul_x(h62, Sk2[j] + m2[j]);
+        d2[4 + j] = k_mul_x(h62, SA2[j] + A2[j]);
     }
 }
 
@@ -457,6 +466,26 @@ __device__ __forceinline__ float err_norm_f(const float y[8], const float d[8], 
     return bad ? __int_as_float(0x7fc00000) : __fdiv_rn(num, den);
 }
 
+// The same error measure for FP64 and float-float: the max over i of
+// |delta_i| / sc_i is kept as one fraction num / den, each comparison
+// cross-multiplied (sc_i, den > 0) and one reciprocal at the end instead of a
+// division per component.
+template <typename T>
+__device__ __forceinline__ T err_norm_d(const T y[8], const T d[8], const T df[8], const T tol)
+{
+    T num = T(0), den = T(1);
+#pragma unroll
+    for (int i = 1; i < 8; ++i) {
+        const T delta = (d[i] - df[i]) * T(1.0 / 15.0);
+        const T sc = tol * (T(1) + k_absmax(y[i], y[i] + d[i]));
+        const T e = fabs(delta);
+        const bool take = !(e * den <= num * sc);
+        num = take ? e : num;
+        den = take ? sc : den;
+    }
+    return num * k_rcp(den);
+}
+
 // One step-doubling attempt: returns the error measure and the increment of
 // the two-half-step solution (10 RHS beyond A0).  With paired right-hand
 // sides the full step and the first half step run in lockstep.
@@ -481,25 +510,10 @@ __device__ __forceinline__ T attempt(const T a, const T a2, const T y[8], const 
         rk4_incr<RM>(a, a2, y, A0, h, df);
         two_halves<RM>(a, a2, y, A0, h, d);
     }
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (std::is_same<T, float>::value)
         return err_norm_f(y, d, df, tol);
-    } else {
-        // FP64 / float-float: the max over i of |delta_i| / sc_i is kept as
-        // one fraction num / den, each comparison cross-multiplied (sc_i,
-        // den > 0) and one reciprocal at the end instead of a division per
-        // component; a NaN takes over and propagates
-        T num = T(0), den = T(1);
-#pragma unroll
-        for (int i = 1; i < 8; ++i) {
-            const T delta = (d[i] - df[i]) * T(1.0 / 15.0);
-            const T sc = tol * (T(1) + k_absmax(y[i], y[i] + d[i]));
-            const T e = fabs(delta);
-            const bool take = !(e * den <= num * sc);
-            num = take ? e : num;
-            den = take ? sc : den;
-        }
-        return num * k_rcp(den);
-    }
+    else
+        return err_norm_d(y, d, df, tol);
 }
 
 // Step-size factor after an attempt: 0.9 err^(-1/5) clamped to [0.2, 5]; 5
@@ -1105,6 +1119,76 @@ static __device__ __noinline__ ZoneResultD zone_step_d(const RayConst rc, const 
     return R;
 }
 
+// One FP64 zone attempt taken by two lanes of a warp (zone phase, its tail):
+// the owner holds the geodesic; its helper, an idle lane, receives the state,
+// the trial step and the spin, and computes the full step of h while the
+// owner computes the first half step (the same instructions on other data,
+// so the warp pays for one); the owner then takes the second half step and
+// reads the full step's increment back.  On GB300 an FP64 warp instruction
+// costs the same whatever its active lanes, so an attempt's latency falls
+// from eleven right-hand sides to eight.  The operations are those of
+// step_once (right-hand sides, RK4 steps, error measure, step_post), so the
+// result is the owner's zone_step_d result bit for bit.  `tmask` holds the
+// owners and their helpers; partner is the other lane of the pair.  A
+// helper's result is meaningless.
+template <int RM>
+static __device__ __noinline__ ZoneResultD zone_step_team(const RayConst rc, const TraceParams &P,
+                                                         int64_t id, Y8d s, float h, float rnow,
+                                                         int since_renorm, bool helper,
+                                                         int partner, unsigned tmask)
+{
+    const int lane = threadIdx.x & 31;
+    const int src = helper ? partner : lane;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        s.v[i] = __shfl_sync(tmask, s.v[i], src);
+    const float hs = __shfl_sync(tmask, h, src);
+    const double a = __shfl_sync(tmask, rc.a, src);
+    const double a2 = a * a;
+    double hd = (double)hs, rd = (double)rnow;
+    double A0[4];
+    rhs<RM>(a, a2, s.v[1], s.v[2], s.v[3], s.v[4], s.v[5], s.v[6], s.v[7], A0);
+    // helper: the full step of h; owner: the first half step
+    double dp[8];
+    rk4_incr<RM>(a, a2, s.v, A0, helper ? hd : 0.5 * hd, dp);
+    double d[8];
+    if (!helper) {
+        double ym[8], Am[4], d2[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            ym[i] = s.v[i] + dp[i];
+        rhs<RM>(a, a2, ym[1], ym[2], ym[3], ym[4], ym[5], ym[6], ym[7], Am);
+        rk4_incr<RM>(a, a2, ym, Am, 0.5 * hd, d2);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            d[i] = dp[i] + d2[i];
+    }
+    double df[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        df[i] = __shfl_sync(tmask, dp[i], helper ? lane : partner);
+    ZoneResultD R;
+    R.nrhs = 0;
+    R.nacc = 0;
+    R.st = ST_NONE;
+    if (!helper) {
+        const double err = err_norm_d(s.v, d, df, P.tol);
+        R.nrhs = 11;
+        double cd[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            cd[i] = 0.0;
+        R.st = step_post<false, double, true, RM>(rc, P, id, a, a2, A0, d, err, s.v, cd, hd, rd,
+                                                  R.nrhs, R.nacc, since_renorm, nullptr,
+                                                  P.clipq ? &R.clip : nullptr);
+    }
+    R.y = s;
+    R.h = (float)hd;
+    R.rnow = (float)rd;
+    R.since_renorm = since_renorm;
+    return R;
+}
+
 // One zone attempt in float-float arithmetic (zone_prec KERR_ZONE_F32X2):
 // the compensated pair (y, c) is already a float-float number, so no FP64
 // instruction is needed.
@@ -1201,6 +1285,25 @@ struct Counters {
         }
     }
 };
+
+// The lowest k set bits of m (k <= popc(m)).
+__device__ __forceinline__ unsigned low_bits(unsigned m, int k)
+{
+    unsigned r = 0;
+    for (int j = 0; j < k && m; ++j) {
+        const unsigned b = m & (0u - m);
+        r |= b;
+        m ^= b;
+    }
+    return r;
+}
+// Index of the k-th (0-based) set bit of m (k < popc(m)).
+__device__ __forceinline__ int nth_bit(unsigned m, int k)
+{
+    for (int j = 0; j < k; ++j)
+        m &= m - 1u;
+    return __ffs(m) - 1;
+}
 
 // Warp-aggregated claim of `cnt` consecutive items from a counter; every
 // lane of the warp gets the base.
@@ -1699,7 +1802,11 @@ __device__ __forceinline__ void load_const_full(const TraceParams &P, int64_t id
     rc.rcaplo = (float)(rc.rcap - (double)rc.rcapf);
 }
 
-template <int PHASE, int BLOCK, int MINB, int RM = RHS_INLINE>
+// TEAM (FP64 zone phase): once at most half as many geodesics remain as the
+// grid has lanes, every warp keeps at most 16 of them (the rest go back to
+// the queue) and pairs each with an idle lane for its zone attempts
+// (zone_step_team).
+template <int PHASE, int BLOCK, int MINB, int RM = RHS_INLINE, bool TEAM = false>
 __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParams P)
 {
     const unsigned FULL = 0xffffffffu;
@@ -1733,7 +1840,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
 
     bool has = false, drained = false, timed_out = false;
     int64_t id = 0;
-    RayConst rc;
+    RayConst rc{};
+    // TEAM: the warp is in the phase's tail (warp-uniform, set once)
+    bool tail = false;
+    uint32_t tcheck = 0;
+    const unsigned long long lanes_total = (unsigned long long)gridDim.x * BLOCK;
     float y[8], c[8];
     float h = 0.f, rnow = 0.f;
     uint32_t nsteps = 0, quantum = 0;
@@ -1754,8 +1865,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
     uint32_t iter = 0;
 
     for (;;) {
-        // ---- refill idle lanes from the queue (one atomic per warp)
-        const unsigned need = __ballot_sync(FULL, !has);
+        // ---- refill idle lanes from the queue (one atomic per warp); in the
+        // tail of a TEAM zone phase up to 16 geodesics per warp
+        unsigned need = __ballot_sync(FULL, !has);
+        if (TEAM && tail)
+            need = low_bits(need, __popc(need) > 16 ? __popc(need) - 16 : 0);
         bool empty = false;
         if (need && !drained) {
             unsigned long long my = 0;
@@ -1766,7 +1880,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                     P.zhead, n0, requeue ? P.zpush : nullptr, need, &take, &empty);
                 const unsigned rank = __popc(need & lt_mask);
                 my = base + rank;
-                got = !has && rank < take;
+                got = ((need >> lane) & 1u) && rank < take;
             } else {
                 const unsigned long long base = warp_claim(P.head, need);
                 if (base + __popc(need) >= n_items)
@@ -1882,6 +1996,44 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
         // clipping deferred to the clip pass: the last step ran in FP32 (front
         // of the clip queue) or in the zone's arithmetic (back)
         bool pend32 = false, pend64 = false, clip_bits = false;
+        // ---- TEAM tail: each geodesic taking a zone attempt gets an idle
+        // lane of its warp as helper, if there are enough (warp-uniform)
+        ZoneResultD TR;
+        bool team_owner = false, fin = false;
+        if (TEAM && PHASE == 1 && tail) {
+            const bool zstep = has && in_zone && !timed_out && (int64_t)nsteps < P.max_steps;
+            const unsigned own = __ballot_sync(FULL, zstep);
+            const unsigned idl = __ballot_sync(FULL, !has);
+            const int no = __popc(own);
+            if (no > 0 && __popc(idl) >= no) {
+                const unsigned helpers = low_bits(idl, no);
+                const unsigned tmask = own | helpers;
+                const bool is_helper = (helpers >> lane) & 1u;
+                if (zstep || is_helper) {
+                    const int partner = zstep ? nth_bit(helpers, __popc(own & lt_mask))
+                                              : nth_bit(own, __popc(helpers & lt_mask));
+                    Y8d ys;
+                    if (zstep) {
+                        if (!zd) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i)
+                                d_to_bits((double)y[i] + (double)c[i], y[i], c[i]);
+                            zd = true;
+                        }
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            ys.v[i] = d_from_bits(y[i], c[i]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            ys.v[i] = 0.0;
+                    }
+                    TR = zone_step_team<RM>(rc, P, id, ys, h, rnow, since_renorm, is_helper,
+                                            partner, tmask);
+                    team_owner = zstep;
+                }
+            }
+        }
         if (has) {
             int st = ST_NONE;
             ClipRec cr;
@@ -1903,11 +2055,16 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                             d_to_bits((double)y[i] + (double)c[i], y[i], c[i]);
                         zd = true;
                     }
-                    Y8d ys;
+                    ZoneResultD R;
+                    if (TEAM && team_owner) {
+                        R = TR;
+                    } else {
+                        Y8d ys;
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        ys.v[i] = d_from_bits(y[i], c[i]);
-                    const ZoneResultD R = zone_step_d<RM>(rc, P, id, ys, h, rnow, since_renorm);
+                        for (int i = 0; i < 8; ++i)
+                            ys.v[i] = d_from_bits(y[i], c[i]);
+                        R = zone_step_d<RM>(rc, P, id, ys, h, rnow, since_renorm);
+                    }
                     h = R.h;
                     rnow = R.rnow;
                     since_renorm = R.since_renorm;
@@ -1995,10 +2152,26 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                 }
                 C.status(st);
                 has = false;
+                fin = true;
             }
         }
         if (P.clipq)
             enqueue_clips(P, pend32, pend64, id, clip_bits);
+        // ---- TEAM: count the phase's finished geodesics; a warp enters the
+        // tail once at most half as many remain as the grid has lanes
+        if (TEAM && PHASE == 1) {
+            const unsigned fm = __ballot_sync(FULL, fin);
+            if (fm && lane == __ffs(fm) - 1)
+                atomicAdd(P.zdone, (unsigned long long)__popc(fm));
+            if (!tail && ((++tcheck & 7u) == 0u)) {
+                int t = 0;
+                if (lane == 0) {
+                    const unsigned long long done = ld_relaxed(P.zdone);
+                    t = 2ull * (n0 - (done < n0 ? done : n0)) <= lanes_total ? 1 : 0;
+                }
+                tail = __shfl_sync(FULL, t, 0) != 0;
+            }
+        }
         // ---- zone phase: every zone_quantum iterations of the warp, a
         // geodesic that took at least half a quantum of attempts yields its
         // lane to one that waits in the queue (processor sharing), so that
@@ -2007,15 +2180,27 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
         // reached the queue counters' compare-and-swap together, each
         // re-queue point cost a warp ~150 us of retries (measured on the
         // 1024 x 1024 image), several attempts' worth.
-        if (PHASE != 0 && requeue && ++wit >= zq) {
-            wit = 0;
-            const bool want = has && !timed_out && quantum >= zq_min;
+        // TEAM tail: a warp keeps at most 16 geodesics, the others go back to
+        // the queue for warps with room (no processor sharing any more)
+        bool rq_point = false, want = false, force = false;
+        if (PHASE != 0 && requeue) {
+            if (TEAM && tail) {
+                const unsigned hm = __ballot_sync(FULL, has);
+                want = has && !timed_out && __popc(hm & lt_mask) >= 16;
+                rq_point = force = true;
+            } else if (++wit >= zq) {
+                wit = 0;
+                want = has && !timed_out && quantum >= zq_min;
+                rq_point = true;
+            }
+        }
+        if (rq_point) {
             const unsigned pm = __ballot_sync(FULL, want);
             if (pm) {
                 const int leader = __ffs(pm) - 1;
                 int waiting = 0;
                 if (lane == leader)
-                    waiting = n0 + ld_relaxed(P.zpush) > ld_relaxed(P.zhead) ? 1 : 0;
+                    waiting = force || n0 + ld_relaxed(P.zpush) > ld_relaxed(P.zhead) ? 1 : 0;
                 waiting = __shfl_sync(FULL, waiting, leader);
                 if (waiting) {
                     const unsigned long long b = warp_claim(P.zpush, pm);

@@ -11,10 +11,10 @@ namespace kerr {
 // no room to choose).
 // Its item count lives on the device, so the grid is fixed by the launch
 // shape (blocks per SM x SMs); threads with nothing to do exit at once.
-template <int PH, int B, int BPS, int RM>
+template <int PH, int B, int BPS, int RM, bool TEAM = false>
 static cudaError_t launch_zone(const TraceParams &P, int sms, cudaStream_t s)
 {
-    trace_f32_kernel<PH, B, BPS, RM><<<(unsigned)(BPS * sms), B, 0, s>>>(P);
+    trace_f32_kernel<PH, B, BPS, RM, TEAM><<<(unsigned)(BPS * sms), B, 0, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -42,6 +42,7 @@ void bind_f32_scratch(TraceParams &P, void *work, unsigned long long *ctr, int64
     P.zpush = ctr + 3 + SC_COUNT;
     P.cq32 = ctr + 4 + SC_COUNT;
     P.cq64 = ctr + 5 + SC_COUNT;
+    P.zdone = ctr + 6 + SC_COUNT;
 }
 
 cudaError_t launch_zone_phase(const TraceParams &P, int zv, int sms, cudaStream_t s)
@@ -53,6 +54,9 @@ cudaError_t launch_zone_phase(const TraceParams &P, int zv, int sms, cudaStream_
                          : launch_zone<1, b, m, rm>(P, sms, s);
         KERR_ZONE_VARIANT_LIST(KERR_ZCASE)
 #undef KERR_ZCASE
+    case kTeamZoneVariant:
+        return P.zone_df ? launch_zone<2, 128, 2, RHS_CALL>(P, sms, s)
+                         : launch_zone<1, 128, 1, RHS_CALL, true>(P, sms, s);
     default:
         return cudaErrorInvalidValue;
     }

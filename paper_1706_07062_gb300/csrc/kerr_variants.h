@@ -42,14 +42,16 @@ constexpr int kVariantRhs[kNumVariants] = {0, 0, 0, 1, 1, 0, 0, 0, 1, 1, 1, 1, 1
 
 // Zone-phase variants: (threads per block, blocks per SM, how FP64 steps
 // evaluate their right-hand sides: 0 inline, 1 one out-of-line copy, 2
-// out-of-line pairs -- see RHS_INLINE / RHS_CALL / RHS_PAIR).
+// out-of-line pairs -- see RHS_INLINE / RHS_CALL / RHS_PAIR).  Variant 7 is
+// variant 3 with two-lane zone attempts in the phase's tail (TEAM).
 #define KERR_ZONE_VARIANT_LIST(X)                                                          \
     X(0, 128, 2, 0) X(1, 128, 1, 0) X(2, 64, 2, 0) X(3, 128, 1, 1) X(4, 128, 1, 2)          \
     X(5, 128, 2, 2) X(6, 64, 2, 2)
-constexpr int kNumZoneVariants = 7;
+constexpr int kNumZoneVariants = 8;
+constexpr int kTeamZoneVariant = 7;
 constexpr Variant kZoneVariants[kNumZoneVariants] = {{128, 2}, {128, 1}, {64, 2}, {128, 1},
-                                                     {128, 1}, {128, 2}, {64, 2}};
-constexpr int kDefaultZoneVariant = 3;
+                                                     {128, 1}, {128, 2}, {64, 2}, {128, 1}};
+constexpr int kDefaultZoneVariant = kTeamZoneVariant;
 
 struct TraceParams;
 
@@ -69,8 +71,9 @@ cudaError_t launch_clip_f32(const TraceParams &P, int sms, cudaStream_t s);
 constexpr size_t kWorkBytesPerGeodesic = (16 + 9) * sizeof(float) + sizeof(float) +
                                          sizeof(double) + sizeof(int64_t);
 // Counters ahead of the FP32 path's scratch: queue head, statistics, zone
-// count / head / re-queue count, clip-queue counts (FP32 front, zone back).
-constexpr int kCounterWords(int sc_count) { return 1 + sc_count + 3 + 2; }
+// count / head / re-queue count, clip-queue counts (FP32 front, zone back),
+// zone geodesics finished.
+constexpr int kCounterWords(int sc_count) { return 1 + sc_count + 3 + 2 + 1; }
 
 // Points the FP32 path's scratch pointers of P into `work` (n geodesics,
 // kWorkBytesPerGeodesic each, 8-byte aligned) and `ctr` (kCounterWords).

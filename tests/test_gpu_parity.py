@@ -397,8 +397,10 @@ def test_two_per_thread_edge_cases(ctx):
 # ---------------------------------------------------------------------------
 # deferred FP64-zone phase
 # ---------------------------------------------------------------------------
-# zone variants: (threads per block, blocks per SM, right-hand-side mode)
-ZONE_RHS_MODE = [0, 0, 0, 1, 2, 2, 2]
+# zone variants: right-hand-side mode (0 inline, 1 one out-of-line copy, 2
+# out-of-line pairs); variant 7 is variant 3 with two-lane attempts in the
+# phase's tail, the same arithmetic
+ZONE_RHS_MODE = [0, 0, 0, 1, 2, 2, 2, 1]
 
 
 def test_zone_launch_shapes_agree(ctx):
