@@ -1998,7 +1998,31 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
         bool pend32 = false, pend64 = false, clip_bits = false;
         // ---- TEAM tail: each geodesic taking a zone attempt gets an idle
         // lane of its warp as helper, if there are enough (warp-uniform)
-        ZoneResultD TR;
+        // a zone attempt's result into the lane: step length, r, status, the
+        // deferred clip, and the state -- FP64 bits while the geodesic stays
+        // in the zone, the FP32 pair once it leaves it
+        auto apply_zone = [&](const ZoneResultD &R, int &st_out, ClipRec &cr_out) {
+            h = R.h;
+            rnow = R.rnow;
+            since_renorm = R.since_renorm;
+            st_out = R.st;
+            cr_out = R.clip;
+            C.rhs64 += R.nrhs;
+            C.acc += R.nacc;
+            ++C.att64;
+            if (R.st == ST_NONE && !(rnow < rc.zonef)) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    zsplit(R.y.v[i], y[i], c[i]);
+                zd = false;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    d_to_bits(R.y.v[i], y[i], c[i]);
+            }
+        };
+        int team_st = ST_NONE;
+        ClipRec team_cr;
         bool team_owner = false, fin = false;
         if (TEAM && PHASE == 1 && tail) {
             const bool zstep = has && in_zone && !timed_out && (int64_t)nsteps < P.max_steps;
@@ -2028,8 +2052,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                         for (int i = 0; i < 8; ++i)
                             ys.v[i] = 0.0;
                     }
-                    TR = zone_step_team<RM>(rc, P, id, ys, h, rnow, since_renorm, is_helper,
-                                            partner, tmask);
+                    const ZoneResultD R = zone_step_team<RM>(rc, P, id, ys, h, rnow,
+                                                             since_renorm, is_helper, partner,
+                                                             tmask);
+                    if (zstep)
+                        apply_zone(R, team_st, team_cr);
                     team_owner = zstep;
                 }
             }
@@ -2049,42 +2076,23 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
                 if (PHASE == 1 && in_zone) {
                     // FP64 zone phase: the state stays FP64 from one attempt
                     // to the next
-                    if (!zd) {
-#pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            d_to_bits((double)y[i] + (double)c[i], y[i], c[i]);
-                        zd = true;
-                    }
-                    ZoneResultD R;
                     if (TEAM && team_owner) {
-                        R = TR;
+                        st = team_st;            // taken with a helper above
+                        cr = team_cr;
                     } else {
+                        if (!zd) {
+#pragma unroll
+                            for (int i = 0; i < 8; ++i)
+                                d_to_bits((double)y[i] + (double)c[i], y[i], c[i]);
+                            zd = true;
+                        }
                         Y8d ys;
 #pragma unroll
                         for (int i = 0; i < 8; ++i)
                             ys.v[i] = d_from_bits(y[i], c[i]);
-                        R = zone_step_d<RM>(rc, P, id, ys, h, rnow, since_renorm);
+                        apply_zone(zone_step_d<RM>(rc, P, id, ys, h, rnow, since_renorm), st, cr);
                     }
-                    h = R.h;
-                    rnow = R.rnow;
-                    since_renorm = R.since_renorm;
-                    st = R.st;
-                    cr = R.clip;
                     zone_step_taken = true;
-                    C.rhs64 += R.nrhs;
-                    C.acc += R.nacc;
-                    ++C.att64;
-                    if (st == ST_NONE && !(rnow < rc.zonef)) {
-                        // leaving the zone: its FP32 steps take the pair
-#pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            zsplit(R.y.v[i], y[i], c[i]);
-                        zd = false;
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            d_to_bits(R.y.v[i], y[i], c[i]);
-                    }
                 } else if (PHASE == 2 && in_zone) {
                     LaneF ls;
 #pragma unroll
