@@ -1840,7 +1840,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) trace_f32_kernel(const TraceParam
 
     bool has = false, drained = false, timed_out = false;
     int64_t id = 0;
-    RayConst rc{};
+    RayConst rc;
+    if (TEAM)
+        rc = RayConst{};     // a helper lane passes its (unused) constants along
     // TEAM: the warp is in the phase's tail (warp-uniform, set once)
     bool tail = false;
     uint32_t tcheck = 0;

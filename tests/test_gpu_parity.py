@@ -430,6 +430,30 @@ def test_zone_launch_shapes_agree(ctx):
         assert max(ex.max(), ek.max()) < 1e-9
 
 
+def test_two_lane_zone_attempts_are_exact():
+    """Zone variant 7 takes the zone phase's tail with two lanes per attempt
+    (the full step on a helper lane, the half steps on the owner's) and
+    re-packs the warps to at most 16 geodesics: the arithmetic is that of
+    variant 3, so every output is bit-identical.  Nearly edge-on at a = 0.99
+    some geodesics orbit inside 1.5 r_h and come out again (FP32 steps in the
+    zone phase), so leaving the zone from a two-lane attempt is covered too."""
+    spec = W.CameraSpec(0.99, np.radians(85.0), 1000.0, 8.0, 160, 160)
+    c = K.kerr_init(spec.a)
+    res = {}
+    for zv in (3, 7):
+        o = K.alloc_out(spec.n, DEV, cross=True)
+        K.kerr_trace_camera(c, cam(spec), K.default_opts(zone_variant=zv), out=o)
+        torch.cuda.synchronize()
+        res[zv] = (o, K.kerr_get_stats(c))
+    c.close()
+    (a, sa), (b, sb) = res[3], res[7]
+    assert sa.attempts_fp32_zone_phase > 0 and sa.queue_errors == 0 and sb.queue_errors == 0
+    assert sa.attempts_fp64 == sb.attempts_fp64
+    for name in ("x", "k", "status", "steps"):
+        assert torch.equal(getattr(a, name), getattr(b, name)), name
+    assert torch.equal(torch.nan_to_num(a.cross, 7.0), torch.nan_to_num(b.cross, 7.0))
+
+
 def test_zone_phase_counts(ctx):
     spec = W.CameraSpec(0.99, 0.3, 1000.0, 25.0, 128, 128)
     K.kerr_trace_camera(ctx, cam(spec), K.default_opts(), device=DEV)
