@@ -486,10 +486,32 @@ __device__ __forceinline__ T err_norm_d(const T y[8], const T d[8], const T df[8
     return num * k_rcp(den);
 }
 
+// The same measure for the FP64 zone steps of the FP32+Kahan path: 1/15 and
+// tol folded into the scale, |d - df| against 15 tol (1 + max(|y|, |y + d|))
+// (one FMA for the scale, no multiply for delta): two FP64 instructions fewer
+// per component.  It rounds differently from err_norm_d in the last bits,
+// which only moves the next trial step by as much; the FP64 path keeps
+// err_norm_d.
+__device__ __forceinline__ double err_norm_zone(const double y[8], const double d[8],
+                                                const double df[8], const double tol)
+{
+    const double s15 = 15.0 * tol;
+    double num = 0.0, den = 1.0;
+#pragma unroll
+    for (int i = 1; i < 8; ++i) {
+        const double e = fabs(d[i] - df[i]);
+        const double sc = k_fma(k_absmax(y[i], y[i] + d[i]), s15, s15);
+        const bool take = !(e * den <= num * sc);
+        num = take ? e : num;
+        den = take ? sc : den;
+    }
+    return num * k_rcp(den);
+}
+
 // One step-doubling attempt: returns the error measure and the increment of
 // the two-half-step solution (10 RHS beyond A0).  With paired right-hand
 // sides the full step and the first half step run in lockstep.
-template <int RM = RHS_INLINE, typename T>
+template <int RM = RHS_INLINE, bool ZONE_NORM = false, typename T>
 __device__ __forceinline__ T attempt(const T a, const T a2, const T y[8], const T A0[4], const T h,
                                      const T tol, T d[8])
 {
@@ -512,6 +534,8 @@ __device__ __forceinline__ T attempt(const T a, const T a2, const T y[8], const 
     }
     if constexpr (std::is_same<T, float>::value)
         return err_norm_f(y, d, df, tol);
+    else if constexpr (ZONE_NORM && std::is_same<T, double>::value)
+        return err_norm_zone(y, d, df, tol);
     else
         return err_norm_d(y, d, df, tol);
 }
@@ -723,7 +747,7 @@ __device__ __forceinline__ int step_post(const RayConst &rc, const TraceParams &
         }
         return ST_NONFINITE;
     }
-    rn = ks_r(a2, yn[1], yn[2], yn[3]);
+    rn = FAST_FACTOR ? ks_r_zone(a2, yn[1], yn[2], yn[3]) : ks_r(a2, yn[1], yn[2], yn[3]);
     // termination: (yn, cn) becomes the end point of the step, clipped onto
     // the surface when an event fires; h_used is its step length
     const T rcap = RC<T>::rcap(rc);
@@ -853,7 +877,8 @@ __device__ __forceinline__ int step_once(const RayConst &rc, const TraceParams &
     T A0[4];
     rhs<RM>(a, a2, y[1], y[2], y[3], y[4], y[5], y[6], y[7], A0);
     T d[8];
-    const T err = attempt<RM>(a, a2, y, A0, h, tol, d);
+    // FP64 zone steps of the FP32+Kahan path (FAST_FACTOR): the cheaper measure
+    const T err = attempt<RM, FAST_FACTOR>(a, a2, y, A0, h, tol, d);
     nrhs += 11;
     return step_post<KAHAN, T, FAST_FACTOR, RM>(rc, P, id, a, a2, A0, d, err, y, c, h, rn, nrhs,
                                                 nacc, since_renorm, h_taken, defer);
@@ -1172,7 +1197,7 @@ static __device__ __noinline__ ZoneResultD zone_step_team(const RayConst rc, con
     R.nacc = 0;
     R.st = ST_NONE;
     if (!helper) {
-        const double err = err_norm_d(s.v, d, df, P.tol);
+        const double err = err_norm_zone(s.v, d, df, P.tol);
         R.nrhs = 11;
         double cd[8];
 #pragma unroll
