@@ -93,6 +93,27 @@ __device__ __forceinline__ double k_absmax(double u, double v)
 }
 __device__ __forceinline__ float k_absmax(float u, float v) { return fmaxf(fabsf(u), fabsf(v)); }
 
+// Order tests against a finite v >= 0 on the bit patterns, with integer
+// instructions: read as unsigned 64-bit integers, the patterns of the numbers
+// >= 0 order like the values, a NaN with the sign bit clear lies above +inf,
+// and every pattern with the sign bit set above those.  Each is false for a
+// NaN u, as the FP64 comparison is.
+__device__ __forceinline__ bool k_le_nonneg(double u, double v)      // u <= v
+{
+    return (unsigned long long)__double_as_longlong(u) <=
+           (unsigned long long)__double_as_longlong(v);
+}
+__device__ __forceinline__ bool k_lt_nonneg(double u, double v)      // u < v
+{
+    return (unsigned long long)__double_as_longlong(u) <
+           (unsigned long long)__double_as_longlong(v);
+}
+__device__ __forceinline__ bool k_gt_nonneg(double u, double v)      // u > v
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+    return b > (unsigned long long)__double_as_longlong(v) && b <= 0x7ff0000000000000ull;
+}
+
 // Two reciprocals 1/p and 1/q.  FP32: two hardware approximations.  FP64:
 // one reciprocal of p q shared by both (p q stays far from overflow for any
 // radius below ~1e50).
@@ -123,9 +144,10 @@ __device__ __forceinline__ T ks_r(T a2, T x, T y, T z)
     return k_sqrt(ks_r2(a2, x, y, z));
 }
 
-// r after an FP64 zone step of the FP32+Kahan path: both roots as v rsqrt(v)
-// without the residual correction (within a few ulp; eight FP64 instructions
-// fewer).  Other types: ks_r.
+// r after an FP64 zone step of the FP32+Kahan path: the right-hand side's
+// halved form of eq. CKSr's root, and both roots as v rsqrt(v) without the
+// residual correction (within a few ulp; ten FP64 instructions fewer than
+// ks_r).  Other types: ks_r.
 template <typename T>
 __device__ __forceinline__ T ks_r_zone(T a2, T x, T y, T z)
 {
@@ -133,9 +155,8 @@ __device__ __forceinline__ T ks_r_zone(T a2, T x, T y, T z)
 }
 __device__ __forceinline__ double ks_r_zone(double a2, double x, double y, double z)
 {
-    const double z2 = z * z;
-    const double d = k_fma(x, x, k_fma(y, y, z2)) - a2;
-    const double r2 = 0.5 * (d + k_sqrt_rhs(k_fma(d, d, 4.0 * a2 * z2)));
+    const double D = 0.5 * k_fma(x, x, k_fma(y, y, k_fma(z, z, -a2)));
+    const double r2 = D + k_sqrt_rhs(k_fma(D, D, (a2 * z) * z));
     return r2 * k_rsqrt(r2);
 }
 
@@ -171,10 +192,12 @@ __device__ __forceinline__ void accel(const T a, const T a2, const T x, const T 
                                       const T kt, const T kx, const T ky, const T kz, T &at,
                                       T &ax, T &ay, T &az)
 {
-    const T z2 = z * z;
-    const T az2 = a2 * z2;
-    const T d = k_fma(x, x, k_fma(y, y, z2)) - a2;
-    const T r2 = T(0.5) * (d + k_sqrt_rhs(k_fma(d, d, T(4) * az2)));
+    // r^2 = D + sqrt(D^2 + a^2 z^2) with D = (x^2 + y^2 + z^2 - a^2) / 2:
+    // eq. CKSr's root with the factors 1/2 and 4 taken out (exact scalings)
+    const T a2z = a2 * z;
+    const T az2 = a2z * z;
+    const T D = T(0.5) * k_fma(x, x, k_fma(y, y, k_fma(z, z, -a2)));
+    const T r2 = D + k_sqrt_rhs(k_fma(D, D, az2));
     const T ir = k_rsqrt(r2);
     const T r = r2 * ir;
     T iq, is;                                   // 1/q, 1/s
@@ -189,7 +212,6 @@ __device__ __forceinline__ void accel(const T a, const T a2, const T x, const T 
     const T L = k_fma(lx, kx, k_fma(ly, ky, k_fma(lz, kz, kt)));
     // d_i r = (f/2) (x, y, zt)_i and k . grad r
     const T ir2 = ir * ir;
-    const T a2z = a2 * z;
     const T zt = k_fma(a2z, ir2, z);
     const T kr = hf * k_fma(x, kx, k_fma(y, ky, zt * kz));
     // d_i f = c1 d_i r + g delta_iz

@@ -283,38 +283,74 @@ __device__ __forceinline__ void rk4_incr_body(const T a, const T a2, const T y[8
                                               const T h, T d[8])
 {
     const T hh = T(0.5) * h;
-    T Sk[4], SA[4];
-    T m[4], A[4];
+    if constexpr (std::is_same<T, double>::value) {
+        // FP64: with stage momenta m2 = k + (h/2) A0, m3 = k + (h/2) A1 and
+        // m4 = k + h A2, the position increment (h/6)(k + 2 m2 + 2 m3 + m4)
+        // is h k + (h^2/6)(A0 + A1 + A2), and the momentum increment
+        // (h/6)(A0 + 2 (A1 + A2) + A3): three FP64 instructions fewer per
+        // step than the running stage sums.
+        T m[4], A[4], C[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        Sk[j] = y[4 + j];
-        SA[j] = A0[j];
-        m[j] = k_fma(hh, A0[j], y[4 + j]);
-    }
-    rhs<RM>(a, a2, k_fma(hh, y[5], y[1]), k_fma(hh, y[6], y[2]), k_fma(hh, y[7], y[3]), m[0],
-            m[1], m[2], m[3], A);
-    T m3[4];
+        for (int j = 0; j < 4; ++j)
+            m[j] = k_fma(hh, A0[j], y[4 + j]);
+        rhs<RM>(a, a2, k_fma(hh, y[5], y[1]), k_fma(hh, y[6], y[2]), k_fma(hh, y[7], y[3]), m[0],
+                m[1], m[2], m[3], A);
+        T m3[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        Sk[j] = k_fma(T(2), m[j], Sk[j]);
-        SA[j] = k_fma(T(2), A[j], SA[j]);
-        m3[j] = k_fma(hh, A[j], y[4 + j]);
-    }
-    rhs<RM>(a, a2, k_fma(hh, m[1], y[1]), k_fma(hh, m[2], y[2]), k_fma(hh, m[3], y[3]), m3[0],
-            m3[1], m3[2], m3[3], A);
+        for (int j = 0; j < 4; ++j) {
+            C[j] = A[j];
+            m3[j] = k_fma(hh, A[j], y[4 + j]);
+        }
+        rhs<RM>(a, a2, k_fma(hh, m[1], y[1]), k_fma(hh, m[2], y[2]), k_fma(hh, m[3], y[3]), m3[0],
+                m3[1], m3[2], m3[3], A);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        Sk[j] = k_fma(T(2), m3[j], Sk[j]);
-        SA[j] = k_fma(T(2), A[j], SA[j]);
-        m[j] = k_fma(h, A[j], y[4 + j]);
-    }
-    rhs<RM>(a, a2, k_fma(h, m3[1], y[1]), k_fma(h, m3[2], y[2]), k_fma(h, m3[3], y[3]), m[0],
-            m[1], m[2], m[3], A);
-    const T h6 = h * T(1.0 / 6.0);
+        for (int j = 0; j < 4; ++j) {
+            C[j] = C[j] + A[j];
+            m[j] = k_fma(h, A[j], y[4 + j]);
+        }
+        rhs<RM>(a, a2, k_fma(h, m3[1], y[1]), k_fma(h, m3[2], y[2]), k_fma(h, m3[3], y[3]), m[0],
+                m[1], m[2], m[3], A);
+        const T h6 = h * T(1.0 / 6.0);
+        const T hh6 = h * h6;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        d[j] = k_mul_x(h6, Sk[j] + m[j]);
-        d[4 + j] = k_mul_x(h6, SA[j] + A[j]);
+        for (int j = 0; j < 4; ++j) {
+            d[j] = k_fma(hh6, A0[j] + C[j], h * y[4 + j]);
+            d[4 + j] = k_mul_x(h6, k_fma(T(2), C[j], A0[j]) + A[j]);
+        }
+    } else {
+        T Sk[4], SA[4];
+        T m[4], A[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            Sk[j] = y[4 + j];
+            SA[j] = A0[j];
+            m[j] = k_fma(hh, A0[j], y[4 + j]);
+        }
+        rhs<RM>(a, a2, k_fma(hh, y[5], y[1]), k_fma(hh, y[6], y[2]), k_fma(hh, y[7], y[3]), m[0],
+                m[1], m[2], m[3], A);
+        T m3[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            Sk[j] = k_fma(T(2), m[j], Sk[j]);
+            SA[j] = k_fma(T(2), A[j], SA[j]);
+            m3[j] = k_fma(hh, A[j], y[4 + j]);
+        }
+        rhs<RM>(a, a2, k_fma(hh, m[1], y[1]), k_fma(hh, m[2], y[2]), k_fma(hh, m[3], y[3]), m3[0],
+                m3[1], m3[2], m3[3], A);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            Sk[j] = k_fma(T(2), m3[j], Sk[j]);
+            SA[j] = k_fma(T(2), A[j], SA[j]);
+            m[j] = k_fma(h, A[j], y[4 + j]);
+        }
+        rhs<RM>(a, a2, k_fma(h, m3[1], y[1]), k_fma(h, m3[2], y[2]), k_fma(h, m3[3], y[3]), m[0],
+                m[1], m[2], m[3], A);
+        const T h6 = h * T(1.0 / 6.0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            d[j] = k_mul_x(h6, Sk[j] + m[j]);
+            d[4 + j] = k_mul_x(h6, SA[j] + A[j]);
+        }
     }
 }
 
@@ -364,12 +400,16 @@ template <int RM, typename T>
 __device__ __forceinline__ void rk4_incr2(const T a, const T a2, const T y[8], const T A0[4],
                                           const T h1, const T h2, T d1[8], T d2[8])
 {
+    if constexpr (!std::is_same<T, double>::value) {
+        // other types: the two steps one after the other
+        rk4_incr<RM>(a, a2, y, A0, h1, d1);
+        rk4_incr<RM>(a, a2, y, A0, h2, d2);
+        return;
+    }
     const T hh1 = T(0.5) * h1, hh2 = T(0.5) * h2;
-    T Sk1[4], SA1[4], m1[4], A1[4], Sk2[4], SA2[4], m2[4], A2[4];
+    T m1[4], m2[4], A1[4], A2[4], C1[4], C2[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        Sk1[j] = Sk2[j] = y[4 + j];
-        SA1[j] = SA2[j] = A0[j];
         m1[j] = k_fma(hh1, A0[j], y[4 + j]);
         m2[j] = k_fma(hh2, A0[j], y[4 + j]);
     }
@@ -383,11 +423,9 @@ __device__ __forceinline__ void rk4_incr2(const T a, const T a2, const T y[8], c
     T n1[4], n2[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        Sk1[j] = k_fma(T(2), m1[j], Sk1[j]);
-        SA1[j] = k_fma(T(2), A1[j], SA1[j]);
+        C1[j] = A1[j];
         n1[j] = k_fma(hh1, A1[j], y[4 + j]);
-        Sk2[j] = k_fma(T(2), m2[j], Sk2[j]);
-        SA2[j] = k_fma(T(2), A2[j], SA2[j]);
+        C2[j] = A2[j];
         n2[j] = k_fma(hh2, A2[j], y[4 + j]);
     }
     {
@@ -399,11 +437,9 @@ __device__ __forceinline__ void rk4_incr2(const T a, const T a2, const T y[8], c
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        Sk1[j] = k_fma(T(2), n1[j], Sk1[j]);
-        SA1[j] = k_fma(T(2), A1[j], SA1[j]);
+        C1[j] = C1[j] + A1[j];
         m1[j] = k_fma(h1, A1[j], y[4 + j]);
-        Sk2[j] = k_fma(T(2), n2[j], Sk2[j]);
-        SA2[j] = k_fma(T(2), A2[j], SA2[j]);
+        C2[j] = C2[j] + A2[j];
         m2[j] = k_fma(h2, A2[j], y[4 + j]);
     }
     {
@@ -414,12 +450,13 @@ __device__ __forceinline__ void rk4_incr2(const T a, const T a2, const T y[8], c
         rhs2<RM>(a, a2, p, q, A1, A2);
     }
     const T h61 = h1 * T(1.0 / 6.0), h62 = h2 * T(1.0 / 6.0);
+    const T hh61 = h1 * h61, hh62 = h2 * h62;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        d1[j] = k_mul_x(h61, Sk1[j] + m1[j]);
-        d1[4 + j] = k_mul_x(h61, SA1[j] + A1[j]);
-        d2[j] = k_mul_x(h62, Sk2[j] + m2[j]);
-        d2[4 + j] = k_mul_x(h62, SA2[j] + A2[j]);
+        d1[j] = k_fma(hh61, A0[j] + C1[j], h1 * y[4 + j]);
+        d1[4 + j] = k_mul_x(h61, k_fma(T(2), C1[j], A0[j]) + A1[j]);
+        d2[j] = k_fma(hh62, A0[j] + C2[j], h2 * y[4 + j]);
+        d2[4 + j] = k_mul_x(h62, k_fma(T(2), C2[j], A0[j]) + A2[j]);
     }
 }
 
@@ -712,21 +749,41 @@ struct ClipRec {
     double s_hi = 0.0;          // event value at the unclipped end of the step
 };
 
+//
+// ZH (FP64 zone steps of the FP32+Kahan path): the step length lives in FP32
+// (*hz; h is its FP64 copy for the arithmetic), and the next one is hz times
+// the FP32 factor -- the value that rounding the FP64 product to FP32 gives,
+// without the conversions; the tests on err and r compare bit patterns of
+// non-negative doubles with integer instructions.  On GB300 each FP64
+// compare or conversion occupies the FP64 pipe like an FMA.
 template <bool KAHAN, typename T, bool FAST_FACTOR = false, int RM = RHS_INLINE,
-          bool LAZY = false>
+          bool LAZY = false, bool ZH = false>
 __device__ __forceinline__ int step_post(const RayConst &rc, const TraceParams &P, int64_t id,
                                          const T a, const T a2, const T A0[4], const T d[8],
                                          const T err, T y[8], T c[8], T &h, T &rn,
                                          uint32_t &nrhs, uint32_t &nacc, int &since_renorm,
-                                         T *h_taken = nullptr, ClipRec *defer = nullptr)
+                                         T *h_taken = nullptr, ClipRec *defer = nullptr,
+                                         float *hz = nullptr)
 {
-    T fac;
-    if constexpr (FAST_FACTOR)
+    static_assert(!ZH || (FAST_FACTOR && std::is_same<T, double>::value), "FP64 zone steps");
+    T fac = T(0);
+    float facz = 0.f;
+    if constexpr (ZH)
+        facz = step_factor((float)err);
+    else if constexpr (FAST_FACTOR)
         fac = step_factor_f(err);
     else
         fac = step_factor(err);
-    if (!(err <= T(1))) {
-        h *= fac;
+    bool accept;
+    if constexpr (ZH)
+        accept = k_le_nonneg(err, 1.0);
+    else
+        accept = err <= T(1);
+    if (!accept) {
+        if constexpr (ZH)
+            *hz *= facz;
+        else
+            h *= fac;
         return ST_NONE;
     }
     ++nacc;
@@ -765,7 +822,15 @@ __device__ __forceinline__ int step_post(const RayConst &rc, const TraceParams &
     T h_used = h;
     bool pending = false;
     T s_pend = T(0);
-    if (rn < rcap) {
+    bool captured, beyond;
+    if constexpr (ZH) {
+        captured = k_lt_nonneg(rn, rcap);
+        beyond = k_gt_nonneg(rn, resc);
+    } else {
+        captured = rn < rcap;
+        beyond = rn > resc;
+    }
+    if (captured) {
         st = ST_CAPTURED;
         if (defer_ok) {
             pending = true;
@@ -775,7 +840,7 @@ __device__ __forceinline__ int step_post(const RayConst &rc, const TraceParams &
             h_used = clip<KAHAN, T, RM>(a, a2, y, c, A0, h, 0, rcap, T(0), s_lo, rn - rcap,
                                         stol * rcap, Prec<T>::eps(), maxit, yn, cn, nrhs);
         }
-    } else if (rn > resc && k_fma(yn[1], yn[5], k_fma(yn[2], yn[6], yn[3] * yn[7])) > T(0)) {
+    } else if (beyond && k_fma(yn[1], yn[5], k_fma(yn[2], yn[6], yn[3] * yn[7])) > T(0)) {
         const T s_lo = event_value<KAHAN>(0, a2, y, c, resc, T(0));
         if (s_lo <= T(0)) {
             if (defer_ok) {
@@ -859,7 +924,10 @@ __device__ __forceinline__ int step_post(const RayConst &rc, const TraceParams &
             c[4] = KAHAN ? from_d<T>(k[0] - to_d(y[4])) : T(0);
         }
     }
-    h *= fac;
+    if constexpr (ZH)
+        *hz *= facz;
+    else
+        h *= fac;
     return ST_NONE;
 }
 
@@ -1130,16 +1198,26 @@ static __device__ __noinline__ ZoneResultD zone_step_d(const RayConst rc, const 
 #pragma unroll
     for (int i = 0; i < 8; ++i)
         cd[i] = 0.0;
-    double hd = (double)h, rd = (double)rnow;
+    const double a = rc.a;
+    const double a2 = a * a;
+    // the step length stays FP32 (hz); r is written by an accepted step only
+    const double hd = (double)h;
+    float hz = h;
+    double rd = -1.0;
+    double A0[4];
+    rhs<RM>(a, a2, s.v[1], s.v[2], s.v[3], s.v[4], s.v[5], s.v[6], s.v[7], A0);
+    double d[8];
+    const double err = attempt<RM, true>(a, a2, s.v, A0, hd, P.tol, d);
     ZoneResultD R;
-    R.nrhs = 0;
+    R.nrhs = 11;
     R.nacc = 0;
-    R.st = step_once<false, double, true, RM>(rc, P, id, P.tol, s.v, cd, hd, rd, R.nrhs,
-                                              R.nacc, since_renorm, nullptr,
-                                              P.clipq ? &R.clip : nullptr);
+    double hu = hd;
+    R.st = step_post<false, double, true, RM, false, true>(
+        rc, P, id, a, a2, A0, d, err, s.v, cd, hu, rd, R.nrhs, R.nacc, since_renorm, nullptr,
+        P.clipq ? &R.clip : nullptr, &hz);
     R.y = s;
-    R.h = (float)hd;
-    R.rnow = (float)rd;
+    R.h = hz;
+    R.rnow = __double2hiint(rd) >= 0 ? (float)rd : rnow;
     R.since_renorm = since_renorm;
     return R;
 }
@@ -1170,7 +1248,9 @@ static __device__ __noinline__ ZoneResultD zone_step_team(const RayConst rc, con
     const float hs = __shfl_sync(tmask, h, src);
     const double a = __shfl_sync(tmask, rc.a, src);
     const double a2 = a * a;
-    double hd = (double)hs, rd = (double)rnow;
+    const double hd = (double)hs;
+    float hz = hs;
+    double rd = -1.0;
     double A0[4];
     rhs<RM>(a, a2, s.v[1], s.v[2], s.v[3], s.v[4], s.v[5], s.v[6], s.v[7], A0);
     // helper: the full step of h; owner: the first half step
@@ -1203,13 +1283,14 @@ static __device__ __noinline__ ZoneResultD zone_step_team(const RayConst rc, con
 #pragma unroll
         for (int i = 0; i < 8; ++i)
             cd[i] = 0.0;
-        R.st = step_post<false, double, true, RM>(rc, P, id, a, a2, A0, d, err, s.v, cd, hd, rd,
-                                                  R.nrhs, R.nacc, since_renorm, nullptr,
-                                                  P.clipq ? &R.clip : nullptr);
+        double hu = hd;
+        R.st = step_post<false, double, true, RM, false, true>(
+            rc, P, id, a, a2, A0, d, err, s.v, cd, hu, rd, R.nrhs, R.nacc, since_renorm, nullptr,
+            P.clipq ? &R.clip : nullptr, &hz);
     }
     R.y = s;
-    R.h = (float)hd;
-    R.rnow = (float)rd;
+    R.h = hz;
+    R.rnow = __double2hiint(rd) >= 0 ? (float)rd : rnow;
     R.since_renorm = since_renorm;
     return R;
 }
