@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace kerr {
 
 // ---------------------------------------------------------------------------
@@ -209,20 +211,43 @@ __device__ __forceinline__ void accel(const T a, const T a2, const T x, const T 
     const T lx = k_fma(P, x, Q * y);
     const T ly = k_fma(P, y, -(Q * x));
     const T lz = z * ir;
-    const T L = k_fma(lx, kx, k_fma(ly, ky, k_fma(lz, kz, kt)));
+    // FP64 keeps the x, y parts of l.k and of (x, y, zt).k apart: e.k is
+    // formed from them, and the vector e then enters x'' and y'' only through
+    // the coefficients of (x, y) and of (l_x, l_y) (two FP64 instructions
+    // fewer per right-hand side; FP32 keeps the explicit e)
+    constexpr bool kFold = std::is_same<T, double>::value;
+    T L, Lxy = T(0), Kxy = T(0);
+    if constexpr (kFold) {
+        Lxy = k_fma(lx, kx, ly * ky);
+        L = Lxy + k_fma(lz, kz, kt);
+    } else {
+        L = k_fma(lx, kx, k_fma(ly, ky, k_fma(lz, kz, kt)));
+    }
     // d_i r = (f/2) (x, y, zt)_i and k . grad r
     const T ir2 = ir * ir;
     const T zt = k_fma(a2z, ir2, z);
-    const T kr = hf * k_fma(x, kx, k_fma(y, ky, zt * kz));
+    T kr;
+    if constexpr (kFold) {
+        Kxy = k_fma(x, kx, y * ky);
+        kr = hf * k_fma(zt, kz, Kxy);
+    } else {
+        kr = hf * k_fma(x, kx, k_fma(y, ky, zt * kz));
+    }
     // d_i f = c1 d_i r + g delta_iz
     const T c1 = f * k_fma(T(3), ir, -(f + f));
     const T g = -(f + f) * a2z * iq;
-    // e of d_al l_i = r_al e_i + M_{al i}
+    // e of d_al l_i = r_al e_i + M_{al i}: e_x = (x - 2 r l_x) / s,
+    // e_y = (y - 2 r l_y) / s, e_z = -z / r^2, and e . k
     const T m2r = -(r + r);
-    const T ex = is * k_fma(m2r, lx, x);
-    const T ey = is * k_fma(m2r, ly, y);
     const T ez = -z * ir2;
-    const T ek = k_fma(ex, kx, k_fma(ey, ky, ez * kz));     // e . k
+    T ek, ex = T(0), ey = T(0);
+    if constexpr (kFold) {
+        ek = k_fma(is, k_fma(m2r, Lxy, Kxy), ez * kz);
+    } else {
+        ex = is * k_fma(m2r, lx, x);
+        ey = is * k_fma(m2r, ly, y);
+        ek = k_fma(ex, kx, k_fma(ey, ky, ez * kz));
+    }
     // A_al k^al and l . grad f
     const T gk = k_fma(c1, kr, g * kz);
     const T dLk = k_fma(kr, ek, k_fma(P, k_fma(kx, kx, ky * ky), (ir * kz) * kz));
@@ -242,8 +267,16 @@ __device__ __forceinline__ void accel(const T a, const T a2, const T x, const T 
     const T hw = hf * k_fma(hLL, c1, fL * ek);
     const T fLkr = fL * kr;
     const T fLQ2 = fL * (Q + Q);
-    ax = k_fma(x, hw, k_fma(-fLkr, ex, k_fma(-fLQ2, ky, lx * FmA)));
-    ay = k_fma(y, hw, k_fma(-fLkr, ey, k_fma(fLQ2, kx, ly * FmA)));
+    if constexpr (kFold) {
+        // -f L (k.grad r) e_i = -fLkr (x_i - 2 r l_i) / s for i = x, y
+        const T al = k_fma(-fLkr, is, hw);
+        const T be = k_fma(P + P, fLkr, FmA);
+        ax = k_fma(x, al, k_fma(lx, be, -(fLQ2 * ky)));
+        ay = k_fma(y, al, k_fma(ly, be, fLQ2 * kx));
+    } else {
+        ax = k_fma(x, hw, k_fma(-fLkr, ex, k_fma(-fLQ2, ky, lx * FmA)));
+        ay = k_fma(y, hw, k_fma(-fLkr, ey, k_fma(fLQ2, kx, ly * FmA)));
+    }
     az = k_fma(zt, hw, k_fma(-fLkr, ez, k_fma(hLL, g, lz * FmA)));
 }
 
@@ -335,9 +368,9 @@ __device__ __forceinline__ bool solve_kt(const KSPoint &p, double k[4], double t
     const double disc = B * B - 4.0 * A * C;
     if (!(disc >= 0.0) || A == 0.0)
         return false;
-    const double q = -0.5 * (B + copysign(sqrt(disc), B));
-    const double r1 = q / A;
-    const double r2 = (q != 0.0) ? C / q : r1;
+    const double q = -0.5 * (B + copysign(k_sqrt(disc), B));
+    const double r1 = q * k_rcp(A);
+    const double r2 = (q != 0.0) ? C * k_rcp(q) : r1;
     const double lo = fmin(r1, r2), hi = fmax(r1, r2);
     if (branch == 0)
         k[0] = (fabs(lo - k[0]) <= fabs(hi - k[0])) ? lo : hi;

@@ -982,8 +982,12 @@ __device__ __forceinline__ int init_geodesic(const TraceParams &P, int64_t id, d
             a = cam.a;
             const int64_t local = pix - cam.offset;
             const int64_t p = local % cam.nx, q = local / cam.nx;
-            al = -cam.w + (p + 0.5) * 2.0 * cam.w / cam.nx;
-            be = -cam.w + (q + 0.5) * 2.0 * cam.w / cam.ny;
+            // pixel centre -w + (p + 1/2) 2w / nx = (2p + 1 - nx) (w / nx), the
+            // first factor an exact integer (one refined reciprocal, no
+            // division: on GB300 an IEEE FP64 division costs a dozen FP64
+            // instructions)
+            al = (double)(2 * p + 1 - cam.nx) * (cam.w * k_rcp((double)cam.nx));
+            be = (double)(2 * q + 1 - cam.ny) * (cam.w * k_rcp((double)cam.ny));
             si = cam.sin_incl;
             ci = cam.cos_incl;
             r_obs = cam.r_obs;
@@ -1034,7 +1038,7 @@ __device__ __forceinline__ int init_geodesic(const TraceParams &P, int64_t id, d
         }
     }
     rc.a = a;
-    const double rh = 1.0 + sqrt(fmax(0.0, 1.0 - a * a));
+    const double rh = 1.0 + k_sqrt(fmax(0.0, 1.0 - a * a));
     rc.rcap = 1.01 * rh;
     rc.zone_r = P.fp64_zone * rh;
     const double tend = P.t_end_each ? P.t_end_each[id] : P.t_end;
@@ -1047,18 +1051,20 @@ __device__ __forceinline__ int init_geodesic(const TraceParams &P, int64_t id, d
         finite = finite && k_isfinite(y[i]);
     if (st == ST_NONE && !finite)
         st = ST_NONFINITE;
-    const double r0 = finite ? ks_r(a * a, y[1], y[2], y[3]) : 0.0;
+    // r, f and l at the start point (the camera branch has them already)
+    if (finite && !have_kp)
+        kp = ks_point(a, y[1], y[2], y[3]);
+    // (kp.r = r^2 rsqrt(r^2) is NaN where r^2 is 0 or inf; ks_r gives 0 / NaN there)
+    const double r0 = !finite ? 0.0 : (k_isfinite(kp.r) ? kp.r : ks_r(a * a, y[1], y[2], y[3]));
     rc.resc = P.r_escape > 0.0 ? P.r_escape : (P.r_escape == 0.0 ? r0 : INFINITY);
     rc.xi = 0.0;
     if (st == ST_NONE) {
-        if (!have_kp)
-            kp = ks_point(a, y[1], y[2], y[3]);
         rc.u2_0 = norm2(kp, y + 4);
         // E = -p_t and L_z = x p_y - y p_x with p = eta k + f l (l.k)
         const double L = y[4] + kp.lx * y[5] + kp.ly * y[6] + kp.lz * y[7];
         const double E = y[4] - kp.f * L;
         const double Lz = y[1] * (y[6] + kp.f * kp.ly * L) - y[2] * (y[5] + kp.f * kp.lx * L);
-        rc.xi = Lz / E;
+        rc.xi = Lz * k_rcp(E);
         if (r0 < rc.rcap)
             st = ST_CAPTURED;
     }
