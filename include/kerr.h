@@ -262,7 +262,9 @@ int kerr_variant_shape(int v, int32_t *block, int32_t *min_blocks, int32_t *rays
  * geodesics remain as the launch has lanes -- keeps at most 16 geodesics per
  * warp and pairs each with an idle lane: the helper computes the full RK4
  * step while the owner computes the half steps (the same arithmetic: results
- * bit-identical to variant 3). */
+ * bit-identical to variant 3).  Variant 8 is variant 4 (right-hand sides of
+ * the full step and the first half step evaluated in interleaved pairs) with
+ * the same two-lane tail, bit-identical to variant 4. */
 int kerr_num_zone_variants(void);
 int kerr_zone_variant_info(int v, int32_t *block, int32_t *blocks_per_sm);
 

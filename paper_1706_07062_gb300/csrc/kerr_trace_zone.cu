@@ -57,6 +57,9 @@ cudaError_t launch_zone_phase(const TraceParams &P, int zv, int sms, cudaStream_
     case kTeamZoneVariant:
         return P.zone_df ? launch_zone<2, 128, 2, RHS_CALL>(P, sms, s)
                          : launch_zone<1, 128, 1, RHS_CALL, true>(P, sms, s);
+    case kTeamPairZoneVariant:
+        return P.zone_df ? launch_zone<2, 128, 2, RHS_CALL>(P, sms, s)
+                         : launch_zone<1, 128, 1, RHS_PAIR, true>(P, sms, s);
     default:
         return cudaErrorInvalidValue;
     }

@@ -42,15 +42,18 @@ constexpr int kVariantRhs[kNumVariants] = {0, 0, 0, 1, 1, 0, 0, 0, 1, 1, 1, 1, 1
 
 // Zone-phase variants: (threads per block, blocks per SM, how FP64 steps
 // evaluate their right-hand sides: 0 inline, 1 one out-of-line copy, 2
-// out-of-line pairs -- see RHS_INLINE / RHS_CALL / RHS_PAIR).  Variant 7 is
-// variant 3 with two-lane zone attempts in the phase's tail (TEAM).
+// out-of-line pairs -- see RHS_INLINE / RHS_CALL / RHS_PAIR).  Variants 7 and
+// 8 are variants 3 and 4 with two-lane zone attempts in the phase's tail
+// (TEAM).
 #define KERR_ZONE_VARIANT_LIST(X)                                                          \
     X(0, 128, 2, 0) X(1, 128, 1, 0) X(2, 64, 2, 0) X(3, 128, 1, 1) X(4, 128, 1, 2)          \
     X(5, 128, 2, 2) X(6, 64, 2, 2)
-constexpr int kNumZoneVariants = 8;
+constexpr int kNumZoneVariants = 9;
 constexpr int kTeamZoneVariant = 7;
-constexpr Variant kZoneVariants[kNumZoneVariants] = {{128, 2}, {128, 1}, {64, 2}, {128, 1},
-                                                     {128, 1}, {128, 2}, {64, 2}, {128, 1}};
+constexpr int kTeamPairZoneVariant = 8;
+constexpr Variant kZoneVariants[kNumZoneVariants] = {{128, 2}, {128, 1}, {64, 2},
+                                                     {128, 1}, {128, 1}, {128, 2},
+                                                     {64, 2},  {128, 1}, {128, 1}};
 constexpr int kDefaultZoneVariant = kTeamZoneVariant;
 
 struct TraceParams;

@@ -400,7 +400,7 @@ def test_two_per_thread_edge_cases(ctx):
 # zone variants: right-hand-side mode (0 inline, 1 one out-of-line copy, 2
 # out-of-line pairs); variant 7 is variant 3 with two-lane attempts in the
 # phase's tail, the same arithmetic
-ZONE_RHS_MODE = [0, 0, 0, 1, 2, 2, 2, 1]
+ZONE_RHS_MODE = [0, 0, 0, 1, 2, 2, 2, 1, 2]
 
 
 def test_zone_launch_shapes_agree(ctx):
@@ -430,23 +430,25 @@ def test_zone_launch_shapes_agree(ctx):
         assert max(ex.max(), ek.max()) < 1e-9
 
 
-def test_two_lane_zone_attempts_are_exact():
-    """Zone variant 7 takes the zone phase's tail with two lanes per attempt
-    (the full step on a helper lane, the half steps on the owner's) and
-    re-packs the warps to at most 16 geodesics: the arithmetic is that of
-    variant 3, so every output is bit-identical.  Nearly edge-on at a = 0.99
-    some geodesics orbit inside 1.5 r_h and come out again (FP32 steps in the
-    zone phase), so leaving the zone from a two-lane attempt is covered too."""
+@pytest.mark.parametrize("one_lane,two_lane", [(3, 7), (4, 8)])
+def test_two_lane_zone_attempts_are_exact(one_lane, two_lane):
+    """Zone variants 7 and 8 take the zone phase's tail with two lanes per
+    attempt (the full step on a helper lane, the half steps on the owner's)
+    and re-pack the warps to at most 16 geodesics: the arithmetic is that of
+    variants 3 and 4, so every output is bit-identical.  Nearly edge-on at
+    a = 0.99 some geodesics orbit inside 1.5 r_h and come out again (FP32
+    steps in the zone phase), so leaving the zone from a two-lane attempt is
+    covered too."""
     spec = W.CameraSpec(0.99, np.radians(85.0), 1000.0, 8.0, 160, 160)
     c = K.kerr_init(spec.a)
     res = {}
-    for zv in (3, 7):
+    for zv in (one_lane, two_lane):
         o = K.alloc_out(spec.n, DEV, cross=True)
         K.kerr_trace_camera(c, cam(spec), K.default_opts(zone_variant=zv), out=o)
         torch.cuda.synchronize()
         res[zv] = (o, K.kerr_get_stats(c))
     c.close()
-    (a, sa), (b, sb) = res[3], res[7]
+    (a, sa), (b, sb) = res[one_lane], res[two_lane]
     assert sa.attempts_fp32_zone_phase > 0 and sa.queue_errors == 0 and sb.queue_errors == 0
     assert sa.attempts_fp64 == sb.attempts_fp64
     for name in ("x", "k", "status", "steps"):
