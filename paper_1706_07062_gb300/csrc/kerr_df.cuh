@@ -41,6 +41,11 @@ struct dfloat {
     __device__ __forceinline__ explicit dfloat(int i) : hi((float)i), lo(0.f) {}
 };
 
+// accel<dfloat> keeps the explicit vector e (see FoldE)
+template <> struct FoldE<dfloat> {
+    static constexpr bool value = false;
+};
+
 __device__ __forceinline__ dfloat quick_two_sum(float a, float b)
 {
     const float s = a + b;

@@ -162,6 +162,12 @@ __device__ __forceinline__ double ks_r_zone(double a2, double x, double y, doubl
     return r2 * k_rsqrt(r2);
 }
 
+// Whether accel<T> folds the vector e of d l into the coefficients of x'' and
+// y'' (every type but float-float, which specialises this to false).
+template <typename T> struct FoldE {
+    static constexpr bool value = true;
+};
+
 // ---------------------------------------------------------------------------
 // Geodesic acceleration d k^mu / d lambda in the split-metric form of
 // Sec. 2.1, eqs. opt0 and opti:
@@ -211,11 +217,11 @@ __device__ __forceinline__ void accel(const T a, const T a2, const T x, const T 
     const T lx = k_fma(P, x, Q * y);
     const T ly = k_fma(P, y, -(Q * x));
     const T lz = z * ir;
-    // FP64 keeps the x, y parts of l.k and of (x, y, zt).k apart: e.k is
-    // formed from them, and the vector e then enters x'' and y'' only through
-    // the coefficients of (x, y) and of (l_x, l_y) (two FP64 instructions
-    // fewer per right-hand side; FP32 keeps the explicit e)
-    constexpr bool kFold = std::is_same<T, double>::value;
+    // The x, y parts of l.k and of (x, y, zt).k are kept apart: e.k is formed
+    // from them, and the vector e then enters x'' and y'' only through the
+    // coefficients of (x, y) and of (l_x, l_y) (two instructions fewer per
+    // right-hand side; float-float keeps the explicit e)
+    constexpr bool kFold = FoldE<T>::value;
     T L, Lxy = T(0), Kxy = T(0);
     if constexpr (kFold) {
         Lxy = k_fma(lx, kx, ly * ky);

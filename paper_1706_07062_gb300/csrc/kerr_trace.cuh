@@ -283,12 +283,12 @@ __device__ __forceinline__ void rk4_incr_body(const T a, const T a2, const T y[8
                                               const T h, T d[8])
 {
     const T hh = T(0.5) * h;
-    if constexpr (std::is_same<T, double>::value) {
-        // FP64: with stage momenta m2 = k + (h/2) A0, m3 = k + (h/2) A1 and
+    if constexpr (!std::is_same<T, dfloat>::value) {
+        // With stage momenta m2 = k + (h/2) A0, m3 = k + (h/2) A1 and
         // m4 = k + h A2, the position increment (h/6)(k + 2 m2 + 2 m3 + m4)
         // is h k + (h^2/6)(A0 + A1 + A2), and the momentum increment
-        // (h/6)(A0 + 2 (A1 + A2) + A3): three FP64 instructions fewer per
-        // step than the running stage sums.
+        // (h/6)(A0 + 2 (A1 + A2) + A3): three instructions fewer per step
+        // than the running stage sums (float-float keeps those).
         T m[4], A[4], C[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
