@@ -101,6 +101,39 @@ def test_paired_arguments():
     assert K.lib().kerr_rk4_fixed(A, 3, K.LAYOUT_SOA, st32.data_ptr(), 4, 1, H, None) != 0
 
 
+def test_fp64_step_inside_the_zone_matches_oracle():
+    """One FP64 RK4 step from states between 1.02 r_h and 1.5 r_h -- the FP64
+    zone of the FP32 path, where f l l is large: the kernel's rearranged
+    right-hand side (eqs. opt0/opti, the vector e of d l never formed) and its
+    RK4 increments from stage sums against the oracle's Christoffel-form step
+    (Sec. 3), component by component.  The geodesic equation is a quadratic
+    form in k whatever the norm of k, so the momenta are drawn freely
+    (past-directed k^t).  Each state's increment is compared relative to its
+    largest component: a direct bound on the right-hand side's error there."""
+    a, h, n = 0.99, 2e-3, 512
+    rh = 1 + np.sqrt(1 - a * a)
+    rng = np.random.default_rng(1706)
+    r = rng.uniform(1.02 * rh, 1.5 * rh, n)
+    th = np.arccos(rng.uniform(-0.95, 0.95, n))
+    ph = rng.uniform(0, 2 * np.pi, n)
+    # Kerr-Schild Cartesian position of (r, theta, phi): x + i y = (r + i a) sin(theta) e^(i phi)
+    x = np.sin(th) * (r * np.cos(ph) - a * np.sin(ph))
+    y = np.sin(th) * (r * np.sin(ph) + a * np.cos(ph))
+    z = r * np.cos(th)
+    assert max(abs(O.ks_r(a, *p) - ri) for p, ri in zip(zip(x, y, z), r)) < 1e-12
+    y0 = np.column_stack([np.zeros(n), x, y, z, -rng.uniform(1.0, 3.0, n),
+                          rng.uniform(-1.0, 1.0, (n, 3))])
+    ref = np.stack([O.rk4_fixed(a, yi, h, 1)[-1] for yi in y0])
+    st = torch.tensor(y0.T, dtype=torch.float64, device=DEV).contiguous()
+    K.kerr_rk4_fixed(a, st, 1, h)
+    torch.cuda.synchronize()
+    got = st.cpu().numpy().T
+    d_ref, d_got = ref - y0, got - y0
+    e_inc = np.abs(d_got - d_ref).max(1) / np.abs(d_ref).max(1)
+    assert e_inc.max() < 1e-12, e_inc.max()
+    assert rel(got, ref).max() < 1e-14
+
+
 def test_fixed_rk4_arguments():
     st = torch.zeros((8, 4), dtype=torch.float64, device=DEV)
     K.kerr_rk4_fixed(A, st, 0, H)                       # no-op
