@@ -485,16 +485,19 @@ __device__ __forceinline__ void two_halves(const T a, const T a2, const T y[8], 
 // The running maximum is kept as one fraction num / den: each candidate
 // e_i / sc_i is compared by cross-multiplying (sc_i, den > 0, products far
 // from overflow), and one division by den remains at the end instead of one
-// per component.  A NaN component makes the measure NaN (a rejected step).
+// per component; 1/15 and tol are folded into the scale, |d_i - df_i|
+// against 15 tol (1 + max(...)) (one FMA for the scale, no multiply for the
+// difference).  A NaN component makes the measure NaN (a rejected step).
 __device__ __forceinline__ float err_norm_f(const float y[8], const float d[8], const float df[8],
                                             const float tol)
 {
+    const float s15 = 15.f * tol;
     float num = 0.f, den = 1.f;
     bool bad = false;
 #pragma unroll
     for (int i = 1; i < 8; ++i) {
-        const float e = fabsf((d[i] - df[i]) * (float)(1.0 / 15.0));
-        const float sc = tol * (1.f + fmaxf(fabsf(y[i]), fabsf(y[i] + d[i])));
+        const float e = fabsf(d[i] - df[i]);
+        const float sc = k_fma(fmaxf(fabsf(y[i]), fabsf(y[i] + d[i])), s15, s15);
         const bool take = e * den > num * sc;
         num = take ? e : num;
         den = take ? sc : den;
