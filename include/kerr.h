@@ -20,9 +20,12 @@
  *              are n int32; diag is a [4][n] float plane (E, L_z, Q, u^2).
  *   Memory     Every pointer may be host memory (pageable or pinned) or device
  *              memory of the current device; the library tells them apart with
- *              cudaPointerGetAttributes.  With any host pointer the call stages
- *              through library-owned device buffers and returns only after the
- *              stream is synchronised.  With device pointers only, the call is
+ *              cudaPointerGetAttributes.  With any host pointer the call
+ *              returns only after the stream is synchronised: host buffers are
+ *              staged through library-owned device buffers, except that the
+ *              end points and diagnostics (x_out, k_out, diag) of the trace
+ *              calls are written by the kernels straight into page-locked
+ *              (pinned) host buffers.  With device pointers only, the call is
  *              asynchronous on `stream`.  Inputs are never modified.  The
  *              caller owns all inputs and outputs; the context owns its
  *              scratch (work-queue counter, statistics, staging buffers,

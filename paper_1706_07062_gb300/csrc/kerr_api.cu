@@ -56,6 +56,20 @@ bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// The device's address of page-locked host memory (cudaHostAlloc,
+// cudaHostRegister), or null for any other pointer.
+void *mapped_host_ptr(void *p)
+{
+    if (!p)
+        return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 } // namespace
 
 // Launch parameters that identify a cached graph.
@@ -559,16 +573,41 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
         if (t_end_each && !is_device_ptr(t_end_each))
             st.push_back({t_end_each, (void **)&P.t_end_each, nn * sizeof(double), true, 0});
     }
-    if (!is_device_ptr(x_out))
-        st.push_back({x_out, (void **)&P.x_out, 4 * nn * sizeof(double), false, 0});
-    if (!is_device_ptr(k_out))
-        st.push_back({k_out, (void **)&P.k_out, 4 * nn * sizeof(double), false, 0});
+    // End points and diagnostics are only written, once per geodesic, by the
+    // kernels (the finishing pass of the FP32 path, the stepping kernel of the
+    // FP64 path): page-locked host buffers receive them in place over the
+    // host link, with no staging copy after the kernels; pageable ones are
+    // staged.  Status, steps and crossings are also read by the kernels and
+    // stay in device memory.
+    bool written_in_place = false;
+    if (!is_device_ptr(x_out)) {
+        if (void *m = mapped_host_ptr(x_out)) {
+            P.x_out = static_cast<double *>(m);
+            written_in_place = true;
+        } else {
+            st.push_back({x_out, (void **)&P.x_out, 4 * nn * sizeof(double), false, 0});
+        }
+    }
+    if (!is_device_ptr(k_out)) {
+        if (void *m = mapped_host_ptr(k_out)) {
+            P.k_out = static_cast<double *>(m);
+            written_in_place = true;
+        } else {
+            st.push_back({k_out, (void **)&P.k_out, 4 * nn * sizeof(double), false, 0});
+        }
+    }
     if (!is_device_ptr(status))
         st.push_back({status, (void **)&P.status, nn * sizeof(int32_t), false, 0});
     if (!is_device_ptr(steps))
         st.push_back({steps, (void **)&P.steps, nn * sizeof(int32_t), false, 0});
-    if (diag && !is_device_ptr(diag))
-        st.push_back({diag, (void **)&P.diag, 4 * nn * sizeof(float), false, 0});
+    if (diag && !is_device_ptr(diag)) {
+        if (void *m = mapped_host_ptr(diag)) {
+            P.diag = static_cast<float *>(m);
+            written_in_place = true;
+        } else {
+            st.push_back({diag, (void **)&P.diag, 4 * nn * sizeof(float), false, 0});
+        }
+    }
     if (cross && !is_device_ptr(cross))
         st.push_back({cross, (void **)&P.cross, 5 * nn * sizeof(float), false, 0});
     size_t total = 0;
@@ -632,6 +671,7 @@ static int trace_common(kerr_ctx *c, int mode, const double *x0, const double *k
         }
     for (auto &s : st)
         any_host = any_host || s.input;
+    any_host = any_host || written_in_place;
     KERR_CUDA(cudaEventRecord(c->ev_out, c->stream));
     KERR_CUDA(cudaStreamWaitEvent(us, c->ev_out, 0));
     if (any_host)

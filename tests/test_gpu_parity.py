@@ -122,19 +122,30 @@ def test_trace_rays_matches_camera(ctx):
     c2.close()
 
 
-def test_host_and_device_buffers_agree(ctx):
+@pytest.mark.parametrize("prec", [K.FP32_KAHAN, K.FP64])
+def test_host_and_device_buffers_agree(ctx, prec):
+    """Pageable host outputs are staged through device memory; page-locked
+    ones receive end points and diagnostics in place from the kernels (twice
+    into the same buffers, so that the second call replays a cached graph)."""
     spec = W.CameraSpec(0.5, 0.7, 1000.0, 10.0, 33, 31)
-    opts = K.default_opts(prec=K.FP32_KAHAN, tol=1e-6)
+    opts = K.default_opts(prec=prec, tol=1e-6)
     dev = K.kerr_trace_camera(ctx, cam(spec), opts, device=DEV)
     host = K.kerr_trace_camera(ctx, cam(spec), opts)               # numpy outputs
     pinned = K.alloc_out(spec.n, device="cpu", pinned=True)
-    K.kerr_trace_camera(ctx, cam(spec), opts, out=pinned)
+    outs = [host]
+    for _ in range(2):
+        for t in (pinned.x, pinned.k, pinned.diag):
+            t.fill_(np.nan)
+        K.kerr_trace_camera(ctx, cam(spec), opts, out=pinned)
+        outs.append(K.TraceOut(pinned.x.clone(), pinned.k.clone(), pinned.status.clone(),
+                               pinned.steps.clone(), pinned.diag.clone()))
     torch.cuda.synchronize()
-    for o in (host, pinned):
+    for o in outs:
         assert np.array_equal(to_np(o.x), to_np(dev.x))
         assert np.array_equal(to_np(o.k), to_np(dev.k))
         assert np.array_equal(to_np(o.status), to_np(dev.status))
         assert np.array_equal(to_np(o.steps), to_np(dev.steps))
+        assert np.array_equal(to_np(o.diag), to_np(dev.diag), equal_nan=True)
 
 
 def test_batched_cameras_equal_single_cameras(ctx):
